@@ -58,7 +58,9 @@ def q_contour(x, kind: int, R0: float, rmax: float, theta: float = 0.0,
 
     SHARP: q = 1 for |x| <= R0, exp(i theta) beyond (Sec. IV, sharp rotation;
            the point |x| = R0 itself is read as unscaled).
-    SECS:  q = exp[i pi/4 (|x|-R0)/dx_CS], dx_CS = rmax - R0 (Eq. qSECS).
+    SECS:  q = exp[i theta (|x|-R0)/dx_CS], dx_CS = rmax - R0: Eq. qSECS with
+           its final angle pi/4 made a parameter (theta = pi/4 is the paper's
+           contour; the laser batch uses theta = 0.5, see the workloads).
     TFECS: q = sqrt(1 + i ytilde(s)), s = (|x|-R0)/dx_CS (Eq. qTFECS).
     TFECS is infinite at |x| = rmax; callers that need 1/q there use
     ``inv_q``."""
@@ -69,7 +71,7 @@ def q_contour(x, kind: int, R0: float, rmax: float, theta: float = 0.0,
     if kind == SHARP:
         q[out] = np.exp(1j * theta)
     elif kind == SECS:
-        q[out] = np.exp(1j * np.pi / 4.0 * (ax[out] - R0) / (rmax - R0))
+        q[out] = np.exp(1j * theta * (ax[out] - R0) / (rmax - R0))
     elif kind == TFECS:
         s = (ax[out] - R0) / (rmax - R0)
         with np.errstate(divide="ignore", invalid="ignore"):
@@ -104,7 +106,7 @@ def z_contour(x, kind: int, R0: float, rmax: float, theta: float = 0.0,
     if kind == SHARP:
         z[out] = sg[out] * (R0 + np.exp(1j * theta) * d)
     elif kind == SECS:
-        c = 1j * np.pi / (4.0 * (rmax - R0))
+        c = 1j * theta / (rmax - R0)
         z[out] = sg[out] * (R0 + (np.exp(c * d) - 1.0) / c)
     elif kind == TFECS:
         from scipy.integrate import quad

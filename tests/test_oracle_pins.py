@@ -96,12 +96,12 @@ def _ks_residual(n, kind):
     analytic in z (Sec. II, Eq. psi_zx and the operator K_s under it)."""
     a, b, R0 = -30.0, 30.0, 10.0
     x, h = T.grid(n, a, b)
-    q = T.q_contour(x, kind, R0, b, 0.0)
-    z = T.z_contour(x, kind, R0, b, 0.0)
+    q = T.q_contour(x, kind, R0, b, math.pi / 4)
+    z = T.z_contour(x, kind, R0, b, math.pi / 4)
     z0, sg = 14.0, 3.0
     f = np.exp(-(z - z0) ** 2 / (2 * sg * sg))
     fpp = f * ((z - z0) ** 2 / sg ** 4 - 1.0 / sg ** 2)
-    s, d, u = T.ks_tridiag(n, a, b, kind, R0, 0.0)
+    s, d, u = T.ks_tridiag(n, a, b, kind, R0, math.pi / 4)
     psi = np.sqrt(q) * f
     ks = s * np.roll(psi, 1) + d * psi + u * np.roll(psi, -1)
     ref = np.sqrt(q) * (-0.5 * fpp)
