@@ -1,0 +1,324 @@
+"""Benchmark: the batched 1D laser workload of the ECS split-operator method.
+
+Workload: 4096 independent 1D instances, N drawn from {2048, 4096, 8192,
+16384}, box [-8N/1024, 8N/1024] (h = 1/64), sharp ECS at 75% of the
+half-width (theta = 0.5), soft-Coulomb a^2 = 2, laser pulse E0 sin^2 sin with
+omega = 0.057, 4 cycles, E0 ~ U[0.01, 0.1]; dt = 0.02.  One benchmark step
+advances every instance by STEPS_PER_CALL time steps in one library call.
+
+Metric: grid-point-steps per second = sum_j N_j * time steps / seconds.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec c64|c128]
+  python bench.py --impl reference      # the FP64 CPU oracle on a sample
+
+One JSON line is printed by rank 0."""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ECS SO-FFT grid-point-steps/s"
+UNIT = "grid-point-steps/s"
+N_INST = 4096
+STEPS_PER_CALL = 256
+L2_BYTES = 129 * 1024 * 1024
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return d, "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def _hbm_peak(d):
+    for k in ("hbm_gbs", "hbm_GBps", "hbm"):
+        if k in d:
+            v = d[k]
+            return float(v["value"] if isinstance(v, dict) else v)
+    return 6800.0
+
+
+# FP32 SIMT peak derived from the unit counts and the maximum clock:
+# 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP64: not measured on this machine; GB300 lists about 1.25 TFLOP/s dense FP64
+FP64_PEAK_TFLOPS = 1.25
+
+
+def flops_per_call(ns, nbs, steps, field=True):
+    """Algorithmic FLOPs of one call: per time step and instance, two FFTs
+    (5 N log2 N each), the kinetic and potential phase products (6 N each),
+    the field phase (6 N) and the strip Crank-Nicolson (32 per strip row:
+    two sweeps, the combination 2x - r and the second potential factor)."""
+    tot = 0.0
+    for n, nb in zip(ns, nbs):
+        tot += 10.0 * n * math.log2(n) + 12.0 * n + (6.0 * n if field else 0.0) + 32.0 * nb
+    return tot * steps
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev=0):
+        self.dev, self.rows, self.proc = dev, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(r[0]) for r in self.rows if r and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for i, nm in enumerate(names):
+                if len(r) > 2 + i and r[2 + i].lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload(count=N_INST):
+    import workloads as W
+    return [W.w2_instance(j) for j in range(count)]
+
+
+def config(prec, instances=N_INST, spc=STEPS_PER_CALL):
+    return {"workload": "1D ECS SO-FFT laser batch: %d instances, N in {2048..16384}, h=1/64, "
+                        "smooth (SECS) ECS from R0=0.75 half-width to theta=0.5 at the edge, soft-Coulomb a2=2, "
+                        "pulse omega=0.057 4 cycles, dt=0.02" % instances,
+            "instances": instances, "time_steps_per_step": spc, "precision": prec,
+            "l2": "inputs larger than L2 (packed state %s)" % ("252 MB c64" if prec == "c64" else "504 MB c128")}
+
+
+def run_reference(args):
+    """The FP64 CPU oracle on a bounded, stratified sample of the workload."""
+    import numpy as np
+    from oracle import propagate as P
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    ws = workload(N_INST)
+    sample = []
+    for n in (2048, 4096, 8192, 16384):
+        sample += [w for w in ws if w["n"] == n][:8]
+    nst = 16
+    probs = [P.Problem1D(w["n"], w["a"], w["b"], w["R0"], theta=w["theta"], kind=w["contour"],
+                         a2=w["a2"], dt=w["dt"]) for w in sample]
+    psis = [w["psi0"] for w in sample]
+    fields = [(w["E0"], w["omega"], w["ncyc"]) for w in sample]
+    P.step_batch(probs, psis, 1, fields=fields)          # warm-up (page-in, threads)
+    times = []
+    for _ in range(max(1, args.warmup)):
+        pass
+    for _ in range(max(1, args.steps)):
+        t = time.perf_counter()
+        P.step_batch(probs, psis, nst, fields=fields)
+        times.append(time.perf_counter() - t)
+    pts = sum(w["n"] for w in sample) * nst
+    v = pts / (sum(times) / len(times))
+    cores = P.num_threads()
+    desc = ("oracle (FP64 C, literal 4-FFT step, full cyclic CN) on %d instances (8 per size) x %d "
+            "time steps per step" % (len(sample), nst))
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": config("c128"),
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def cpu_baseline_sample():
+    """Oracle timed on a bounded sample (about 10-20 s of CPU work)."""
+    from oracle import propagate as P
+    ws = workload(N_INST)
+    sample = []
+    for n in (2048, 4096, 8192, 16384):
+        sample += [w for w in ws if w["n"] == n][:4]
+    nst = 16
+    probs = [P.Problem1D(w["n"], w["a"], w["b"], w["R0"], theta=w["theta"], kind=w["contour"],
+                         a2=w["a2"], dt=w["dt"]) for w in sample]
+    psis = [w["psi0"] for w in sample]
+    fields = [(w["E0"], w["omega"], w["ncyc"]) for w in sample]
+    P.step_batch(probs, psis, 1, fields=fields)
+    t = time.perf_counter()
+    P.step_batch(probs, psis, nst, fields=fields)
+    dt = time.perf_counter() - t
+    pts = sum(w["n"] for w in sample) * nst
+    return {"value": pts / dt, "unit": UNIT, "cores": P.num_threads(), "kind": "oracle",
+            "sample": "%d instances (4 per size) x %d time steps, FP64 C oracle, OpenMP over "
+                      "instances" % (len(sample), nst)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--prec", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--instances", type=int, default=N_INST,
+                    help="fewer instances for profiling captures (not a bench line)")
+    ap.add_argument("--steps-per-call", type=int, default=STEPS_PER_CALL)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1505_06707_gb300 as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = S.SOFT_C64 if args.prec == "c64" else S.SOFT_C128
+    cdt = torch.complex64 if prec == S.SOFT_C64 else torch.complex128
+
+    # weak scaling: every rank runs its own 4096-instance batch (independent problems)
+    spc = args.steps_per_call
+    ws = workload(args.instances)
+    plan = S.soft_create_batch([w["n"] for w in ws], [(w["a"], w["b"]) for w in ws],
+                               [w["R0"] for w in ws], [w["theta"] for w in ws],
+                               [(w["E0"], w["omega"], w["ncyc"]) for w in ws], 0.02, prec=prec,
+                               contour=ws[0]["contour"])
+    offs, total = S.soft_batch_layout(plan)
+    host0 = np.concatenate([w["psi0"] for w in ws]).astype(np.complex64 if prec == S.SOFT_C64
+                                                          else np.complex128)
+    psi = torch.from_numpy(host0).to(dev)
+    ns = [w["n"] for w in ws]
+    nbs = [n // 4 + 2 for n in ns]   # strip block: 2 x N/8 strip rows + 2 coupled neighbours
+    flops = flops_per_call(ns, nbs, spc)
+    pts_call = float(sum(ns)) * spc
+    stream = torch.cuda.current_stream(dev)
+
+    t = 0.0
+    for _ in range(args.warmup):
+        t = S.soft_step_batch(plan, psi, spc, t, stream=stream)
+    torch.cuda.synchronize()
+    launches_per_call = S.soft_last_launches(plan)
+
+    # device-timed region: state resident in HBM
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        t = S.soft_step_batch(plan, psi, spc, t, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+        dist.barrier()
+    sec = ms / 1e3
+    value = pts_call * args.steps * world / sec
+    kern_s = sec / args.steps            # one call is one kernel launch per size group
+    achieved = flops / kern_s / 1e12
+
+    # end to end through the public call with host buffers: H2D of the state,
+    # the call, D2H of the state, every step
+    hbuf = torch.from_numpy(host0).pin_memory()
+    obuf = torch.empty_like(hbuf).pin_memory()
+    for _ in range(2):
+        psi.copy_(hbuf, non_blocking=True)
+        S.soft_step_batch(plan, psi, spc, 0.0, stream=stream)
+        obuf.copy_(psi, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ke = max(3, args.steps // 2)
+    for _ in range(ke):
+        psi.copy_(hbuf, non_blocking=True)
+        S.soft_step_batch(plan, psi, spc, 0.0, stream=stream)
+        obuf.copy_(psi, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = e0.elapsed_time(e1) / 1e3
+    e2e = pts_call * ke * world / e2e_s
+    nbytes = host0.nbytes
+
+    peaks, src = _peaks()
+    hbm = _hbm_peak(peaks)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": args.prec.replace("c64", "c64 (f32)")
+           .replace("c128", "c128 (f64)"), "data": "synthetic", "config": config(args.prec, args.instances, spc)}
+    peak = FP32_PEAK_TFLOPS if prec == S.SOFT_C64 else FP64_PEAK_TFLOPS
+    out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                       "frac": achieved / peak, "traffic": None,
+                       "kernel": "soft1d_kernel (all size groups of one call)",
+                       "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
+                       if prec == S.SOFT_C64 else "GB300 FP64 listing (not measured)"}
+    # the same throughput against HBM, counting one read + one write of the state per time step
+    bytes_pt = 16 if prec == S.SOFT_C64 else 32
+    out["hbm_effective"] = {"GBps": value / world * bytes_pt / 1e9, "peak": hbm,
+                            "frac": value / world * bytes_pt / 1e9 / hbm,
+                            "peak_source": src, "note": "state stays in shared memory for a whole "
+                            "call; this is the rate a one-pass-per-step design would need"}
+    out["e2e"] = {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+    out["gpu_launches"] = int(launches_per_call * args.steps)
+    out["clocks"] = clocks
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_sample()
+    S.soft_destroy(plan)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

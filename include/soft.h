@@ -1,0 +1,190 @@
+/*
+ * soft.h -- C ABI of the GB300 library for the method of Serov & Sergeeva,
+ * "Solution of the Schroedinger equation using exterior complex scaling and
+ * fast Fourier transform" (arXiv:1505.06707).
+ *
+ *   - soft_create / soft_create_batch / soft_step / soft_step_batch:
+ *     the exterior-complex-scaled split-operator FFT time step of Sec. II,
+ *       psi(t+tau) = F^-1 e^{-iK tau/2} F e^{-iU tau/2} e^{-iC tau}
+ *                    e^{-iU tau/2} F^-1 e^{-iK tau/2} F psi(t)
+ *     (the scheme printed after Eq. C_FD), with e^{-iC tau} by Crank-Nicolson.
+ *   - sse_pcg_solve: the stationary equation A psi = f,
+ *     A = F^-1 K F + C + U - E I (Sec. III, under Eq. linsys), by
+ *     complex-symmetric conjugate gradients with the FFT preconditioner of
+ *     Eq. PreconFFT or the banded ECS preconditioner of Eq. PreconFFT_ECS.
+ *
+ * Conventions shared by every call
+ *   Grid.   Axis d has n[d] = 2^m points x_j = a + h (j + 1/2), j = 0..n-1,
+ *           h = (b - a)/n (Sec. II, Eq. DVRgrid, 0-based).  The box must be
+ *           symmetric (a = -b): the contour q(x) is even.
+ *   State.  psi holds samples psi~(x_j) of the scaled wave function
+ *           psi~ = sqrt(q) psi(z(x)) (Sec. II, Eq. psi_zx), interleaved complex
+ *           (re, im), float for SOFT_C64 and double for SOFT_C128.  2D states
+ *           are row-major [ny][nx] (x fastest).  The paper's sqrt(h) DVR factor
+ *           (Sec. II after Eq. FFTbasis) is dropped: every operator is linear.
+ *   Memory. Pointers documented "device" must point to CUDA device memory of
+ *           the calling thread's current device, owned by the caller and
+ *           aligned to 16 bytes.  Pointers documented "host" are ordinary
+ *           host memory.  Plans own their tables and workspaces.
+ *   Streams. Every call that takes a cudaStream_t (passed as void*, NULL =
+ *           legacy default stream) only enqueues work; results are valid once
+ *           that stream has been synchronised.  A plan must not be used from
+ *           two streams at once.
+ *   Errors. Every call returns an int status (SOFT_OK = 0 or a negative
+ *           soft_status).  No call aborts, traps or throws.  Arguments are
+ *           checked on the host before any launch; device-side failures are
+ *           reported through status words read back by the host.
+ */
+#ifndef SOFT_H
+#define SOFT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SOFT_OK = 0,
+    SOFT_ERR_INVALID_ARG = -1,   /* NULL pointer, non-positive size, bad enum  */
+    SOFT_ERR_NOT_POW2 = -2,      /* grid size not a power of two              */
+    SOFT_ERR_OOM = -3,           /* cudaMalloc failed                         */
+    SOFT_ERR_CUDA = -4,          /* a CUDA runtime call failed                */
+    SOFT_ERR_NOT_CONVERGED = -5, /* PCG hit maxit; outputs are still written  */
+    SOFT_ERR_BREAKDOWN = -6,     /* PCG: p^T A p or r^T z vanished            */
+    SOFT_ERR_TIMEOUT = -7,       /* a bounded device wait gave up             */
+    SOFT_ERR_NONFINITE = -8,     /* NaN/Inf in an input or a result           */
+    SOFT_ERR_UNSUPPORTED = -9,   /* size/precision combination not built      */
+    SOFT_ERR_SETUP = -10         /* plan tables failed a self-check           */
+} soft_status;
+
+typedef enum { SOFT_C64 = 1, SOFT_C128 = 2 } soft_prec;
+
+/* Contour q(x) of Sec. II, Eq. ECSintdef, used on every axis.
+ *   SHARP: q = 1 for |x| <= R0, e^{i theta} beyond (Sec. IV, first contour).
+ *   SECS:  q = exp[i theta (|x| - R0)/(b - R0)] beyond R0: Eq. qSECS (Sec. IV)
+ *          with its final angle pi/4 made the parameter theta.
+ *   TFECS: q = sqrt(1 + i y~(s)), y~ = alpha[(1-s)^-2 - (1+s)^-2 - 4s],
+ *          s = (|x| - R0)/(b - R0) (Sec. IV, Eq. qTFECS).                   */
+typedef enum { SOFT_CONTOUR_SHARP = 0, SOFT_CONTOUR_SECS = 1, SOFT_CONTOUR_TFECS = 2 } soft_contour;
+
+typedef struct {
+    int ndim;        /* 1 or 2                                             */
+    int64_t n[2];    /* points per axis, powers of two; n[1] unused in 1D  */
+} soft_grid;
+
+/* Optional settings; NULL means the defaults given in brackets. */
+typedef struct {
+    int prec;            /* soft_prec [SOFT_C128]                            */
+    int contour;         /* soft_contour [SOFT_CONTOUR_SHARP]                */
+    double tfecs_alpha;  /* alpha of Eq. qTFECS [0.5]                        */
+    double soft_a2;      /* a^2 of U = -Z/sqrt(|z|^2 + a^2) [2.0]            */
+    double charge;       /* Z [1.0]; 0 gives U = 0                           */
+    int band_width;      /* N_BW of the banded preconditioner [10]           */
+} soft_options;
+
+/* Laser pulse (length gauge, x-polarised), E(t) = E0 sin^2(pi t/T) sin(omega t)
+ * for 0 <= t <= T = ncycles 2 pi/omega, zero outside.  It couples as
+ * U_L = E(t) xc with xc = clamp(x, -R0, R0): the field is held constant
+ * inside the scaled strips (continuing E z into complex z would grow
+ * exponentially there).  U is taken at t + tau/2 (Sec. II under Eq. SSFFT). */
+typedef struct {
+    double E0, omega, ncycles;
+} soft_field;
+
+typedef struct soft_plan soft_plan;   /* opaque, library-owned */
+
+void soft_default_options(soft_options* opt);
+
+/* soft_create -- build the tables of one problem (Sec. II, Sec. III).
+ *   grid   host; 1D or 2D sizes.
+ *   box    host; a0, b0 [, a1, b1] with a = -b on each axis.
+ *   R0     onset |x| of the scaling, 0 < R0 < b on each axis.
+ *   theta  rotation angle of the sharp contour, final angle of SECS (pi/4 is
+ *          the paper's SECS); ignored by TFECS.
+ *   dt     time step tau (may be negative: backwards propagation).
+ *   opt    host, may be NULL.
+ *   out    host; receives the plan.
+ * Tables are computed on the host in FP64 and uploaded once.  Fails with
+ * SOFT_ERR_NOT_POW2 for sizes that are not powers of two in [64, 16384],
+ * SOFT_ERR_SETUP if the strip Crank-Nicolson factorisation is not accurate
+ * to 1e-12 in FP64. */
+int soft_create(const soft_grid* grid, const double* box, double R0, double theta,
+                double dt, const soft_options* opt, soft_plan** out);
+
+/* soft_create_batch -- `count` independent 1D problems that advance together
+ * (one launch for all).  grids[count], boxes[2*count], R0[count],
+ * theta[count] and fields[count] (NULL = no field) are host arrays.  The
+ * states are packed back to back in creation order; soft_batch_layout gives
+ * the element offset of each. */
+int soft_create_batch(int count, const soft_grid* grids, const double* boxes,
+                      const double* R0, const double* theta, const soft_field* fields,
+                      double dt, const soft_options* opt, soft_plan** out);
+
+/* offsets: host int64[count]; element (not byte) offset of each instance in
+ * the packed state.  total: host; total number of complex elements. */
+int soft_batch_layout(const soft_plan* plan, int64_t* offsets, int64_t* total);
+
+/* soft_step -- advance psi by nsteps steps of the scheme printed after
+ * Eq. C_FD (Sec. II).  psi: device, in/out.  field: host, may be NULL (batch
+ * plans use their own per-instance fields and ignore it).  t_inout: host,
+ * the time at entry, advanced by nsteps*dt on return.  The half-kinetic
+ * factors of consecutive steps inside one call are merged (the scheme is
+ * unchanged up to rounding).  nsteps = 0 is a no-op. */
+int soft_step(soft_plan* plan, void* psi, int64_t nsteps, const soft_field* field,
+              double* t_inout, void* stream);
+
+/* soft_step_batch -- soft_step for a batch plan; psi is the packed state. */
+int soft_step_batch(soft_plan* plan, void* psi, int64_t nsteps, double* t_inout,
+                    void* stream);
+
+/* soft_observe -- norm inside the unscaled region, h sum_{|x_j|<R0} |psi_j|^2,
+ * and the probability flux j = Im(psi^* dpsi/dx) at x = -R0 and x = +R0
+ * (two-point mean and difference across the edge, which lies half-way
+ * between grid points).  These are the quantities a t-SURFF analysis draws
+ * from the propagated state (Sec. I, Sec. IV).  1D plans only.
+ *   psi       device (packed state for batch plans).
+ *   norm_in   device double[count].
+ *   flux      device double[2*count] (left, right per instance).
+ * FP64 accumulation. */
+int soft_observe(const soft_plan* plan, const void* psi, double* norm_in, double* flux,
+                 void* stream);
+
+/* sse_pcg_solve -- solve A psi_e = f for nE energies E[e] by complex-symmetric
+ * CG (Sec. III: the unconjugated form r^T z replaces the inner product),
+ * x0 = 0, stopping when ||r||_2 / ||f||_2 < tol (Hermitian norms, FP64).
+ *   E        host double[nE].
+ *   rhs      device, one right-hand side f shared by all energies.
+ *   psi_out  device, nE consecutive solutions.
+ *   precond  0: simple FFT preconditioner (Eq. PreconFFT);
+ *            1: banded ECS preconditioner (Eq. PreconFFT_ECS).
+ *   iters_out, relres_out: host int[nE], double[nE]; may be NULL.
+ * Returns SOFT_ERR_NOT_CONVERGED if any energy stopped at maxit (its last
+ * iterate is written), SOFT_ERR_BREAKDOWN on a vanishing CG denominator.
+ * C128 plans only.  Workspace is allocated by the plan on first use. */
+int sse_pcg_solve(soft_plan* plan, const double* E, int nE, const void* rhs, void* psi_out,
+                  double tol, int maxit, int precond, int* iters_out, double* relres_out,
+                  void* stream);
+
+/* sse_apply_A / sse_apply_precond -- one application of A (Sec. III under
+ * Eq. linsys) or of the chosen preconditioner, for one energy, device in
+ * and out (x and y must not alias).  Exposed for testing and for callers
+ * that run their own Krylov method. */
+int sse_apply_A(soft_plan* plan, double E, const void* x, void* y, void* stream);
+int sse_apply_precond(soft_plan* plan, double E, int precond, const void* x, void* y,
+                      void* stream);
+
+void soft_destroy(soft_plan* plan);
+const char* soft_strerror(int status);
+
+/* Plan queries: number of instances, grid points of instance i, the element
+ * precision, and the number of kernel launches the last call enqueued. */
+int soft_plan_count(const soft_plan* plan);
+int64_t soft_plan_points(const soft_plan* plan, int i);
+int soft_plan_prec(const soft_plan* plan);
+int64_t soft_last_launches(const soft_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SOFT_H */

@@ -1,0 +1,72 @@
+// Internal declarations shared by the host plan code and the kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <complex>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "soft.h"
+#include "host_tables.h"
+
+namespace soft {
+
+using cd = std::complex<double>;
+
+// Device descriptor of one 1D instance (read by the 1D step kernel).
+struct Inst1D {
+    int64_t off;          // element offset of the instance in the packed state
+    const void* TK;       // e^{-i k^2 tau/2}/N in the forward FFT's output order
+    const void* TKh;      // e^{-i k^2 tau/4}/N, same order (first/last half step)
+    const void* TV;       // e^{-iU0 tau} off the strip block, e^{-iU0 tau/2} on it
+    const void* W;        // per-pass twiddle bases (see soft1d.cuh)
+    const void* cn;       // strip CN coefficients: mf[nb], mb[nb], g[nb]
+    int nb;               // strip block length (0: no absorbing term)
+    int blk0;             // first grid index of the block (cyclic)
+    double x0, h, R0, tau;
+    double E0;            // field amplitude; the pulse shape comes from a per-call table
+    int has_field;
+    int fcls;             // index of the pulse-shape class in that table
+    int iL, iR;           // x_n <= -R0 for n < iL, x_n >= R0 for n >= iR
+    int n;                // grid points
+    int pad_;
+};
+
+// Table set of one distinct 1D problem (shared by identical instances).
+struct Tables1D {
+    int prec = 0, logn = 0, loge = 0, logrm = 0;
+    int nb = 0, blk0 = 0, iL = 0, iR = 0;
+    double R0 = 0, theta = 0;
+    Axis1D ax;                    // host FP64 grid, contour, C
+    std::vector<cd> U0;           // potential at z(x_j)
+    void* TK = nullptr;           // device buffers in the plan's precision
+    void* TKh = nullptr;
+    void* TV = nullptr;
+    void* W = nullptr;
+    void* cn = nullptr;
+};
+
+struct Group1D {                  // instances sharing one kernel configuration
+    int logn = 0, loge = 0, logrm = 0;
+    std::vector<int> members;     // instance indices
+    Inst1D* d_inst = nullptr;     // device descriptors
+    size_t smem = 0;
+};
+
+// kernel launchers (defined in soft1d_*.cu)
+int launch_soft1d(int prec, int logn, int loge, int logrm, const Inst1D* d_inst, int count,
+                  void* psi, int64_t nsteps, const double* ftab, int64_t ftab_stride, int* d_status,
+                  cudaStream_t st, size_t* smem_out);
+// f_c(s) = sin^2(pi t/Tp) sin(omega t) at t = t0 + (s + 1/2) tau for each pulse class c
+int launch_field_table(const double* d_cls /*omega, Tp pairs*/, int ncls, double t0, double tau,
+                       int64_t nsteps, double* out, int64_t stride, cudaStream_t st);
+bool soft1d_supported(int prec, int logn, int loge, int logrm);
+void soft1d_default_cfg(int prec, int logn, int* loge, int* logrm);
+size_t soft1d_smem_bytes(int prec, int logn, int loge);
+
+int launch_observe1d(int prec, const Inst1D* d_inst, int count, const void* psi,
+                     double* norm_in, double* flux, cudaStream_t st);
+
+}  // namespace soft

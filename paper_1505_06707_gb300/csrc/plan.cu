@@ -1,0 +1,437 @@
+// C ABI of the library: plan construction (host FP64 tables, uploaded once)
+// and the 1D step / observables entry points.  The 2D and stationary entry
+// points live in plan2d.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <tuple>
+
+#include "plan_internal.h"
+
+using namespace soft;
+
+namespace soft {
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return SOFT_OK;
+    if (e == cudaErrorMemoryAllocation) return SOFT_ERR_OOM;
+    return SOFT_ERR_CUDA;
+}
+
+int upload(void** dst, const void* src, size_t bytes) {
+    if (bytes == 0) { *dst = nullptr; return SOFT_OK; }
+    cudaError_t e = cudaMalloc(dst, bytes);
+    if (e != cudaSuccess) { *dst = nullptr; return cuda_status(e); }
+    e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+    return cuda_status(e);
+}
+
+// phase table: double2 for complex128 plans; (hi, lo) float4 for complex64 plans
+int upload_tab(void** dst, const std::vector<cd>& v, int prec) {
+    if (prec == SOFT_C128) return upload_c(dst, v, prec);
+    std::vector<float> buf(4 * v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+        const float hr = (float)v[i].real(), hi = (float)v[i].imag();
+        buf[4 * i] = hr;
+        buf[4 * i + 1] = hi;
+        buf[4 * i + 2] = (float)(v[i].real() - (double)hr);
+        buf[4 * i + 3] = (float)(v[i].imag() - (double)hi);
+    }
+    return upload(dst, buf.data(), buf.size() * sizeof(float));
+}
+
+// round a complex FP64 vector to the plan precision and upload it
+int upload_c(void** dst, const std::vector<cd>& v, int prec) {
+    if (prec == SOFT_C128) {
+        std::vector<double> buf(2 * v.size());
+        for (size_t i = 0; i < v.size(); ++i) { buf[2 * i] = v[i].real(); buf[2 * i + 1] = v[i].imag(); }
+        return upload(dst, buf.data(), buf.size() * sizeof(double));
+    }
+    std::vector<float> buf(2 * v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+        buf[2 * i] = (float)v[i].real();
+        buf[2 * i + 1] = (float)v[i].imag();
+    }
+    return upload(dst, buf.data(), buf.size() * sizeof(float));
+}
+
+static int ilog2(int64_t n) {
+    int l = 0;
+    while ((int64_t(1) << l) < n) ++l;
+    return (int64_t(1) << l) == n ? l : -1;
+}
+
+static void free_tables(Tables1D* t) {
+    cudaFree(t->TK); cudaFree(t->TKh); cudaFree(t->TV); cudaFree(t->W); cudaFree(t->cn);
+}
+
+// Build (host FP64) and upload the tables of one 1D problem.
+int make_tables_1d(Tables1D* T, int n, double a, double b, double R0, double theta, double tau,
+                   const soft_options& o, int loge, int logrm) {
+    const int logn = ilog2(n);
+    T->prec = o.prec; T->logn = logn; T->loge = loge; T->logrm = logrm;
+    T->R0 = R0; T->theta = theta;
+    ContourFn cf(o.contour, R0, b, theta, o.tfecs_alpha);
+    build_axis(T->ax, n, a, b, cf, tau);
+    const Axis1D& A = T->ax;
+    int rc = find_block(A, &T->blk0, &T->nb);
+    if (rc) return rc;
+    T->iL = 0; T->iR = 0;
+    for (int j = 0; j < n; ++j) {
+        if (A.x[j] <= -R0) T->iL = j + 1;
+        if (A.x[j] < R0) T->iR = j + 1;
+    }
+    T->U0.resize(n);
+    for (int j = 0; j < n; ++j) T->U0[j] = soft_coulomb(&A.z[j], 1, o.soft_a2, o.charge);
+    // kinetic tables in the forward FFT's output order, 1/N folded in
+    const std::vector<int> perm = dif_output_order(logn, logrm);
+    std::vector<cd> tk(n), tkh(n), tv(n);
+    const std::vector<cd> w = pass_twiddles(logn, logrm);
+    for (int p = 0; p < n; ++p) {
+        const double k = A.k[perm[p]];
+        tk[p] = std::polar(1.0 / n, -0.5 * k * k * tau);
+        tkh[p] = std::polar(1.0 / n, -0.25 * k * k * tau);
+    }
+    // potential factor: full step off the block, half step on it
+    for (int j = 0; j < n; ++j) {
+        const bool inblk = ((j - T->blk0 + n) % n) < T->nb;
+        tv[j] = std::exp(cd(0.0, -1.0) * T->U0[j] * tau * (inblk ? 0.5 : 1.0));
+    }
+    std::vector<cd> mf, mb, g, cnv;
+    if (T->nb > 0) {
+        double err = 0;
+        rc = strip_factor(A, T->blk0, T->nb, mf, mb, g, &err);
+        if (rc) return rc;
+        cnv.insert(cnv.end(), mf.begin(), mf.end());
+        cnv.insert(cnv.end(), mb.begin(), mb.end());
+        cnv.insert(cnv.end(), g.begin(), g.end());
+    }
+    if ((rc = upload_tab(&T->TK, tk, o.prec))) return rc;
+    if ((rc = upload_tab(&T->TKh, tkh, o.prec))) return rc;
+    if ((rc = upload_tab(&T->TV, tv, o.prec))) return rc;
+    if ((rc = upload_c(&T->W, w, o.prec))) return rc;
+    if ((rc = upload_c(&T->cn, cnv, o.prec))) return rc;
+    return SOFT_OK;
+}
+
+}  // namespace soft
+
+// ------------------------------------------------------------------------ ABI
+extern "C" {
+
+void soft_default_options(soft_options* opt) {
+    if (!opt) return;
+    opt->prec = SOFT_C128;
+    opt->contour = SOFT_CONTOUR_SHARP;
+    opt->tfecs_alpha = 0.5;
+    opt->soft_a2 = 2.0;
+    opt->charge = 1.0;
+    opt->band_width = 10;
+}
+
+const char* soft_strerror(int s) {
+    switch (s) {
+    case SOFT_OK: return "ok";
+    case SOFT_ERR_INVALID_ARG: return "invalid argument";
+    case SOFT_ERR_NOT_POW2: return "grid size must be a power of two in the supported range";
+    case SOFT_ERR_OOM: return "device memory allocation failed";
+    case SOFT_ERR_CUDA: return "CUDA runtime error";
+    case SOFT_ERR_NOT_CONVERGED: return "PCG did not reach the tolerance within maxit";
+    case SOFT_ERR_BREAKDOWN: return "PCG breakdown (vanishing bilinear form)";
+    case SOFT_ERR_TIMEOUT: return "device wait timed out";
+    case SOFT_ERR_NONFINITE: return "non-finite value in input or result";
+    case SOFT_ERR_UNSUPPORTED: return "size/precision combination not supported";
+    case SOFT_ERR_SETUP: return "plan tables failed a self-check";
+    }
+    return "unknown status";
+}
+
+static int check_opts(const soft_options* opt, soft_options* o) {
+    soft_default_options(o);
+    if (opt) *o = *opt;
+    if (o->prec != SOFT_C64 && o->prec != SOFT_C128) return SOFT_ERR_INVALID_ARG;
+    if (o->contour < 0 || o->contour > 2) return SOFT_ERR_INVALID_ARG;
+    if (!(o->soft_a2 > 0) && o->charge != 0) return SOFT_ERR_INVALID_ARG;
+    if (o->band_width < 1) return SOFT_ERR_INVALID_ARG;
+    return SOFT_OK;
+}
+
+static int check_axis(int64_t n, double a, double b, double R0) {
+    const int l = ilog2(n);
+    if (l < 6 || l > 14) return SOFT_ERR_NOT_POW2;
+    if (!(b > 0) || std::fabs(a + b) > 1e-12 * b) return SOFT_ERR_INVALID_ARG;
+    if (!(R0 > 0 && R0 < b)) return SOFT_ERR_INVALID_ARG;
+    return SOFT_OK;
+}
+
+// shared by soft_create (1D) and soft_create_batch
+static int create_1d(int count, const soft_grid* grids, const double* boxes, const double* R0,
+                     const double* theta, const soft_field* fields, double dt,
+                     const soft_options& o, bool single, soft_plan** out) {
+    std::unique_ptr<soft_plan> P(new soft_plan());
+    P->kind = 1;
+    P->single = single;
+    P->prec = o.prec;
+    P->opt = o;
+    P->dt = dt;
+    std::map<std::tuple<int64_t, double, double, double, double>, int> seen;
+    std::map<std::pair<double, double>, int> cls;
+    int64_t off = 0;
+    for (int i = 0; i < count; ++i) {
+        if (grids[i].ndim != 1) return SOFT_ERR_INVALID_ARG;
+        const int64_t n = grids[i].n[0];
+        const double a = boxes[2 * i], b = boxes[2 * i + 1];
+        int rc = check_axis(n, a, b, R0[i]);
+        if (rc) return rc;
+        const int logn = ilog2(n);
+        int loge, logrm;
+        soft1d_default_cfg(o.prec, logn, &loge, &logrm);
+        if (!soft1d_supported(o.prec, logn, loge, logrm)) return SOFT_ERR_UNSUPPORTED;
+        auto key = std::make_tuple(n, a, b, R0[i], theta[i]);
+        int tab;
+        auto it = seen.find(key);
+        if (it == seen.end()) {
+            std::unique_ptr<Tables1D> T(new Tables1D());
+            rc = make_tables_1d(T.get(), (int)n, a, b, R0[i], theta[i], dt, o, loge, logrm);
+            if (rc) { free_tables(T.get()); return rc; }
+            // strip rows per thread must fit the kernel's register budget
+            const int thr = (int)(n >> loge);
+            const int chunk = (T->nb + thr - 1) / thr;
+            if (chunk > (1 << loge) / 4 + 2) { free_tables(T.get()); return SOFT_ERR_UNSUPPORTED; }
+            tab = (int)P->tabs.size();
+            P->tabs.push_back(std::move(T));
+            seen[key] = tab;
+        } else {
+            tab = it->second;
+        }
+        soft_plan::InstHost ih;
+        ih.tab = tab; ih.off = off; ih.n = (int)n;
+        ih.has_field = 0; ih.fcls = 0; ih.E0 = 0;
+        if (fields) {
+            const soft_field& f = fields[i];
+            if (f.E0 != 0.0) {
+                if (!(f.omega > 0 && f.ncycles > 0)) return SOFT_ERR_INVALID_ARG;
+                const double Tp = f.ncycles * 2 * 3.14159265358979323846 / f.omega;
+                auto k = std::make_pair(f.omega, Tp);
+                auto c = cls.find(k);
+                if (c == cls.end()) {
+                    const int id = (int)P->h_cls.size() / 2;
+                    P->h_cls.push_back(f.omega);
+                    P->h_cls.push_back(Tp);
+                    cls[k] = id;
+                    ih.fcls = id;
+                } else {
+                    ih.fcls = c->second;
+                }
+                ih.has_field = 1;
+                ih.E0 = f.E0;
+            }
+        }
+        P->inst.push_back(ih);
+        off += n;
+    }
+    P->total = off;
+    int rc = P->build_1d_device();
+    if (rc) return rc;
+    *out = P.release();
+    return SOFT_OK;
+}
+
+int soft_create(const soft_grid* grid, const double* box, double R0, double theta, double dt,
+                const soft_options* opt, soft_plan** out) {
+    if (!grid || !box || !out) return SOFT_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!std::isfinite(dt) || dt == 0.0 || !std::isfinite(theta)) return SOFT_ERR_INVALID_ARG;
+    soft_options o;
+    int rc = check_opts(opt, &o);
+    if (rc) return rc;
+    if (grid->ndim == 1) return create_1d(1, grid, box, &R0, &theta, nullptr, dt, o, true, out);
+    if (grid->ndim == 2) return create_2d(grid, box, R0, theta, dt, o, out);
+    return SOFT_ERR_INVALID_ARG;
+}
+
+int soft_create_batch(int count, const soft_grid* grids, const double* boxes, const double* R0,
+                      const double* theta, const soft_field* fields, double dt,
+                      const soft_options* opt, soft_plan** out) {
+    if (count <= 0 || !grids || !boxes || !R0 || !theta || !out) return SOFT_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!std::isfinite(dt) || dt == 0.0) return SOFT_ERR_INVALID_ARG;
+    soft_options o;
+    int rc = check_opts(opt, &o);
+    if (rc) return rc;
+    return create_1d(count, grids, boxes, R0, theta, fields, dt, o, false, out);
+}
+
+int soft_batch_layout(const soft_plan* P, int64_t* offsets, int64_t* total) {
+    if (!P || P->kind != 1) return SOFT_ERR_INVALID_ARG;
+    if (offsets)
+        for (size_t i = 0; i < P->inst.size(); ++i) offsets[i] = P->inst[i].off;
+    if (total) *total = P->total;
+    return SOFT_OK;
+}
+
+int soft_step(soft_plan* P, void* psi, int64_t nsteps, const soft_field* field, double* t_inout,
+              void* stream) {
+    if (!P || !psi || !t_inout || nsteps < 0) return SOFT_ERR_INVALID_ARG;
+    if (P->kind == 2) return P->step_2d(psi, nsteps, t_inout, (cudaStream_t)stream);
+    if (P->kind != 1) return SOFT_ERR_INVALID_ARG;
+    if (P->single) {
+        int rc = P->set_single_field(field);
+        if (rc) return rc;
+    }
+    return P->step_1d(psi, nsteps, t_inout, (cudaStream_t)stream);
+}
+
+int soft_step_batch(soft_plan* P, void* psi, int64_t nsteps, double* t_inout, void* stream) {
+    if (!P || !psi || !t_inout || nsteps < 0 || P->kind != 1) return SOFT_ERR_INVALID_ARG;
+    return P->step_1d(psi, nsteps, t_inout, (cudaStream_t)stream);
+}
+
+int soft_observe(const soft_plan* P, const void* psi, double* norm_in, double* flux, void* stream) {
+    if (!P || !psi || !norm_in || !flux || P->kind != 1) return SOFT_ERR_INVALID_ARG;
+    int rc = launch_observe1d(P->prec, P->d_inst_obs, (int)P->inst.size(), psi, norm_in, flux,
+                              (cudaStream_t)stream);
+    const_cast<soft_plan*>(P)->last_launches = 1;
+    return rc;
+}
+
+void soft_destroy(soft_plan* P) { delete P; }
+
+int soft_plan_count(const soft_plan* P) {
+    if (!P) return 0;
+    return P->kind == 1 ? (int)P->inst.size() : 1;
+}
+int64_t soft_plan_points(const soft_plan* P, int i) {
+    if (!P) return 0;
+    if (P->kind == 1) return (i >= 0 && i < (int)P->inst.size()) ? P->inst[i].n : 0;
+    return P->points_2d();
+}
+int soft_plan_prec(const soft_plan* P) { return P ? P->prec : 0; }
+int64_t soft_last_launches(const soft_plan* P) { return P ? P->last_launches : 0; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- soft_plan
+soft_plan::~soft_plan() {
+    for (auto& t : tabs) {
+        cudaFree(t->TK); cudaFree(t->TKh); cudaFree(t->TV); cudaFree(t->W); cudaFree(t->cn);
+    }
+    for (auto& g : groups) cudaFree(g.d_inst);
+    cudaFree(d_inst_obs);
+    cudaFree(d_cls);
+    cudaFree(d_ftab);
+    cudaFree(d_status);
+    free_2d();
+}
+
+Inst1D soft_plan::descriptor(int i) const {
+    const InstHost& ih = inst[i];
+    const Tables1D& T = *tabs[ih.tab];
+    Inst1D d;
+    std::memset(&d, 0, sizeof(d));
+    d.off = ih.off;
+    d.TK = T.TK; d.TKh = T.TKh; d.TV = T.TV; d.W = T.W; d.cn = T.cn;
+    d.nb = T.nb; d.blk0 = T.blk0;
+    d.x0 = T.ax.x[0]; d.h = T.ax.h; d.R0 = T.R0; d.tau = dt;
+    d.E0 = ih.E0; d.has_field = ih.has_field; d.fcls = ih.fcls;
+    d.iL = T.iL; d.iR = T.iR; d.n = ih.n;
+    return d;
+}
+
+int soft_plan::build_1d_device() {
+    // groups by kernel configuration, largest N first
+    std::map<std::pair<int, int>, int> gid;
+    for (size_t i = 0; i < inst.size(); ++i) {
+        const Tables1D& T = *tabs[inst[i].tab];
+        auto key = std::make_pair(-T.logn, T.loge * 8 + T.logrm);
+        auto it = gid.find(key);
+        if (it == gid.end()) {
+            Group1D g;
+            g.logn = T.logn; g.loge = T.loge; g.logrm = T.logrm;
+            gid[key] = (int)groups.size();
+            groups.push_back(g);
+            it = gid.find(key);
+        }
+        groups[it->second].members.push_back((int)i);
+    }
+    std::sort(groups.begin(), groups.end(), [](const Group1D& a, const Group1D& b) { return a.logn > b.logn; });
+    int rc;
+    for (auto& g : groups) {
+        std::vector<Inst1D> d;
+        for (int i : g.members) d.push_back(descriptor(i));
+        if ((rc = upload((void**)&g.d_inst, d.data(), d.size() * sizeof(Inst1D)))) return rc;
+        g.smem = soft1d_smem_bytes(prec, g.logn, g.loge);
+    }
+    h_obs.clear();
+    for (size_t i = 0; i < inst.size(); ++i) h_obs.push_back(descriptor((int)i));
+    if ((rc = upload((void**)&d_inst_obs, h_obs.data(), h_obs.size() * sizeof(Inst1D)))) return rc;
+    ncls = (int)h_cls.size() / 2;
+    // room for one extra class used by soft_step's per-call field
+    std::vector<double> c = h_cls;
+    c.push_back(1.0); c.push_back(1.0);
+    if ((rc = upload((void**)&d_cls, c.data(), c.size() * sizeof(double)))) return rc;
+    ftab_cap = 4096;
+    if ((rc = cuda_status(cudaMalloc((void**)&d_ftab, sizeof(double) * ftab_cap * (ncls + 1))))) return rc;
+    if ((rc = cuda_status(cudaMalloc((void**)&d_status, sizeof(int))))) return rc;
+    if ((rc = cuda_status(cudaMemset(d_status, 0, sizeof(int))))) return rc;
+    return SOFT_OK;
+}
+
+// soft_step on a single-instance plan: the call's field replaces the plan's
+int soft_plan::set_single_field(const soft_field* f) {
+    InstHost& ih = inst[0];
+    int has = 0, fc = 0;
+    double E0 = 0;
+    if (f && f->E0 != 0.0) {
+        if (!(f->omega > 0 && f->ncycles > 0)) return SOFT_ERR_INVALID_ARG;
+        const double Tp = f->ncycles * 2 * 3.14159265358979323846 / f->omega;
+        if (call_cls[0] != f->omega || call_cls[1] != Tp) {
+            call_cls[0] = f->omega;
+            call_cls[1] = Tp;
+            int rc = cuda_status(cudaMemcpy(d_cls + 2 * ncls, call_cls, 2 * sizeof(double),
+                                            cudaMemcpyHostToDevice));
+            if (rc) return rc;
+        }
+        has = 1; fc = ncls; E0 = f->E0;
+    }
+    if (has != ih.has_field || fc != ih.fcls || E0 != ih.E0) {
+        ih.has_field = has; ih.fcls = fc; ih.E0 = E0;
+        Inst1D d = descriptor(0);
+        for (auto& g : groups) {
+            int rc = cuda_status(cudaMemcpy(g.d_inst, &d, sizeof(d), cudaMemcpyHostToDevice));
+            if (rc) return rc;
+        }
+        h_obs[0] = d;
+        int rc = cuda_status(cudaMemcpy(d_inst_obs, &d, sizeof(d), cudaMemcpyHostToDevice));
+        if (rc) return rc;
+    }
+    return SOFT_OK;
+}
+
+int soft_plan::step_1d(void* psi, int64_t nsteps, double* t_inout, cudaStream_t st) {
+    last_launches = 0;
+    if (nsteps == 0) return SOFT_OK;
+    double t = *t_inout;
+    const int nc = ncls + (single ? 1 : 0);
+    int64_t done = 0;
+    while (done < nsteps) {
+        const int64_t chunk = std::min<int64_t>(ftab_cap, nsteps - done);
+        int rc;
+        if (nc > 0) {
+            rc = launch_field_table(d_cls, nc, t, dt, chunk, d_ftab, ftab_cap, st);
+            if (rc) return rc;
+            ++last_launches;
+        }
+        for (auto& g : groups) {
+            rc = launch_soft1d(prec, g.logn, g.loge, g.logrm, g.d_inst, (int)g.members.size(), psi, chunk,
+                               d_ftab, ftab_cap, d_status, st, nullptr);
+            if (rc) return rc;
+            ++last_launches;
+        }
+        t += (double)chunk * dt;
+        done += chunk;
+    }
+    *t_inout = t;
+    return SOFT_OK;
+}

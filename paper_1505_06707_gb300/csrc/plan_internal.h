@@ -1,0 +1,63 @@
+// The opaque plan object behind the C ABI.
+#pragma once
+#include <memory>
+#include <vector>
+
+#include "internal.h"
+
+namespace soft {
+int cuda_status(cudaError_t e);
+int upload(void** dst, const void* src, size_t bytes);
+int upload_c(void** dst, const std::vector<cd>& v, int prec);
+int upload_tab(void** dst, const std::vector<cd>& v, int prec);
+int make_tables_1d(Tables1D* T, int n, double a, double b, double R0, double theta, double tau,
+                   const soft_options& o, int loge, int logrm);
+struct Plan2D;
+}  // namespace soft
+
+struct soft_plan {
+    int kind = 0;              // 1: 1D (single or batch), 2: 2D
+    bool single = false;
+    int prec = SOFT_C128;
+    soft_options opt{};
+    double dt = 0;
+    int64_t last_launches = 0;
+
+    // ---- 1D
+    struct InstHost {
+        int tab;
+        int64_t off;
+        int n;
+        int has_field, fcls;
+        double E0;
+    };
+    std::vector<std::unique_ptr<soft::Tables1D>> tabs;
+    std::vector<InstHost> inst;
+    std::vector<soft::Group1D> groups;
+    std::vector<soft::Inst1D> h_obs;
+    soft::Inst1D* d_inst_obs = nullptr;
+    std::vector<double> h_cls;     // (omega, Tp) per pulse class
+    int ncls = 0;
+    double call_cls[2] = {0, 0};   // the class slot used by soft_step's field
+    double* d_cls = nullptr;
+    double* d_ftab = nullptr;
+    int64_t ftab_cap = 0;
+    int* d_status = nullptr;
+    int64_t total = 0;
+
+    soft::Inst1D descriptor(int i) const;
+    int build_1d_device();
+    int set_single_field(const soft_field* f);
+    int step_1d(void* psi, int64_t nsteps, double* t_inout, cudaStream_t st);
+
+    // ---- 2D (plan2d.cu)
+    soft::Plan2D* p2 = nullptr;
+    int step_2d(void* psi, int64_t nsteps, double* t_inout, cudaStream_t st);
+    int64_t points_2d() const;
+    void free_2d();
+
+    ~soft_plan();
+};
+
+int create_2d(const soft_grid* grid, const double* box, double R0, double theta, double dt,
+              const soft_options& o, soft_plan** out);

@@ -1,0 +1,267 @@
+"""ctypes binding of ``include/soft.h`` (argument marshalling only).
+
+Device buffers are passed as integers (``tensor.data_ptr()``) or as torch
+tensors; streams as ``torch.cuda.Stream`` / raw handles / None.  Every
+function raises ``SoftError`` on a non-zero status, except the PCG solve,
+which returns its status for NOT_CONVERGED so that callers can inspect the
+partial result."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+__all__ = [
+    "SoftError", "SOFT_C64", "SOFT_C128", "CONTOUR_SHARP", "CONTOUR_SECS", "CONTOUR_TFECS",
+    "load", "lib_path", "exported_symbols", "Options", "Field", "soft_create", "soft_create_batch",
+    "soft_batch_layout", "soft_step", "soft_step_batch", "soft_observe", "sse_pcg_solve",
+    "sse_apply_A", "sse_apply_precond", "soft_destroy", "soft_plan_points", "soft_plan_count",
+    "soft_last_launches", "Plan",
+]
+
+SOFT_C64, SOFT_C128 = 1, 2
+CONTOUR_SHARP, CONTOUR_SECS, CONTOUR_TFECS = 0, 1, 2
+ERR_NOT_CONVERGED = -5
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_lib", "libsoft.so")
+_lib = None
+
+# every symbol include/soft.h declares
+exported_symbols = [
+    "soft_default_options", "soft_create", "soft_create_batch", "soft_batch_layout", "soft_step",
+    "soft_step_batch", "soft_observe", "sse_pcg_solve", "sse_apply_A", "sse_apply_precond",
+    "soft_destroy", "soft_strerror", "soft_plan_count", "soft_plan_points", "soft_plan_prec",
+    "soft_last_launches",
+]
+
+
+class SoftError(RuntimeError):
+    def __init__(self, status, where):
+        msg = load().soft_strerror(status).decode() if _lib is not None else str(status)
+        super().__init__("%s failed: %s (%d)" % (where, msg, status))
+        self.status = status
+
+
+class Grid(C.Structure):
+    _fields_ = [("ndim", C.c_int), ("n", C.c_int64 * 2)]
+
+
+class Options(C.Structure):
+    _fields_ = [("prec", C.c_int), ("contour", C.c_int), ("tfecs_alpha", C.c_double),
+                ("soft_a2", C.c_double), ("charge", C.c_double), ("band_width", C.c_int)]
+
+
+class Field(C.Structure):
+    _fields_ = [("E0", C.c_double), ("omega", C.c_double), ("ncycles", C.c_double)]
+
+
+def lib_path():
+    return _LIB_PATH
+
+
+def load():
+    """Load libsoft.so (built by ``__graft_entry__.build()`` or
+    ``python -m paper_1505_06707_gb300._build``).  Raises if missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError("libsoft.so not built (%s); run the build step first" % _LIB_PATH)
+    L = C.CDLL(_LIB_PATH)
+    P = C.c_void_p
+    i64 = C.c_int64
+    dbl = C.c_double
+    L.soft_default_options.argtypes = [C.POINTER(Options)]
+    L.soft_create.argtypes = [C.POINTER(Grid), C.POINTER(dbl), dbl, dbl, dbl, C.POINTER(Options),
+                              C.POINTER(P)]
+    L.soft_create_batch.argtypes = [C.c_int, C.POINTER(Grid), C.POINTER(dbl), C.POINTER(dbl),
+                                    C.POINTER(dbl), C.POINTER(Field), dbl, C.POINTER(Options),
+                                    C.POINTER(P)]
+    L.soft_batch_layout.argtypes = [P, C.POINTER(i64), C.POINTER(i64)]
+    L.soft_step.argtypes = [P, P, i64, C.POINTER(Field), C.POINTER(dbl), P]
+    L.soft_step_batch.argtypes = [P, P, i64, C.POINTER(dbl), P]
+    L.soft_observe.argtypes = [P, P, P, P, P]
+    L.sse_pcg_solve.argtypes = [P, C.POINTER(dbl), C.c_int, P, P, dbl, C.c_int, C.c_int,
+                                C.POINTER(C.c_int), C.POINTER(dbl), P]
+    L.sse_apply_A.argtypes = [P, dbl, P, P, P]
+    L.sse_apply_precond.argtypes = [P, dbl, C.c_int, P, P, P]
+    L.soft_destroy.argtypes = [P]
+    L.soft_destroy.restype = None
+    L.soft_strerror.argtypes = [C.c_int]
+    L.soft_strerror.restype = C.c_char_p
+    L.soft_plan_count.argtypes = [P]
+    L.soft_plan_points.argtypes = [P, C.c_int]
+    L.soft_plan_points.restype = i64
+    L.soft_plan_prec.argtypes = [P]
+    L.soft_last_launches.argtypes = [P]
+    L.soft_last_launches.restype = i64
+    for name in exported_symbols:
+        if name not in ("soft_destroy", "soft_strerror", "soft_plan_points", "soft_last_launches",
+                        "soft_default_options"):
+            getattr(L, name).restype = C.c_int
+    L.soft_default_options.restype = None
+    _lib = L
+    return L
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError("expected a device pointer or tensor")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(rc, where):
+    if rc != 0:
+        raise SoftError(rc, where)
+
+
+def _options(prec=SOFT_C128, contour=CONTOUR_SHARP, tfecs_alpha=0.5, soft_a2=2.0, charge=1.0,
+             band_width=10):
+    o = Options()
+    load().soft_default_options(C.byref(o))
+    o.prec, o.contour, o.tfecs_alpha = prec, contour, tfecs_alpha
+    o.soft_a2, o.charge, o.band_width = soft_a2, charge, band_width
+    return o
+
+
+def soft_create(n, box, R0, theta, dt, **opts):
+    """n: int (1D) or (nx, ny); box: (a, b) or (ax, bx, ay, by)."""
+    L = load()
+    g = Grid()
+    if isinstance(n, (tuple, list)):
+        g.ndim, g.n[0], g.n[1] = 2, n[0], n[1]
+    else:
+        g.ndim, g.n[0], g.n[1] = 1, n, 0
+    bx = (C.c_double * len(box))(*box)
+    o = _options(**opts)
+    out = C.c_void_p()
+    _check(L.soft_create(C.byref(g), bx, R0, theta, dt, C.byref(o), C.byref(out)), "soft_create")
+    return out.value
+
+
+def soft_create_batch(ns, boxes, R0s, thetas, fields, dt, **opts):
+    L = load()
+    cnt = len(ns)
+    G = (Grid * cnt)()
+    for i, n in enumerate(ns):
+        G[i].ndim, G[i].n[0], G[i].n[1] = 1, n, 0
+    bx = (C.c_double * (2 * cnt))(*[v for b in boxes for v in b])
+    r0 = (C.c_double * cnt)(*R0s)
+    th = (C.c_double * cnt)(*thetas)
+    F = None
+    if fields is not None:
+        F = (Field * cnt)()
+        for i, f in enumerate(fields):
+            if f is not None:
+                F[i].E0, F[i].omega, F[i].ncycles = f
+    o = _options(**opts)
+    out = C.c_void_p()
+    _check(L.soft_create_batch(cnt, G, bx, r0, th, F, dt, C.byref(o), C.byref(out)),
+           "soft_create_batch")
+    return out.value
+
+
+def soft_batch_layout(plan):
+    cnt = load().soft_plan_count(plan)
+    off = (C.c_int64 * cnt)()
+    tot = C.c_int64()
+    _check(load().soft_batch_layout(plan, off, C.byref(tot)), "soft_batch_layout")
+    return list(off), tot.value
+
+
+def soft_step(plan, psi, nsteps, t, field=None, stream=None):
+    """Returns the advanced time."""
+    tt = C.c_double(t)
+    F = None
+    if field is not None:
+        F = Field(*field)
+    _check(load().soft_step(plan, _ptr(psi), int(nsteps), C.byref(F) if F is not None else None,
+                            C.byref(tt), _stream(stream)), "soft_step")
+    return tt.value
+
+
+def soft_step_batch(plan, psi, nsteps, t, stream=None):
+    tt = C.c_double(t)
+    _check(load().soft_step_batch(plan, _ptr(psi), int(nsteps), C.byref(tt), _stream(stream)),
+           "soft_step_batch")
+    return tt.value
+
+
+def soft_observe(plan, psi, norm_in, flux, stream=None):
+    _check(load().soft_observe(plan, _ptr(psi), _ptr(norm_in), _ptr(flux), _stream(stream)),
+           "soft_observe")
+
+
+def sse_pcg_solve(plan, E, rhs, psi_out, tol=1e-8, maxit=1000, precond=1, stream=None):
+    """Returns (status, iterations list, relative residual list)."""
+    nE = len(E)
+    Ea = (C.c_double * nE)(*E)
+    it = (C.c_int * nE)()
+    rr = (C.c_double * nE)()
+    rc = load().sse_pcg_solve(plan, Ea, nE, _ptr(rhs), _ptr(psi_out), tol, maxit, precond, it, rr,
+                              _stream(stream))
+    if rc not in (0, ERR_NOT_CONVERGED):
+        raise SoftError(rc, "sse_pcg_solve")
+    return rc, list(it), list(rr)
+
+
+def sse_apply_A(plan, E, x, y, stream=None):
+    _check(load().sse_apply_A(plan, E, _ptr(x), _ptr(y), _stream(stream)), "sse_apply_A")
+
+
+def sse_apply_precond(plan, E, precond, x, y, stream=None):
+    _check(load().sse_apply_precond(plan, E, precond, _ptr(x), _ptr(y), _stream(stream)),
+           "sse_apply_precond")
+
+
+def soft_destroy(plan):
+    if plan:
+        load().soft_destroy(plan)
+
+
+def soft_plan_points(plan, i=0):
+    return load().soft_plan_points(plan, i)
+
+
+def soft_plan_count(plan):
+    return load().soft_plan_count(plan)
+
+
+def soft_last_launches(plan):
+    return load().soft_last_launches(plan)
+
+
+class Plan:
+    """Owns a plan handle (destroyed on close / garbage collection)."""
+
+    def __init__(self, handle):
+        self.h = handle
+
+    def close(self):
+        if self.h:
+            soft_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
