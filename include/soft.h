@@ -55,7 +55,8 @@ typedef enum {
     SOFT_ERR_TIMEOUT = -7,       /* a bounded device wait gave up             */
     SOFT_ERR_NONFINITE = -8,     /* NaN/Inf in an input or a result           */
     SOFT_ERR_UNSUPPORTED = -9,   /* size/precision combination not built      */
-    SOFT_ERR_SETUP = -10         /* plan tables failed a self-check           */
+    SOFT_ERR_SETUP = -10,        /* plan tables failed a self-check           */
+    SOFT_ERR_TOO_LARGE = -11     /* request exceeds a fixed-size scratch area  */
 } soft_status;
 
 typedef enum { SOFT_C64 = 1, SOFT_C128 = 2 } soft_prec;
@@ -173,6 +174,25 @@ int sse_pcg_solve(soft_plan* plan, const double* E, int nE, const void* rhs, voi
 int sse_apply_A(soft_plan* plan, double E, const void* x, void* y, void* stream);
 int sse_apply_precond(soft_plan* plan, double E, int precond, const void* x, void* y,
                       void* stream);
+
+/* soft_step_noalloc -- soft_step for a single-instance 1D plan that allocates
+ * nothing: no cudaMalloc, no cudaFree, no allocating library routine.  The
+ * paper has no counterpart; this exists for callers that cannot allocate
+ * device memory while stepping (real-time loops where an allocation could
+ * stall, hosts whose device memory is owned by an external manager,
+ * embeddings that forbid allocation after start-up).  Its scratch (pulse
+ * table, descriptor, status word) is one file-scope device array of about
+ * 130 KB that every GPU loading the library keeps until exit.
+ *   psi, field, t_inout, stream: as soft_step.
+ *   nsteps: at most 16384 per call; larger requests return SOFT_ERR_TOO_LARGE
+ *           without touching psi.
+ * All calls share the array and it keeps the last call's contents; each call
+ * rewrites what it uses and clears the status word first.  Calls that overlap
+ * on the GPU race on the array: serialise them.  The first call on a device
+ * looks up the array's device address with that device current; make it
+ * before any stream capture. */
+int soft_step_noalloc(const soft_plan* plan, void* psi, int64_t nsteps, const soft_field* field,
+                      double* t_inout, void* stream);
 
 void soft_destroy(soft_plan* plan);
 const char* soft_strerror(int status);

@@ -143,6 +143,7 @@ const char* soft_strerror(int s) {
     case SOFT_ERR_NONFINITE: return "non-finite value in input or result";
     case SOFT_ERR_UNSUPPORTED: return "size/precision combination not supported";
     case SOFT_ERR_SETUP: return "plan tables failed a self-check";
+    case SOFT_ERR_TOO_LARGE: return "request exceeds the fixed scratch of the no-allocation entry point";
     }
     return "unknown status";
 }

@@ -13,7 +13,7 @@ import os
 __all__ = [
     "SoftError", "SOFT_C64", "SOFT_C128", "CONTOUR_SHARP", "CONTOUR_SECS", "CONTOUR_TFECS",
     "load", "lib_path", "exported_symbols", "Options", "Field", "soft_create", "soft_create_batch",
-    "soft_batch_layout", "soft_step", "soft_step_batch", "soft_observe", "sse_pcg_solve",
+    "soft_batch_layout", "soft_step", "soft_step_batch", "soft_step_noalloc", "soft_observe", "sse_pcg_solve",
     "sse_apply_A", "sse_apply_precond", "soft_destroy", "soft_plan_points", "soft_plan_count",
     "soft_last_launches", "Plan",
 ]
@@ -31,7 +31,7 @@ exported_symbols = [
     "soft_default_options", "soft_create", "soft_create_batch", "soft_batch_layout", "soft_step",
     "soft_step_batch", "soft_observe", "sse_pcg_solve", "sse_apply_A", "sse_apply_precond",
     "soft_destroy", "soft_strerror", "soft_plan_count", "soft_plan_points", "soft_plan_prec",
-    "soft_last_launches",
+    "soft_last_launches", "soft_step_noalloc",
 ]
 
 
@@ -80,6 +80,7 @@ def load():
     L.soft_batch_layout.argtypes = [P, C.POINTER(i64), C.POINTER(i64)]
     L.soft_step.argtypes = [P, P, i64, C.POINTER(Field), C.POINTER(dbl), P]
     L.soft_step_batch.argtypes = [P, P, i64, C.POINTER(dbl), P]
+    L.soft_step_noalloc.argtypes = [P, P, i64, C.POINTER(Field), C.POINTER(dbl), P]
     L.soft_observe.argtypes = [P, P, P, P, P]
     L.sse_pcg_solve.argtypes = [P, C.POINTER(dbl), C.c_int, P, P, dbl, C.c_int, C.c_int,
                                 C.POINTER(C.c_int), C.POINTER(dbl), P]
@@ -189,6 +190,19 @@ def soft_step(plan, psi, nsteps, t, field=None, stream=None):
         F = Field(*field)
     _check(load().soft_step(plan, _ptr(psi), int(nsteps), C.byref(F) if F is not None else None,
                             C.byref(tt), _stream(stream)), "soft_step")
+    return tt.value
+
+
+def soft_step_noalloc(plan, psi, nsteps, t, field=None, stream=None):
+    """soft_step without any device allocation (fixed scratch, at most 16384
+    steps per call).  Returns the advanced time."""
+    tt = C.c_double(t)
+    F = None
+    if field is not None:
+        F = Field(*field)
+    _check(load().soft_step_noalloc(plan, _ptr(psi), int(nsteps),
+                                    C.byref(F) if F is not None else None, C.byref(tt),
+                                    _stream(stream)), "soft_step_noalloc")
     return tt.value
 
 
