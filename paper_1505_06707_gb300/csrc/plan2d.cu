@@ -1,27 +1,206 @@
-// 2D split-operator step and the stationary PCG solve (entry points).
+// 2D plans: host FP64 tables for a [ny][nx] grid and the step driver (row,
+// column and y-strip passes, replayed from a CUDA graph).  The stationary
+// PCG entry points live in pcg.cu.
+#include <cmath>
+#include <cstring>
+
 #include "plan_internal.h"
+#include "soft2d.cuh"
 
 using namespace soft;
 
 namespace soft {
-struct Plan2D {};
+
+int soft2d_row_c64(int, int, int, int, const Geo2D&, void*, int, int, const void*, cudaStream_t);
+int soft2d_row_c128(int, int, int, int, const Geo2D&, void*, int, int, const void*, cudaStream_t);
+int soft2d_col_c64(int, int, int, const Geo2D&, void*, const void*, cudaStream_t);
+int soft2d_col_c128(int, int, int, const Geo2D&, void*, const void*, cudaStream_t);
+int soft2d_cny_c64(const Geo2D&, void*, cudaStream_t);
+int soft2d_cny_c128(const Geo2D&, void*, cudaStream_t);
+
+static int ilog2_2d(int64_t n) {
+    int l = 0;
+    while ((int64_t(1) << l) < n) ++l;
+    return (int64_t(1) << l) == n ? l : -1;
+}
+
+Plan2D::~Plan2D() {
+    void* bufs[] = {Wx, Wy, TKx, TKhx, TKy, TKhy, TVh, cnx, cny};
+    for (void* b : bufs) cudaFree(b);
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    free_pcg();
+}
+
+int Plan2D::row(int mode, void* psi, int row0, int nrows, const void* tkx, cudaStream_t st) {
+    ++launches;
+    if (prec == SOFT_C64) return soft2d_row_c64(lx, lex, lrx, mode, geo, psi, row0, nrows, tkx, st);
+    return soft2d_row_c128(lx, lex, lrx, mode, geo, psi, row0, nrows, tkx, st);
+}
+int Plan2D::col(void* psi, const void* tky, cudaStream_t st) {
+    ++launches;
+    if (prec == SOFT_C64) return soft2d_col_c64(ly, ley, lry, geo, psi, tky, st);
+    return soft2d_col_c128(ly, ley, lry, geo, psi, tky, st);
+}
+int Plan2D::ypass(void* psi, cudaStream_t st) {
+    ++launches;
+    if (prec == SOFT_C64) return soft2d_cny_c64(geo, psi, st);
+    return soft2d_cny_c128(geo, psi, st);
+}
+
+// one full step in (k_x, y) representation; last = use the half kinetic tables
+int Plan2D::enqueue_step(void* psi, bool last, cudaStream_t st) {
+    const void* tkx = last ? TKhx : TKx;
+    const void* tky = last ? TKhy : TKy;
+    int rc;
+    const int nb = geo.nby;
+    // rows outside the y-strip block: F_x^-1, V with CN_x, F_x, x kinetic factor
+    if ((rc = row(ROW_FULL, psi, (geo.blk0y + nb) % ny, ny - nb, tkx, st))) return rc;
+    if (nb > 0) {
+        if ((rc = row(ROW_A, psi, geo.blk0y, nb, nullptr, st))) return rc;
+        if ((rc = ypass(psi, st))) return rc;
+        if ((rc = row(ROW_B, psi, geo.blk0y, nb, tkx, st))) return rc;
+    }
+    return col(psi, tky, st);
+}
+
 }  // namespace soft
 
-int create_2d(const soft_grid*, const double*, double, double, double, const soft_options&,
-              soft_plan**) {
-    return SOFT_ERR_UNSUPPORTED;
+int create_2d(const soft_grid* grid, const double* box, double R0, double theta, double dt,
+              const soft_options& o, soft_plan** out) {
+    const int64_t nx = grid->n[0], ny = grid->n[1];
+    const int lx = ilog2_2d(nx), ly = ilog2_2d(ny);
+    if (lx < 8 || lx > 11 || ly < 8 || ly > 11) return SOFT_ERR_NOT_POW2;
+    for (int d = 0; d < 2; ++d) {
+        const double a = box[2 * d], b = box[2 * d + 1];
+        if (!(b > 0) || std::fabs(a + b) > 1e-12 * b || !(R0 > 0 && R0 < b)) return SOFT_ERR_INVALID_ARG;
+    }
+    std::unique_ptr<soft_plan> P(new soft_plan());
+    P->kind = 2;
+    P->prec = o.prec;
+    P->opt = o;
+    P->dt = dt;
+    Plan2D* Q = new Plan2D();
+    P->p2 = Q;
+    Q->prec = o.prec;
+    Q->nx = (int)nx; Q->ny = (int)ny;
+    Q->lx = lx; Q->ly = ly;
+    soft1d_default_cfg(o.prec, lx, &Q->lex, &Q->lrx);
+    soft1d_default_cfg(o.prec, ly, &Q->ley, &Q->lry);
+    Q->R0 = R0; Q->theta = theta; Q->tau = dt;
+    ContourFn cx(o.contour, R0, box[1], theta, o.tfecs_alpha);
+    ContourFn cy(o.contour, R0, box[3], theta, o.tfecs_alpha);
+    build_axis(Q->ax, (int)nx, box[0], box[1], cx, dt);
+    build_axis(Q->ay, (int)ny, box[2], box[3], cy, dt);
+    int rc;
+    int bx0, nbx, by0, nby;
+    if ((rc = find_block(Q->ax, &bx0, &nbx))) return rc;
+    if ((rc = find_block(Q->ay, &by0, &nby))) return rc;
+    // strip rows per thread of the row pass, and per lane of the y pass
+    const int thr = (int)(nx >> Q->lex);
+    if ((nbx + thr - 1) / thr > (1 << Q->lex) / 4 + 2) return SOFT_ERR_UNSUPPORTED;
+    if ((nby + 31) / 32 > 24) return SOFT_ERR_UNSUPPORTED;
+    // potential at (z(x), z(y)) and e^{-iU tau/2}
+    Q->U.resize((size_t)nx * ny);
+    std::vector<cd> tvh((size_t)nx * ny);
+    for (int64_t yy = 0; yy < ny; ++yy)
+        for (int64_t xx = 0; xx < nx; ++xx) {
+            const cd z[2] = {Q->ax.z[xx], Q->ay.z[yy]};
+            const cd u = soft_coulomb(z, 2, o.soft_a2, o.charge);
+            Q->U[yy * nx + xx] = u;
+            tvh[yy * nx + xx] = std::exp(cd(0.0, -0.5 * dt) * u);
+        }
+    // kinetic factors per axis, in each FFT's output order, 1/n folded in
+    auto ktab = [&](const Axis1D& A, int logn, int logrm, double frac) {
+        const std::vector<int> perm = dif_output_order(logn, logrm);
+        std::vector<cd> t(A.n);
+        for (int p = 0; p < A.n; ++p) {
+            const double k = A.k[perm[p]];
+            t[p] = std::polar(1.0 / A.n, -0.5 * k * k * dt * frac);
+        }
+        return t;
+    };
+    std::vector<cd> mfx, mbx, gx, mfy, mby, gy, cnx, cny;
+    double err;
+    if (nbx > 0) {
+        if ((rc = strip_factor(Q->ax, bx0, nbx, mfx, mbx, gx, &err))) return rc;
+        cnx = mfx; cnx.insert(cnx.end(), mbx.begin(), mbx.end()); cnx.insert(cnx.end(), gx.begin(), gx.end());
+    }
+    if (nby > 0) {
+        if ((rc = strip_factor(Q->ay, by0, nby, mfy, mby, gy, &err))) return rc;
+        cny = mfy; cny.insert(cny.end(), mby.begin(), mby.end()); cny.insert(cny.end(), gy.begin(), gy.end());
+    }
+    const int pr = o.prec;
+    if ((rc = upload_c(&Q->Wx, pass_twiddles(lx, Q->lrx), pr))) return rc;
+    if ((rc = upload_c(&Q->Wy, pass_twiddles(ly, Q->lry), pr))) return rc;
+    if ((rc = upload_tab(&Q->TKx, ktab(Q->ax, lx, Q->lrx, 1.0), pr))) return rc;
+    if ((rc = upload_tab(&Q->TKhx, ktab(Q->ax, lx, Q->lrx, 0.5), pr))) return rc;
+    if ((rc = upload_tab(&Q->TKy, ktab(Q->ay, ly, Q->lry, 1.0), pr))) return rc;
+    if ((rc = upload_tab(&Q->TKhy, ktab(Q->ay, ly, Q->lry, 0.5), pr))) return rc;
+    if ((rc = upload_tab(&Q->TVh, tvh, pr))) return rc;
+    if ((rc = upload_c(&Q->cnx, cnx, pr))) return rc;
+    if ((rc = upload_c(&Q->cny, cny, pr))) return rc;
+    Geo2D& g = Q->geo;
+    g.Wx = Q->Wx; g.Wy = Q->Wy; g.TVh = Q->TVh; g.cnx = Q->cnx; g.cny = Q->cny;
+    g.nx = (int)nx; g.ny = (int)ny;
+    g.nbx = nbx; g.blk0x = bx0; g.nby = nby; g.blk0y = by0;
+    // set every kernel's shared-memory attribute now, outside any stream capture
+    for (int m = ROW_FWD; m <= ROW_INV; ++m)
+        if ((rc = Q->row(m, nullptr, 0, 0, nullptr, 0))) return rc;
+    if ((rc = Q->col(nullptr, nullptr, 0))) return rc;
+    if ((rc = Q->ypass(nullptr, 0))) return rc;
+    Q->launches = 0;
+    *out = P.release();
+    return SOFT_OK;
 }
-int soft_plan::step_2d(void*, int64_t, double*, cudaStream_t) { return SOFT_ERR_UNSUPPORTED; }
-int64_t soft_plan::points_2d() const { return 0; }
-void soft_plan::free_2d() { delete p2; p2 = nullptr; }
 
-extern "C" {
-int sse_pcg_solve(soft_plan*, const double*, int, const void*, void*, double, int, int, int*,
-                  double*, void*) {
-    return SOFT_ERR_UNSUPPORTED;
+// K^1/2 (V K)^{n-1} V K^1/2: forward row pass with the half x factor, a half
+// column pass, n steps (the last with half kinetic factors), inverse row pass.
+// The middle steps are replayed from a CUDA graph captured once per state
+// pointer and stream (chunks of GRAPH_STEPS steps).
+int soft_plan::step_2d(void* psi, int64_t nsteps, double* t_inout, cudaStream_t st) {
+    Plan2D* Q = p2;
+    Q->launches = 0;
+    last_launches = 0;
+    if (nsteps == 0) return SOFT_OK;
+    int rc;
+    if ((rc = Q->row(ROW_FWD, psi, 0, Q->ny, Q->TKhx, st))) return rc;
+    if ((rc = Q->col(psi, Q->TKhy, st))) return rc;
+    int64_t mid = nsteps - 1;
+    const int64_t G = Plan2D::GRAPH_STEPS;
+    if (mid >= G) {
+        if (!Q->graph_exec || Q->graph_psi != psi || Q->graph_stream != st) {
+            if (Q->graph_exec) { cudaGraphExecDestroy(Q->graph_exec); Q->graph_exec = nullptr; }
+            cudaStream_t cap;
+            if ((rc = cuda_status(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)))) return rc;
+            cudaGraph_t graph;
+            const int64_t before = Q->launches;
+            rc = cuda_status(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+            for (int64_t s = 0; s < G && rc == SOFT_OK; ++s) rc = Q->enqueue_step(psi, false, cap);
+            cudaError_t e = cudaStreamEndCapture(cap, &graph);
+            if (rc == SOFT_OK) rc = cuda_status(e);
+            if (rc == SOFT_OK) rc = cuda_status(cudaGraphInstantiate(&Q->graph_exec, graph, 0));
+            if (e == cudaSuccess) cudaGraphDestroy(graph);
+            cudaStreamDestroy(cap);
+            if (rc) { Q->graph_exec = nullptr; return rc; }
+            Q->graph_psi = psi;
+            Q->graph_stream = st;
+            Q->graph_launches = Q->launches - before;   // kernels in one replay
+            Q->launches = before;
+        }
+        while (mid >= G) {
+            if ((rc = cuda_status(cudaGraphLaunch(Q->graph_exec, st)))) return rc;
+            Q->launches += Q->graph_launches;
+            mid -= G;
+        }
+    }
+    for (int64_t s = 0; s < mid; ++s)
+        if ((rc = Q->enqueue_step(psi, false, st))) return rc;
+    if ((rc = Q->enqueue_step(psi, true, st))) return rc;
+    if ((rc = Q->row(ROW_INV, psi, 0, Q->ny, nullptr, st))) return rc;
+    last_launches = Q->launches;
+    *t_inout += (double)nsteps * dt;
+    return SOFT_OK;
 }
-int sse_apply_A(soft_plan*, double, const void*, void*, void*) { return SOFT_ERR_UNSUPPORTED; }
-int sse_apply_precond(soft_plan*, double, int, const void*, void*, void*) {
-    return SOFT_ERR_UNSUPPORTED;
-}
-}
+
+int64_t soft_plan::points_2d() const { return p2 ? (int64_t)p2->nx * p2->ny : 0; }
+void soft_plan::free_2d() { delete p2; p2 = nullptr; }

@@ -12,7 +12,37 @@ int upload_c(void** dst, const std::vector<cd>& v, int prec);
 int upload_tab(void** dst, const std::vector<cd>& v, int prec);
 int make_tables_1d(Tables1D* T, int n, double a, double b, double R0, double theta, double tau,
                    const soft_options& o, int loge, int logrm);
-struct Plan2D;
+
+struct Geo2D;
+}  // namespace soft
+
+#include "soft2d_geo.h"
+
+namespace soft {
+// 2D plan state (plan2d.cu) and the stationary solver workspace (pcg.cu)
+struct Plan2D {
+    static constexpr int64_t GRAPH_STEPS = 16;
+    int prec = SOFT_C128;
+    int nx = 0, ny = 0, lx = 0, ly = 0, lex = 0, lrx = 0, ley = 0, lry = 0;
+    double R0 = 0, theta = 0, tau = 0;
+    Axis1D ax, ay;                 // host FP64 axes (grid, k, q, z, C)
+    std::vector<cd> U;             // U(z(x), z(y)), [ny][nx]
+    void *Wx = nullptr, *Wy = nullptr, *TKx = nullptr, *TKhx = nullptr, *TKy = nullptr,
+         *TKhy = nullptr, *TVh = nullptr, *cnx = nullptr, *cny = nullptr;
+    Geo2D geo{};
+    int64_t launches = 0, graph_launches = 0;
+    cudaGraphExec_t graph_exec = nullptr;
+    void* graph_psi = nullptr;
+    cudaStream_t graph_stream = nullptr;
+    struct Pcg* pcg = nullptr;
+
+    int row(int mode, void* psi, int row0, int nrows, const void* tkx, cudaStream_t st);
+    int col(void* psi, const void* tky, cudaStream_t st);
+    int ypass(void* psi, cudaStream_t st);
+    int enqueue_step(void* psi, bool last, cudaStream_t st);
+    void free_pcg();
+    ~Plan2D();
+};
 }  // namespace soft
 
 struct soft_plan {

@@ -115,7 +115,8 @@ __device__ __forceinline__ void load_tw(C* b, const C* __restrict__ t) {
 
 // forward DIF pass P (radix 2^LOGR on sub-transforms of length 2^LOGL)
 template <typename R, int LOGN, int LOGE, int LOGRM, int P>
-__device__ __forceinline__ void fwd_pass(typename CT<R>::C* S, const typename CT<R>::C* __restrict__ W) {
+__device__ __forceinline__ void fwd_pass(typename CT<R>::C* S, const typename CT<R>::C* __restrict__ W,
+                                         int tid) {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
     using C = typename K::C;
     using G = PassGeom<LOGN, LOGRM, P>;
@@ -125,7 +126,7 @@ __device__ __forceinline__ void fwd_pass(typename CT<R>::C* S, const typename CT
     constexpr int NB = G::LOGR;               // twiddle bases needed: 2^0 .. 2^(LOGR-1)
 #pragma unroll 1
     for (int u = 0; u < K::E / RR; ++u) {      // one butterfly live at a time
-        const int b = threadIdx.x + u * K::T;
+        const int b = tid + u * K::T;
         const int blk = b / s, off = b & (s - 1);
         const int base = blk * L + off;
         C v[RR];
@@ -140,7 +141,8 @@ __device__ __forceinline__ void fwd_pass(typename CT<R>::C* S, const typename CT
 
 // inverse DIT pass P (undoes fwd_pass P up to the factor 2^LOGR)
 template <typename R, int LOGN, int LOGE, int LOGRM, int P>
-__device__ __forceinline__ void inv_pass(typename CT<R>::C* S, const typename CT<R>::C* __restrict__ W) {
+__device__ __forceinline__ void inv_pass(typename CT<R>::C* S, const typename CT<R>::C* __restrict__ W,
+                                         int tid) {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
     using C = typename K::C;
     using G = PassGeom<LOGN, LOGRM, P>;
@@ -150,7 +152,7 @@ __device__ __forceinline__ void inv_pass(typename CT<R>::C* S, const typename CT
     constexpr int NB = G::LOGR;
 #pragma unroll 1
     for (int u = 0; u < K::E / RR; ++u) {      // one butterfly live at a time
-        const int b = threadIdx.x + u * K::T;
+        const int b = tid + u * K::T;
         const int blk = b / s, off = b & (s - 1);
         const int base = blk * L + off;
         C v[RR];
@@ -162,34 +164,104 @@ __device__ __forceinline__ void inv_pass(typename CT<R>::C* S, const typename CT
     }
 }
 
+// Whole transforms.  tid is the thread's index within the group of T threads
+// that own this transform; every thread of the CTA must call (the passes are
+// separated by __syncthreads), so several transforms can share a CTA.
 template <typename R, int LOGN, int LOGE, int LOGRM, int P>
-__device__ __forceinline__ void fwd_fft(typename CT<R>::C* S, const typename CT<R>::C* W) {
+__device__ __forceinline__ void fwd_fft(typename CT<R>::C* S, const typename CT<R>::C* W, int tid) {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
     if constexpr (P < K::NPASS) {
-        fwd_pass<R, LOGN, LOGE, LOGRM, P>(S, W);
+        fwd_pass<R, LOGN, LOGE, LOGRM, P>(S, W, tid);
         __syncthreads();
-        fwd_fft<R, LOGN, LOGE, LOGRM, P + 1>(S, W);
+        fwd_fft<R, LOGN, LOGE, LOGRM, P + 1>(S, W, tid);
     }
 }
 template <typename R, int LOGN, int LOGE, int LOGRM, int P>
-__device__ __forceinline__ void inv_fft(typename CT<R>::C* S, const typename CT<R>::C* W) {
+__device__ __forceinline__ void inv_fft(typename CT<R>::C* S, const typename CT<R>::C* W, int tid) {
     if constexpr (P >= 0) {
-        inv_pass<R, LOGN, LOGE, LOGRM, P>(S, W);
+        inv_pass<R, LOGN, LOGE, LOGRM, P>(S, W, tid);
         __syncthreads();
-        inv_fft<R, LOGN, LOGE, LOGRM, P - 1>(S, W);
+        inv_fft<R, LOGN, LOGE, LOGRM, P - 1>(S, W, tid);
     }
 }
 
 // k-space factor (table already in the digit-reversed order of fwd_fft)
 template <typename R, int LOGN, int LOGE, int LOGRM>
-__device__ __forceinline__ void kmul(typename CT<R>::C* S, const typename TabT<R>::T* __restrict__ tab) {
+__device__ __forceinline__ void kmul(typename CT<R>::C* S, const typename TabT<R>::T* __restrict__ tab,
+                                     int tid) {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
 #pragma unroll 4
     for (int j = 0; j < K::E; ++j) {
-        const int n = threadIdx.x + j * K::T;
+        const int n = tid + j * K::T;
         S[swz<typename K::C>(n)] = tmul(S[swz<typename K::C>(n)], __ldg(&tab[n]));
     }
     __syncthreads();
+}
+
+// Crank-Nicolson factor on the strip block (Sec. II, CN form of e^{-iC tau}):
+// with M = 1 + i tau C/2 factored on the host (no pivoting) into the
+// recurrences y_i = mf_i y_{i-1} + r_i and x_i = mb_i x_{i+1} + g_i y_i, the
+// block rows r_i = S[(blk0 + i) mod N] become post(n, 2 x_i - r_i), which is
+// (1 + i tau C/2)^{-1} (1 - i tau C/2) r.  Each thread runs a contiguous chunk
+// of rows; the chunks are joined by block-wide scans of the affine maps.
+// cn holds mf[nb], mb[nb], g[nb].  All T threads must call.
+template <typename C, int T, int CMAX, int N, class Post>
+__device__ __forceinline__ void strip_cn(C* S, const C* __restrict__ cn, int nb, int blk0, int tid,
+                                         C* scan, Post post) {
+    const int chunk = (nb + T - 1) / T;          // host guarantees chunk <= CMAX
+    const int i0 = tid * chunk;
+    C y[CMAX];
+    C Mp; Mp.x = 1; Mp.y = 0;
+    C yl; yl.x = 0; yl.y = 0;
+#pragma unroll
+    for (int c = 0; c < CMAX; ++c) {
+        const int i = i0 + c;
+        if (c < chunk && i < nb) {
+            const C rc = S[swz<C>((blk0 + i) & (N - 1))];
+            const C m = __ldg(&cn[i]);
+            yl = cfma(m, yl, rc);
+            Mp = cmul(m, Mp);
+            y[c] = yl;
+        }
+    }
+    C carry = affine_carry<C, T, false>(Mp, yl, scan);
+    {
+        C pr; pr.x = 1; pr.y = 0;
+#pragma unroll
+        for (int c = 0; c < CMAX; ++c) {
+            const int i = i0 + c;
+            if (c < chunk && i < nb) {
+                pr = cmul(__ldg(&cn[i]), pr);
+                y[c] = cfma(pr, carry, y[c]);
+            }
+        }
+    }
+    Mp.x = 1; Mp.y = 0;
+    C xl; xl.x = 0; xl.y = 0;
+#pragma unroll
+    for (int c = CMAX - 1; c >= 0; --c) {
+        const int i = i0 + c;
+        if (c < chunk && i < nb) {
+            const C m = __ldg(&cn[nb + i]);
+            const C g = __ldg(&cn[2 * nb + i]);
+            xl = cfma(m, xl, cmul(g, y[c]));
+            Mp = cmul(m, Mp);
+            y[c] = xl;
+        }
+    }
+    carry = affine_carry<C, T, true>(Mp, xl, scan);
+    C pr; pr.x = 1; pr.y = 0;
+#pragma unroll
+    for (int c = CMAX - 1; c >= 0; --c) {
+        const int i = i0 + c;
+        if (c < chunk && i < nb) {
+            pr = cmul(__ldg(&cn[nb + i]), pr);
+            const C xv = cfma(pr, carry, y[c]);
+            const int n = (blk0 + i) & (N - 1);
+            const C rc = S[swz<C>(n)];
+            S[swz<C>(n)] = post(n, cmk<C>(2 * xv.x - rc.x, 2 * xv.y - rc.y));
+        }
+    }
 }
 
 __device__ __forceinline__ void sincos_r(float a, float* s, float* c) { sincosf(a, s, c); }
@@ -219,7 +291,6 @@ soft1d_kernel(const Inst1D* __restrict__ insts, void* __restrict__ psi_base, int
     const C* __restrict__ cn = reinterpret_cast<const C*>(I.cn);
     const int tid = threadIdx.x;
     const int nb = I.nb, blk0 = I.blk0;
-    const int chunk = (nb + T - 1) / T;      // host guarantees chunk <= CMAX
 
     // load the state
 #pragma unroll
@@ -230,9 +301,9 @@ soft1d_kernel(const Inst1D* __restrict__ insts, void* __restrict__ psi_base, int
     __syncthreads();
 
     // first half-kinetic factor of this call
-    fwd_fft<R, LOGN, LOGE, LOGRM, 0>(S, W);
-    kmul<R, LOGN, LOGE, LOGRM>(S, TKh);
-    inv_fft<R, LOGN, LOGE, LOGRM, K::NPASS - 1>(S, W);
+    fwd_fft<R, LOGN, LOGE, LOGRM, 0>(S, W, tid);
+    kmul<R, LOGN, LOGE, LOGRM>(S, TKh, tid);
+    inv_fft<R, LOGN, LOGE, LOGRM, K::NPASS - 1>(S, W, tid);
 
     const double* __restrict__ ftab = I.has_field ? ftab_base + (int64_t)I.fcls * ftab_stride : nullptr;
     for (int64_t step = 0; step < nsteps; ++step) {
@@ -278,85 +349,29 @@ soft1d_kernel(const Inst1D* __restrict__ insts, void* __restrict__ psi_base, int
             }
         }
         __syncthreads();
-        // ---- Crank-Nicolson on the strip block
+        // ---- Crank-Nicolson on the strip block, then the second e^{-iU tau/2}
         if (nb > 0) {
-            C y[K::CMAX];
-            const int i0 = tid * chunk;
-            // forward sweep y_i = mf_i y_{i-1} + r_i
-            C Mp; Mp.x = 1; Mp.y = 0;
-            C yl; yl.x = 0; yl.y = 0;
-#pragma unroll
-            for (int c = 0; c < K::CMAX; ++c) {
-                const int i = i0 + c;
-                if (c < chunk && i < nb) {
-                    const C rc = S[swz<C>((blk0 + i) & (N - 1))];
-                    const C m = __ldg(&cn[i]);
-                    yl = cfma(m, yl, rc);
-                    Mp = cmul(m, Mp);
-                    y[c] = yl;
-                }
-            }
-            C carry = affine_carry<C, T, false>(Mp, yl, scan);
-            {
-                C pr; pr.x = 1; pr.y = 0;
-#pragma unroll
-                for (int c = 0; c < K::CMAX; ++c) {
-                    const int i = i0 + c;
-                    if (c < chunk && i < nb) {
-                        pr = cmul(__ldg(&cn[i]), pr);
-                        y[c] = cfma(pr, carry, y[c]);
+            strip_cn<C, T, K::CMAX, N>(S, cn, nb, blk0, tid, scan, [&](int n, C v) {
+                v = tmul(v, __ldg(&TV[n]));
+                if (I.has_field) {
+                    C f;
+                    if (n >= I.iR) f = fc[0];
+                    else if (n < I.iL) f = fc[1];
+                    else {
+                        R sv, cv;
+                        sincos_r(-al * ((R)I.x0 + (R)n * (R)I.h), &sv, &cv);
+                        f = cmk<C>(cv, sv);
                     }
+                    v = cmul(v, f);
                 }
-            }
-            // backward sweep x_i = mb_i x_{i+1} + g_i y_i (reuse y for x)
-            Mp.x = 1; Mp.y = 0;
-            C xl; xl.x = 0; xl.y = 0;
-#pragma unroll
-            for (int c = K::CMAX - 1; c >= 0; --c) {
-                const int i = i0 + c;
-                if (c < chunk && i < nb) {
-                    const C m = __ldg(&cn[nb + i]);
-                    const C g = __ldg(&cn[2 * nb + i]);
-                    xl = cfma(m, xl, cmul(g, y[c]));
-                    Mp = cmul(m, Mp);
-                    y[c] = xl;
-                }
-            }
-            carry = affine_carry<C, T, true>(Mp, xl, scan);
-            {
-                C pr; pr.x = 1; pr.y = 0;
-#pragma unroll
-                for (int c = K::CMAX - 1; c >= 0; --c) {
-                    const int i = i0 + c;
-                    if (c < chunk && i < nb) {
-                        pr = cmul(__ldg(&cn[nb + i]), pr);
-                        C xv = cfma(pr, carry, y[c]);
-                        // psi_new = 2 x - r, then the second e^{-iU tau/2}
-                        const int n = (blk0 + i) & (N - 1);
-                        const C rc = S[swz<C>(n)];
-                        C v = cmk<C>(2 * xv.x - rc.x, 2 * xv.y - rc.y);
-                        v = tmul(v, __ldg(&TV[n]));
-                        if (I.has_field) {
-                            C f;
-                            if (n >= I.iR) f = fc[0];
-                            else if (n < I.iL) f = fc[1];
-                            else {
-                                R sv, cv;
-                                sincos_r(-al * ((R)I.x0 + (R)n * (R)I.h), &sv, &cv);
-                                f = cmk<C>(cv, sv);
-                            }
-                            v = cmul(v, f);
-                        }
-                        S[swz<C>(n)] = v;
-                    }
-                }
-            }
+                return v;
+            });
             __syncthreads();
         }
         // ---- kinetic: forward FFT, e^{-iK tau} (or tau/2 on the last step), inverse FFT
-        fwd_fft<R, LOGN, LOGE, LOGRM, 0>(S, W);
-        kmul<R, LOGN, LOGE, LOGRM>(S, step + 1 < nsteps ? TK : TKh);
-        inv_fft<R, LOGN, LOGE, LOGRM, K::NPASS - 1>(S, W);
+        fwd_fft<R, LOGN, LOGE, LOGRM, 0>(S, W, tid);
+        kmul<R, LOGN, LOGE, LOGRM>(S, step + 1 < nsteps ? TK : TKh, tid);
+        inv_fft<R, LOGN, LOGE, LOGRM, K::NPASS - 1>(S, W, tid);
     }
 
     // store

@@ -1,0 +1,249 @@
+// 2D split-operator step (Sec. II, with K = (kx^2 + ky^2)/2 and
+// C = C_x (x) I + I (x) C_y) as passes over a row-major [ny][nx] state.
+//
+// Between passes the state is kept in (k_x, y) -- rows transformed along x,
+// in the row FFT's output order -- so one step is
+//   row pass   F_x^-1, e^{-iU tau/2}, CN_x, e^{-iU tau/2}, F_x, e^{-i kx^2 tau/2}
+//   column pass F_y, e^{-i ky^2 tau/2}, F_y^-1
+// The kinetic factor e^{-i(kx^2+ky^2) tau/2} splits into an x factor (row
+// pass) and a y factor (column pass) because F_x and F_y act on different
+// indices.  Rows inside the y-strip block also need e^{-iC_y tau}, which
+// couples rows: for them the row pass stops after CN_x (mode A), a column
+// pass over the y block applies CN_y, and a second row pass finishes
+// (mode B).  CN_x and CN_y commute, so this is the paper's e^{-iC tau}.
+#pragma once
+#include "soft1d.cuh"
+#include "soft2d_geo.h"
+
+namespace soft {
+
+enum RowMode { ROW_FWD = 0, ROW_FULL = 1, ROW_A = 2, ROW_B = 3, ROW_INV = 4 };
+
+template <typename R, int LOGN, int LOGE, int LOGRM>
+struct Cfg2DRow : Cfg1D<R, LOGN, LOGE, LOGRM> {
+    static constexpr size_t SMEM2 = sizeof(typename CT<R>::C) * ((1 << LOGN) + 64) + 64;
+};
+
+// One CTA per row.  rows are (row0 + blockIdx.x) mod ny.
+template <typename R, int LOGN, int LOGE, int LOGRM, int MODE>
+__global__ void __launch_bounds__(Cfg1D<R, LOGN, LOGE, LOGRM>::T, Cfg1D<R, LOGN, LOGE, LOGRM>::MINB)
+row_pass_kernel(Geo2D g, void* __restrict__ psi_v, int row0, const void* __restrict__ tkx_v)
+{
+    using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
+    using C = typename K::C;
+    using TT = typename K::TT;
+    constexpr int N = K::N, T = K::T, E = K::E;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* S = reinterpret_cast<C*>(smem_raw);
+    C* scan = S + N;
+    const int tid = threadIdx.x;
+    const int y = (row0 + (int)blockIdx.x) % g.ny;
+    C* __restrict__ row = reinterpret_cast<C*>(psi_v) + (int64_t)y * N;
+    const C* __restrict__ W = reinterpret_cast<const C*>(g.Wx);
+    const TT* __restrict__ tv = reinterpret_cast<const TT*>(g.TVh) + (int64_t)y * N;
+    const TT* __restrict__ tkx = reinterpret_cast<const TT*>(tkx_v);
+
+#pragma unroll 4
+    for (int j = 0; j < E; ++j) {
+        const int n = tid + j * T;
+        C v = row[n];
+        if (MODE == ROW_B) v = tmul(v, __ldg(&tv[n]));
+        S[swz<C>(n)] = v;
+    }
+    __syncthreads();
+    if (MODE == ROW_FULL || MODE == ROW_A || MODE == ROW_INV) inv_fft<R, LOGN, LOGE, LOGRM, K::NPASS - 1>(S, W, tid);
+    if (MODE == ROW_FULL || MODE == ROW_A) {
+#pragma unroll 4
+        for (int j = 0; j < E; ++j) {
+            const int n = tid + j * T;
+            const TT t = __ldg(&tv[n]);
+            C v = tmul(S[swz<C>(n)], t);
+            if (MODE == ROW_FULL && ((n - g.blk0x) & (N - 1)) >= g.nbx) v = tmul(v, t);
+            S[swz<C>(n)] = v;
+        }
+        __syncthreads();
+        if (g.nbx > 0) {
+            const C* cn = reinterpret_cast<const C*>(g.cnx);
+            if (MODE == ROW_FULL)
+                strip_cn<C, T, K::CMAX, N>(S, cn, g.nbx, g.blk0x, tid, scan,
+                                           [&](int n, C v) { return tmul(v, __ldg(&tv[n])); });
+            else
+                strip_cn<C, T, K::CMAX, N>(S, cn, g.nbx, g.blk0x, tid, scan, [](int, C v) { return v; });
+            __syncthreads();
+        }
+    }
+    if (MODE == ROW_FULL || MODE == ROW_B || MODE == ROW_FWD) {
+        fwd_fft<R, LOGN, LOGE, LOGRM, 0>(S, W, tid);
+        kmul<R, LOGN, LOGE, LOGRM>(S, tkx, tid);
+    }
+#pragma unroll 4
+    for (int j = 0; j < E; ++j) {
+        const int n = tid + j * T;
+        row[n] = S[swz<C>(n)];
+    }
+}
+
+// Column pass: TW columns per CTA, each transformed by T = ny/E threads:
+// F_y, e^{-i ky^2 tau/2}/ny (table in the column FFT's output order), F_y^-1.
+template <typename R, int LOGN, int LOGE, int LOGRM, int TW>
+__global__ void __launch_bounds__(TW * Cfg1D<R, LOGN, LOGE, LOGRM>::T, 1)
+col_pass_kernel(Geo2D g, void* __restrict__ psi_v, const void* __restrict__ tky_v)
+{
+    using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
+    using C = typename K::C;
+    using TT = typename K::TT;
+    constexpr int N = K::N, T = K::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* S = reinterpret_cast<C*>(smem_raw);
+    C* __restrict__ psi = reinterpret_cast<C*>(psi_v);
+    const int c0 = blockIdx.x * TW;
+    const int nx = g.nx;
+    for (int idx = threadIdx.x; idx < TW * N; idx += TW * T) {
+        const int yy = idx / TW, j = idx % TW;
+        S[j * N + swz<C>(yy)] = psi[(int64_t)yy * nx + c0 + j];
+    }
+    __syncthreads();
+    const int col = threadIdx.x / T, tid = threadIdx.x % T;
+    C* Sc = S + col * N;
+    const C* W = reinterpret_cast<const C*>(g.Wy);
+    fwd_fft<R, LOGN, LOGE, LOGRM, 0>(Sc, W, tid);
+    kmul<R, LOGN, LOGE, LOGRM>(Sc, reinterpret_cast<const TT*>(tky_v), tid);
+    inv_fft<R, LOGN, LOGE, LOGRM, K::NPASS - 1>(Sc, W, tid);
+    for (int idx = threadIdx.x; idx < TW * N; idx += TW * T) {
+        const int yy = idx / TW, j = idx % TW;
+        psi[(int64_t)yy * nx + c0 + j] = S[j * N + swz<C>(yy)];
+    }
+}
+
+// y-strip Crank-Nicolson: 16 columns per CTA, one warp per column, each lane a
+// contiguous chunk of the nby block rows; the tile is staged in shared memory
+// with a padded pitch so that the lanes' strided rows hit distinct banks.
+template <typename C, int CH>
+__global__ void __launch_bounds__(512, 1)
+cny_kernel(Geo2D g, void* __restrict__ psi_v)
+{
+    constexpr int TWC = 16, PITCH = TWC + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* S = reinterpret_cast<C*>(smem_raw);
+    C* __restrict__ psi = reinterpret_cast<C*>(psi_v);
+    const C* __restrict__ cn = reinterpret_cast<const C*>(g.cny);
+    const int c0 = blockIdx.x * TWC;
+    const int nb = g.nby, nx = g.nx, ny = g.ny;
+    for (int idx = threadIdx.x; idx < nb * TWC; idx += blockDim.x) {
+        const int r = idx / TWC, j = idx % TWC;
+        const int yy = (g.blk0y + r) % ny;
+        S[r * PITCH + j] = psi[(int64_t)yy * nx + c0 + j];
+    }
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ch = (nb + 31) / 32;          // host guarantees ch <= CH
+    const int i0 = lane * ch;
+    C yv[CH];
+    C Mp; Mp.x = 1; Mp.y = 0;
+    C yl; yl.x = 0; yl.y = 0;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        const int i = i0 + c;
+        if (c < ch && i < nb) {
+            const C m = __ldg(&cn[i]);
+            yl = cfma(m, yl, S[i * PITCH + w]);
+            Mp = cmul(m, Mp);
+            yv[c] = yl;
+        }
+    }
+    C carry = affine_carry<C, 32, false>(Mp, yl, nullptr);
+    {
+        C pr; pr.x = 1; pr.y = 0;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int i = i0 + c;
+            if (c < ch && i < nb) {
+                pr = cmul(__ldg(&cn[i]), pr);
+                yv[c] = cfma(pr, carry, yv[c]);
+            }
+        }
+    }
+    Mp.x = 1; Mp.y = 0;
+    C xl; xl.x = 0; xl.y = 0;
+#pragma unroll
+    for (int c = CH - 1; c >= 0; --c) {
+        const int i = i0 + c;
+        if (c < ch && i < nb) {
+            const C m = __ldg(&cn[nb + i]);
+            const C gg = __ldg(&cn[2 * nb + i]);
+            xl = cfma(m, xl, cmul(gg, yv[c]));
+            Mp = cmul(m, Mp);
+            yv[c] = xl;
+        }
+    }
+    carry = affine_carry<C, 32, true>(Mp, xl, nullptr);
+    {
+        C pr; pr.x = 1; pr.y = 0;
+#pragma unroll
+        for (int c = CH - 1; c >= 0; --c) {
+            const int i = i0 + c;
+            if (c < ch && i < nb) {
+                pr = cmul(__ldg(&cn[nb + i]), pr);
+                const C xv = cfma(pr, carry, yv[c]);
+                const C rc = S[i * PITCH + w];
+                S[i * PITCH + w] = cmk<C>(2 * xv.x - rc.x, 2 * xv.y - rc.y);
+            }
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nb * TWC; idx += blockDim.x) {
+        const int r = idx / TWC, j = idx % TWC;
+        const int yy = (g.blk0y + r) % ny;
+        psi[(int64_t)yy * nx + c0 + j] = S[r * PITCH + j];
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+template <typename R, int LOGN, int LOGE, int LOGRM>
+int launch_row_t(int mode, const Geo2D& g, void* psi, int row0, int nrows, const void* tkx,
+                 cudaStream_t st) {
+    using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
+    const size_t smem = Cfg2DRow<R, LOGN, LOGE, LOGRM>::SMEM2;
+    void (*k)(Geo2D, void*, int, const void*) = nullptr;
+    switch (mode) {
+    case ROW_FWD: k = row_pass_kernel<R, LOGN, LOGE, LOGRM, ROW_FWD>; break;
+    case ROW_FULL: k = row_pass_kernel<R, LOGN, LOGE, LOGRM, ROW_FULL>; break;
+    case ROW_A: k = row_pass_kernel<R, LOGN, LOGE, LOGRM, ROW_A>; break;
+    case ROW_B: k = row_pass_kernel<R, LOGN, LOGE, LOGRM, ROW_B>; break;
+    case ROW_INV: k = row_pass_kernel<R, LOGN, LOGE, LOGRM, ROW_INV>; break;
+    default: return SOFT_ERR_INVALID_ARG;
+    }
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return SOFT_ERR_CUDA;
+    if (nrows <= 0 || !psi) return SOFT_OK;
+    k<<<nrows, K::T, smem, st>>>(g, psi, row0, tkx);
+    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+}
+
+template <typename R, int LOGN, int LOGE, int LOGRM, int TW>
+int launch_col_t(const Geo2D& g, void* psi, const void* tky, cudaStream_t st) {
+    using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
+    const size_t smem = sizeof(typename K::C) * TW * K::N;
+    auto k = col_pass_kernel<R, LOGN, LOGE, LOGRM, TW>;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return SOFT_ERR_CUDA;
+    if (!psi) return SOFT_OK;             // attribute set only
+    k<<<g.nx / TW, TW * K::T, smem, st>>>(g, psi, tky);
+    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+}
+
+template <typename C, int CH>
+int launch_cny_t(const Geo2D& g, void* psi, cudaStream_t st) {
+    const size_t smem = sizeof(C) * (size_t)g.nby * 17;
+    auto k = cny_kernel<C, CH>;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return SOFT_ERR_CUDA;
+    if (g.nby <= 0 || !psi) return SOFT_OK;
+    k<<<g.nx / 16, 512, smem, st>>>(g, psi);
+    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+}
+
+}  // namespace soft

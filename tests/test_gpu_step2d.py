@@ -1,0 +1,115 @@
+"""GPU parity of the 2D ECS split-operator step (Sec. II with separable K and
+C = C_x (x) I + I (x) C_y) against the oracle's literal 4-FFT 2D step.
+complex128: rel-L2 <= 1e-11.  complex64: the FP32 drift bound of the 1D
+tests, with log2 of the larger axis."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import paper_1505_06707_gb300 as S  # noqa: E402
+import workloads as W  # noqa: E402
+from oracle import propagate as P  # noqa: E402
+
+CT = {S.SOFT_C64: torch.complex64, S.SOFT_C128: torch.complex128}
+
+
+def tol(prec, nsteps, n):
+    if prec == S.SOFT_C128:
+        return 1e-11
+    return max(3e-6, 2.5e-8 * math.log2(n) * nsteps * 1.5)
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def run2d(nx, ny, box, R0, theta, dt, psi0, nsteps, prec, **opt):
+    plan = S.soft_create((nx, ny), box, R0, theta, dt, prec=prec, **opt)
+    try:
+        d = torch.tensor(psi0, dtype=CT[prec], device="cuda")
+        t = S.soft_step(plan, d, nsteps, 0.0)
+        torch.cuda.synchronize()
+        assert abs(t - nsteps * dt) < 1e-9
+        launches = S.soft_last_launches(plan)
+        return d.cpu().numpy().astype(np.complex128), launches
+    finally:
+        S.soft_destroy(plan)
+
+
+def packet2d(nx, ny, box, seed):
+    rng = np.random.default_rng(seed)
+    x = box[0] + (box[1] - box[0]) / nx * (np.arange(nx) + 0.5)
+    y = box[2] + (box[3] - box[2]) / ny * (np.arange(ny) + 0.5)
+    psi = np.zeros((ny, nx), dtype=np.complex128)
+    for _ in range(3):
+        cx, cy = rng.uniform(-0.5, 0.5, 2) * box[1]
+        kx, ky = rng.uniform(-1.5, 1.5, 2)
+        s = rng.uniform(2.0, 4.0)
+        psi += np.exp(-((y[:, None] - cy) ** 2 + (x[None, :] - cx) ** 2) / (2 * s * s)
+                      + 1j * (kx * x[None, :] + ky * y[:, None]))
+    # a small random component reaches every mode, including the strips
+    psi += 1e-3 * (rng.standard_normal((ny, nx)) + 1j * rng.standard_normal((ny, nx)))
+    return psi
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    S.load()
+
+
+@pytest.mark.parametrize("prec", [S.SOFT_C128, S.SOFT_C64])
+@pytest.mark.parametrize("shape", [(256, 256), (512, 256), (256, 512)])
+def test_small_grids_match_oracle(shape, prec):
+    """Square and non-square grids (the same box, so h differs per axis),
+    sharp ECS theta = 0.4 on both axes, soft-Coulomb a^2 = 1; 40 steps
+    (exercises the captured-graph path)."""
+    nx, ny = shape
+    box = (-40.0, 40.0, -40.0, 40.0)
+    R0 = 30.0
+    psi0 = packet2d(nx, ny, box, nx + 7 * ny)
+    ref = P.Problem2D(nx, ny, box, R0, theta=0.4, a2=1.0, dt=0.02).step(psi0, 40)
+    got, launches = run2d(nx, ny, box, R0, 0.4, 0.02, psi0, 40, prec, soft_a2=1.0)
+    assert relerr(got, ref) < tol(prec, 40, max(nx, ny))
+    assert launches >= 5 * 40
+
+
+def test_free_gaussian_closed_form_2d():
+    """theta = 0, U = 0: the 2D step must reproduce the separable closed-form
+    free Gaussian (summed over periodic images)."""
+    n, b = 256, 40.0
+    x = -b + 2 * b / n * (np.arange(n) + 0.5)
+    L = 2 * b
+
+    def free1(t, k0, s2=4.0):
+        out = 0
+        for m in range(-3, 4):
+            xx = x + m * L
+            out = out + ((s2 / math.pi) ** 0.25 * (s2 + 1j * t) ** -0.5
+                         * np.exp(-(xx - k0 * t) ** 2 / (2 * (s2 + 1j * t)) + 1j * k0 * xx
+                                  - 0.5j * k0 * k0 * t))
+        return out
+    psi0 = free1(0.0, 0.7)[None, :] * free1(0.0, -0.4)[:, None]
+    got, _ = run2d(n, n, (-b, b, -b, b), 30.0, 0.0, 0.02, psi0, 50, S.SOFT_C128, charge=0.0)
+    ref = free1(1.0, 0.7)[None, :] * free1(1.0, -0.4)[:, None]
+    assert relerr(got, ref) < 1e-11
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", [S.SOFT_C128, S.SOFT_C64])
+def test_w3_full_size_few_steps(prec):
+    """The 2D workload at full size (2048^2, [-200,200]^2, sharp theta = 0.4,
+    four seeded Gaussians) for 6 steps, the same launch configuration the
+    2D benchmark times, compared point by point with the oracle."""
+    w = W.w3()
+    nst = 6
+    ref = P.Problem2D(w["nx"], w["ny"], w["box"], w["R0"], theta=w["theta"], a2=w["a2"],
+                      dt=w["dt"]).step(w["psi0"], nst)
+    got, _ = run2d(w["nx"], w["ny"], w["box"], w["R0"], w["theta"], w["dt"], w["psi0"], nst,
+                   prec, soft_a2=w["a2"])
+    assert relerr(got, ref) < tol(prec, nst, w["nx"])
