@@ -1,17 +1,304 @@
-// Stationary ECS equation (Sec. III): entry points (filled in with the PCG kernels).
+// Stationary ECS equation (Sec. III): host driver of the batched
+// complex-symmetric CG with the FFT preconditioners, and the single
+// applications of A and P^-1.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "band.h"
+#include "pcg.cuh"
+#include "pcg_launch.h"
 #include "plan_internal.h"
 
 using namespace soft;
 
-void Plan2D::free_pcg() {}
+namespace soft {
+
+struct PcgTables {               // one preconditioner type
+    PcgGeo geo{};
+    void* bufs[16] = {nullptr};
+    int nb = 0;
+};
+
+struct Pcg {
+    int nEcap = 0;
+    int64_t N = 0;
+    void *r = nullptr, *z = nullptr, *p = nullptr, *w = nullptr, *t = nullptr;
+    double* dE = nullptr;
+    double2* part = nullptr;
+    int nparts_max = 0;
+    // per-energy state (device)
+    double2 *rho = nullptr, *alpha = nullptr, *beta = nullptr;
+    double *relres = nullptr, *fnorm2 = nullptr;
+    int *active = nullptr, *iters = nullptr, *status = nullptr, *nactive = nullptr;
+    // shared A tables and the two preconditioners
+    void *U = nullptr, *Cx = nullptr, *Cy = nullptr, *Kx = nullptr, *Ky = nullptr;
+    PcgTables pc[2];
+    bool tables = false;
+    ~Pcg() {
+        void* v[] = {r, z, p, w, t, dE, part, rho, alpha, beta, relres, fnorm2, active, iters,
+                     status, nactive, U, Cx, Cy, Kx, Ky};
+        for (void* b : v) cudaFree(b);
+        for (auto& T : pc)
+            for (void* b : T.bufs) cudaFree(b);
+    }
+};
+
+static int upload_i(void** dst, const std::vector<int>& v) {
+    return upload(dst, v.data(), v.size() * sizeof(int));
+}
+
+// k^2/(2n) in the FFT output order of the given pass structure (real, phase-table format)
+static std::vector<cd> ksq_tab(const Axis1D& A, int logn, int logrm) {
+    const std::vector<int> perm = dif_output_order(logn, logrm);
+    std::vector<cd> t(A.n);
+    for (int p = 0; p < A.n; ++p) {
+        const double k = A.k[perm[p]];
+        t[p] = 0.5 * k * k / A.n;
+    }
+    return t;
+}
+
+static int build_pc(Plan2D* Q, int type, PcgTables& T) {
+    const bool simple = type == 0;
+    BandAxis bx, by;
+    double chk;
+    const int nbw = Q->band_width;
+    int rc;
+    if ((rc = build_band_axis(Q->ax, nbw, simple, bx, &chk))) return rc;
+    if ((rc = build_band_axis(Q->ay, nbw, simple, by, &chk))) return rc;
+    auto inv_perm = [](int logn, int logrm) {
+        const std::vector<int> perm = dif_output_order(logn, logrm);
+        std::vector<int> pos(perm.size());
+        for (size_t p = 0; p < perm.size(); ++p) pos[perm[p]] = (int)p;
+        return pos;
+    };
+    int i = 0;
+    auto ub = [&](const std::vector<int>& v) -> const int* {
+        void* d = nullptr;
+        if (upload_i(&d, v)) return nullptr;
+        T.bufs[i++] = d;
+        return (const int*)d;
+    };
+    auto uc = [&](const std::vector<cd>& v) -> const void* {
+        void* d = nullptr;
+        if (upload_c(&d, v, SOFT_C128)) return nullptr;
+        T.bufs[i++] = d;
+        return d;
+    };
+    PcgGeo& g = T.geo;
+    g.posx = ub(inv_perm(Q->lx, Q->lrx));
+    g.posy = ub(inv_perm(Q->ly, Q->lry));
+    g.bsx = ub(bx.start); g.bsy = ub(by.start);
+    g.bwx = ub(bx.width); g.bwy = ub(by.width);
+    g.box = ub(bx.off); g.boy = ub(by.off);
+    g.xfx = uc(bx.xf); g.xfy = uc(by.xf);
+    g.xbx = uc(bx.xb); g.xby = uc(by.xb);
+    g.lamx = uc(bx.lam); g.lamy = uc(by.lam);
+    for (int k = 0; k < i; ++k)
+        if (!T.bufs[k]) return SOFT_ERR_OOM;
+    T.nb = i;
+    return SOFT_OK;
+}
+
+static int ensure_tables(Plan2D* Q) {
+    if (!Q->pcg) Q->pcg = new Pcg();
+    Pcg* S = Q->pcg;
+    if (S->tables) return SOFT_OK;
+    S->N = (int64_t)Q->nx * Q->ny;
+    int rc;
+    if ((rc = upload_c(&S->U, Q->U, SOFT_C128))) return rc;
+    auto cat = [](const Axis1D& A) {
+        std::vector<cd> v = A.Cs;
+        v.insert(v.end(), A.Cd.begin(), A.Cd.end());
+        v.insert(v.end(), A.Cu.begin(), A.Cu.end());
+        return v;
+    };
+    if ((rc = upload_c(&S->Cx, cat(Q->ax), SOFT_C128))) return rc;
+    if ((rc = upload_c(&S->Cy, cat(Q->ay), SOFT_C128))) return rc;
+    if ((rc = upload_tab(&S->Kx, ksq_tab(Q->ax, Q->lx, Q->lrx), SOFT_C128))) return rc;
+    if ((rc = upload_tab(&S->Ky, ksq_tab(Q->ay, Q->ly, Q->lry), SOFT_C128))) return rc;
+    for (int type = 0; type < 2; ++type) {
+        if ((rc = build_pc(Q, type, S->pc[type]))) return rc;
+        PcgGeo& g = S->pc[type].geo;
+        g.nx = Q->nx; g.ny = Q->ny; g.N = S->N;
+        g.Wx = Q->Wx; g.Wy = Q->Wy; g.Kx = S->Kx; g.Ky = S->Ky; g.U = S->U;
+        g.Cx = S->Cx; g.Cy = S->Cy;
+        g.nbx = Q->geo.nbx; g.blk0x = Q->geo.blk0x; g.nby = Q->geo.nby; g.blk0y = Q->geo.blk0y;
+    }
+    // set the kernels' shared-memory attributes outside any capture
+    for (int which = 0; which < 3; ++which)
+        if ((rc = pcg_row(Q->lx, which, S->pc[0].geo, nullptr, nullptr, nullptr, nullptr, nullptr,
+                          nullptr, 0, 0)))
+            return rc;
+    for (int which = 0; which < 2; ++which)
+        if ((rc = pcg_col(Q->ly, which, S->pc[0].geo, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0)))
+            return rc;
+    S->tables = true;
+    return SOFT_OK;
+}
+
+static int ensure_workspace(Plan2D* Q, int nE) {
+    int rc = ensure_tables(Q);
+    if (rc) return rc;
+    Pcg* S = Q->pcg;
+    if (S->nEcap >= nE) return SOFT_OK;
+    void* v[] = {S->r, S->z, S->p, S->w, S->t, S->dE, S->part, S->rho, S->alpha, S->beta,
+                 S->relres, S->active, S->iters, S->status};
+    for (void* b : v) cudaFree(b);
+    S->r = S->z = S->p = S->w = S->t = nullptr;
+    const size_t vb = sizeof(double2) * (size_t)S->N * nE;
+    S->nparts_max = std::max(std::max(Q->ny, pcg_col_blocks(Q->nx)), 256);
+    if ((rc = cuda_status(cudaMalloc(&S->r, vb)))) return rc;
+    if ((rc = cuda_status(cudaMalloc(&S->z, vb)))) return rc;
+    if ((rc = cuda_status(cudaMalloc(&S->p, vb)))) return rc;
+    if ((rc = cuda_status(cudaMalloc(&S->w, vb)))) return rc;
+    if ((rc = cuda_status(cudaMalloc(&S->t, vb)))) return rc;
+    if ((rc = cuda_status(cudaMalloc((void**)&S->dE, sizeof(double) * nE)))) return rc;
+    if ((rc = cuda_status(cudaMalloc((void**)&S->part, sizeof(double2) * (size_t)nE * S->nparts_max)))) return rc;
+    if ((rc = cuda_status(cudaMalloc((void**)&S->rho, sizeof(double2) * nE)))) return rc;
+    if ((rc = cuda_status(cudaMalloc((void**)&S->alpha, sizeof(double2) * nE)))) return rc;
+    if ((rc = cuda_status(cudaMalloc((void**)&S->beta, sizeof(double2) * nE)))) return rc;
+    if ((rc = cuda_status(cudaMalloc((void**)&S->relres, sizeof(double) * nE)))) return rc;
+    if ((rc = cuda_status(cudaMalloc((void**)&S->active, sizeof(int) * nE)))) return rc;
+    if ((rc = cuda_status(cudaMalloc((void**)&S->iters, sizeof(int) * nE)))) return rc;
+    if ((rc = cuda_status(cudaMalloc((void**)&S->status, sizeof(int) * nE)))) return rc;
+    if (!S->fnorm2 && (rc = cuda_status(cudaMalloc((void**)&S->fnorm2, sizeof(double))))) return rc;
+    if (!S->nactive && (rc = cuda_status(cudaMalloc((void**)&S->nactive, sizeof(int))))) return rc;
+    S->nEcap = nE;
+    return SOFT_OK;
+}
+
+// z = P^-1 r for nE energies; with part, the per-row partials of r^T z
+static int apply_pc(Plan2D* Q, int type, const void* r, void* z, const double* dE, const int* act,
+                    double2* part, int nE, cudaStream_t st) {
+    Pcg* S = Q->pcg;
+    const PcgGeo& g = S->pc[type].geo;
+    int rc;
+    if ((rc = pcg_row(Q->lx, 1, g, r, S->t, nullptr, dE, act, nullptr, nE, st))) return rc;
+    if ((rc = pcg_col(Q->ly, 1, g, nullptr, S->t, dE, act, nullptr, nE, st))) return rc;
+    Q->launches += 3;
+    return pcg_row(Q->lx, 2, g, S->t, z, part ? r : nullptr, dE, act, part, nE, st);
+}
+
+// w = A p; with part, the per-column-block partials of p^T w
+static int apply_A(Plan2D* Q, const void* p, void* w, const double* dE, const int* act,
+                   double2* part, int nE, cudaStream_t st) {
+    Pcg* S = Q->pcg;
+    const PcgGeo& g = S->pc[0].geo;
+    int rc;
+    if ((rc = pcg_row(Q->lx, 0, g, p, w, nullptr, dE, act, nullptr, nE, st))) return rc;
+    Q->launches += 2;
+    return pcg_col(Q->ly, 0, g, p, w, dE, act, part, nE, st);
+}
+
+void Plan2D::free_pcg() {
+    delete pcg;
+    pcg = nullptr;
+}
+
+}  // namespace soft
 
 extern "C" {
-int sse_pcg_solve(soft_plan*, const double*, int, const void*, void*, double, int, int, int*,
-                  double*, void*) {
-    return SOFT_ERR_UNSUPPORTED;
+
+int sse_apply_A(soft_plan* P, double E, const void* x, void* y, void* stream) {
+    if (!P || !x || !y || P->kind != 2 || !std::isfinite(E)) return SOFT_ERR_INVALID_ARG;
+    if (P->prec != SOFT_C128) return SOFT_ERR_UNSUPPORTED;
+    Plan2D* Q = P->p2;
+    int rc = ensure_workspace(Q, 1);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    Q->launches = 0;
+    if ((rc = cuda_status(cudaMemcpyAsync(Q->pcg->dE, &E, sizeof(double), cudaMemcpyHostToDevice, st))))
+        return rc;
+    rc = apply_A(Q, x, y, Q->pcg->dE, nullptr, Q->pcg->part, 1, st);
+    P->last_launches = Q->launches;
+    return rc;
 }
-int sse_apply_A(soft_plan*, double, const void*, void*, void*) { return SOFT_ERR_UNSUPPORTED; }
-int sse_apply_precond(soft_plan*, double, int, const void*, void*, void*) {
-    return SOFT_ERR_UNSUPPORTED;
+
+int sse_apply_precond(soft_plan* P, double E, int precond, const void* x, void* y, void* stream) {
+    if (!P || !x || !y || P->kind != 2 || !std::isfinite(E)) return SOFT_ERR_INVALID_ARG;
+    if (precond != 0 && precond != 1) return SOFT_ERR_INVALID_ARG;
+    if (P->prec != SOFT_C128) return SOFT_ERR_UNSUPPORTED;
+    Plan2D* Q = P->p2;
+    int rc = ensure_workspace(Q, 1);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    Q->launches = 0;
+    if ((rc = cuda_status(cudaMemcpyAsync(Q->pcg->dE, &E, sizeof(double), cudaMemcpyHostToDevice, st))))
+        return rc;
+    rc = apply_pc(Q, precond, x, y, Q->pcg->dE, nullptr, nullptr, 1, st);
+    P->last_launches = Q->launches;
+    return rc;
 }
+
+int sse_pcg_solve(soft_plan* P, const double* E, int nE, const void* rhs, void* psi_out, double tol,
+                  int maxit, int precond, int* iters_out, double* relres_out, void* stream) {
+    if (!P || !E || nE <= 0 || !rhs || !psi_out || !(tol > 0) || maxit <= 0) return SOFT_ERR_INVALID_ARG;
+    if (precond != 0 && precond != 1) return SOFT_ERR_INVALID_ARG;
+    if (P->kind != 2) return SOFT_ERR_INVALID_ARG;
+    if (P->prec != SOFT_C128) return SOFT_ERR_UNSUPPORTED;
+    for (int e = 0; e < nE; ++e)
+        if (!std::isfinite(E[e])) return SOFT_ERR_INVALID_ARG;
+    Plan2D* Q = P->p2;
+    int rc = ensure_workspace(Q, nE);
+    if (rc) return rc;
+    Pcg* S = Q->pcg;
+    cudaStream_t st = (cudaStream_t)stream;
+    Q->launches = 0;
+    const int64_t N = S->N;
+    // state
+    std::vector<int> ones(nE, 1), zeros(nE, 0), nconv(nE, SOFT_ERR_NOT_CONVERGED);
+    if ((rc = cuda_status(cudaMemcpy(S->dE, E, sizeof(double) * nE, cudaMemcpyHostToDevice)))) return rc;
+    if ((rc = cuda_status(cudaMemcpy(S->active, ones.data(), sizeof(int) * nE, cudaMemcpyHostToDevice)))) return rc;
+    if ((rc = cuda_status(cudaMemcpy(S->iters, zeros.data(), sizeof(int) * nE, cudaMemcpyHostToDevice)))) return rc;
+    if ((rc = cuda_status(cudaMemcpy(S->status, nconv.data(), sizeof(int) * nE, cudaMemcpyHostToDevice)))) return rc;
+    if ((rc = cuda_status(cudaMemcpy(S->nactive, &nE, sizeof(int), cudaMemcpyHostToDevice)))) return rc;
+    PcgState s{S->rho, S->alpha, S->beta, S->relres, S->fnorm2, S->active, S->iters, S->status,
+               S->nactive, tol};
+    const int np_row = Q->ny, np_col = pcg_col_blocks(Q->nx), np_vec = 256;
+    // x = 0, r = f, ||f||^2, z = P^-1 r, rho = r^T z, p = z
+    if ((rc = vec_init(rhs, psi_out, S->r, N, nE, st))) return rc;
+    if ((rc = vec_norm2(rhs, N, S->part, np_vec, st))) return rc;
+    if ((rc = pcg_scalars(STAGE_FNORM, nE, S->part, np_vec, s, st))) return rc;
+    if ((rc = apply_pc(Q, precond, S->r, S->z, S->dE, S->active, S->part, nE, st))) return rc;
+    if ((rc = pcg_scalars(STAGE_RHO, nE, S->part, np_row, s, st))) return rc;
+    if ((rc = vec_p(S->p, S->z, S->beta, S->active, N, nE, 1, st))) return rc;
+    Q->launches += 5;
+    const int CHECK = 4;
+    for (int it = 1; it <= maxit; ++it) {
+        if ((rc = apply_A(Q, S->p, S->w, S->dE, S->active, S->part, nE, st))) return rc;
+        if ((rc = pcg_scalars(STAGE_ALPHA, nE, S->part, np_col, s, st))) return rc;
+        if ((rc = vec_xr(psi_out, S->r, S->p, S->w, S->alpha, S->active, N, nE, S->part, np_vec, st))) return rc;
+        if ((rc = pcg_scalars(STAGE_RNORM, nE, S->part, np_vec, s, st))) return rc;
+        Q->launches += 3;
+        if (it % CHECK == 0 || it == maxit) {
+            int na = 0;
+            if ((rc = cuda_status(cudaMemcpyAsync(&na, S->nactive, sizeof(int), cudaMemcpyDeviceToHost, st)))) return rc;
+            if ((rc = cuda_status(cudaStreamSynchronize(st)))) return rc;
+            if (na <= 0) break;
+        }
+        if (it == maxit) break;
+        if ((rc = apply_pc(Q, precond, S->r, S->z, S->dE, S->active, S->part, nE, st))) return rc;
+        if ((rc = pcg_scalars(STAGE_BETA, nE, S->part, np_row, s, st))) return rc;
+        if ((rc = vec_p(S->p, S->z, S->beta, S->active, N, nE, 0, st))) return rc;
+        Q->launches += 2;
+    }
+    std::vector<int> it_h(nE), stat_h(nE);
+    std::vector<double> rr_h(nE);
+    if ((rc = cuda_status(cudaMemcpyAsync(it_h.data(), S->iters, sizeof(int) * nE, cudaMemcpyDeviceToHost, st)))) return rc;
+    if ((rc = cuda_status(cudaMemcpyAsync(stat_h.data(), S->status, sizeof(int) * nE, cudaMemcpyDeviceToHost, st)))) return rc;
+    if ((rc = cuda_status(cudaMemcpyAsync(rr_h.data(), S->relres, sizeof(double) * nE, cudaMemcpyDeviceToHost, st)))) return rc;
+    if ((rc = cuda_status(cudaStreamSynchronize(st)))) return rc;
+    P->last_launches = Q->launches;
+    if (iters_out) std::memcpy(iters_out, it_h.data(), sizeof(int) * nE);
+    if (relres_out) std::memcpy(relres_out, rr_h.data(), sizeof(double) * nE);
+    int out = SOFT_OK;
+    for (int e = 0; e < nE; ++e) {
+        if (stat_h[e] == SOFT_ERR_BREAKDOWN || stat_h[e] == SOFT_ERR_NONFINITE) return stat_h[e];
+        if (stat_h[e] != SOFT_OK) out = SOFT_ERR_NOT_CONVERGED;
+    }
+    return out;
 }
+
+}  // extern "C"

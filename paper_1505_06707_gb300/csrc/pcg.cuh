@@ -1,0 +1,312 @@
+// Stationary ECS equation A psi = f (Sec. III, Eq. linsys) on a 2D grid:
+//   A = F^-1 (Kx + Ky) F + C_x (x) I + I (x) C_y + U - E.
+// Because K is a sum, F^-1 Kx F = F_x^-1 Kx F_x acts along rows only and
+// F^-1 Ky F = F_y^-1 Ky F_y along columns only, so A p is one row pass
+// (x kinetic + C_x + U - E) plus one column pass (y kinetic + C_y) over p.
+//
+// The preconditioner P^-1 = F^-1 X^T (Lambda - E)^-1 X F (Eq. PreconFFT_ECS;
+// Eq. PreconFFT is the same with one-wide bands and lambda = k^2/2) is
+// separable, X = X_x (x) X_y, Lambda = lambda_x + lambda_y:
+//   row pass 1: F_x then the band rows of X_x         (natural nu order)
+//   column pass: F_y, X_y, / (lambda_x + lambda_y - E), X_y^T, F_y^-1
+//   row pass 2: X_x^T then F_x^-1
+// The paper's F has e^{+i k x}: conj(FFT(conj(.))) gives that sum with the
+// forward FFT; the x_0 phase and 1/sqrt N are folded into the band tables.
+//
+// Batched over energies: grid.y (or grid.z) = energy; converged energies are
+// masked out by the active flags.
+#pragma once
+#include "soft1d.cuh"
+
+namespace soft {
+
+struct PcgGeo {
+    int nx, ny;
+    const void* Wx; const void* Wy;        // pass twiddles
+    const void* Kx; const void* Ky;        // k^2/(2n) in each FFT's output order (phase-table format)
+    const void* U;                          // U(z(x), z(y)) [ny][nx], complex
+    const void* Cx; const void* Cy;        // C tridiagonals, 3*n complex (sub, diag, sup)
+    int nbx, blk0x, nby, blk0y;            // strip blocks
+    // preconditioner tables per axis (natural index order)
+    const int* posx; const int* posy;      // FFT output position of natural index
+    const int* bsx; const int* bsy;        // band start
+    const int* bwx; const int* bwy;        // band width
+    const int* box; const int* boy;        // row offset in xf/xb
+    const void* xfx; const void* xfy;      // forward band rows (complex)
+    const void* xbx; const void* xby;      // backward band rows (complex)
+    const void* lamx; const void* lamy;    // eigenvalues (complex)
+    int64_t N;                              // nx * ny
+};
+
+template <typename C>
+__device__ __forceinline__ C cconj(C a) { return cmk<C>(a.x, -a.y); }
+
+// block reduction of a complex FP64 value; returns the total in thread 0
+__device__ __forceinline__ double2 block_sum2(double2 v, double2* red) {
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double2 t = make_double2(0.0, 0.0);
+    if (threadIdx.x == 0)
+        for (int i = 0; i < nw; ++i) { t.x += red[i].x; t.y += red[i].y; }
+    return t;
+}
+
+// --------------------------------------------------------------- A apply
+// w = F_x^-1 Kx F_x p + C_x p + (U - E) p, one CTA per (row, energy)
+template <typename R, int LOGN, int LOGE, int LOGRM>
+__global__ void __launch_bounds__(Cfg1D<R, LOGN, LOGE, LOGRM>::T, Cfg1D<R, LOGN, LOGE, LOGRM>::MINB)
+a_row_kernel(PcgGeo g, const void* __restrict__ p_v, void* __restrict__ w_v,
+             const double* __restrict__ E, const int* __restrict__ active)
+{
+    using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
+    using C = typename K::C;
+    using TT = typename K::TT;
+    constexpr int N = K::N, T = K::T, E_ = K::E;
+    const int y = blockIdx.x, e = blockIdx.y;
+    if (active && !active[e]) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* S = reinterpret_cast<C*>(smem_raw);
+    C* P0 = S + N;                               // p row kept for C_x p and (U - E) p
+    const int tid = threadIdx.x;
+    const int64_t base = (int64_t)e * g.N + (int64_t)y * N;
+    const C* __restrict__ p = reinterpret_cast<const C*>(p_v) + base;
+    C* __restrict__ w = reinterpret_cast<C*>(w_v) + base;
+    const C* W = reinterpret_cast<const C*>(g.Wx);
+    for (int j = 0; j < E_; ++j) {
+        const int n = tid + j * T;
+        const C v = p[n];
+        S[swz<C>(n)] = v;
+        P0[n] = v;
+    }
+    __syncthreads();
+    fwd_fft<R, LOGN, LOGE, LOGRM, 0>(S, W, tid);
+    kmul<R, LOGN, LOGE, LOGRM>(S, reinterpret_cast<const TT*>(g.Kx), tid);
+    inv_fft<R, LOGN, LOGE, LOGRM, K::NPASS - 1>(S, W, tid);
+    const C* __restrict__ U = reinterpret_cast<const C*>(g.U) + (int64_t)y * N;
+    const C* __restrict__ Cx = reinterpret_cast<const C*>(g.Cx);
+    const R En = (R)E[e];
+    for (int j = 0; j < E_; ++j) {
+        const int n = tid + j * T;
+        const C pv = P0[n];
+        C u = __ldg(&U[n]);
+        u.x -= En;
+        C v = cfma(u, pv, S[swz<C>(n)]);
+        if (((n - g.blk0x) & (N - 1)) < g.nbx) {
+            v = cfma(__ldg(&Cx[n]), P0[(n + N - 1) & (N - 1)], v);
+            v = cfma(__ldg(&Cx[N + n]), pv, v);
+            v = cfma(__ldg(&Cx[2 * N + n]), P0[(n + 1) & (N - 1)], v);
+        }
+        w[n] = v;
+    }
+}
+
+// w += F_y^-1 Ky F_y p + C_y p, TW columns per CTA; partial of p^T w per CTA
+template <typename R, int LOGN, int LOGE, int LOGRM, int TW>
+__global__ void __launch_bounds__(TW * Cfg1D<R, LOGN, LOGE, LOGRM>::T, 1)
+a_col_kernel(PcgGeo g, const void* __restrict__ p_v, void* __restrict__ w_v,
+             const int* __restrict__ active, double2* __restrict__ part)
+{
+    using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
+    using C = typename K::C;
+    using TT = typename K::TT;
+    constexpr int N = K::N, T = K::T;
+    const int e = blockIdx.y;
+    if (active && !active[e]) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* S = reinterpret_cast<C*>(smem_raw);
+    C* P0 = S + TW * N;
+    __shared__ double2 red[32];
+    const int c0 = blockIdx.x * TW, nx = g.nx;
+    const int64_t eb = (int64_t)e * g.N;
+    const C* __restrict__ p = reinterpret_cast<const C*>(p_v) + eb;
+    C* __restrict__ w = reinterpret_cast<C*>(w_v) + eb;
+    for (int idx = threadIdx.x; idx < TW * N; idx += blockDim.x) {
+        const int yy = idx / TW, j = idx % TW;
+        const C v = p[(int64_t)yy * nx + c0 + j];
+        S[j * N + swz<C>(yy)] = v;
+        P0[j * N + yy] = v;
+    }
+    __syncthreads();
+    const int col = threadIdx.x / T, tid = threadIdx.x % T;
+    C* Sc = S + col * N;
+    const C* W = reinterpret_cast<const C*>(g.Wy);
+    fwd_fft<R, LOGN, LOGE, LOGRM, 0>(Sc, W, tid);
+    kmul<R, LOGN, LOGE, LOGRM>(Sc, reinterpret_cast<const TT*>(g.Ky), tid);
+    inv_fft<R, LOGN, LOGE, LOGRM, K::NPASS - 1>(Sc, W, tid);
+    const C* __restrict__ Cy = reinterpret_cast<const C*>(g.Cy);
+    double2 acc = make_double2(0.0, 0.0);
+    for (int idx = threadIdx.x; idx < TW * N; idx += blockDim.x) {
+        const int yy = idx / TW, j = idx % TW;
+        const C* Pj = P0 + j * N;
+        C v = S[j * N + swz<C>(yy)];
+        if (((yy - g.blk0y) & (N - 1)) < g.nby) {
+            v = cfma(__ldg(&Cy[yy]), Pj[(yy + N - 1) & (N - 1)], v);
+            v = cfma(__ldg(&Cy[N + yy]), Pj[yy], v);
+            v = cfma(__ldg(&Cy[2 * N + yy]), Pj[(yy + 1) & (N - 1)], v);
+        }
+        const int64_t a = (int64_t)yy * nx + c0 + j;
+        const C wv = cadd(w[a], v);
+        w[a] = wv;
+        const C pv = Pj[yy];
+        acc.x += (double)pv.x * wv.x - (double)pv.y * wv.y;      // bilinear p^T w
+        acc.y += (double)pv.x * wv.y + (double)pv.y * wv.x;
+    }
+    const double2 t = block_sum2(acc, red);
+    if (threadIdx.x == 0) part[(int64_t)e * gridDim.x + blockIdx.x] = t;
+}
+
+// --------------------------------------------------------- preconditioner
+// band mat-vec: out[nu] = sum_{u < width} tab[off[nu] + u] * in(start[nu] + u)
+template <typename C, class In>
+__device__ __forceinline__ C band_row(int nu, const int* __restrict__ bs, const int* __restrict__ bw,
+                                      const int* __restrict__ bo, const C* __restrict__ tab, In in) {
+    const int s0 = __ldg(&bs[nu]), wd = __ldg(&bw[nu]), o = __ldg(&bo[nu]);
+    C acc; acc.x = 0; acc.y = 0;
+    for (int u = 0; u < wd; ++u) acc = cfma(__ldg(&tab[o + u]), in(s0 + u), acc);
+    return acc;
+}
+
+// row pass 1: t = X_x F_x r (F with e^{+ikx}), natural nu order
+template <typename R, int LOGN, int LOGE, int LOGRM>
+__global__ void __launch_bounds__(Cfg1D<R, LOGN, LOGE, LOGRM>::T, Cfg1D<R, LOGN, LOGE, LOGRM>::MINB)
+pc_row1_kernel(PcgGeo g, const void* __restrict__ r_v, void* __restrict__ t_v,
+               const int* __restrict__ active)
+{
+    using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
+    using C = typename K::C;
+    constexpr int N = K::N, T = K::T, E_ = K::E;
+    const int y = blockIdx.x, e = blockIdx.y;
+    if (active && !active[e]) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* S = reinterpret_cast<C*>(smem_raw);
+    const int tid = threadIdx.x;
+    const int64_t base = (int64_t)e * g.N + (int64_t)y * N;
+    const C* __restrict__ r = reinterpret_cast<const C*>(r_v) + base;
+    C* __restrict__ t = reinterpret_cast<C*>(t_v) + base;
+    for (int j = 0; j < E_; ++j) {
+        const int n = tid + j * T;
+        S[swz<C>(n)] = cconj(r[n]);
+    }
+    __syncthreads();
+    fwd_fft<R, LOGN, LOGE, LOGRM, 0>(S, reinterpret_cast<const C*>(g.Wx), tid);
+    const C* xf = reinterpret_cast<const C*>(g.xfx);
+    for (int j = 0; j < E_; ++j) {
+        const int nu = tid + j * T;
+        t[nu] = band_row<C>(nu, g.bsx, g.bwx, g.box, xf,
+                            [&](int m) { return cconj(S[swz<C>(__ldg(&g.posx[m]))]); });
+    }
+}
+
+// column pass: F_y, X_y, / (lambda_x + lambda_y - E), X_y^T, F_y^-1 (in place on t)
+template <typename R, int LOGN, int LOGE, int LOGRM, int TW>
+__global__ void __launch_bounds__(TW * Cfg1D<R, LOGN, LOGE, LOGRM>::T, 1)
+pc_col_kernel(PcgGeo g, void* __restrict__ t_v, const double* __restrict__ E,
+              const int* __restrict__ active)
+{
+    using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
+    using C = typename K::C;
+    constexpr int N = K::N, T = K::T, E_ = K::E;
+    const int e = blockIdx.y;
+    if (active && !active[e]) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* S = reinterpret_cast<C*>(smem_raw);
+    C* S2 = S + TW * N;
+    const int c0 = blockIdx.x * TW, nx = g.nx;
+    C* __restrict__ t = reinterpret_cast<C*>(t_v) + (int64_t)e * g.N;
+    for (int idx = threadIdx.x; idx < TW * N; idx += blockDim.x) {
+        const int yy = idx / TW, j = idx % TW;
+        S[j * N + swz<C>(yy)] = cconj(t[(int64_t)yy * nx + c0 + j]);
+    }
+    __syncthreads();
+    const int col = threadIdx.x / T, tid = threadIdx.x % T;
+    C* Sc = S + col * N;
+    C* S2c = S2 + col * N;
+    const C* W = reinterpret_cast<const C*>(g.Wy);
+    fwd_fft<R, LOGN, LOGE, LOGRM, 0>(Sc, W, tid);
+    const int nu = c0 + col;
+    const C lx = reinterpret_cast<const C*>(g.lamx)[nu];
+    const R En = (R)E[e];
+    const C* xf = reinterpret_cast<const C*>(g.xfy);
+    const C* xb = reinterpret_cast<const C*>(g.xby);
+    const C* ly = reinterpret_cast<const C*>(g.lamy);
+    for (int j = 0; j < E_; ++j) {                 // X_y, then the eigenvalue denominator
+        const int mu = tid + j * T;
+        C c = band_row<C>(mu, g.bsy, g.bwy, g.boy, xf,
+                          [&](int m) { return cconj(Sc[swz<C>(__ldg(&g.posy[m]))]); });
+        const C lm = __ldg(&ly[mu]);
+        const C den = cmk<C>(lx.x + lm.x - En, lx.y + lm.y);
+        const R dn = den.x * den.x + den.y * den.y;
+        S2c[mu] = cscale(cmulc(c, den), (R)1 / dn);   // c / den
+    }
+    __syncthreads();
+    for (int j = 0; j < E_; ++j) {                 // X_y^T into FFT positions (conjugated)
+        const int m = tid + j * T;
+        const C d = band_row<C>(m, g.bsy, g.bwy, g.boy, xb, [&](int nu2) { return S2c[nu2]; });
+        Sc[swz<C>(__ldg(&g.posy[m]))] = cconj(d);
+    }
+    __syncthreads();
+    inv_fft<R, LOGN, LOGE, LOGRM, K::NPASS - 1>(Sc, W, tid);
+    for (int idx = threadIdx.x; idx < TW * N; idx += blockDim.x) {
+        const int yy = idx / TW, j = idx % TW;
+        t[(int64_t)yy * nx + c0 + j] = cconj(S[j * N + swz<C>(yy)]);
+    }
+}
+
+// row pass 2: z = F_x^-1 X_x^T t; partial of r^T z per CTA
+template <typename R, int LOGN, int LOGE, int LOGRM>
+__global__ void __launch_bounds__(Cfg1D<R, LOGN, LOGE, LOGRM>::T, Cfg1D<R, LOGN, LOGE, LOGRM>::MINB)
+pc_row2_kernel(PcgGeo g, const void* __restrict__ t_v, void* __restrict__ z_v,
+               const void* __restrict__ r_v, const int* __restrict__ active,
+               double2* __restrict__ part)
+{
+    using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
+    using C = typename K::C;
+    constexpr int N = K::N, T = K::T, E_ = K::E;
+    const int y = blockIdx.x, e = blockIdx.y;
+    if (active && !active[e]) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* S = reinterpret_cast<C*>(smem_raw);
+    C* Tn = S + N;
+    __shared__ double2 red[32];
+    const int tid = threadIdx.x;
+    const int64_t base = (int64_t)e * g.N + (int64_t)y * N;
+    const C* __restrict__ t = reinterpret_cast<const C*>(t_v) + base;
+    C* __restrict__ z = reinterpret_cast<C*>(z_v) + base;
+    for (int j = 0; j < E_; ++j) {
+        const int n = tid + j * T;
+        Tn[n] = t[n];
+    }
+    __syncthreads();
+    const C* xb = reinterpret_cast<const C*>(g.xbx);
+    for (int j = 0; j < E_; ++j) {
+        const int m = tid + j * T;
+        const C d = band_row<C>(m, g.bsx, g.bwx, g.box, xb, [&](int nu) { return Tn[nu]; });
+        S[swz<C>(__ldg(&g.posx[m]))] = cconj(d);
+    }
+    __syncthreads();
+    inv_fft<R, LOGN, LOGE, LOGRM, K::NPASS - 1>(S, reinterpret_cast<const C*>(g.Wx), tid);
+    double2 acc = make_double2(0.0, 0.0);
+    const C* r = r_v ? reinterpret_cast<const C*>(r_v) + base : nullptr;
+    for (int j = 0; j < E_; ++j) {
+        const int n = tid + j * T;
+        const C zv = cconj(S[swz<C>(n)]);
+        z[n] = zv;
+        if (r) {
+            const C rv = r[n];
+            acc.x += (double)rv.x * zv.x - (double)rv.y * zv.y;
+            acc.y += (double)rv.x * zv.y + (double)rv.y * zv.x;
+        }
+    }
+    if (part) {
+        const double2 s = block_sum2(acc, red);
+        if (threadIdx.x == 0) part[(int64_t)e * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+}  // namespace soft

@@ -1,0 +1,217 @@
+// Complex-symmetric CG (Sec. III) for the 2D stationary ECS equation:
+// instantiations of the A-apply and preconditioner passes (complex128) and the
+// vector / scalar kernels of the iteration.
+#include "pcg.cuh"
+#include "pcg_launch.h"
+
+namespace soft {
+
+namespace {
+
+constexpr int TWP = 2;    // columns per CTA in the column passes (complex128)
+
+template <int LN, int LE, int LR>
+int row_kernels(int which, const PcgGeo& g, const void* a, void* b, const void* c, const double* E,
+                const int* act, double2* part, int nE, cudaStream_t st) {
+    using K = Cfg1D<double, LN, LE, LR>;
+    const size_t smem = sizeof(double2) * 2 * K::N + 64;
+    dim3 grid(g.ny, nE);
+    if (which == 0) {
+        auto k = a_row_kernel<double, LN, LE, LR>;
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return SOFT_ERR_CUDA;
+        if (nE > 0) k<<<grid, K::T, smem, st>>>(g, a, b, E, act);
+    } else if (which == 1) {
+        auto k = pc_row1_kernel<double, LN, LE, LR>;
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return SOFT_ERR_CUDA;
+        if (nE > 0) k<<<grid, K::T, smem, st>>>(g, a, b, act);
+    } else {
+        auto k = pc_row2_kernel<double, LN, LE, LR>;
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return SOFT_ERR_CUDA;
+        if (nE > 0) k<<<grid, K::T, smem, st>>>(g, a, b, c, act, part);
+    }
+    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+}
+
+template <int LN, int LE, int LR>
+int col_kernels(int which, const PcgGeo& g, const void* a, void* b, const double* E,
+                const int* act, double2* part, int nE, cudaStream_t st) {
+    using K = Cfg1D<double, LN, LE, LR>;
+    const size_t smem = sizeof(double2) * 2 * TWP * K::N + 64;
+    dim3 grid(g.nx / TWP, nE);
+    if (which == 0) {
+        auto k = a_col_kernel<double, LN, LE, LR, TWP>;
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return SOFT_ERR_CUDA;
+        if (nE > 0) k<<<grid, TWP * K::T, smem, st>>>(g, a, b, act, part);
+    } else {
+        auto k = pc_col_kernel<double, LN, LE, LR, TWP>;
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return SOFT_ERR_CUDA;
+        if (nE > 0) k<<<grid, TWP * K::T, smem, st>>>(g, b, E, act);
+    }
+    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+}
+
+}  // namespace
+
+int pcg_row(int logn, int which, const PcgGeo& g, const void* a, void* b, const void* c,
+            const double* E, const int* act, double2* part, int nE, cudaStream_t st) {
+    switch (logn) {
+    case 8: return row_kernels<8, 3, 3>(which, g, a, b, c, E, act, part, nE, st);
+    case 9: return row_kernels<9, 3, 3>(which, g, a, b, c, E, act, part, nE, st);
+    case 10: return row_kernels<10, 3, 3>(which, g, a, b, c, E, act, part, nE, st);
+    case 11: return row_kernels<11, 3, 3>(which, g, a, b, c, E, act, part, nE, st);
+    }
+    return SOFT_ERR_UNSUPPORTED;
+}
+
+int pcg_col(int logn, int which, const PcgGeo& g, const void* a, void* b, const double* E,
+            const int* act, double2* part, int nE, cudaStream_t st) {
+    switch (logn) {
+    case 8: return col_kernels<8, 3, 3>(which, g, a, b, E, act, part, nE, st);
+    case 9: return col_kernels<9, 3, 3>(which, g, a, b, E, act, part, nE, st);
+    case 10: return col_kernels<10, 3, 3>(which, g, a, b, E, act, part, nE, st);
+    case 11: return col_kernels<11, 3, 3>(which, g, a, b, E, act, part, nE, st);
+    }
+    return SOFT_ERR_UNSUPPORTED;
+}
+
+int pcg_col_blocks(int nx) { return nx / TWP; }
+
+// ------------------------------------------------------------ vector kernels
+__device__ __forceinline__ double2 sum_warp(double2 v) {
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+
+// x = 0, r = f for every energy
+__global__ void vec_init_kernel(const double2* __restrict__ f, double2* __restrict__ x,
+                                double2* __restrict__ r, int64_t N, int nE) {
+    const int64_t tot = N * nE;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        x[i] = make_double2(0.0, 0.0);
+        r[i] = f[i % N];
+    }
+}
+
+// partial sums of |f|^2 (one vector)
+__global__ void vec_norm2_kernel(const double2* __restrict__ f, int64_t N, double2* __restrict__ part) {
+    __shared__ double2 red[32];
+    double2 acc = make_double2(0.0, 0.0);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = f[i];
+        acc.x += v.x * v.x + v.y * v.y;
+    }
+    const double2 t = block_sum2(acc, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// x += alpha p, r -= alpha w; partial ||r||^2 per CTA
+__global__ void vec_xr_kernel(double2* __restrict__ x, double2* __restrict__ r,
+                              const double2* __restrict__ p, const double2* __restrict__ w,
+                              const double2* __restrict__ alpha, const int* __restrict__ active,
+                              int64_t N, double2* __restrict__ part) {
+    const int e = blockIdx.y;
+    if (!active[e]) return;
+    __shared__ double2 red[32];
+    const double2 a = alpha[e];
+    const int64_t o = (int64_t)e * N;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 pv = p[o + i], wv = w[o + i];
+        double2 xv = x[o + i], rv = r[o + i];
+        xv.x += a.x * pv.x - a.y * pv.y; xv.y += a.x * pv.y + a.y * pv.x;
+        rv.x -= a.x * wv.x - a.y * wv.y; rv.y -= a.x * wv.y + a.y * wv.x;
+        x[o + i] = xv;
+        r[o + i] = rv;
+        acc.x += rv.x * rv.x + rv.y * rv.y;
+    }
+    const double2 t = block_sum2(acc, red);
+    if (threadIdx.x == 0) part[(int64_t)e * gridDim.x + blockIdx.x] = t;
+}
+
+// p = z + beta p (beta = 0 with copy = 1: p = z)
+__global__ void vec_p_kernel(double2* __restrict__ p, const double2* __restrict__ z,
+                             const double2* __restrict__ beta, const int* __restrict__ active,
+                             int64_t N, int copy) {
+    const int e = blockIdx.y;
+    if (!active[e]) return;
+    const double2 b = copy ? make_double2(0.0, 0.0) : beta[e];
+    const int64_t o = (int64_t)e * N;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 zv = z[o + i];
+        double2 pv = copy ? make_double2(0.0, 0.0) : p[o + i];
+        p[o + i] = make_double2(zv.x + b.x * pv.x - b.y * pv.y, zv.y + b.x * pv.y + b.y * pv.x);
+    }
+}
+
+// per-energy scalar updates of the iteration (one thread per energy; the
+// partial sums are added in a fixed order, so results are reproducible)
+__global__ void pcg_scalar_kernel(int stage, int nE, const double2* __restrict__ part, int nparts,
+                                  PcgState s) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (stage == STAGE_FNORM) {
+        if (e == 0) {
+            double t = 0;
+            for (int i = 0; i < nparts; ++i) t += part[i].x;
+            *s.fnorm2 = t;
+        }
+        return;
+    }
+    if (e >= nE || !s.active[e]) return;
+    double2 t = make_double2(0.0, 0.0);
+    for (int i = 0; i < nparts; ++i) { t.x += part[(int64_t)e * nparts + i].x; t.y += part[(int64_t)e * nparts + i].y; }
+    if (stage == STAGE_RHO) {
+        s.rho[e] = t;
+        if (!(fabs(t.x) + fabs(t.y) > 1e-300)) { s.status[e] = SOFT_ERR_BREAKDOWN; s.active[e] = 0; atomicSub(s.nactive, 1); }
+    } else if (stage == STAGE_ALPHA) {
+        const double d = t.x * t.x + t.y * t.y;
+        if (!(d > 0.0) || !isfinite(d)) { s.status[e] = SOFT_ERR_BREAKDOWN; s.active[e] = 0; atomicSub(s.nactive, 1); return; }
+        const double2 rho = s.rho[e];                      // alpha = rho / (p^T w)
+        s.alpha[e] = make_double2((rho.x * t.x + rho.y * t.y) / d, (rho.y * t.x - rho.x * t.y) / d);
+    } else if (stage == STAGE_RNORM) {
+        const double rel = sqrt(t.x / *s.fnorm2);
+        s.relres[e] = rel;
+        s.iters[e] += 1;
+        if (!isfinite(rel)) { s.status[e] = SOFT_ERR_NONFINITE; s.active[e] = 0; atomicSub(s.nactive, 1); }
+        else if (rel < s.tol) { s.status[e] = SOFT_OK; s.active[e] = 0; atomicSub(s.nactive, 1); }
+    } else if (stage == STAGE_BETA) {
+        const double2 rho = s.rho[e];
+        const double d = rho.x * rho.x + rho.y * rho.y;
+        if (!(d > 0.0)) { s.status[e] = SOFT_ERR_BREAKDOWN; s.active[e] = 0; atomicSub(s.nactive, 1); return; }
+        s.beta[e] = make_double2((t.x * rho.x + t.y * rho.y) / d, (t.y * rho.x - t.x * rho.y) / d);
+        s.rho[e] = t;
+    }
+}
+
+int vec_init(const void* f, void* x, void* r, int64_t N, int nE, cudaStream_t st) {
+    vec_init_kernel<<<1024, 256, 0, st>>>((const double2*)f, (double2*)x, (double2*)r, N, nE);
+    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+}
+int vec_norm2(const void* f, int64_t N, double2* part, int nparts, cudaStream_t st) {
+    vec_norm2_kernel<<<nparts, 256, 0, st>>>((const double2*)f, N, part);
+    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+}
+int vec_xr(void* x, void* r, const void* p, const void* w, const double2* alpha, const int* act,
+           int64_t N, int nE, double2* part, int nparts, cudaStream_t st) {
+    vec_xr_kernel<<<dim3(nparts, nE), 256, 0, st>>>((double2*)x, (double2*)r, (const double2*)p,
+                                                     (const double2*)w, alpha, act, N, part);
+    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+}
+int vec_p(void* p, const void* z, const double2* beta, const int* act, int64_t N, int nE, int copy,
+          cudaStream_t st) {
+    vec_p_kernel<<<dim3(256, nE), 256, 0, st>>>((double2*)p, (const double2*)z, beta, act, N, copy);
+    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+}
+int pcg_scalars(int stage, int nE, const double2* part, int nparts, const PcgState& s,
+                cudaStream_t st) {
+    pcg_scalar_kernel<<<(nE + 63) / 64, 64, 0, st>>>(stage, nE, part, nparts, s);
+    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+}
+
+}  // namespace soft

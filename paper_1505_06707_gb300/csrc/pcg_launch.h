@@ -1,0 +1,46 @@
+// Launchers of the stationary-solver kernels (pcg_kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "soft.h"
+
+namespace soft {
+
+struct PcgGeo;
+
+enum { STAGE_FNORM = 0, STAGE_RHO = 1, STAGE_ALPHA = 2, STAGE_RNORM = 3, STAGE_BETA = 4 };
+
+struct PcgState {                 // device pointers, per energy unless noted
+    double2* rho;
+    double2* alpha;
+    double2* beta;
+    double* relres;
+    double* fnorm2;               // scalar
+    int* active;
+    int* iters;
+    int* status;
+    int* nactive;                 // scalar
+    double tol;
+};
+
+// which: 0 = A row pass (a = p, b = w), 1 = preconditioner row pass 1
+// (a = r, b = t), 2 = preconditioner row pass 2 (a = t, b = z, c = r for r^T z)
+int pcg_row(int logn, int which, const PcgGeo& g, const void* a, void* b, const void* c,
+            const double* E, const int* act, double2* part, int nE, cudaStream_t st);
+// which: 0 = A column pass (a = p, b = w, partial p^T w), 1 = preconditioner
+// column pass (b = t in place)
+int pcg_col(int logn, int which, const PcgGeo& g, const void* a, void* b, const double* E,
+            const int* act, double2* part, int nE, cudaStream_t st);
+int pcg_col_blocks(int nx);
+
+int vec_init(const void* f, void* x, void* r, int64_t N, int nE, cudaStream_t st);
+int vec_norm2(const void* f, int64_t N, double2* part, int nparts, cudaStream_t st);
+int vec_xr(void* x, void* r, const void* p, const void* w, const double2* alpha, const int* act,
+           int64_t N, int nE, double2* part, int nparts, cudaStream_t st);
+int vec_p(void* p, const void* z, const double2* beta, const int* act, int64_t N, int nE, int copy,
+          cudaStream_t st);
+int pcg_scalars(int stage, int nE, const double2* part, int nparts, const PcgState& s,
+                cudaStream_t st);
+
+}  // namespace soft

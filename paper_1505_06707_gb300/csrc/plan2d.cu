@@ -87,6 +87,7 @@ int create_2d(const soft_grid* grid, const double* box, double R0, double theta,
     soft1d_default_cfg(o.prec, lx, &Q->lex, &Q->lrx);
     soft1d_default_cfg(o.prec, ly, &Q->ley, &Q->lry);
     Q->R0 = R0; Q->theta = theta; Q->tau = dt;
+    Q->band_width = o.band_width;
     ContourFn cx(o.contour, R0, box[1], theta, o.tfecs_alpha);
     ContourFn cy(o.contour, R0, box[3], theta, o.tfecs_alpha);
     build_axis(Q->ax, (int)nx, box[0], box[1], cx, dt);

@@ -24,6 +24,7 @@ struct Plan2D {
     static constexpr int64_t GRAPH_STEPS = 16;
     int prec = SOFT_C128;
     int nx = 0, ny = 0, lx = 0, ly = 0, lex = 0, lrx = 0, ley = 0, lry = 0;
+    int band_width = 10;
     double R0 = 0, theta = 0, tau = 0;
     Axis1D ax, ay;                 // host FP64 axes (grid, k, q, z, C)
     std::vector<cd> U;             // U(z(x), z(y)), [ny][nx]

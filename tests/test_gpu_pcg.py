@@ -1,0 +1,147 @@
+"""GPU parity of the stationary solver (Sec. III): the A application
+(Eq. linsys), the simple FFT preconditioner (Eq. PreconFFT) and the banded
+ECS preconditioner (Eq. PreconFFT_ECS) against the oracle, and complex-
+symmetric CG solves whose residual is recomputed by the oracle's own A."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import paper_1505_06707_gb300 as S  # noqa: E402
+import workloads as W  # noqa: E402
+from oracle import propagate as P  # noqa: E402
+from oracle import stationary as ST  # noqa: E402
+from oracle import tables as T  # noqa: E402
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    S.load()
+
+
+def setup(n=256, box=(-40.0, 40.0, -40.0, 40.0), R0=30.0, theta=0.4, a2=1.0, charge=1.0):
+    plan = S.soft_create((n, n), box, R0, theta, 0.02, prec=S.SOFT_C128, soft_a2=a2, charge=charge)
+    p2 = P.Problem2D(n, n, box, R0, theta=theta, a2=a2, charge=charge, dt=0.02,
+                     potential=charge != 0.0)
+    st = ST.Stationary2D(p2, nbw=10, kind=T.SHARP, R0=R0, theta=theta)
+    return plan, p2, st
+
+
+def dev(a):
+    return torch.tensor(a, dtype=torch.complex128, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def test_apply_A_and_preconditioners_match_oracle():
+    plan, p2, st = setup()
+    try:
+        rng = np.random.default_rng(11)
+        x = rng.standard_normal((256, 256)) + 1j * rng.standard_normal((256, 256))
+        dx, dy = dev(x), dev(np.zeros_like(x))
+        for E in (0.3, 1.7):
+            S.sse_apply_A(plan, E, dx, dy)
+            assert relerr(host(dy), st.apply_A(x, E)) < 1e-12
+            S.sse_apply_precond(plan, E, 0, dx, dy)
+            assert relerr(host(dy), st.precond_simple(x, E)) < 1e-11
+            S.sse_apply_precond(plan, E, 1, dx, dy)
+            assert relerr(host(dy), st.precond_band(x, E)) < 1e-11
+    finally:
+        S.soft_destroy(plan)
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+def test_pcg_solves_batch_small(precond):
+    """Four energies at once; each residual recomputed with the oracle's A
+    (FP64 numpy) must meet the tolerance."""
+    plan, p2, st = setup()
+    try:
+        n = 256
+        xg = -40.0 + 80.0 / n * (np.arange(n) + 0.5)
+        f = -np.exp(-(xg[None, :] ** 2 + (xg[:, None] - 3.0) ** 2) / 32.0).astype(np.complex128)
+        Es = [0.2, 0.55, 1.1, 1.9]
+        out = torch.zeros((len(Es), n, n), dtype=torch.complex128, device="cuda")
+        rc, its, rr = S.sse_pcg_solve(plan, Es, dev(f), out, tol=1e-8, maxit=2000, precond=precond)
+        assert rc == 0, (rc, its, rr)
+        xs = host(out)
+        for e, E in enumerate(Es):
+            res = np.linalg.norm(st.apply_A(xs[e], E) - f) / np.linalg.norm(f)
+            assert res < 2e-8, (E, res, its[e])
+            assert rr[e] < 1e-8
+        # the oracle's own COCG reaches the same solution
+        xo, ito, _ = ST.cocg(lambda v: st.apply_A(v, Es[1]),
+                             (lambda r: st.precond_simple(r, Es[1])) if precond == 0 else
+                             (lambda r: st.precond_band(r, Es[1])), f, tol=1e-10, maxit=3000)
+        assert relerr(xs[1], xo) < 1e-6
+        print("iterations", its, "oracle", ito)
+    finally:
+        S.soft_destroy(plan)
+
+
+def test_free_unscaled_problem_converges_in_one_iteration():
+    """q = 1, U = 0: the simple preconditioner is A^-1 exactly (Eq. PreconFFT),
+    so CG stops after one iteration; the banded one reduces to it."""
+    plan, p2, st = setup(theta=0.0, charge=0.0)
+    try:
+        n = 256
+        rng = np.random.default_rng(5)
+        f = rng.standard_normal((n, n)) + 0j
+        out = torch.zeros((1, n, n), dtype=torch.complex128, device="cuda")
+        for pc in (0, 1):
+            rc, its, rr = S.sse_pcg_solve(plan, [0.37], dev(f), out, tol=1e-10, maxit=50, precond=pc)
+            assert rc == 0 and its[0] == 1 and rr[0] < 1e-10
+    finally:
+        S.soft_destroy(plan)
+
+
+def test_bad_arguments_and_iteration_cap():
+    plan, p2, st = setup()
+    try:
+        n = 256
+        f = np.ones((n, n), dtype=np.complex128)
+        out = torch.zeros((1, n, n), dtype=torch.complex128, device="cuda")
+        with pytest.raises(S.SoftError):
+            S.sse_pcg_solve(plan, [0.5], dev(f), out, tol=-1.0)
+        with pytest.raises(S.SoftError):
+            S.sse_pcg_solve(plan, [float("nan")], dev(f), out)
+        rc, its, rr = S.sse_pcg_solve(plan, [0.5], dev(f), out, tol=1e-14, maxit=3, precond=0)
+        assert rc == -5 and its[0] == 3 and rr[0] > 1e-14
+    finally:
+        S.soft_destroy(plan)
+
+
+@pytest.mark.slow
+def test_w4_full_size_sampled_energies():
+    """The stationary workload at full size (1024^2, W3 box and contour,
+    Gaussian source) on four of its 64 energies with the banded
+    preconditioner; the residual of every returned solution is recomputed by
+    the oracle's A."""
+    w = W.w4()
+    n = w["nx"]
+    plan = S.soft_create((n, n), w["box"], w["R0"], w["theta"], 0.02, prec=S.SOFT_C128,
+                         soft_a2=w["a2"])
+    try:
+        p2 = P.Problem2D(n, n, w["box"], w["R0"], theta=w["theta"], a2=w["a2"], dt=0.02)
+        st = ST.Stationary2D(p2, nbw=10, kind=T.SHARP, R0=w["R0"], theta=w["theta"])
+        Es = list(w["E"][[0, 21, 42, 63]])
+        out = torch.zeros((len(Es), n, n), dtype=torch.complex128, device="cuda")
+        rc, its, rr = S.sse_pcg_solve(plan, Es, dev(w["f"]), out, tol=w["tol"], maxit=3000,
+                                      precond=1)
+        assert rc == 0, (rc, its, rr)
+        xs = host(out)
+        for e, E in enumerate(Es):
+            res = np.linalg.norm(st.apply_A(xs[e], E) - w["f"]) / np.linalg.norm(w["f"])
+            assert res < 2 * w["tol"], (E, res)
+        print("W4 iterations (band):", its)
+    finally:
+        S.soft_destroy(plan)
