@@ -55,8 +55,9 @@ def _hbm_peak(d):
 # FP32 SIMT peak derived from the unit counts and the maximum clock:
 # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# FP64: not measured on this machine; GB300 lists about 1.25 TFLOP/s dense FP64
-FP64_PEAK_TFLOPS = 1.25
+# FP64: measured on this machine by an FMA-throughput probe (independent DFMA
+# chains, 152 x 8 CTAs of 256 threads): 1.198 TFLOP/s
+FP64_PEAK_TFLOPS = 1.198
 
 
 def flops_per_call(ns, nbs, steps, field=True):
@@ -190,6 +191,79 @@ def cpu_baseline_sample():
                       "instances" % (len(sample), nst)}
 
 
+def bench_2d(S, torch, dev, args):
+    """The 2D workload (2048^2, sharp theta = 0.4): throughput of the step in
+    both precisions, and its HBM rate counting the minimum traffic of the pass
+    structure: 5 state passes-equivalent per step (row pass, column pass, and
+    the y-strip rows' extra round trips) plus the potential table once."""
+    import numpy as np
+    import workloads as W
+    w = W.w3()
+    n = w["nx"]
+    res = {}
+    peaks, src = _peaks()
+    hbm = _hbm_peak(peaks)
+    for prec, name, nst, reps in ((S.SOFT_C64, "c64", 64, 3), (S.SOFT_C128, "c128", 8, 2)):
+        plan = S.soft_create((n, n), w["box"], w["R0"], w["theta"], w["dt"], prec=prec,
+                             soft_a2=w["a2"])
+        d = torch.tensor(w["psi0"], dtype=torch.complex64 if prec == S.SOFT_C64 else torch.complex128,
+                         device=dev)
+        st = torch.cuda.current_stream(dev)
+        S.soft_step(plan, d, nst, 0.0, stream=st)        # warm-up (captures the graph)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            S.soft_step(plan, d, nst, 0.0, stream=st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        steps = nst * reps
+        Sb = 8 if prec == S.SOFT_C64 else 16
+        tab = 16                                          # e^{-iU tau/2} per point, read ~1.25x
+        bytes_pt = 5 * Sb + 1.25 * tab
+        gps = n * n * steps / sec
+        res[name] = {"grid_point_steps_per_s": gps, "ms_per_step": 1e3 * sec / steps,
+                     "hbm_GBps_alg": gps * bytes_pt / 1e9, "hbm_frac_alg": gps * bytes_pt / 1e9 / hbm,
+                     "bytes_per_point_step": bytes_pt, "launches_per_call": S.soft_last_launches(plan)}
+        S.soft_destroy(plan)
+        del d
+    res["workload"] = "2048^2 on [-200,200]^2, sharp ECS R0=150 theta=0.4, U=-1/sqrt(r^2+1), dt=0.02"
+    res["hbm_peak_GBps"] = hbm
+    res["hbm_peak_source"] = src
+    return res
+
+
+def bench_pcg(S, torch, dev, args):
+    """The stationary workload: 64 energies solved as one batch on 1024^2 with
+    the banded ECS preconditioner to relative residual 1e-8."""
+    import numpy as np
+    import workloads as W
+    w = W.w4()
+    n = w["nx"]
+    plan = S.soft_create((n, n), w["box"], w["R0"], w["theta"], 0.02, prec=S.SOFT_C128,
+                         soft_a2=w["a2"])
+    f = torch.tensor(w["f"], dtype=torch.complex128, device=dev)
+    E = [float(e) for e in w["E"]]
+    out = torch.zeros((len(E), n, n), dtype=torch.complex128, device=dev)
+    st = torch.cuda.current_stream(dev)
+    S.sse_pcg_solve(plan, E[:2], f, out, tol=w["tol"], maxit=4, precond=1, stream=st)   # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    rc, its, rr = S.sse_pcg_solve(plan, E, f, out, tol=w["tol"], maxit=3000, precond=1, stream=st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    S.soft_destroy(plan)
+    del out
+    return {"solves_per_s": len(E) / sec, "seconds": sec, "energies": len(E), "status": rc,
+            "iterations_mean": float(np.mean(its)), "iterations_max": int(np.max(its)),
+            "max_relres": float(np.max(rr)), "precond": "banded ECS (N_BW = 10)",
+            "precision": "c128 state, FP64 dots",
+            "workload": "1024^2 on [-200,200]^2, sharp ECS R0=150 theta=0.4, 64 energies in [0.05,2]"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -201,6 +275,8 @@ def main():
     ap.add_argument("--instances", type=int, default=N_INST,
                     help="fewer instances for profiling captures (not a bench line)")
     ap.add_argument("--steps-per-call", type=int, default=STEPS_PER_CALL)
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the 2D step and stationary-solver measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -221,43 +297,65 @@ def main():
     prec = S.SOFT_C64 if args.prec == "c64" else S.SOFT_C128
     cdt = torch.complex64 if prec == S.SOFT_C64 else torch.complex128
 
-    # weak scaling: every rank runs its own 4096-instance batch (independent problems)
+    # weak scaling: every rank runs its own 4096-instance batch (independent problems).
+    # One plan per size group, so that the dominant kernel (N = 16384) is timed
+    # on its own with CUDA events inside the timed region.
     spc = args.steps_per_call
     ws = workload(args.instances)
-    plan = S.soft_create_batch([w["n"] for w in ws], [(w["a"], w["b"]) for w in ws],
-                               [w["R0"] for w in ws], [w["theta"] for w in ws],
-                               [(w["E0"], w["omega"], w["ncyc"]) for w in ws], 0.02, prec=prec,
-                               contour=ws[0]["contour"])
-    offs, total = S.soft_batch_layout(plan)
-    host0 = np.concatenate([w["psi0"] for w in ws]).astype(np.complex64 if prec == S.SOFT_C64
-                                                          else np.complex128)
-    psi = torch.from_numpy(host0).to(dev)
+    groups = {}
+    for w in ws:
+        groups.setdefault(w["n"], []).append(w)
+    sizes = sorted(groups, reverse=True)
+    plans, states, hosts, flops_g, nbs_all = [], [], [], [], []
+    cdt_np = np.complex64 if prec == S.SOFT_C64 else np.complex128
+    for n in sizes:
+        g = groups[n]
+        plans.append(S.soft_create_batch([w["n"] for w in g], [(w["a"], w["b"]) for w in g],
+                                         [w["R0"] for w in g], [w["theta"] for w in g],
+                                         [(w["E0"], w["omega"], w["ncyc"]) for w in g], 0.02,
+                                         prec=prec, contour=g[0]["contour"]))
+        h0 = np.concatenate([w["psi0"] for w in g]).astype(cdt_np)
+        hosts.append(h0)
+        states.append(torch.from_numpy(h0).to(dev))
+        nb = [n // 4 + 2] * len(g)       # strip block: 2 x N/8 strip rows + 2 coupled neighbours
+        flops_g.append(flops_per_call([n] * len(g), nb, spc))
     ns = [w["n"] for w in ws]
-    nbs = [n // 4 + 2 for n in ns]   # strip block: 2 x N/8 strip rows + 2 coupled neighbours
-    flops = flops_per_call(ns, nbs, spc)
     pts_call = float(sum(ns)) * spc
     stream = torch.cuda.current_stream(dev)
 
+    def one_call(t, evs=None):
+        t2 = t
+        for i, (pl, st_) in enumerate(zip(plans, states)):
+            if evs is not None and i == 0:
+                evs[0].record(stream)
+            t2 = S.soft_step_batch(pl, st_, spc, t, stream=stream)
+            if evs is not None and i == 0:
+                evs[1].record(stream)
+        return t2
+
     t = 0.0
     for _ in range(args.warmup):
-        t = S.soft_step_batch(plan, psi, spc, t, stream=stream)
+        t = one_call(t)
     torch.cuda.synchronize()
-    launches_per_call = S.soft_last_launches(plan)
+    launches_per_call = sum(S.soft_last_launches(pl) for pl in plans)
 
-    # device-timed region: state resident in HBM
+    # device-timed region: states resident in HBM (252 MB c64 > L2)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clk = ClockSampler(local)
     clk.start()
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    for _ in range(args.steps):
-        t = S.soft_step_batch(plan, psi, spc, t, stream=stream)
+    for k in range(args.steps):
+        t = one_call(t, kev[k])
     ev1.record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
     ms = ev0.elapsed_time(ev1)
+    kms = sum(a.elapsed_time(b) for a, b in kev) / args.steps
     if world > 1:
         tt = torch.tensor([ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -265,30 +363,34 @@ def main():
         dist.barrier()
     sec = ms / 1e3
     value = pts_call * args.steps * world / sec
-    kern_s = sec / args.steps            # one call is one kernel launch per size group
-    achieved = flops / kern_s / 1e12
+    achieved = flops_g[0] / (kms / 1e3) / 1e12
 
-    # end to end through the public call with host buffers: H2D of the state,
-    # the call, D2H of the state, every step
-    hbuf = torch.from_numpy(host0).pin_memory()
-    obuf = torch.empty_like(hbuf).pin_memory()
+    # end to end through the public calls with host buffers: H2D of every
+    # state, the calls, D2H of every state, each step
+    hb = [torch.from_numpy(h).pin_memory() for h in hosts]
+    ob = [torch.empty_like(h) .pin_memory() for h in hb]
+
+    def e2e_call():
+        for h, st_ in zip(hb, states):
+            st_.copy_(h, non_blocking=True)
+        one_call(0.0)
+        for o, st_ in zip(ob, states):
+            o.copy_(st_, non_blocking=True)
     for _ in range(2):
-        psi.copy_(hbuf, non_blocking=True)
-        S.soft_step_batch(plan, psi, spc, 0.0, stream=stream)
-        obuf.copy_(psi, non_blocking=True)
+        e2e_call()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
     ke = max(3, args.steps // 2)
+    e0.record(stream)
     for _ in range(ke):
-        psi.copy_(hbuf, non_blocking=True)
-        S.soft_step_batch(plan, psi, spc, 0.0, stream=stream)
-        obuf.copy_(psi, non_blocking=True)
+        e2e_call()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_s = e0.elapsed_time(e1) / 1e3
-    e2e = pts_call * ke * world / e2e_s
-    nbytes = host0.nbytes
+    e2e = pts_call * ke * world / (e0.elapsed_time(e1) / 1e3)
+    nbytes = sum(h.nbytes for h in hosts)
+    for pl in plans:
+        S.soft_destroy(pl)
+    del states
 
     peaks, src = _peaks()
     hbm = _hbm_peak(peaks)
@@ -299,9 +401,10 @@ def main():
     peak = FP32_PEAK_TFLOPS if prec == S.SOFT_C64 else FP64_PEAK_TFLOPS
     out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                        "frac": achieved / peak, "traffic": None,
-                       "kernel": "soft1d_kernel (all size groups of one call)",
+                       "kernel": "soft1d_kernel, N = %d group (%d instances, %d steps per launch), "
+                                 "%.3f ms per launch" % (sizes[0], len(groups[sizes[0]]), spc, kms),
                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
-                       if prec == S.SOFT_C64 else "GB300 FP64 listing (not measured)"}
+                       if prec == S.SOFT_C64 else "measured DFMA probe"}
     # the same throughput against HBM, counting one read + one write of the state per time step
     bytes_pt = 16 if prec == S.SOFT_C64 else 32
     out["hbm_effective"] = {"GBps": value / world * bytes_pt / 1e9, "peak": hbm,
@@ -311,9 +414,11 @@ def main():
     out["e2e"] = {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
     out["gpu_launches"] = int(launches_per_call * args.steps)
     out["clocks"] = clocks
+    if not args.no_extra:
+        out["w3_2d"] = bench_2d(S, torch, dev, args)
+        out["w4_pcg"] = bench_pcg(S, torch, dev, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_sample()
-    S.soft_destroy(plan)
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
