@@ -82,6 +82,8 @@ typedef struct {
     double soft_a2;      /* a^2 of U = -Z/sqrt(|z|^2 + a^2) [2.0]            */
     double charge;       /* Z [1.0]; 0 gives U = 0                           */
     int band_width;      /* N_BW of the banded preconditioner [10]           */
+    int autotune;        /* 1: time the built kernel variants of every 1D size
+                            at plan creation and keep the fastest [0]       */
 } soft_options;
 
 /* Laser pulse (length gauge, x-polarised), E(t) = E0 sin^2(pi t/T) sin(omega t)
@@ -109,7 +111,9 @@ void soft_default_options(soft_options* opt);
  * Tables are computed on the host in FP64 and uploaded once.  Fails with
  * SOFT_ERR_NOT_POW2 for sizes that are not powers of two in [64, 16384],
  * SOFT_ERR_SETUP if the strip Crank-Nicolson factorisation is not accurate
- * to 1e-12 in FP64. */
+ * to 1e-12 in FP64.  With opt->autotune the plan times every built
+ * (elements per thread, radix) variant of each 1D size on the device and keeps
+ * the fastest; this launches kernels and allocates temporary buffers. */
 int soft_create(const soft_grid* grid, const double* box, double R0, double theta,
                 double dt, const soft_options* opt, soft_plan** out);
 
@@ -135,7 +139,11 @@ int soft_batch_layout(const soft_plan* plan, int64_t* offsets, int64_t* total);
 int soft_step(soft_plan* plan, void* psi, int64_t nsteps, const soft_field* field,
               double* t_inout, void* stream);
 
-/* soft_step_batch -- soft_step for a batch plan; psi is the packed state. */
+/* soft_step_batch -- soft_step for a batch plan; psi is the packed state.
+ * Calls are replayed from a CUDA graph (captured on the first call with a
+ * given state pointer, stream and step count): the pulse-shape table and one
+ * kernel per size group, the groups on parallel branches so that their CTAs
+ * share the GPU. */
 int soft_step_batch(soft_plan* plan, void* psi, int64_t nsteps, double* t_inout,
                     void* stream);
 

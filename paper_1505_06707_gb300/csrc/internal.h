@@ -62,6 +62,10 @@ int launch_soft1d(int prec, int logn, int loge, int logrm, const Inst1D* d_inst,
 // f_c(s) = sin^2(pi t/Tp) sin(omega t) at t = t0 + (s + 1/2) tau for each pulse class c
 int launch_field_table(const double* d_cls /*omega, Tp pairs*/, int ncls, double t0, double tau,
                        int64_t nsteps, double* out, int64_t stride, cudaStream_t st);
+int launch_field_table_dev(const double* d_cls, int ncls, const double* d_t0, double tau,
+                           int64_t nsteps, double* out, int64_t stride, cudaStream_t st);
+int soft1d_variants(int prec, int logn, int* loge, int* logrm, int maxv);
+int launch_advance_time(double* d_t, double dt, cudaStream_t st);
 bool soft1d_supported(int prec, int logn, int loge, int logrm);
 void soft1d_default_cfg(int prec, int logn, int* loge, int* logrm);
 size_t soft1d_smem_bytes(int prec, int logn, int loge);

@@ -166,6 +166,64 @@ static int check_axis(int64_t n, double a, double b, double R0) {
     return SOFT_OK;
 }
 
+// Time every built kernel variant of one 1D size on a sample of instances
+// (up to four waves of 152 SMs) and return the fastest configuration.
+static int autotune_size(const soft_options& o, int n, double a, double b, double R0, double theta,
+                         double dt, int count, int* best_e, int* best_r) {
+    int le[16], lr[16];
+    const int logn = ilog2(n);
+    const int nv = soft1d_variants(o.prec, logn, le, lr, 16);
+    if (nv <= 1) return SOFT_OK;
+    const int ns = std::min(count, 4 * 152);
+    const size_t eb = o.prec == SOFT_C64 ? 8 : 16;
+    void* psi = nullptr;
+    int rc = cuda_status(cudaMalloc(&psi, eb * (size_t)ns * n));
+    if (rc) return rc;
+    cudaMemset(psi, 0x3c, eb * (size_t)ns * n);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int v = 0; v < nv && rc == SOFT_OK; ++v) {
+        Tables1D T;
+        if (make_tables_1d(&T, n, a, b, R0, theta, dt, o, le[v], lr[v]) == SOFT_OK) {
+            const int thr = n >> le[v];
+            if ((T.nb + thr - 1) / thr <= (1 << le[v]) / 4 + 2) {
+                std::vector<Inst1D> d(ns);
+                for (int i = 0; i < ns; ++i) {
+                    std::memset(&d[i], 0, sizeof(Inst1D));
+                    d[i].off = (int64_t)i * n;
+                    d[i].TK = T.TK; d[i].TKh = T.TKh; d[i].TV = T.TV; d[i].W = T.W; d[i].cn = T.cn;
+                    d[i].nb = T.nb; d[i].blk0 = T.blk0; d[i].x0 = T.ax.x[0]; d[i].h = T.ax.h;
+                    d[i].R0 = R0; d[i].tau = dt; d[i].iL = T.iL; d[i].iR = T.iR; d[i].n = n;
+                }
+                void* dd = nullptr;
+                if (upload(&dd, d.data(), d.size() * sizeof(Inst1D)) == SOFT_OK) {
+                    launch_soft1d(o.prec, logn, le[v], lr[v], (Inst1D*)dd, ns, psi, 2, nullptr, 0,
+                                  nullptr, 0, nullptr);
+                    cudaEventRecord(e0, 0);
+                    launch_soft1d(o.prec, logn, le[v], lr[v], (Inst1D*)dd, ns, psi, 8, nullptr, 0,
+                                  nullptr, 0, nullptr);
+                    cudaEventRecord(e1, 0);
+                    if (cudaEventSynchronize(e1) == cudaSuccess) {
+                        float ms = 0;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        if (ms < best) { best = ms; *best_e = le[v]; *best_r = lr[v]; }
+                    } else {
+                        rc = SOFT_ERR_CUDA;
+                    }
+                }
+                cudaFree(dd);
+            }
+        }
+        free_tables(&T);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(psi);
+    return rc;
+}
+
 // shared by soft_create (1D) and soft_create_batch
 static int create_1d(int count, const soft_grid* grids, const double* boxes, const double* R0,
                      const double* theta, const soft_field* fields, double dt,
@@ -193,6 +251,13 @@ static int create_1d(int count, const soft_grid* grids, const double* boxes, con
         int tab;
         auto it = seen.find(key);
         if (it == seen.end()) {
+            if (o.autotune) {
+                int cnt = 0;
+                for (int j = i; j < count; ++j)
+                    if (grids[j].n[0] == n) ++cnt;
+                rc = autotune_size(o, (int)n, a, b, R0[i], theta[i], dt, cnt, &loge, &logrm);
+                if (rc) return rc;
+            }
             std::unique_ptr<Tables1D> T(new Tables1D());
             rc = make_tables_1d(T.get(), (int)n, a, b, R0[i], theta[i], dt, o, loge, logrm);
             if (rc) { free_tables(T.get()); return rc; }
@@ -323,6 +388,15 @@ soft_plan::~soft_plan() {
     cudaFree(d_cls);
     cudaFree(d_ftab);
     cudaFree(d_status);
+    cudaFree(d_t0);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (side_ready) {
+        for (size_t g = 0; g < groups.size() && g < MAX_SIDE; ++g) {
+            cudaStreamDestroy(side[g]);
+            cudaEventDestroy(ev_join[g]);
+        }
+        cudaEventDestroy(ev_fork);
+    }
     free_2d();
 }
 
@@ -376,6 +450,7 @@ int soft_plan::build_1d_device() {
     if ((rc = cuda_status(cudaMalloc((void**)&d_ftab, sizeof(double) * ftab_cap * (ncls + 1))))) return rc;
     if ((rc = cuda_status(cudaMalloc((void**)&d_status, sizeof(int))))) return rc;
     if ((rc = cuda_status(cudaMemset(d_status, 0, sizeof(int))))) return rc;
+    if ((rc = cuda_status(cudaMalloc((void**)&d_t0, sizeof(double))))) return rc;
     return SOFT_OK;
 }
 
@@ -410,29 +485,76 @@ int soft_plan::set_single_field(const soft_field* f) {
     return SOFT_OK;
 }
 
+// one chunk of steps on the given stream: pulse table from the device start
+// time, the size groups on parallel branches, then the start time advanced
+int soft_plan::enqueue_chunk(void* psi, int64_t chunk, cudaStream_t st) {
+    const int nc = ncls + (single ? 1 : 0);
+    int rc;
+    if (nc > 0) {
+        if ((rc = launch_field_table_dev(d_cls, nc, d_t0, dt, chunk, d_ftab, ftab_cap, st))) return rc;
+        ++last_launches;
+    }
+    const bool fork = groups.size() > 1;
+    if (fork && (rc = cuda_status(cudaEventRecord(ev_fork, st)))) return rc;
+    for (size_t g = 0; g < groups.size(); ++g) {
+        cudaStream_t gs = fork ? side[g] : st;
+        if (fork && (rc = cuda_status(cudaStreamWaitEvent(gs, ev_fork, 0)))) return rc;
+        const Group1D& G = groups[g];
+        rc = launch_soft1d(prec, G.logn, G.loge, G.logrm, G.d_inst, (int)G.members.size(), psi, chunk,
+                           d_ftab, ftab_cap, d_status, gs, nullptr);
+        if (rc) return rc;
+        ++last_launches;
+        if (fork) {
+            if ((rc = cuda_status(cudaEventRecord(ev_join[g], gs)))) return rc;
+            if ((rc = cuda_status(cudaStreamWaitEvent(st, ev_join[g], 0)))) return rc;
+        }
+    }
+    if ((rc = launch_advance_time(d_t0, (double)chunk * dt, st))) return rc;
+    ++last_launches;
+    return SOFT_OK;
+}
+
 int soft_plan::step_1d(void* psi, int64_t nsteps, double* t_inout, cudaStream_t st) {
     last_launches = 0;
     if (nsteps == 0) return SOFT_OK;
-    double t = *t_inout;
-    const int nc = ncls + (single ? 1 : 0);
+    int rc;
+    if (!side_ready) {
+        for (size_t g = 0; g < groups.size() && g < MAX_SIDE; ++g) {
+            if ((rc = cuda_status(cudaStreamCreateWithFlags(&side[g], cudaStreamNonBlocking)))) return rc;
+            if ((rc = cuda_status(cudaEventCreateWithFlags(&ev_join[g], cudaEventDisableTiming)))) return rc;
+        }
+        if ((rc = cuda_status(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming)))) return rc;
+        side_ready = true;
+    }
+    if (groups.size() > MAX_SIDE) return SOFT_ERR_UNSUPPORTED;
+    // start time: a pageable copy is consumed before the call returns
+    const double t0 = *t_inout;
+    if ((rc = cuda_status(cudaMemcpyAsync(d_t0, &t0, sizeof(double), cudaMemcpyHostToDevice, st)))) return rc;
     int64_t done = 0;
     while (done < nsteps) {
         const int64_t chunk = std::min<int64_t>(ftab_cap, nsteps - done);
-        int rc;
-        if (nc > 0) {
-            rc = launch_field_table(d_cls, nc, t, dt, chunk, d_ftab, ftab_cap, st);
-            if (rc) return rc;
-            ++last_launches;
+        if (!gexec || gpsi != psi || gchunk != chunk || gstream != st) {
+            if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+            cudaStream_t cap;
+            if ((rc = cuda_status(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)))) return rc;
+            cudaGraph_t graph;
+            const int64_t before = last_launches;
+            rc = cuda_status(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+            if (rc == SOFT_OK) rc = enqueue_chunk(psi, chunk, cap);
+            cudaError_t e = cudaStreamEndCapture(cap, &graph);
+            if (rc == SOFT_OK) rc = cuda_status(e);
+            if (rc == SOFT_OK) rc = cuda_status(cudaGraphInstantiate(&gexec, graph, 0));
+            if (e == cudaSuccess) cudaGraphDestroy(graph);
+            cudaStreamDestroy(cap);
+            if (rc) { gexec = nullptr; return rc; }
+            glaunches = last_launches - before;
+            last_launches = before;
+            gpsi = psi; gchunk = chunk; gstream = st;
         }
-        for (auto& g : groups) {
-            rc = launch_soft1d(prec, g.logn, g.loge, g.logrm, g.d_inst, (int)g.members.size(), psi, chunk,
-                               d_ftab, ftab_cap, d_status, st, nullptr);
-            if (rc) return rc;
-            ++last_launches;
-        }
-        t += (double)chunk * dt;
+        if ((rc = cuda_status(cudaGraphLaunch(gexec, st)))) return rc;
+        last_launches += glaunches;
         done += chunk;
     }
-    *t_inout = t;
+    *t_inout = t0 + (double)nsteps * dt;
     return SOFT_OK;
 }

@@ -76,9 +76,22 @@ struct soft_plan {
     int* d_status = nullptr;
     int64_t total = 0;
 
+    // graph replay of one chunk (pulse table, size groups on parallel streams)
+    static constexpr size_t MAX_SIDE = 16;
+    double* d_t0 = nullptr;
+    cudaStream_t side[MAX_SIDE] = {};
+    cudaEvent_t ev_join[MAX_SIDE] = {};
+    cudaEvent_t ev_fork = nullptr;
+    bool side_ready = false;
+    cudaGraphExec_t gexec = nullptr;
+    void* gpsi = nullptr;
+    int64_t gchunk = 0, glaunches = 0;
+    cudaStream_t gstream = nullptr;
+
     soft::Inst1D descriptor(int i) const;
     int build_1d_device();
     int set_single_field(const soft_field* f);
+    int enqueue_chunk(void* psi, int64_t chunk, cudaStream_t st);
     int step_1d(void* psi, int64_t nsteps, double* t_inout, cudaStream_t st);
 
     // ---- 2D (plan2d.cu)

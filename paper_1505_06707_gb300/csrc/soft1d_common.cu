@@ -39,6 +39,15 @@ void soft1d_default_cfg(int prec, int logn, int* loge, int* logrm) {
     if (prec == SOFT_C128 && *logrm > 3) *logrm = 3;   // radix 16 in FP64 does not fit 128 registers
 }
 
+// every built (elements per thread, radix) variant of a size
+int soft1d_variants(int prec, int logn, int* loge, int* logrm, int maxv) {
+    int k = 0;
+    for (int e = 1; e <= 5; ++e)
+        for (int r = 1; r <= 4 && r <= e; ++r)
+            if (k < maxv && find1d(prec, logn, e, r)) { loge[k] = e; logrm[k] = r; ++k; }
+    return k;
+}
+
 size_t soft1d_smem_bytes(int prec, int logn, int loge) {
     const size_t c = prec == SOFT_C64 ? 8 : 16;
     return c * ((size_t(1) << logn) + 64 + (size_t(1) << loge) + 4) + 64;
@@ -69,11 +78,43 @@ __global__ void field_table_kernel(const double* __restrict__ cls, int ncls, dou
     out[c * stride + s] = v;
 }
 
+// the same table with the start time read from device memory (graph replays)
+__global__ void field_table_dev_kernel(const double* __restrict__ cls, int ncls,
+                                       const double* __restrict__ t0p, double tau, int64_t nsteps,
+                                       double* __restrict__ out, int64_t stride) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (s >= nsteps || c >= ncls) return;
+    const double om = cls[2 * c], Tp = cls[2 * c + 1];
+    const double t = *t0p + ((double)s + 0.5) * tau;
+    double v = 0.0;
+    if (t >= 0.0 && t <= Tp) {
+        const double a = sin(M_PI * t / Tp);
+        v = a * a * sin(om * t);
+    }
+    out[c * stride + s] = v;
+}
+
+int launch_field_table_dev(const double* d_cls, int ncls, const double* d_t0, double tau,
+                           int64_t nsteps, double* out, int64_t stride, cudaStream_t st) {
+    if (ncls <= 0 || nsteps <= 0) return SOFT_OK;
+    dim3 grid((unsigned)((nsteps + 255) / 256), (unsigned)ncls);
+    field_table_dev_kernel<<<grid, 256, 0, st>>>(d_cls, ncls, d_t0, tau, nsteps, out, stride);
+    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+}
+
 int launch_field_table(const double* d_cls, int ncls, double t0, double tau, int64_t nsteps,
                        double* out, int64_t stride, cudaStream_t st) {
     if (ncls <= 0 || nsteps <= 0) return SOFT_OK;
     dim3 grid((unsigned)((nsteps + 255) / 256), (unsigned)ncls);
     field_table_kernel<<<grid, 256, 0, st>>>(d_cls, ncls, t0, tau, nsteps, out, stride);
+    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+}
+
+__global__ void advance_time_kernel(double* t, double dt) { *t += dt; }
+
+int launch_advance_time(double* d_t, double dt, cudaStream_t st) {
+    advance_time_kernel<<<1, 1, 0, st>>>(d_t, dt);
     return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
 }
 

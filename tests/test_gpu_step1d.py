@@ -219,3 +219,36 @@ def test_observables_match_oracle():
         assert abs(nrm[i] - O.norm_inside(st, x, h, w["R0"])) < 1e-12 * nrm[i]
         fl = O.flux_at_edges(st, x, h, w["R0"])
         assert np.allclose(flx[2 * i:2 * i + 2], fl, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("prec", [S.SOFT_C128, S.SOFT_C64])
+def test_autotuned_batch_matches_default(prec):
+    """A batch plan whose kernel variants were chosen by timing (autotune)
+    computes the same states as the default variants, and repeated calls
+    (replayed from the captured graph) continue the propagation correctly."""
+    idx = [j for j in range(40) if prec == S.SOFT_C64 or W.w2_instance(j)["n"] <= 8192][:12]
+    ws = [W.w2_instance(j) for j in idx]
+    args = ([w["n"] for w in ws], [(w["a"], w["b"]) for w in ws], [w["R0"] for w in ws],
+            [w["theta"] for w in ws], [(w["E0"], w["omega"], w["ncyc"]) for w in ws], W.W2_DT)
+    packed = np.concatenate([w["psi0"] for w in ws])
+    outs = []
+    for tune in (0, 1):
+        plan = S.soft_create_batch(*args, prec=prec, contour=W.W2_CONTOUR, autotune=tune)
+        try:
+            d = torch.tensor(packed, dtype=CT[prec], device="cuda")
+            t = 20.0
+            for _ in range(3):
+                t = S.soft_step_batch(plan, d, 10, t)
+            torch.cuda.synchronize()
+            assert abs(t - 20.6) < 1e-12
+            outs.append(d.cpu().numpy().astype(np.complex128))
+        finally:
+            S.soft_destroy(plan)
+    probs = [P.Problem1D(w["n"], w["a"], w["b"], w["R0"], theta=w["theta"], kind=w["contour"],
+                         a2=w["a2"], dt=w["dt"]) for w in ws]
+    refs = P.step_batch(probs, [w["psi0"] for w in ws], 30, t0s=[20.0] * len(ws),
+                        fields=[(w["E0"], w["omega"], w["ncyc"]) for w in ws])
+    offs = np.concatenate([[0], np.cumsum([w["n"] for w in ws])[:-1]])
+    for out in outs:
+        for o, w, r in zip(offs, ws, refs):
+            assert relerr(out[o:o + w["n"]], r) < tol(prec, 30, w["n"])
