@@ -264,6 +264,74 @@ def bench_pcg(S, torch, dev, args):
             "workload": "1024^2 on [-200,200]^2, sharp ECS R0=150 theta=0.4, 64 energies in [0.05,2]"}
 
 
+def bench_learned(S, torch, dev, args):
+    """The learned correction on the stationary workload: errors of plain
+    banded CG runs at 8 training energies are cut into 128^2 crops and the
+    network is trained on the GPU; then 8 held-out energies of the workload
+    are solved by COCG with the banded preconditioner (the paper's method),
+    by flexible GCR with it, and by flexible GCR with the trained correction.
+    Everything runs through the library's own calls."""
+    import numpy as np
+    import workloads as W
+    w = W.w4()
+    n = w["nx"]
+    gamma = 0.1
+    plan = S.soft_create((n, n), w["box"], w["R0"], w["theta"], 0.02, prec=S.SOFT_C128,
+                         soft_a2=w["a2"])
+    f = torch.tensor(w["f"], dtype=torch.complex128, device=dev)
+    rng = np.random.default_rng(15055)
+    train_E = [float(e) for e in np.sort(rng.uniform(0.05, 2.0, 8))]
+    test_E = [float(e) for e in w["E"][4::8]]
+    st = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    xs = torch.zeros((len(train_E), n, n), dtype=torch.complex128, device=dev)
+    S.sse_pcg_solve(plan, train_E, f, xs, tol=1e-11, maxit=4000, precond=1, stream=st)
+    ins, tgs = [], []
+    Ax = torch.zeros((n, n), dtype=torch.complex128, device=dev)
+    z = torch.zeros_like(Ax)
+    for k in (2, 5, 10, 20, 40, 80):
+        xk = torch.zeros_like(xs)
+        S.sse_pcg_solve(plan, train_E, f, xk, tol=1e-14, maxit=k, precond=1, stream=st)
+        for e, E in enumerate(train_E):
+            S.sse_apply_A(plan, E, xk[e], Ax, stream=st)
+            r = f - Ax
+            S.sse_apply_precond(plan, E, 1, r, z, stream=st)
+            err = xs[e] - xk[e]
+            sc = torch.sqrt(torch.mean(torch.abs(z) ** 2) / 2)
+            tgt = gamma * (err * (torch.linalg.norm(z) / torch.linalg.norm(err)) - z) / sc
+            zin = z / sc
+            for _ in range(16):
+                y0, x0 = (int(v) for v in rng.integers(0, n - 128, 2))
+                ins.append(zin[y0:y0 + 128, x0:x0 + 128].to(torch.complex64))
+                tgs.append(tgt[y0:y0 + 128, x0:x0 + 128].to(torch.complex64))
+    ins = torch.stack(ins).contiguous()
+    tgs = torch.stack(tgs).contiguous()
+    torch.cuda.synchronize()
+    t_harvest = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    losses = S.sse_nn_train(plan, ins, tgs, steps=400, batch=32, lr=2e-3, seed=7, stream=st)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    res = {"train_energies": len(train_E), "crops": int(ins.shape[0]), "crop": 128,
+           "harvest_s": t_harvest, "train_s": t_train, "train_steps": 400,
+           "loss_first": float(np.mean(losses[:10])), "loss_last": float(np.mean(losses[-10:])),
+           "test_energies": len(test_E), "gamma": gamma}
+    out = torch.zeros((len(test_E), n, n), dtype=torch.complex128, device=dev)
+    for name, pc in (("cocg_band", 1), ("fgcr_band", 3), ("fgcr_band_learned", 2)):
+        out.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        rc, its, rr = S.sse_pcg_solve(plan, test_E, f, out, tol=w["tol"], maxit=2000, precond=pc,
+                                      stream=st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        res[name] = {"status": rc, "iterations": [int(i) for i in its],
+                     "iterations_mean": float(np.mean(its)), "seconds": e0.elapsed_time(e1) / 1e3,
+                     "max_relres": float(np.max(rr))}
+    S.soft_destroy(plan)
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -443,6 +511,7 @@ def main():
     if not args.no_extra:
         out["w3_2d"] = bench_2d(S, torch, dev, args)
         out["w4_pcg"] = bench_pcg(S, torch, dev, args)
+        out["w5_learned"] = bench_learned(S, torch, dev, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_sample()
     if rank == 0:

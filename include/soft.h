@@ -166,10 +166,19 @@ int soft_observe(const soft_plan* plan, const void* psi, double* norm_in, double
  *   rhs      device, one right-hand side f shared by all energies.
  *   psi_out  device, nE consecutive solutions.
  *   precond  0: simple FFT preconditioner (Eq. PreconFFT);
- *            1: banded ECS preconditioner (Eq. PreconFFT_ECS).
+ *            1: banded ECS preconditioner (Eq. PreconFFT_ECS);
+ *            2: the banded preconditioner plus the plan's learned correction
+ *               z <- z + s NN(z/s), s = RMS of z per energy, inside flexible
+ *               GCR with the last 16 directions (minimal residual with
+ *               Hermitian inner products: valid for a preconditioner that
+ *               changes between iterations); grids with nx % 128 == 0;
+ *            3: the banded preconditioner alone inside the same flexible GCR
+ *               (the reference for what the learned correction gains).
  *   iters_out, relres_out: host int[nE], double[nE]; may be NULL.
  * Returns SOFT_ERR_NOT_CONVERGED if any energy stopped at maxit (its last
  * iterate is written), SOFT_ERR_BREAKDOWN on a vanishing CG denominator.
+ * Workspace (and, for precond 2/3, 32 direction vectors per energy) is
+ * allocated by the plan on first use.
  * C128 plans only.  Workspace is allocated by the plan on first use. */
 int sse_pcg_solve(soft_plan* plan, const double* E, int nE, const void* rhs, void* psi_out,
                   double tol, int maxit, int precond, int* iters_out, double* relres_out,
@@ -201,6 +210,32 @@ int sse_apply_precond(soft_plan* plan, double E, int precond, const void* x, voi
  * before any stream capture. */
 int soft_step_noalloc(const soft_plan* plan, void* psi, int64_t nsteps, const soft_field* field,
                       double* t_inout, void* stream);
+
+/* Learned correction of the FFT preconditioner.  The paper has no learned
+ * component; the network only corrects the output of Eq. PreconFFT_ECS inside
+ * a flexible CG, and the plain preconditioner stays available (precond 1).
+ * Network: 3x3 convolutions 2 -> 32 -> 32 -> 2 channels (real and imaginary
+ * parts), ReLU between layers, periodic padding, BF16 weights and
+ * activations with FP32 accumulation on the tensor cores.  The 10434 FP32
+ * parameters are, in order: W1[32][2][3][3], b1[32], W2[32][32][3][3], b2[32],
+ * W3[2][32][3][3], b3[2] (out[o](y,x) = b[o] + sum W[o][i][dy+1][dx+1]
+ * in[i](y+dy, x+dx), indices mod H, W).  Every 2D plan owns one network,
+ * initialised from a fixed seed on first use.
+ *   Fields: device complex64 arrays [n][H][W], W a multiple of 128, H >= 3.
+ * sse_nn_set_weights / sse_nn_get_weights: host float[10434].
+ * sse_nn_forward: out = NN(x), device float [n][H][W][2].
+ * sse_nn_grad: mean-square loss of NN(x) against targets and its gradient
+ *   (host float[10434]); no update.
+ * sse_nn_train: `steps` Adam steps (lr, beta 0.9/0.999) on minibatches of
+ *   `batch` fields drawn from the n inputs with the seed; loss_out: host
+ *   double[steps] or NULL. */
+int sse_nn_set_weights(soft_plan* plan, const float* w);
+int sse_nn_get_weights(soft_plan* plan, float* w);
+int sse_nn_forward(soft_plan* plan, const void* x, int n, int H, int W, void* out, void* stream);
+int sse_nn_grad(soft_plan* plan, const void* inputs, const void* targets, int n, int H, int W,
+                float* grad_out, double* loss_out, void* stream);
+int sse_nn_train(soft_plan* plan, const void* inputs, const void* targets, int n, int H, int W,
+                 int steps, int batch, double lr, uint64_t seed, double* loss_out, void* stream);
 
 void soft_destroy(soft_plan* plan);
 const char* soft_strerror(int status);

@@ -6,6 +6,7 @@
 #include <cstring>
 
 #include "band.h"
+#include "nn.h"
 #include "pcg.cuh"
 #include "pcg_launch.h"
 #include "plan_internal.h"
@@ -26,6 +27,7 @@ struct Pcg {
     void *r = nullptr, *z = nullptr, *p = nullptr, *w = nullptr, *t = nullptr;
     double* dE = nullptr;
     double2* part = nullptr;
+    double2* part2 = nullptr;
     int nparts_max = 0;
     // per-energy state (device)
     double2 *rho = nullptr, *alpha = nullptr, *beta = nullptr;
@@ -35,9 +37,15 @@ struct Pcg {
     void *U = nullptr, *Cx = nullptr, *Cy = nullptr, *Kx = nullptr, *Ky = nullptr;
     PcgTables pc[2];
     bool tables = false;
+    // flexible GCR: GCR_M stored direction pairs per energy
+    static constexpr int GCR_M = 16;
+    void *gP = nullptr, *gQ = nullptr;
+    double2 *gbeta = nullptr, *gpart = nullptr;
+    double* gqn = nullptr;
+    int gcap = 0;
     ~Pcg() {
-        void* v[] = {r, z, p, w, t, dE, part, rho, alpha, beta, relres, fnorm2, active, iters,
-                     status, nactive, U, Cx, Cy, Kx, Ky};
+        void* v[] = {r, z, p, w, t, dE, part, part2, rho, alpha, beta, relres, fnorm2, active, iters,
+                     status, nactive, U, Cx, Cy, Kx, Ky, gP, gQ, gbeta, gpart, gqn};
         for (void* b : v) cudaFree(b);
         for (auto& T : pc)
             for (void* b : T.bufs) cudaFree(b);
@@ -143,7 +151,7 @@ static int ensure_workspace(Plan2D* Q, int nE) {
     if (rc) return rc;
     Pcg* S = Q->pcg;
     if (S->nEcap >= nE) return SOFT_OK;
-    void* v[] = {S->r, S->z, S->p, S->w, S->t, S->dE, S->part, S->rho, S->alpha, S->beta,
+    void* v[] = {S->r, S->z, S->p, S->w, S->t, S->dE, S->part, S->part2, S->rho, S->alpha, S->beta,
                  S->relres, S->active, S->iters, S->status};
     for (void* b : v) cudaFree(b);
     S->r = S->z = S->p = S->w = S->t = nullptr;
@@ -156,6 +164,7 @@ static int ensure_workspace(Plan2D* Q, int nE) {
     if ((rc = cuda_status(cudaMalloc(&S->t, vb)))) return rc;
     if ((rc = cuda_status(cudaMalloc((void**)&S->dE, sizeof(double) * nE)))) return rc;
     if ((rc = cuda_status(cudaMalloc((void**)&S->part, sizeof(double2) * (size_t)nE * S->nparts_max)))) return rc;
+    if ((rc = cuda_status(cudaMalloc((void**)&S->part2, sizeof(double2) * (size_t)nE * S->nparts_max)))) return rc;
     if ((rc = cuda_status(cudaMalloc((void**)&S->rho, sizeof(double2) * nE)))) return rc;
     if ((rc = cuda_status(cudaMalloc((void**)&S->alpha, sizeof(double2) * nE)))) return rc;
     if ((rc = cuda_status(cudaMalloc((void**)&S->beta, sizeof(double2) * nE)))) return rc;
@@ -190,6 +199,22 @@ static int apply_A(Plan2D* Q, const void* p, void* w, const double* dE, const in
     if ((rc = pcg_row(Q->lx, 0, g, p, w, nullptr, dE, act, nullptr, nE, st))) return rc;
     Q->launches += 2;
     return pcg_col(Q->ly, 0, g, p, w, dE, act, part, nE, st);
+}
+
+static int ensure_gcr(Pcg* S, int nE) {
+    if (S->gcap >= nE) return SOFT_OK;
+    void* v[] = {S->gP, S->gQ, S->gbeta, S->gpart, S->gqn};
+    for (void* b : v) cudaFree(b);
+    S->gP = S->gQ = nullptr; S->gbeta = S->gpart = nullptr; S->gqn = nullptr;
+    const size_t vb = sizeof(double2) * (size_t)S->N * nE * Pcg::GCR_M;
+    int rc;
+    if ((rc = cuda_status(cudaMalloc(&S->gP, vb)))) return rc;
+    if ((rc = cuda_status(cudaMalloc(&S->gQ, vb)))) return rc;
+    if ((rc = cuda_status(cudaMalloc((void**)&S->gbeta, sizeof(double2) * nE * Pcg::GCR_M)))) return rc;
+    if ((rc = cuda_status(cudaMalloc((void**)&S->gqn, sizeof(double) * nE * Pcg::GCR_M)))) return rc;
+    if ((rc = cuda_status(cudaMalloc((void**)&S->gpart, sizeof(double2) * (size_t)nE * Pcg::GCR_M * 256)))) return rc;
+    S->gcap = nE;
+    return SOFT_OK;
 }
 
 void Plan2D::free_pcg() {
@@ -235,7 +260,18 @@ int sse_apply_precond(soft_plan* P, double E, int precond, const void* x, void* 
 int sse_pcg_solve(soft_plan* P, const double* E, int nE, const void* rhs, void* psi_out, double tol,
                   int maxit, int precond, int* iters_out, double* relres_out, void* stream) {
     if (!P || !E || nE <= 0 || !rhs || !psi_out || !(tol > 0) || maxit <= 0) return SOFT_ERR_INVALID_ARG;
-    if (precond != 0 && precond != 1) return SOFT_ERR_INVALID_ARG;
+    if (precond < 0 || precond > 3) return SOFT_ERR_INVALID_ARG;
+    const bool flexible = precond >= 2;
+    const bool learned = precond == 2;
+    if (learned) {
+        if (!P->p2 || P->p2->nx % 128) return SOFT_ERR_UNSUPPORTED;
+        if (!P->nn) {
+            P->nn = new NNState();
+            int r0 = P->nn->init(1505);
+            if (r0) return r0;
+        }
+    }
+    if (flexible) precond = 1;
     if (P->kind != 2) return SOFT_ERR_INVALID_ARG;
     if (P->prec != SOFT_C128) return SOFT_ERR_UNSUPPORTED;
     for (int e = 0; e < nE; ++e)
@@ -261,28 +297,60 @@ int sse_pcg_solve(soft_plan* P, const double* E, int nE, const void* rhs, void* 
     if ((rc = vec_init(rhs, psi_out, S->r, N, nE, st))) return rc;
     if ((rc = vec_norm2(rhs, N, S->part, np_vec, st))) return rc;
     if ((rc = pcg_scalars(STAGE_FNORM, nE, S->part, np_vec, s, st))) return rc;
-    if ((rc = apply_pc(Q, precond, S->r, S->z, S->dE, S->active, S->part, nE, st))) return rc;
-    if ((rc = pcg_scalars(STAGE_RHO, nE, S->part, np_row, s, st))) return rc;
-    if ((rc = vec_p(S->p, S->z, S->beta, S->active, N, nE, 1, st))) return rc;
-    Q->launches += 5;
-    const int CHECK = 4;
-    for (int it = 1; it <= maxit; ++it) {
-        if ((rc = apply_A(Q, S->p, S->w, S->dE, S->active, S->part, nE, st))) return rc;
-        if ((rc = pcg_scalars(STAGE_ALPHA, nE, S->part, np_col, s, st))) return rc;
-        if ((rc = vec_xr(psi_out, S->r, S->p, S->w, S->alpha, S->active, N, nE, S->part, np_vec, st))) return rc;
-        if ((rc = pcg_scalars(STAGE_RNORM, nE, S->part, np_vec, s, st))) return rc;
-        Q->launches += 3;
-        if (it % CHECK == 0 || it == maxit) {
-            int na = 0;
-            if ((rc = cuda_status(cudaMemcpyAsync(&na, S->nactive, sizeof(int), cudaMemcpyDeviceToHost, st)))) return rc;
-            if ((rc = cuda_status(cudaStreamSynchronize(st)))) return rc;
-            if (na <= 0) break;
-        }
-        if (it == maxit) break;
+    if (!flexible) {
+        // COCG (Sec. III): z = P^-1 r, rho = r^T z, p = z
         if ((rc = apply_pc(Q, precond, S->r, S->z, S->dE, S->active, S->part, nE, st))) return rc;
-        if ((rc = pcg_scalars(STAGE_BETA, nE, S->part, np_row, s, st))) return rc;
-        if ((rc = vec_p(S->p, S->z, S->beta, S->active, N, nE, 0, st))) return rc;
-        Q->launches += 2;
+        if ((rc = pcg_scalars(STAGE_RHO, nE, S->part, np_row, s, st))) return rc;
+        if ((rc = vec_p(S->p, S->z, S->beta, S->active, N, nE, 1, st))) return rc;
+        Q->launches += 5;
+        const int CHECK = 4;
+        for (int it = 1; it <= maxit; ++it) {
+            if ((rc = apply_A(Q, S->p, S->w, S->dE, S->active, S->part, nE, st))) return rc;
+            if ((rc = pcg_scalars(STAGE_ALPHA, nE, S->part, np_col, s, st))) return rc;
+            if ((rc = vec_xr(psi_out, S->r, S->p, S->w, S->alpha, S->active, N, nE, S->part, np_vec, st))) return rc;
+            if ((rc = pcg_scalars(STAGE_RNORM, nE, S->part, np_vec, s, st))) return rc;
+            Q->launches += 3;
+            if (it % CHECK == 0 || it == maxit) {
+                int na = 0;
+                if ((rc = cuda_status(cudaMemcpyAsync(&na, S->nactive, sizeof(int), cudaMemcpyDeviceToHost, st)))) return rc;
+                if ((rc = cuda_status(cudaStreamSynchronize(st)))) return rc;
+                if (na <= 0) break;
+            }
+            if (it == maxit) break;
+            if ((rc = apply_pc(Q, precond, S->r, S->z, S->dE, S->active, S->part, nE, st))) return rc;
+            if ((rc = pcg_scalars(STAGE_BETA, nE, S->part, np_row, s, st))) return rc;
+            if ((rc = vec_p(S->p, S->z, S->beta, S->active, N, nE, 0, st))) return rc;
+            Q->launches += 5;
+        }
+    } else {
+        // flexible GCR with the last GCR_M direction pairs (minimal residual,
+        // valid for a preconditioner that changes from one iteration to the
+        // next, e.g. the learned correction)
+        if ((rc = ensure_gcr(S, nE))) return rc;
+        const int M = Pcg::GCR_M;
+        const int64_t ss = N * nE;
+        double2* gPb = (double2*)S->gP;
+        double2* gQb = (double2*)S->gQ;
+        const int CHECK = 4;
+        for (int it = 1; it <= maxit; ++it) {
+            const int slot = (it - 1) % M, mu = std::min(it, M);
+            double2* Ps = gPb + slot * ss;
+            double2* Qs = gQb + slot * ss;
+            if ((rc = apply_pc(Q, precond, S->r, Ps, S->dE, S->active, nullptr, nE, st))) return rc;
+            if (learned && (rc = P->nn->correct_c128(Ps, nE, Q->ny, Q->nx, S->active, st))) return rc;
+            if ((rc = apply_A(Q, Ps, Qs, S->dE, S->active, S->part, nE, st))) return rc;
+            if ((rc = gcr_step(0, gPb, gQb, ss, mu, M, slot, S->gbeta, S->gqn, S->r, S->active, N, nE,
+                               S->gpart, S->part, S->part2, np_vec, s, st))) return rc;
+            if ((rc = vec_xr(psi_out, S->r, Ps, Qs, S->alpha, S->active, N, nE, S->part, np_vec, st))) return rc;
+            if ((rc = pcg_scalars(STAGE_RNORM, nE, S->part, np_vec, s, st))) return rc;
+            Q->launches += (learned ? 4 : 0) + 3 + 2 + 4 + 2;
+            if (it % CHECK == 0 || it == maxit) {
+                int na = 0;
+                if ((rc = cuda_status(cudaMemcpyAsync(&na, S->nactive, sizeof(int), cudaMemcpyDeviceToHost, st)))) return rc;
+                if ((rc = cuda_status(cudaStreamSynchronize(st)))) return rc;
+                if (na <= 0) break;
+            }
+        }
     }
     std::vector<int> it_h(nE), stat_h(nE);
     std::vector<double> rr_h(nE);

@@ -153,7 +153,7 @@ __global__ void vec_p_kernel(double2* __restrict__ p, const double2* __restrict_
 // per-energy scalar updates of the iteration (one thread per energy; the
 // partial sums are added in a fixed order, so results are reproducible)
 __global__ void pcg_scalar_kernel(int stage, int nE, const double2* __restrict__ part, int nparts,
-                                  PcgState s) {
+                                  PcgState s, const double2* __restrict__ part2) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (stage == STAGE_FNORM) {
         if (e == 0) {
@@ -180,6 +180,16 @@ __global__ void pcg_scalar_kernel(int stage, int nE, const double2* __restrict__
         s.iters[e] += 1;
         if (!isfinite(rel)) { s.status[e] = SOFT_ERR_NONFINITE; s.active[e] = 0; atomicSub(s.nactive, 1); }
         else if (rel < s.tol) { s.status[e] = SOFT_OK; s.active[e] = 0; atomicSub(s.nactive, 1); }
+    } else if (stage == STAGE_BETA_FLEX) {
+        // flexible (Polak-Ribiere) beta = z'^T (r' - r) / rho = -alpha z'^T w / rho
+        double2 u = make_double2(0.0, 0.0);
+        for (int i = 0; i < nparts; ++i) { u.x += part2[(int64_t)e * nparts + i].x; u.y += part2[(int64_t)e * nparts + i].y; }
+        const double2 rho = s.rho[e], al = s.alpha[e];
+        const double d = rho.x * rho.x + rho.y * rho.y;
+        if (!(d > 0.0)) { s.status[e] = SOFT_ERR_BREAKDOWN; s.active[e] = 0; atomicSub(s.nactive, 1); return; }
+        const double2 au = make_double2(al.x * u.x - al.y * u.y, al.x * u.y + al.y * u.x);
+        s.beta[e] = make_double2(-(au.x * rho.x + au.y * rho.y) / d, -(au.y * rho.x - au.x * rho.y) / d);
+        s.rho[e] = t;
     } else if (stage == STAGE_BETA) {
         const double2 rho = s.rho[e];
         const double d = rho.x * rho.x + rho.y * rho.y;
@@ -208,9 +218,146 @@ int vec_p(void* p, const void* z, const double2* beta, const int* act, int64_t N
     vec_p_kernel<<<dim3(256, nE), 256, 0, st>>>((double2*)p, (const double2*)z, beta, act, N, copy);
     return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
 }
+// r^T z and z^T w partials per CTA
+__global__ void vec_dot2_kernel(const double2* __restrict__ r, const double2* __restrict__ z,
+                                const double2* __restrict__ w, const int* __restrict__ active,
+                                int64_t N, double2* __restrict__ p1, double2* __restrict__ p2) {
+    const int e = blockIdx.y;
+    if (!active[e]) return;
+    __shared__ double2 red[32];
+    const int64_t o = (int64_t)e * N;
+    double2 a1 = make_double2(0.0, 0.0), a2 = make_double2(0.0, 0.0);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 rv = r[o + i], zv = z[o + i], wv = w[o + i];
+        a1.x += rv.x * zv.x - rv.y * zv.y; a1.y += rv.x * zv.y + rv.y * zv.x;
+        a2.x += zv.x * wv.x - zv.y * wv.y; a2.y += zv.x * wv.y + zv.y * wv.x;
+    }
+    const double2 t1 = block_sum2(a1, red);
+    if (threadIdx.x == 0) p1[(int64_t)e * gridDim.x + blockIdx.x] = t1;
+    const double2 t2 = block_sum2(a2, red);
+    if (threadIdx.x == 0) p2[(int64_t)e * gridDim.x + blockIdx.x] = t2;
+}
+
+int vec_dot2(const void* r, const void* z, const void* w, const int* act, int64_t N, int nE,
+             double2* part1, double2* part2, int nparts, cudaStream_t st) {
+    vec_dot2_kernel<<<dim3(nparts, nE), 256, 0, st>>>((const double2*)r, (const double2*)z,
+                                                       (const double2*)w, act, N, part1, part2);
+    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+}
+
+// ------------------------------------------------- flexible GCR (truncated)
+// c_j = <Q_j, q> (Hermitian) for the mu stored directions j != slot
+__global__ void gcr_dots_kernel(const double2* __restrict__ Q, int64_t slot_stride, int mu, int ld, int slot,
+                                const int* __restrict__ active, int64_t N, double2* __restrict__ part) {
+    const int e = blockIdx.y;
+    if (!active[e]) return;
+    __shared__ double2 red[32];
+    const int64_t o = (int64_t)e * N;
+    const double2* q = Q + slot * slot_stride + o;
+    for (int j = 0; j < mu; ++j) {
+        double2 acc = make_double2(0.0, 0.0);
+        if (j != slot) {
+            const double2* qj = Q + j * slot_stride + o;
+            for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+                 i += (int64_t)gridDim.x * blockDim.x) {
+                const double2 a = qj[i], b = q[i];
+                acc.x += a.x * b.x + a.y * b.y;        // conj(a) b
+                acc.y += a.x * b.y - a.y * b.x;
+            }
+        }
+        const double2 t = block_sum2(acc, red);
+        if (threadIdx.x == 0) part[((int64_t)e * ld + j) * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+// beta_j = c_j / <Q_j, Q_j> per energy (one thread per (energy, j))
+__global__ void gcr_beta_kernel(const double2* __restrict__ part, int nparts, int mu, int ld, int slot,
+                                const double* __restrict__ qnorm, const int* __restrict__ active,
+                                int nE, double2* __restrict__ beta) {
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = id / mu, j = id % mu;
+    if (e >= nE || !active[e]) return;
+    double2 t = make_double2(0.0, 0.0);
+    if (j != slot) {
+        for (int i = 0; i < nparts; ++i) { t.x += part[((int64_t)e * ld + j) * nparts + i].x; t.y += part[((int64_t)e * ld + j) * nparts + i].y; }
+        const double qn = qnorm[(int64_t)e * ld + j];
+        t.x /= qn; t.y /= qn;
+    }
+    beta[(int64_t)e * ld + j] = t;
+}
+
+// P_s -= sum_j beta_j P_j, Q_s -= sum_j beta_j Q_j; partials of <Q_s,Q_s> and <Q_s, r>
+__global__ void gcr_update_kernel(double2* __restrict__ Pb, double2* __restrict__ Q, int64_t slot_stride,
+                                  int mu, int ld, int slot, const double2* __restrict__ beta,
+                                  const double2* __restrict__ r, const int* __restrict__ active,
+                                  int64_t N, double2* __restrict__ p1, double2* __restrict__ p2) {
+    const int e = blockIdx.y;
+    if (!active[e]) return;
+    __shared__ double2 red[32];
+    const int64_t o = (int64_t)e * N;
+    double2 a1 = make_double2(0.0, 0.0), a2 = make_double2(0.0, 0.0);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double2 pv = Pb[slot * slot_stride + o + i], qv = Q[slot * slot_stride + o + i];
+        for (int j = 0; j < mu; ++j) {
+            if (j == slot) continue;
+            const double2 b = beta[(int64_t)e * ld + j];
+            const double2 pj = Pb[j * slot_stride + o + i], qj = Q[j * slot_stride + o + i];
+            pv.x -= b.x * pj.x - b.y * pj.y; pv.y -= b.x * pj.y + b.y * pj.x;
+            qv.x -= b.x * qj.x - b.y * qj.y; qv.y -= b.x * qj.y + b.y * qj.x;
+        }
+        Pb[slot * slot_stride + o + i] = pv;
+        Q[slot * slot_stride + o + i] = qv;
+        const double2 rv = r[o + i];
+        a1.x += qv.x * qv.x + qv.y * qv.y;
+        a2.x += qv.x * rv.x + qv.y * rv.y;          // conj(q) r
+        a2.y += qv.x * rv.y - qv.y * rv.x;
+    }
+    const double2 t1 = block_sum2(a1, red);
+    if (threadIdx.x == 0) p1[(int64_t)e * gridDim.x + blockIdx.x] = t1;
+    const double2 t2 = block_sum2(a2, red);
+    if (threadIdx.x == 0) p2[(int64_t)e * gridDim.x + blockIdx.x] = t2;
+}
+
+// nq_s = <Q_s, Q_s>, alpha = <Q_s, r>/nq_s
+__global__ void gcr_alpha_kernel(const double2* __restrict__ p1, const double2* __restrict__ p2, int nparts,
+                                 int ld, int slot, double* __restrict__ qnorm, PcgState s, int nE) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nE || !s.active[e]) return;
+    double n = 0;
+    double2 c = make_double2(0.0, 0.0);
+    for (int i = 0; i < nparts; ++i) {
+        n += p1[(int64_t)e * nparts + i].x;
+        c.x += p2[(int64_t)e * nparts + i].x;
+        c.y += p2[(int64_t)e * nparts + i].y;
+    }
+    if (!(n > 0.0) || !isfinite(n)) {
+        s.status[e] = SOFT_ERR_BREAKDOWN; s.active[e] = 0; atomicSub(s.nactive, 1);
+        return;
+    }
+    qnorm[(int64_t)e * ld + slot] = n;
+    s.alpha[e] = make_double2(c.x / n, c.y / n);
+}
+
+int gcr_step(int phase, void* Pb, void* Q, int64_t slot_stride, int mu, int ld, int slot, double2* beta,
+             double* qnorm, const void* r, const int* act, int64_t N, int nE, double2* gpart, double2* part,
+             double2* part2, int nparts, const PcgState& s, cudaStream_t st) {
+    if (phase == 0) {
+        if (mu > 1) {
+            gcr_dots_kernel<<<dim3(nparts, nE), 256, 0, st>>>((const double2*)Q, slot_stride, mu, ld, slot, act, N, gpart);
+            gcr_beta_kernel<<<(nE * mu + 127) / 128, 128, 0, st>>>(gpart, nparts, mu, ld, slot, qnorm, act, nE, beta);
+        }
+        gcr_update_kernel<<<dim3(nparts, nE), 256, 0, st>>>((double2*)Pb, (double2*)Q, slot_stride, mu, ld, slot,
+                                                            beta, (const double2*)r, act, N, part, part2);
+        gcr_alpha_kernel<<<(nE + 63) / 64, 64, 0, st>>>(part, part2, nparts, ld, slot, qnorm, s, nE);
+    }
+    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+}
+
 int pcg_scalars(int stage, int nE, const double2* part, int nparts, const PcgState& s,
-                cudaStream_t st) {
-    pcg_scalar_kernel<<<(nE + 63) / 64, 64, 0, st>>>(stage, nE, part, nparts, s);
+                cudaStream_t st, const double2* part2) {
+    pcg_scalar_kernel<<<(nE + 63) / 64, 64, 0, st>>>(stage, nE, part, nparts, s, part2);
     return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
 }
 

@@ -9,7 +9,7 @@ namespace soft {
 
 struct PcgGeo;
 
-enum { STAGE_FNORM = 0, STAGE_RHO = 1, STAGE_ALPHA = 2, STAGE_RNORM = 3, STAGE_BETA = 4 };
+enum { STAGE_FNORM = 0, STAGE_RHO = 1, STAGE_ALPHA = 2, STAGE_RNORM = 3, STAGE_BETA = 4, STAGE_BETA_FLEX = 5 };
 
 struct PcgState {                 // device pointers, per energy unless noted
     double2* rho;
@@ -41,6 +41,14 @@ int vec_xr(void* x, void* r, const void* p, const void* w, const double2* alpha,
 int vec_p(void* p, const void* z, const double2* beta, const int* act, int64_t N, int nE, int copy,
           cudaStream_t st);
 int pcg_scalars(int stage, int nE, const double2* part, int nparts, const PcgState& s,
-                cudaStream_t st);
+                cudaStream_t st, const double2* part2 = nullptr);
+// one flexible-GCR orthogonalisation of slot `slot` against the other mu-1
+// stored (P, Q = A P) pairs, then alpha = <Q_s, r>/<Q_s, Q_s> (Hermitian)
+int gcr_step(int phase, void* Pb, void* Q, int64_t slot_stride, int mu, int ld, int slot, double2* beta,
+             double* qnorm, const void* r, const int* act, int64_t N, int nE, double2* gpart, double2* part,
+             double2* part2, int nparts, const PcgState& s, cudaStream_t st);
+// partials of the bilinear forms r^T z and z^T w (flexible CG)
+int vec_dot2(const void* r, const void* z, const void* w, const int* act, int64_t N, int nE,
+             double2* part1, double2* part2, int nparts, cudaStream_t st);
 
 }  // namespace soft

@@ -7,6 +7,7 @@
 #include <map>
 #include <tuple>
 
+#include "nn.h"
 #include "plan_internal.h"
 
 using namespace soft;
@@ -389,6 +390,7 @@ soft_plan::~soft_plan() {
     cudaFree(d_ftab);
     cudaFree(d_status);
     cudaFree(d_t0);
+    delete nn;
     if (gexec) cudaGraphExecDestroy(gexec);
     if (side_ready) {
         for (size_t g = 0; g < groups.size() && g < MAX_SIDE; ++g) {

@@ -14,6 +14,7 @@ int make_tables_1d(Tables1D* T, int n, double a, double b, double R0, double the
                    const soft_options& o, int loge, int logrm);
 
 struct Geo2D;
+struct NNState;
 }  // namespace soft
 
 #include "soft2d_geo.h"
@@ -94,8 +95,9 @@ struct soft_plan {
     int enqueue_chunk(void* psi, int64_t chunk, cudaStream_t st);
     int step_1d(void* psi, int64_t nsteps, double* t_inout, cudaStream_t st);
 
-    // ---- 2D (plan2d.cu)
+    // ---- 2D (plan2d.cu), learned correction (nn.cu)
     soft::Plan2D* p2 = nullptr;
+    soft::NNState* nn = nullptr;
     int step_2d(void* psi, int64_t nsteps, double* t_inout, cudaStream_t st);
     int64_t points_2d() const;
     void free_2d();

@@ -14,7 +14,8 @@ __all__ = [
     "SoftError", "SOFT_C64", "SOFT_C128", "CONTOUR_SHARP", "CONTOUR_SECS", "CONTOUR_TFECS",
     "load", "lib_path", "exported_symbols", "Options", "Field", "soft_create", "soft_create_batch",
     "soft_batch_layout", "soft_step", "soft_step_batch", "soft_step_noalloc", "soft_observe", "sse_pcg_solve",
-    "sse_apply_A", "sse_apply_precond", "soft_destroy", "soft_plan_points", "soft_plan_count",
+    "sse_apply_A", "sse_apply_precond", "soft_destroy", "sse_nn_set_weights", "sse_nn_get_weights",
+    "sse_nn_forward", "sse_nn_grad", "sse_nn_train", "NN_PARAMS", "soft_plan_points", "soft_plan_count",
     "soft_last_launches", "Plan",
 ]
 
@@ -31,7 +32,8 @@ exported_symbols = [
     "soft_default_options", "soft_create", "soft_create_batch", "soft_batch_layout", "soft_step",
     "soft_step_batch", "soft_observe", "sse_pcg_solve", "sse_apply_A", "sse_apply_precond",
     "soft_destroy", "soft_strerror", "soft_plan_count", "soft_plan_points", "soft_plan_prec",
-    "soft_last_launches", "soft_step_noalloc",
+    "soft_last_launches", "soft_step_noalloc", "sse_nn_set_weights", "sse_nn_get_weights",
+    "sse_nn_forward", "sse_nn_grad", "sse_nn_train",
 ]
 
 
@@ -87,6 +89,12 @@ def load():
                                 C.POINTER(C.c_int), C.POINTER(dbl), P]
     L.sse_apply_A.argtypes = [P, dbl, P, P, P]
     L.sse_apply_precond.argtypes = [P, dbl, C.c_int, P, P, P]
+    L.sse_nn_set_weights.argtypes = [P, P]
+    L.sse_nn_get_weights.argtypes = [P, P]
+    L.sse_nn_forward.argtypes = [P, P, C.c_int, C.c_int, C.c_int, P, P]
+    L.sse_nn_grad.argtypes = [P, P, P, C.c_int, C.c_int, C.c_int, P, C.POINTER(dbl), P]
+    L.sse_nn_train.argtypes = [P, P, P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, dbl,
+                               C.c_uint64, P, P]
     L.soft_destroy.argtypes = [P]
     L.soft_destroy.restype = None
     L.soft_strerror.argtypes = [C.c_int]
@@ -240,6 +248,51 @@ def sse_apply_A(plan, E, x, y, stream=None):
 def sse_apply_precond(plan, E, precond, x, y, stream=None):
     _check(load().sse_apply_precond(plan, E, precond, _ptr(x), _ptr(y), _stream(stream)),
            "sse_apply_precond")
+
+
+NN_PARAMS = 10434
+
+
+def sse_nn_set_weights(plan, w):
+    import numpy as np
+    a = np.ascontiguousarray(w, dtype=np.float32)
+    assert a.size == NN_PARAMS
+    _check(load().sse_nn_set_weights(plan, a.ctypes.data), "sse_nn_set_weights")
+
+
+def sse_nn_get_weights(plan):
+    import numpy as np
+    a = np.zeros(NN_PARAMS, dtype=np.float32)
+    _check(load().sse_nn_get_weights(plan, a.ctypes.data), "sse_nn_get_weights")
+    return a
+
+
+def sse_nn_forward(plan, x, out, stream=None):
+    """x: device complex64 [n][H][W]; out: device float32 [n][H][W][2]."""
+    n, H, W = x.shape
+    _check(load().sse_nn_forward(plan, _ptr(x), n, H, W, _ptr(out), _stream(stream)),
+           "sse_nn_forward")
+
+
+def sse_nn_grad(plan, x, t, stream=None):
+    """Returns (loss, gradient float32[10434]) of the mean-square loss."""
+    import numpy as np
+    n, H, W = x.shape
+    g = np.zeros(NN_PARAMS, dtype=np.float32)
+    loss = C.c_double()
+    _check(load().sse_nn_grad(plan, _ptr(x), _ptr(t), n, H, W, g.ctypes.data, C.byref(loss),
+                              _stream(stream)), "sse_nn_grad")
+    return loss.value, g
+
+
+def sse_nn_train(plan, x, t, steps, batch, lr, seed=0, stream=None):
+    """Adam training; returns the loss of every step."""
+    import numpy as np
+    n, H, W = x.shape
+    losses = np.zeros(steps, dtype=np.float64)
+    _check(load().sse_nn_train(plan, _ptr(x), _ptr(t), n, H, W, steps, batch, lr, seed,
+                               losses.ctypes.data, _stream(stream)), "sse_nn_train")
+    return losses
 
 
 def soft_destroy(plan):
