@@ -160,13 +160,29 @@ __device__ __forceinline__ C affine_carry(C M, C Y, C* scratch) {
         const int tail = REV ? 0 : 31;
         if (lane == tail) { scratch[2 * warp] = M; scratch[2 * warp + 1] = Y; }
         __syncthreads();
-        // carry entering this warp: fold the totals of the preceding warps
-        C carry; carry.x = 0; carry.y = 0;
-        if constexpr (!REV) {
-            for (int w = 0; w < warp; ++w) carry = cfma(scratch[2 * w], carry, scratch[2 * w + 1]);
-        } else {
-            for (int w = NW - 1; w > warp; --w) carry = cfma(scratch[2 * w], carry, scratch[2 * w + 1]);
+        // carry entering each warp: warp 0 scans the warp totals (lane l holds
+        // the l-th warp in composition order) and leaves warp w's carry in
+        // scratch[2 w]
+        if (warp == 0) {
+            const int w = REV ? NW - 1 - lane : lane;
+            C Mw, Yw;
+            Mw.x = 1; Mw.y = 0; Yw.x = 0; Yw.y = 0;
+            if (lane < NW) { Mw = scratch[2 * w]; Yw = scratch[2 * w + 1]; }
+#pragma unroll
+            for (int d = 1; d < NW; d <<= 1) {
+                C Mo, Yo;
+                Mo.x = __shfl_up_sync(0xffffffffu, Mw.x, d); Mo.y = __shfl_up_sync(0xffffffffu, Mw.y, d);
+                Yo.x = __shfl_up_sync(0xffffffffu, Yw.x, d); Yo.y = __shfl_up_sync(0xffffffffu, Yw.y, d);
+                if (lane >= d) { Yw = cfma(Mw, Yo, Yw); Mw = cmul(Mw, Mo); }
+            }
+            C cw;
+            cw.x = __shfl_up_sync(0xffffffffu, Yw.x, 1); cw.y = __shfl_up_sync(0xffffffffu, Yw.y, 1);
+            if (lane == 0) { cw.x = 0; cw.y = 0; }
+            __syncwarp();
+            if (lane < NW) scratch[2 * w] = cw;
         }
+        __syncthreads();
+        const C carry = scratch[2 * warp];
         __syncthreads();
         return cfma(Mex, carry, Yex);
     }

@@ -18,11 +18,12 @@ using cd = std::complex<double>;
 // Device descriptor of one 1D instance (read by the 1D step kernel).
 struct Inst1D {
     int64_t off;          // element offset of the instance in the packed state
-    const void* TK;       // e^{-i k^2 tau/2}/N in the forward FFT's output order
+    const void* TK;       // e^{-i k^2 tau/2}/N, forward FFT output order, last-pass transposed
     const void* TKh;      // e^{-i k^2 tau/4}/N, same order (first/last half step)
     const void* TV;       // e^{-iU0 tau} off the strip block, e^{-iU0 tau/2} on it
     const void* W;        // per-pass twiddle bases (see soft1d.cuh)
-    const void* cn;       // strip CN coefficients: mf[nb], mb[nb], g[nb]
+    const void* cn;       // strip CN coefficients, chunk-transposed (soft1d.cuh, strip_cn_1d)
+    const void* TVs;      // TV on the strip rows, same transposed order
     int nb;               // strip block length (0: no absorbing term)
     int blk0;             // first grid index of the block (cyclic)
     double x0, h, R0, tau;
@@ -46,6 +47,7 @@ struct Tables1D {
     void* TV = nullptr;
     void* W = nullptr;
     void* cn = nullptr;
+    void* TVs = nullptr;
 };
 
 struct Group1D {                  // instances sharing one kernel configuration
@@ -68,7 +70,7 @@ int soft1d_variants(int prec, int logn, int* loge, int* logrm, int maxv);
 int launch_advance_time(double* d_t, double dt, cudaStream_t st);
 bool soft1d_supported(int prec, int logn, int loge, int logrm);
 void soft1d_default_cfg(int prec, int logn, int* loge, int* logrm);
-size_t soft1d_smem_bytes(int prec, int logn, int loge);
+size_t soft1d_smem_bytes(int prec, int logn, int loge, int logrm);
 
 int launch_observe1d(int prec, const Inst1D* d_inst, int count, const void* psi,
                      double* norm_in, double* flux, cudaStream_t st);

@@ -65,6 +65,7 @@ static int ilog2(int64_t n) {
 
 static void free_tables(Tables1D* t) {
     cudaFree(t->TK); cudaFree(t->TKh); cudaFree(t->TV); cudaFree(t->W); cudaFree(t->cn);
+    cudaFree(t->TVs);
 }
 
 // Build (host FP64) and upload the tables of one 1D problem.
@@ -89,30 +90,61 @@ int make_tables_1d(Tables1D* T, int n, double a, double b, double R0, double the
     const std::vector<int> perm = dif_output_order(logn, logrm);
     std::vector<cd> tk(n), tkh(n), tv(n);
     const std::vector<cd> w = pass_twiddles(logn, logrm);
+    // The step kernel reads them in its last forward pass, whose butterflies
+    // hold R consecutive positions b*R + m (R its radix): entry (b, m) is
+    // stored at m*(n/R) + b, so that a warp's reads are contiguous.
+    const int lrl = (logn % logrm) ? logn % logrm : logrm;
+    const int Rl = 1 << lrl, nbf = n >> lrl;
     for (int p = 0; p < n; ++p) {
         const double k = A.k[perm[p]];
-        tk[p] = std::polar(1.0 / n, -0.5 * k * k * tau);
-        tkh[p] = std::polar(1.0 / n, -0.25 * k * k * tau);
+        const int q = (p % Rl) * nbf + p / Rl;
+        tk[q] = std::polar(1.0 / n, -0.5 * k * k * tau);
+        tkh[q] = std::polar(1.0 / n, -0.25 * k * k * tau);
     }
     // potential factor: full step off the block, half step on it
     for (int j = 0; j < n; ++j) {
         const bool inblk = ((j - T->blk0 + n) % n) < T->nb;
         tv[j] = std::exp(cd(0.0, -1.0) * T->U0[j] * tau * (inblk ? 0.5 : 1.0));
     }
-    std::vector<cd> mf, mb, g, cnv;
+    // Strip CN coefficients for the kernel's chunked solve: thread t of the
+    // T = n >> loge threads owns rows t*ch .. t*ch + ch - 1 (ch = ceil(nb/T));
+    // row i = t*ch + c is stored at c*T + t of five arrays (mf, the product of
+    // mf over the chunk up to row i, mb, g, the product of mb from row i to
+    // the chunk's end), and TV of the row at the same place of tvs.
+    std::vector<cd> mf, mb, g, cnv, tvs;
     if (T->nb > 0) {
         double err = 0;
         rc = strip_factor(A, T->blk0, T->nb, mf, mb, g, &err);
         if (rc) return rc;
-        cnv.insert(cnv.end(), mf.begin(), mf.end());
-        cnv.insert(cnv.end(), mb.begin(), mb.end());
-        cnv.insert(cnv.end(), g.begin(), g.end());
+        const int thr = n >> loge, nb = T->nb;
+        const int ch = (nb + thr - 1) / thr, P = ch * thr;
+        cnv.assign(5 * (size_t)P, 0.0);
+        tvs.assign(P, 1.0);
+        for (int t = 0; t < thr; ++t) {
+            const int i0 = t * ch, i1 = std::min(i0 + ch, nb);
+            cd pf = 1.0, pb = 1.0;
+            for (int i = i0; i < i1; ++i) {
+                const size_t q = (size_t)(i - i0) * thr + t;
+                pf *= mf[i];
+                cnv[q] = mf[i];
+                cnv[P + q] = pf;
+                cnv[2 * (size_t)P + q] = mb[i];
+                cnv[3 * (size_t)P + q] = g[i];
+                tvs[q] = tv[(T->blk0 + i) % n];
+            }
+            for (int i = i1 - 1; i >= i0; --i) {
+                const size_t q = (size_t)(i - i0) * thr + t;
+                pb *= mb[i];
+                cnv[4 * (size_t)P + q] = pb;
+            }
+        }
     }
     if ((rc = upload_tab(&T->TK, tk, o.prec))) return rc;
     if ((rc = upload_tab(&T->TKh, tkh, o.prec))) return rc;
     if ((rc = upload_tab(&T->TV, tv, o.prec))) return rc;
     if ((rc = upload_c(&T->W, w, o.prec))) return rc;
     if ((rc = upload_c(&T->cn, cnv, o.prec))) return rc;
+    if ((rc = upload_tab(&T->TVs, tvs, o.prec))) return rc;
     return SOFT_OK;
 }
 
@@ -195,6 +227,7 @@ static int autotune_size(const soft_options& o, int n, double a, double b, doubl
                     std::memset(&d[i], 0, sizeof(Inst1D));
                     d[i].off = (int64_t)i * n;
                     d[i].TK = T.TK; d[i].TKh = T.TKh; d[i].TV = T.TV; d[i].W = T.W; d[i].cn = T.cn;
+                    d[i].TVs = T.TVs;
                     d[i].nb = T.nb; d[i].blk0 = T.blk0; d[i].x0 = T.ax.x[0]; d[i].h = T.ax.h;
                     d[i].R0 = R0; d[i].tau = dt; d[i].iL = T.iL; d[i].iR = T.iR; d[i].n = n;
                 }
@@ -381,9 +414,7 @@ int64_t soft_last_launches(const soft_plan* P) { return P ? P->last_launches : 0
 
 // ---------------------------------------------------------------- soft_plan
 soft_plan::~soft_plan() {
-    for (auto& t : tabs) {
-        cudaFree(t->TK); cudaFree(t->TKh); cudaFree(t->TV); cudaFree(t->W); cudaFree(t->cn);
-    }
+    for (auto& t : tabs) free_tables(t.get());
     for (auto& g : groups) cudaFree(g.d_inst);
     cudaFree(d_inst_obs);
     cudaFree(d_cls);
@@ -408,7 +439,7 @@ Inst1D soft_plan::descriptor(int i) const {
     Inst1D d;
     std::memset(&d, 0, sizeof(d));
     d.off = ih.off;
-    d.TK = T.TK; d.TKh = T.TKh; d.TV = T.TV; d.W = T.W; d.cn = T.cn;
+    d.TK = T.TK; d.TKh = T.TKh; d.TV = T.TV; d.W = T.W; d.cn = T.cn; d.TVs = T.TVs;
     d.nb = T.nb; d.blk0 = T.blk0;
     d.x0 = T.ax.x[0]; d.h = T.ax.h; d.R0 = T.R0; d.tau = dt;
     d.E0 = ih.E0; d.has_field = ih.has_field; d.fcls = ih.fcls;
@@ -438,7 +469,7 @@ int soft_plan::build_1d_device() {
         std::vector<Inst1D> d;
         for (int i : g.members) d.push_back(descriptor(i));
         if ((rc = upload((void**)&g.d_inst, d.data(), d.size() * sizeof(Inst1D)))) return rc;
-        g.smem = soft1d_smem_bytes(prec, g.logn, g.loge);
+        g.smem = soft1d_smem_bytes(prec, g.logn, g.loge, g.logrm);
     }
     h_obs.clear();
     for (size_t i = 0; i < inst.size(); ++i) h_obs.push_back(descriptor((int)i));

@@ -48,13 +48,13 @@ struct Cfg1D {
     static constexpr int CMAX = E / 4 + 2;   // strip rows per thread
     static constexpr int NW = (T + 31) / 32;
     static constexpr int MINB = T >= 512 ? 1 : 512 / T;   // CTAs per SM the registers must allow (128 regs)
-    static constexpr size_t SMEM = sizeof(C) * (N + 2 * 32 + E + 4) + 64;
 };
 
-// Twiddle tables: for pass P (sub-transform length L, stride s = L/R) and
-// every offset off < s, four entries W_L^{off}, W_L^{2 off}, W_L^{4 off},
-// W_L^{8 off} (W_L = e^{-2 pi i/L}); a butterfly forms W_L^{m off} for
-// m < 16 from the binary digits of m with at most two products.
+// Twiddle tables: for pass P (sub-transform length L, stride s = L/R) four
+// rows of s entries, row k holding W_L^{2^k off} for off < s (W_L =
+// e^{-2 pi i/L}), so the lanes of a warp read consecutive entries of a row; a
+// butterfly forms W_L^{m off} for m < 16 from the binary digits of m with at
+// most two products.
 template <int LOGN, int LOGRM, int P>
 struct PassGeom {
     static constexpr int NFULL = LOGN / LOGRM;
@@ -107,14 +107,23 @@ struct StoreNat {   // x_M = v[bitrev(M)] stored at base + M s
     }
 };
 
-template <typename C, int NB>
+// SH: the table has been copied to shared memory (plain loads), else it is
+// read from global memory through the read-only path
+template <typename C, int NB, int ST, bool SH>
 __device__ __forceinline__ void load_tw(C* b, const C* __restrict__ t) {
 #pragma unroll
-    for (int k = 0; k < NB; ++k) b[k] = __ldg(&t[k]);
+    for (int k = 0; k < NB; ++k) b[k] = SH ? t[k * ST] : __ldg(&t[k * ST]);
 }
 
+// number of twiddle entries of all passes
+template <int LOGN, int LOGRM>
+struct TwCount {
+    static constexpr int NP = LOGN / LOGRM + ((LOGN % LOGRM) ? 1 : 0);
+    static constexpr int value = PassGeom<LOGN, LOGRM, NP - 1>::TOFF + 4 * PassGeom<LOGN, LOGRM, NP - 1>::S;
+};
+
 // forward DIF pass P (radix 2^LOGR on sub-transforms of length 2^LOGL)
-template <typename R, int LOGN, int LOGE, int LOGRM, int P>
+template <typename R, int LOGN, int LOGE, int LOGRM, int P, bool SH = false>
 __device__ __forceinline__ void fwd_pass(typename CT<R>::C* S, const typename CT<R>::C* __restrict__ W,
                                          int tid) {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
@@ -134,13 +143,13 @@ __device__ __forceinline__ void fwd_pass(typename CT<R>::C* S, const typename CT
         for (int j = 0; j < RR; ++j) v[j] = S[swz<C>(base + j * s)];
         dft_reg<C, RR, -1>(v);
         C tb[4];
-        if constexpr (s > 1) load_tw<C, NB>(tb, W + G::TOFF + 4 * off);
+        if constexpr (s > 1) load_tw<C, NB, s, SH>(tb, W + G::TOFF + off);
         StoreFwd<C, RR, 0>::run(S, v, tb, base, s, s > 1);
     }
 }
 
 // inverse DIT pass P (undoes fwd_pass P up to the factor 2^LOGR)
-template <typename R, int LOGN, int LOGE, int LOGRM, int P>
+template <typename R, int LOGN, int LOGE, int LOGRM, int P, bool SH = false>
 __device__ __forceinline__ void inv_pass(typename CT<R>::C* S, const typename CT<R>::C* __restrict__ W,
                                          int tid) {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
@@ -157,7 +166,7 @@ __device__ __forceinline__ void inv_pass(typename CT<R>::C* S, const typename CT
         const int base = blk * L + off;
         C v[RR];
         C tb[4];
-        if constexpr (s > 1) load_tw<C, NB>(tb, W + G::TOFF + 4 * off);
+        if constexpr (s > 1) load_tw<C, NB, s, SH>(tb, W + G::TOFF + off);
         LoadInv<C, RR, 0>::run(S, v, tb, base, s, s > 1);
         dft_reg<C, RR, +1>(v);
         StoreNat<C, RR, 0>::run(S, v, base, s);
@@ -264,8 +273,268 @@ __device__ __forceinline__ void strip_cn(C* S, const C* __restrict__ cn, int nb,
     }
 }
 
+// The same solve for the 1D step kernel with the coefficients laid out by the
+// host for coalesced reads: with P = ch*T (ch = ceil(nb/T) rows per thread),
+// row i = t*ch + c of thread t sits at q = c*T + t of the arrays
+//   cn[0 P..]: mf_i          cn[1 P..]: mf_i mf_{i-1} .. mf_{t ch}  (in-chunk prefix)
+//   cn[2 P..]: mb_i          cn[3 P..]: g_i
+//   cn[4 P..]: mb_i mb_{i+1} .. mb_{last row of the chunk}       (in-chunk suffix)
+// and tvs[q] = TV at the row.  The in-chunk products turn both carry
+// corrections into one multiply-add per row, with their loads issued before
+// the block scan that precedes them.  post(n, tv, v) gets the row's grid
+// index and potential factor.
+template <typename C, typename TT, int T, int CMAX, int N, class Post>
+__device__ __forceinline__ void strip_cn_1d(C* S, const C* __restrict__ cn, const TT* __restrict__ tvs,
+                                            int nb, int blk0, int tid, C* scan, Post post) {
+    const int ch = (nb + T - 1) / T;             // host guarantees ch <= CMAX
+    const int P = ch * T;
+    const int i0 = tid * ch;
+    C y[CMAX], pf[CMAX];
+    C Mp; Mp.x = 1; Mp.y = 0;
+    C yl; yl.x = 0; yl.y = 0;
+#pragma unroll
+    for (int c = 0; c < CMAX; ++c) {
+        const int q = c * T + tid;
+        if (c < ch && i0 + c < nb) {
+            const C rc = S[swz<C>((blk0 + i0 + c) & (N - 1))];
+            const C m = __ldg(&cn[q]);
+            pf[c] = __ldg(&cn[P + q]);
+            yl = cfma(m, yl, rc);
+            Mp = cmul(m, Mp);
+            y[c] = yl;
+        }
+    }
+    C carry = affine_carry<C, T, false>(Mp, yl, scan);
+    Mp.x = 1; Mp.y = 0;
+    C xl; xl.x = 0; xl.y = 0;
+#pragma unroll
+    for (int c = CMAX - 1; c >= 0; --c) {
+        const int q = c * T + tid;
+        if (c < ch && i0 + c < nb) {
+            const C yc = cfma(pf[c], carry, y[c]);
+            const C m = __ldg(&cn[2 * P + q]);
+            xl = cfma(m, xl, cmul(__ldg(&cn[3 * P + q]), yc));
+            Mp = cmul(m, Mp);
+            y[c] = xl;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < CMAX; ++c) {
+        const int q = c * T + tid;
+        if (c < ch && i0 + c < nb) pf[c] = __ldg(&cn[4 * P + q]);
+    }
+    carry = affine_carry<C, T, true>(Mp, xl, scan);
+#pragma unroll
+    for (int c = 0; c < CMAX; ++c) {
+        const int q = c * T + tid;
+        if (c < ch && i0 + c < nb) {
+            const C xv = cfma(pf[c], carry, y[c]);
+            const int n = (blk0 + i0 + c) & (N - 1);
+            const C rc = S[swz<C>(n)];
+            S[swz<C>(n)] = post(n, __ldg(&tvs[q]), cmk<C>(2 * xv.x - rc.x, 2 * xv.y - rc.y));
+        }
+    }
+}
+
 __device__ __forceinline__ void sincos_r(float a, float* s, float* c) { sincosf(a, s, c); }
 __device__ __forceinline__ void sincos_r(double a, double* s, double* c) { sincos(a, s, c); }
+
+// ---------------------------------------------------------------------------
+// Pieces of the resident step kernel.  Twiddles are read from a shared-memory
+// copy; the last forward pass, the k-space factor and the first inverse pass
+// run as one in-register butterfly; the potential factor is applied as the
+// last inverse pass stores its outputs.
+
+template <typename R, int LOGN, int LOGRM>
+struct Step1D {
+    static constexpr int NPASS = LOGN / LOGRM + ((LOGN % LOGRM) ? 1 : 0);
+    static constexpr int TWN = TwCount<LOGN, LOGRM>::value;
+    static constexpr int LOGR0 = PassGeom<LOGN, LOGRM, 0>::LOGR;   // radix of pass 0
+    static constexpr int R0 = 1 << LOGR0;
+};
+
+// shared-memory bytes of soft1d_kernel: state, twiddles, scan scratch, field
+// phases (E per-butterfly, 16 per-output, 4 clamped, 16 strip rows inside R0)
+template <typename R, int LOGN, int LOGE, int LOGRM>
+__host__ __device__ constexpr size_t soft1d_smem() {
+    return sizeof(typename CT<R>::C) *
+               ((size_t(1) << LOGN) + TwCount<LOGN, LOGRM>::value + 64 + (size_t(1) << LOGE) + 36) + 64;
+}
+
+template <typename R, int LOGN, int LOGE, int LOGRM, int P, int PEND>
+__device__ __forceinline__ void fwd_passes(typename CT<R>::C* S, const typename CT<R>::C* Ws, int tid) {
+    if constexpr (P < PEND) {
+        fwd_pass<R, LOGN, LOGE, LOGRM, P, true>(S, Ws, tid);
+        __syncthreads();
+        fwd_passes<R, LOGN, LOGE, LOGRM, P + 1, PEND>(S, Ws, tid);
+    }
+}
+template <typename R, int LOGN, int LOGE, int LOGRM, int P, int PSTOP>
+__device__ __forceinline__ void inv_passes(typename CT<R>::C* S, const typename CT<R>::C* Ws, int tid) {
+    if constexpr (P >= PSTOP) {
+        inv_pass<R, LOGN, LOGE, LOGRM, P, true>(S, Ws, tid);
+        __syncthreads();
+        inv_passes<R, LOGN, LOGE, LOGRM, P - 1, PSTOP>(S, Ws, tid);
+    }
+}
+
+// last forward pass (stride 1, no twiddles), the k-space table, the first
+// inverse pass: butterfly b owns the R consecutive points b*R + m of the
+// digit-reversed spectrum, whose factors the table holds at m*(N/R) + b
+template <typename R, int LOGN, int LOGE, int LOGRM>
+__device__ __forceinline__ void kcenter(typename CT<R>::C* S, const typename TabT<R>::T* __restrict__ tab,
+                                        int tid) {
+    using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
+    using C = typename K::C;
+    using G = PassGeom<LOGN, LOGRM, K::NPASS - 1>;
+    static_assert(G::S == 1, "the last pass has stride 1");
+    constexpr int LOGR = G::LOGR, RR = 1 << LOGR;
+    using TT = typename TabT<R>::T;
+    constexpr int NU = K::E / RR;
+    // the table entries of butterfly u + 1 are requested before butterfly u
+    // is computed (radix <= 4: the loads of one butterfly alone would leave
+    // the L2 latency exposed)
+    constexpr bool PF = RR <= 4 && NU > 1;
+    TT tn[PF ? RR : 1];
+    if constexpr (PF) {
+#pragma unroll
+        for (int m = 0; m < RR; ++m) tn[m] = __ldg(&tab[m * (K::N / RR) + tid]);
+    }
+#pragma unroll 1
+    for (int u = 0; u < NU; ++u) {
+        const int base = (tid + u * K::T) * RR;
+        TT tc[RR];
+        if constexpr (PF) {
+#pragma unroll
+            for (int m = 0; m < RR; ++m) tc[m] = tn[m];
+            if (u + 1 < NU) {
+#pragma unroll
+                for (int m = 0; m < RR; ++m) tn[m] = __ldg(&tab[m * (K::N / RR) + tid + (u + 1) * K::T]);
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < RR; ++m) tc[m] = __ldg(&tab[m * (K::N / RR) + tid + u * K::T]);
+        }
+        C v[RR];
+#pragma unroll
+        for (int j = 0; j < RR; ++j) v[j] = S[swz<C>(base + j)];
+        dft_reg<C, RR, -1>(v);
+        C w[RR];
+#pragma unroll
+        for (int m = 0; m < RR; ++m) w[m] = tmul(v[bitrev_c(m, LOGR)], tc[m]);
+        dft_reg<C, RR, +1>(w);
+#pragma unroll
+        for (int m = 0; m < RR; ++m) S[swz<C>(base + m)] = w[bitrev_c(m, LOGR)];
+    }
+}
+
+// Field phases of one step, alpha = tau E(t + tau/2)/2 (the half factor
+// exp(-i alpha x)), at fr[]: [u] = exp(-i alpha u T h) for the butterflies of
+// the last inverse pass (u < E/R0); [E + m] = exp(-i alpha m (N/R0) h) for
+// their outputs (m < R0); [E + 16], [E + 17] = the clamped values beyond +R0
+// and -R0; [E + 20 + k] = exp(-i alpha x_n) at n = iL + k and [E + 28 + k] at
+// n = iR - 8 + k (k < 8), the strip rows just inside R0.
+template <typename R, int LOGN, int LOGE, int LOGRM>
+__device__ __forceinline__ void field_setup(typename CT<R>::C* fr, R al, const Inst1D& I, int tid) {
+    using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
+    using C = typename K::C;
+    using Q = Step1D<R, LOGN, LOGRM>;
+    constexpr int NB = K::E / Q::R0;
+    for (int i = tid; i < NB + Q::R0 + 17; i += K::T) {
+        R sv, cv;
+        if (i < NB) {
+            sincos_r(-al * ((R)(i * K::T) * (R)I.h), &sv, &cv);
+            fr[i] = cmk<C>(cv, sv);
+        } else if (i < NB + Q::R0) {
+            const int m = i - NB;
+            sincos_r(-al * ((R)(m * (K::N / Q::R0)) * (R)I.h), &sv, &cv);
+            fr[K::E + m] = cmk<C>(cv, sv);
+        } else if (i == NB + Q::R0) {
+            sincos_r(-al * (R)I.R0, &sv, &cv);
+            fr[K::E + 16] = cmk<C>(cv, sv);      // x >= R0
+            fr[K::E + 17] = cmk<C>(cv, -sv);     // x <= -R0
+        } else {
+            const int k = i - (NB + Q::R0 + 1);  // 0..15
+            const int n = k < 8 ? I.iL + k : I.iR - 16 + k;
+            sincos_r(-al * ((R)I.x0 + (R)n * (R)I.h), &sv, &cv);
+            fr[K::E + 20 + k] = cmk<C>(cv, sv);
+        }
+    }
+}
+
+// Inverse pass 0; with V set, followed by the potential factor of the next
+// step on every output: the full e^{-iU tau} off the strip block, the half
+// factor on it (U = U0(z) + E(t + tau/2) x, Sec. II under Eq. SSFFT).
+template <typename R, int LOGN, int LOGE, int LOGRM>
+__device__ __forceinline__ void inv_pass0_v(typename CT<R>::C* S, const typename CT<R>::C* __restrict__ Ws,
+                                            const typename TabT<R>::T* __restrict__ TV,
+                                            const typename CT<R>::C* fr, R al, const Inst1D& I, int tid,
+                                            bool V) {
+    using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
+    using C = typename K::C;
+    using G = PassGeom<LOGN, LOGRM, 0>;
+    constexpr int N = K::N;
+    constexpr int LOGR = G::LOGR, RR = 1 << LOGR;
+    constexpr int s = G::S;                    // = N / RR
+    constexpr int NB = G::LOGR;
+    const int nb = I.nb, blk0 = I.blk0, iL = I.iL, iR = I.iR;
+    const bool fld = V && I.has_field;
+    C ft; ft.x = 1; ft.y = 0;
+    C fcR = ft, fcL = ft;
+    if (fld) {
+        R sv, cv; sincos_r(-al * ((R)I.x0 + (R)tid * (R)I.h), &sv, &cv);
+        ft = cmk<C>(cv, sv);
+        fcR = fr[K::E + 16];
+        fcL = fr[K::E + 17];
+    }
+#pragma unroll 1
+    for (int u = 0; u < K::E / RR; ++u) {
+        const int off = tid + u * K::T;        // L = N: a single block
+        C v[RR];
+        C tb[4];
+        if constexpr (s > 1) load_tw<C, NB, s, true>(tb, Ws + G::TOFF + off);
+        LoadInv<C, RR, 0>::run(S, v, tb, off, s, s > 1);
+        dft_reg<C, RR, +1>(v);
+        if (!V) {
+            StoreNat<C, RR, 0>::run(S, v, off, s);
+            continue;
+        }
+        const C fb = fld ? cmul(ft, fr[u]) : ft;
+#pragma unroll
+        for (int m = 0; m < RR; ++m) {
+            const int n = off + m * s;
+            C x = tmul(v[bitrev_c(m, LOGR)], __ldg(&TV[n]));
+            if (fld) {
+                const C fh = cmul(fb, fr[K::E + m]);          // exp(-i alpha x_n)
+                const C ff = cmul(fh, fh);
+                const bool inb = ((n - blk0) & (N - 1)) < nb;
+                const C fk = n >= iR ? fcR : (n < iL ? fcL : fh);
+                x = cmul(x, inb ? fk : ff);
+            }
+            S[swz<C>(n)] = x;
+        }
+    }
+}
+
+// exp(-i alpha x_n) computed directly (strip rows inside R0 that the table
+// of field_setup does not cover; kept out of line: not taken for contours
+// whose strip block ends next to R0)
+template <typename R, typename C>
+__device__ __noinline__ C field_direct(R al, double x0, double h, int n) {
+    R sv, cv;
+    sincos_r(-al * ((R)x0 + (R)n * (R)h), &sv, &cv);
+    return cmk<C>(cv, sv);
+}
+
+// half field factor on strip row n: clamped beyond +-R0, else exp(-i alpha x_n)
+template <typename R, typename C, int E>
+__device__ __forceinline__ C strip_field(const C* fr, R al, const Inst1D& I, int n) {
+    if (n >= I.iR) return fr[E + 16];
+    if (n < I.iL) return fr[E + 17];
+    if (n < I.iL + 8) return fr[E + 20 + (n - I.iL)];
+    if (n >= I.iR - 8) return fr[E + 28 + (n - (I.iR - 8))];
+    return field_direct<R, C>(al, I.x0, I.h, n);
+}
 
 template <typename R, int LOGN, int LOGE, int LOGRM>
 __global__ void __launch_bounds__(Cfg1D<R, LOGN, LOGE, LOGRM>::T, Cfg1D<R, LOGN, LOGE, LOGRM>::MINB)
@@ -273,13 +542,17 @@ soft1d_kernel(const Inst1D* __restrict__ insts, void* __restrict__ psi_base, int
               const double* __restrict__ ftab_base, int64_t ftab_stride, int* __restrict__ status)
 {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
+    using Q = Step1D<R, LOGN, LOGRM>;
     using C = typename K::C;
     constexpr int N = K::N, T = K::T, E = K::E;
+    static_assert(K::NPASS >= 2, "at least two FFT passes");
+    static_assert(Q::R0 <= 16, "pass radix <= 16");
+    static_assert(soft1d_smem<R, LOGN, LOGE, LOGRM>() <= 227 * 1024, "shared memory");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* S = reinterpret_cast<C*>(smem_raw);
-    C* scan = S + N;                 // 2*32 complex
-    C* fr = scan + 64;               // E complex: field ratio powers
-    C* fc = fr + E;                  // 4 complex: clamped field phases
+    C* Ws = S + N;                   // twiddles, TWN complex
+    C* scan = Ws + Q::TWN;           // 2*32 complex
+    C* fr = scan + 64;               // E + 36 complex: field phases (field_setup)
 
     const Inst1D I = insts[blockIdx.x];
     C* __restrict__ g_psi = reinterpret_cast<C*>(psi_base) + I.off;
@@ -289,89 +562,51 @@ soft1d_kernel(const Inst1D* __restrict__ insts, void* __restrict__ psi_base, int
     const TT* __restrict__ TKh = reinterpret_cast<const TT*>(I.TKh);
     const TT* __restrict__ TV = reinterpret_cast<const TT*>(I.TV);
     const C* __restrict__ cn = reinterpret_cast<const C*>(I.cn);
+    const TT* __restrict__ TVs = reinterpret_cast<const TT*>(I.TVs);
     const int tid = threadIdx.x;
     const int nb = I.nb, blk0 = I.blk0;
+    if (nsteps <= 0) return;
 
-    // load the state
+    // load the state and the twiddles
 #pragma unroll
     for (int j = 0; j < E; ++j) {
         const int n = tid + j * T;
         S[swz<C>(n)] = g_psi[n];
     }
+    for (int i = tid; i < Q::TWN; i += T) Ws[i] = __ldg(&W[i]);
     __syncthreads();
 
-    // first half-kinetic factor of this call
-    fwd_fft<R, LOGN, LOGE, LOGRM, 0>(S, W, tid);
-    kmul<R, LOGN, LOGE, LOGRM>(S, TKh, tid);
-    inv_fft<R, LOGN, LOGE, LOGRM, K::NPASS - 1>(S, W, tid);
-
     const double* __restrict__ ftab = I.has_field ? ftab_base + (int64_t)I.fcls * ftab_stride : nullptr;
-    for (int64_t step = 0; step < nsteps; ++step) {
-        // ---- field phase of this step: f_half(x) = exp(-i alpha xc), alpha = tau E(t+tau/2)/2
-        R al = 0;
-        if (I.has_field) {
-            al = (R)(0.5 * I.tau * I.E0 * __ldg(&ftab[step]));
-            if (tid < E) {                    // ratio powers exp(-i al j T h)
-                R sv, cv; sincos_r(-al * ((R)(tid * T) * (R)I.h), &sv, &cv);
-                fr[tid] = cmk<C>(cv, sv);
-            }
-            if (tid == 0) {
-                R sv, cv;
-                sincos_r(-al * (R)I.R0, &sv, &cv);
-                fc[0] = cmk<C>(cv, sv);      // x >= R0
-                fc[1] = cmk<C>(cv, -sv);     // x <= -R0
-            }
-            __syncthreads();
-        }
-        // ---- V on every point: full factor off the block, half on it
-        {
-            C base; base.x = 1; base.y = 0;
-            if (I.has_field) {
-                R sv, cv; sincos_r(-al * ((R)I.x0 + (R)tid * (R)I.h), &sv, &cv);
-                base = cmk<C>(cv, sv);
-            }
-#pragma unroll 4
-            for (int j = 0; j < E; ++j) {
-                const int n = tid + j * T;
-                C v = tmul(S[swz<C>(n)], __ldg(&TV[n]));
-                const bool inblk = ((n - blk0) & (N - 1)) < nb;
-                if (I.has_field) {
-                    C f = cmul(base, fr[j]);
-                    if (inblk) {
-                        if (n >= I.iR) f = fc[0];
-                        else if (n < I.iL) f = fc[1];
-                    } else {
-                        f = cmul(f, f);
-                    }
-                    v = cmul(v, f);
-                }
-                S[swz<C>(n)] = v;
-            }
-        }
-        __syncthreads();
+    // field amplitude of step s: alpha = tau E(t + tau/2) / 2
+    auto alpha = [&](int64_t st) -> R { return (R)(0.5 * I.tau * I.E0 * __ldg(&ftab[st])); };
+
+    // Pass step = -1 is the first half-kinetic factor of the call; every pass
+    // ends with the potential factor of the next step, applied as the last
+    // inverse FFT pass stores (none after the final half-kinetic factor).
+    R al = 0;
+    for (int64_t step = -1; step < nsteps; ++step) {
         // ---- Crank-Nicolson on the strip block, then the second e^{-iU tau/2}
-        if (nb > 0) {
-            strip_cn<C, T, K::CMAX, N>(S, cn, nb, blk0, tid, scan, [&](int n, C v) {
-                v = tmul(v, __ldg(&TV[n]));
-                if (I.has_field) {
-                    C f;
-                    if (n >= I.iR) f = fc[0];
-                    else if (n < I.iL) f = fc[1];
-                    else {
-                        R sv, cv;
-                        sincos_r(-al * ((R)I.x0 + (R)n * (R)I.h), &sv, &cv);
-                        f = cmk<C>(cv, sv);
-                    }
-                    v = cmul(v, f);
-                }
+        if (step >= 0 && nb > 0) {
+            strip_cn_1d<C, TT, T, K::CMAX, N>(S, cn, TVs, nb, blk0, tid, scan, [&](int n, const TT& tv, C v) {
+                v = tmul(v, tv);
+                if (I.has_field) v = cmul(v, strip_field<R, C, E>(fr, al, I, n));
                 return v;
             });
             __syncthreads();
         }
-        // ---- kinetic: forward FFT, e^{-iK tau} (or tau/2 on the last step), inverse FFT
-        fwd_fft<R, LOGN, LOGE, LOGRM, 0>(S, W, tid);
-        kmul<R, LOGN, LOGE, LOGRM>(S, step + 1 < nsteps ? TK : TKh, tid);
-        inv_fft<R, LOGN, LOGE, LOGRM, K::NPASS - 1>(S, W, tid);
+        // ---- kinetic: forward FFT, e^{-iK tau} (e^{-iK tau/2} in the first
+        //      and last pass of the call), inverse FFT, potential of the next step
+        const bool more = step + 1 < nsteps;
+        fwd_passes<R, LOGN, LOGE, LOGRM, 0, K::NPASS - 1>(S, Ws, tid);
+        kcenter<R, LOGN, LOGE, LOGRM>(S, (step >= 0 && more) ? TK : TKh, tid);
+        if (more && I.has_field) {
+            al = alpha(step + 1);
+            field_setup<R, LOGN, LOGE, LOGRM>(fr, al, I, tid);
+        }
+        __syncthreads();
+        inv_passes<R, LOGN, LOGE, LOGRM, K::NPASS - 2, 1>(S, Ws, tid);
+        inv_pass0_v<R, LOGN, LOGE, LOGRM>(S, Ws, TV, fr, al, I, tid, more);
+        __syncthreads();
     }
 
     // store
@@ -393,7 +628,7 @@ int launch_soft1d_t(const Inst1D* d_inst, int count, void* psi, int64_t nsteps,
 {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
     auto kern = soft1d_kernel<R, LOGN, LOGE, LOGRM>;
-    const size_t smem = K::SMEM;
+    const size_t smem = soft1d_smem<R, LOGN, LOGE, LOGRM>();
     if (smem > 48 * 1024) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return SOFT_ERR_CUDA;

@@ -48,9 +48,17 @@ int soft1d_variants(int prec, int logn, int* loge, int* logrm, int maxv) {
     return k;
 }
 
-size_t soft1d_smem_bytes(int prec, int logn, int loge) {
+// shared memory of soft1d_kernel (state, twiddles of every pass, scan
+// scratch, field phases)
+size_t soft1d_smem_bytes(int prec, int logn, int loge, int logrm) {
     const size_t c = prec == SOFT_C64 ? 8 : 16;
-    return c * ((size_t(1) << logn) + 64 + (size_t(1) << loge) + 4) + 64;
+    size_t tw = 0;
+    for (int logl = logn; logl > 0;) {
+        const int lr = logl >= logrm ? logrm : logl;
+        tw += 4 * (size_t(1) << (logl - lr));
+        logl -= lr;
+    }
+    return c * ((size_t(1) << logn) + tw + 64 + (size_t(1) << loge) + 16 + 4) + 64;
 }
 
 int launch_soft1d(int prec, int logn, int loge, int logrm, const Inst1D* d_inst, int count,

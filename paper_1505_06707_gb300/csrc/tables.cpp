@@ -222,14 +222,14 @@ static std::vector<int> pass_radices(int logn, int logrm) {
 }
 
 // Twiddle bases of the in-place FFT passes: for pass p (length L, stride
-// s = L/R) and off < s, the four values W_L^{off 2^k}, k = 0..3.
+// s = L/R) four rows of s values, row k holding W_L^{off 2^k} for off < s.
 std::vector<cd> pass_twiddles(int logn, int logrm) {
     std::vector<cd> out;
     int logl = logn;
     for (int lr : pass_radices(logn, logrm)) {
         const int L = 1 << logl, s = 1 << (logl - lr);
-        for (int off = 0; off < s; ++off)
-            for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 4; ++k)          // row k: W_L^{2^k off}, off < s
+            for (int off = 0; off < s; ++off) {
                 const long e = (long)off << k;
                 const double ang = -2.0 * PI * (double)(e % L) / (double)L;
                 out.push_back(cd(std::cos(ang), std::sin(ang)));
