@@ -107,37 +107,30 @@ int make_tables_1d(Tables1D* T, int n, double a, double b, double R0, double the
         tv[j] = std::exp(cd(0.0, -1.0) * T->U0[j] * tau * (inblk ? 0.5 : 1.0));
     }
     // Strip CN coefficients for the kernel's chunked solve: thread t of the
-    // T = n >> loge threads owns rows t*ch .. t*ch + ch - 1 (ch = ceil(nb/T));
-    // row i = t*ch + c is stored at c*T + t of five arrays (mf, the product of
-    // mf over the chunk up to row i, mb, g, the product of mb from row i to
-    // the chunk's end), and TV of the row at the same place of tvs.
+    // T = n >> loge threads owns rows t*ch .. t*ch + ch - 1 (ch = ceil(nb/T)).
+    // M is complex symmetric, so mb_i = mf_{i+1}: the kernel reads mf of rows
+    // t*ch + c, c <= ch, at c*T + t (0 past the block), then g of row t*ch + c
+    // at (ch+1)*T + c*T + t, and TV of the row at c*T + t of tvs.
     std::vector<cd> mf, mb, g, cnv, tvs;
     if (T->nb > 0) {
         double err = 0;
         rc = strip_factor(A, T->blk0, T->nb, mf, mb, g, &err);
         if (rc) return rc;
         const int thr = n >> loge, nb = T->nb;
-        const int ch = (nb + thr - 1) / thr, P = ch * thr;
-        cnv.assign(5 * (size_t)P, 0.0);
-        tvs.assign(P, 1.0);
-        for (int t = 0; t < thr; ++t) {
-            const int i0 = t * ch, i1 = std::min(i0 + ch, nb);
-            cd pf = 1.0, pb = 1.0;
-            for (int i = i0; i < i1; ++i) {
-                const size_t q = (size_t)(i - i0) * thr + t;
-                pf *= mf[i];
-                cnv[q] = mf[i];
-                cnv[P + q] = pf;
-                cnv[2 * (size_t)P + q] = mb[i];
-                cnv[3 * (size_t)P + q] = g[i];
-                tvs[q] = tv[(T->blk0 + i) % n];
+        for (int i = 0; i + 1 < nb; ++i)
+            if (std::abs(mb[i] - mf[i + 1]) > 1e-12 * (std::abs(mb[i]) + 1e-300)) return SOFT_ERR_SETUP;
+        const int ch = (nb + thr - 1) / thr, P1 = (ch + 1) * thr;
+        cnv.assign((size_t)P1 + (size_t)ch * thr, 0.0);
+        tvs.assign((size_t)ch * thr, 1.0);
+        for (int t = 0; t < thr; ++t)
+            for (int c = 0; c <= ch; ++c) {
+                const int i = t * ch + c;
+                if (i < nb) cnv[(size_t)c * thr + t] = mf[i];
+                if (c < ch && i < nb) {
+                    cnv[P1 + (size_t)c * thr + t] = g[i];
+                    tvs[(size_t)c * thr + t] = tv[(T->blk0 + i) % n];
+                }
             }
-            for (int i = i1 - 1; i >= i0; --i) {
-                const size_t q = (size_t)(i - i0) * thr + t;
-                pb *= mb[i];
-                cnv[4 * (size_t)P + q] = pb;
-            }
-        }
     }
     if ((rc = upload_tab(&T->TK, tk, o.prec))) return rc;
     if ((rc = upload_tab(&T->TKh, tkh, o.prec))) return rc;

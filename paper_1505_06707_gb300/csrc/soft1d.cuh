@@ -273,65 +273,67 @@ __device__ __forceinline__ void strip_cn(C* S, const C* __restrict__ cn, int nb,
     }
 }
 
-// The same solve for the 1D step kernel with the coefficients laid out by the
-// host for coalesced reads: with P = ch*T (ch = ceil(nb/T) rows per thread),
-// row i = t*ch + c of thread t sits at q = c*T + t of the arrays
-//   cn[0 P..]: mf_i          cn[1 P..]: mf_i mf_{i-1} .. mf_{t ch}  (in-chunk prefix)
-//   cn[2 P..]: mb_i          cn[3 P..]: g_i
-//   cn[4 P..]: mb_i mb_{i+1} .. mb_{last row of the chunk}       (in-chunk suffix)
-// and tvs[q] = TV at the row.  The in-chunk products turn both carry
-// corrections into one multiply-add per row, with their loads issued before
-// the block scan that precedes them.  post(n, tv, v) gets the row's grid
-// index and potential factor.
+// The same solve for the 1D step kernel.  M is complex symmetric (C is,
+// Sec. II), so mb_i = mf_{i+1} and one multiplier array serves both sweeps.
+// The host lays the coefficients out for coalesced reads: thread t owns rows
+// i0 = t*ch .. i0 + ch - 1 (ch = ceil(nb/T)); cn[c*T + t] = mf_{i0+c} for
+// c <= ch (0 past the block), cn[(ch+1)*T + c*T + t] = g_{i0+c}, and
+// tvs[c*T + t] = TV at row i0 + c.  Every coefficient is read once, before
+// the sweep that uses it; the in-chunk products of the carry corrections are
+// formed from registers.  post(n, tv, v) gets the row's grid index and potential.
 template <typename C, typename TT, int T, int CMAX, int N, class Post>
 __device__ __forceinline__ void strip_cn_1d(C* S, const C* __restrict__ cn, const TT* __restrict__ tvs,
                                             int nb, int blk0, int tid, C* scan, Post post) {
     const int ch = (nb + T - 1) / T;             // host guarantees ch <= CMAX
-    const int P = ch * T;
+    const int P1 = (ch + 1) * T;
     const int i0 = tid * ch;
-    C y[CMAX], pf[CMAX];
+    const int nv = min(ch, nb - i0);             // rows of this thread (may be <= 0)
+    C y[CMAX], m[CMAX + 1];
+#pragma unroll
+    for (int c = 0; c <= CMAX; ++c)
+        if (c <= ch) m[c] = __ldg(&cn[c * T + tid]);
     C Mp; Mp.x = 1; Mp.y = 0;
     C yl; yl.x = 0; yl.y = 0;
 #pragma unroll
     for (int c = 0; c < CMAX; ++c) {
-        const int q = c * T + tid;
-        if (c < ch && i0 + c < nb) {
+        if (c < nv) {
             const C rc = S[swz<C>((blk0 + i0 + c) & (N - 1))];
-            const C m = __ldg(&cn[q]);
-            pf[c] = __ldg(&cn[P + q]);
-            yl = cfma(m, yl, rc);
-            Mp = cmul(m, Mp);
+            yl = cfma(m[c], yl, rc);
+            Mp = cmul(m[c], Mp);
             y[c] = yl;
         }
     }
     C carry = affine_carry<C, T, false>(Mp, yl, scan);
+    {
+        C pr; pr.x = 1; pr.y = 0;
+#pragma unroll
+        for (int c = 0; c < CMAX; ++c) {
+            if (c < nv) {
+                pr = cmul(m[c], pr);
+                y[c] = cfma(pr, carry, y[c]);
+            }
+        }
+    }
     Mp.x = 1; Mp.y = 0;
     C xl; xl.x = 0; xl.y = 0;
 #pragma unroll
     for (int c = CMAX - 1; c >= 0; --c) {
-        const int q = c * T + tid;
-        if (c < ch && i0 + c < nb) {
-            const C yc = cfma(pf[c], carry, y[c]);
-            const C m = __ldg(&cn[2 * P + q]);
-            xl = cfma(m, xl, cmul(__ldg(&cn[3 * P + q]), yc));
-            Mp = cmul(m, Mp);
+        if (c < nv) {
+            xl = cfma(m[c + 1], xl, cmul(__ldg(&cn[P1 + c * T + tid]), y[c]));
+            Mp = cmul(m[c + 1], Mp);
             y[c] = xl;
         }
     }
-#pragma unroll
-    for (int c = 0; c < CMAX; ++c) {
-        const int q = c * T + tid;
-        if (c < ch && i0 + c < nb) pf[c] = __ldg(&cn[4 * P + q]);
-    }
     carry = affine_carry<C, T, true>(Mp, xl, scan);
+    C pr; pr.x = 1; pr.y = 0;
 #pragma unroll
-    for (int c = 0; c < CMAX; ++c) {
-        const int q = c * T + tid;
-        if (c < ch && i0 + c < nb) {
-            const C xv = cfma(pf[c], carry, y[c]);
+    for (int c = CMAX - 1; c >= 0; --c) {
+        if (c < nv) {
+            pr = cmul(m[c + 1], pr);
+            const C xv = cfma(pr, carry, y[c]);
             const int n = (blk0 + i0 + c) & (N - 1);
             const C rc = S[swz<C>(n)];
-            S[swz<C>(n)] = post(n, __ldg(&tvs[q]), cmk<C>(2 * xv.x - rc.x, 2 * xv.y - rc.y));
+            S[swz<C>(n)] = post(n, __ldg(&tvs[c * T + tid]), cmk<C>(2 * xv.x - rc.x, 2 * xv.y - rc.y));
         }
     }
 }

@@ -105,13 +105,15 @@ void build_axis(Axis1D& A, int n, double a, double b, const ContourFn& cf, doubl
     }
     const double c = -0.5 / (A.h * A.h);
     A.Cs.resize(n); A.Cd.resize(n); A.Cu.resize(n);
+    // the coupling of j and j+1 is one product, stored as C[j][j+1] and
+    // C[j+1][j], so that C is symmetric to the last bit (the strip solve
+    // uses one multiplier array for both sweeps)
     for (int j = 0; j < n; ++j) {
         const int jm = (j + n - 1) % n, jp = (j + 1) % n;
-        const cd sup = c * qh[j] * qh[jp] * iqm[j];
-        const cd sub = c * qh[j] * qh[jm] * iqm[jm];
+        const cd e = c * qh[j] * qh[jp] * iqm[j] - c;
         const cd dia = -c * qh[j] * qh[j] * (iqm[j] + iqm[jm]);
-        A.Cu[j] = sup - c;
-        A.Cs[j] = sub - c;
+        A.Cu[j] = e;
+        A.Cs[jp] = e;
         A.Cd[j] = dia + 2.0 * c;
     }
     A.tau = tau;
