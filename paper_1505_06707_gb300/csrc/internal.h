@@ -20,7 +20,7 @@ struct Inst1D {
     int64_t off;          // element offset of the instance in the packed state
     const void* TK;       // e^{-i k^2 tau/2}/N, forward FFT output order, last-pass transposed
     const void* TKh;      // e^{-i k^2 tau/4}/N, same order (first/last half step)
-    const void* TV;       // e^{-iU0 tau} off the strip block, e^{-iU0 tau/2} on it
+    const void* TV;       // e^{-iU0 tau} off the strip block, e^{-iU0 tau/2} on it (minus 1 for complex64)
     const void* W;        // per-pass twiddle bases (see soft1d.cuh)
     const void* cn;       // strip CN coefficients, chunk-transposed (soft1d.cuh, strip_cn_1d)
     const void* TVs;      // TV on the strip rows, same transposed order

@@ -42,6 +42,18 @@ int upload_tab(void** dst, const std::vector<cd>& v, int prec) {
     return upload(dst, buf.data(), buf.size() * sizeof(float));
 }
 
+// potential factor table: the factor itself (double2) for complex128 plans;
+// its difference from 1 (float2) for complex64 plans
+int upload_vtab(void** dst, const std::vector<cd>& v, int prec) {
+    if (prec == SOFT_C128) return upload_c(dst, v, prec);
+    std::vector<float> buf(2 * v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+        buf[2 * i] = (float)(v[i].real() - 1.0);
+        buf[2 * i + 1] = (float)v[i].imag();
+    }
+    return upload(dst, buf.data(), buf.size() * sizeof(float));
+}
+
 // round a complex FP64 vector to the plan precision and upload it
 int upload_c(void** dst, const std::vector<cd>& v, int prec) {
     if (prec == SOFT_C128) {
@@ -134,10 +146,10 @@ int make_tables_1d(Tables1D* T, int n, double a, double b, double R0, double the
     }
     if ((rc = upload_tab(&T->TK, tk, o.prec))) return rc;
     if ((rc = upload_tab(&T->TKh, tkh, o.prec))) return rc;
-    if ((rc = upload_tab(&T->TV, tv, o.prec))) return rc;
+    if ((rc = upload_vtab(&T->TV, tv, o.prec))) return rc;
     if ((rc = upload_c(&T->W, w, o.prec))) return rc;
     if ((rc = upload_c(&T->cn, cnv, o.prec))) return rc;
-    if ((rc = upload_tab(&T->TVs, tvs, o.prec))) return rc;
+    if ((rc = upload_vtab(&T->TVs, tvs, o.prec))) return rc;
     return SOFT_OK;
 }
 

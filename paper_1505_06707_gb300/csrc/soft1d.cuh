@@ -35,6 +35,18 @@ __device__ __forceinline__ float2 tmul(float2 x, float4 t) {
 }
 __device__ __forceinline__ double2 tmul(double2 x, double2 t) { return cmul(x, t); }
 
+// Potential phase tables: e^{-iU0 tau} (or its half) stays within |U0 tau| of
+// 1, so complex64 plans store d = e^{-iU0 tau} - 1 (FP64 difference rounded to
+// FP32, error below |d| 2^-24) and apply psi + psi d; complex128 plans store
+// the factor itself.
+template <typename R> struct VabT;
+template <> struct VabT<float> { using T = float2; };
+template <> struct VabT<double> { using T = double2; };
+__device__ __forceinline__ float2 vmul(float2 x, float2 d) {
+    return make_float2(fmaf(x.x, d.x, fmaf(-x.y, d.y, x.x)), fmaf(x.x, d.y, fmaf(x.y, d.x, x.y)));
+}
+__device__ __forceinline__ double2 vmul(double2 x, double2 t) { return cmul(x, t); }
+
 template <typename R, int LOGN, int LOGE, int LOGRM>
 struct Cfg1D {
     using C = typename CT<R>::C;
@@ -281,8 +293,8 @@ __device__ __forceinline__ void strip_cn(C* S, const C* __restrict__ cn, int nb,
 // tvs[c*T + t] = TV at row i0 + c.  Every coefficient is read once, before
 // the sweep that uses it; the in-chunk products of the carry corrections are
 // formed from registers.  post(n, tv, v) gets the row's grid index and potential.
-template <typename C, typename TT, int T, int CMAX, int N, class Post>
-__device__ __forceinline__ void strip_cn_1d(C* S, const C* __restrict__ cn, const TT* __restrict__ tvs,
+template <typename C, typename VT, int T, int CMAX, int N, class Post>
+__device__ __forceinline__ void strip_cn_1d(C* S, const C* __restrict__ cn, const VT* __restrict__ tvs,
                                             int nb, int blk0, int tid, C* scan, Post post) {
     const int ch = (nb + T - 1) / T;             // host guarantees ch <= CMAX
     const int P1 = (ch + 1) * T;
@@ -469,7 +481,7 @@ __device__ __forceinline__ void field_setup(typename CT<R>::C* fr, R al, const I
 // factor on it (U = U0(z) + E(t + tau/2) x, Sec. II under Eq. SSFFT).
 template <typename R, int LOGN, int LOGE, int LOGRM>
 __device__ __forceinline__ void inv_pass0_v(typename CT<R>::C* S, const typename CT<R>::C* __restrict__ Ws,
-                                            const typename TabT<R>::T* __restrict__ TV,
+                                            const typename VabT<R>::T* __restrict__ TV,
                                             const typename CT<R>::C* fr, R al, const Inst1D& I, int tid,
                                             bool V) {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
@@ -501,13 +513,14 @@ __device__ __forceinline__ void inv_pass0_v(typename CT<R>::C* S, const typename
             StoreNat<C, RR, 0>::run(S, v, off, s);
             continue;
         }
-        const C fb = fld ? cmul(ft, fr[u]) : ft;
+        C fb = ft;
+        if (fld) fb = cmul(ft, fr[u]);
 #pragma unroll
         for (int m = 0; m < RR; ++m) {
             const int n = off + m * s;
-            C x = tmul(v[bitrev_c(m, LOGR)], __ldg(&TV[n]));
-            if (fld) {
-                const C fh = cmul(fb, fr[K::E + m]);          // exp(-i alpha x_n)
+            C x = vmul(v[bitrev_c(m, LOGR)], __ldg(&TV[n]));
+            if (fld) {        // branch-free, so that the table loads of all m issue early
+                const C fh = cmul(fb, fr[K::E + m]);              // exp(-i alpha x_n)
                 const C ff = cmul(fh, fh);
                 const bool inb = ((n - blk0) & (N - 1)) < nb;
                 const C fk = n >= iR ? fcR : (n < iL ? fcL : fh);
@@ -562,9 +575,10 @@ soft1d_kernel(const Inst1D* __restrict__ insts, void* __restrict__ psi_base, int
     using TT = typename K::TT;
     const TT* __restrict__ TK = reinterpret_cast<const TT*>(I.TK);
     const TT* __restrict__ TKh = reinterpret_cast<const TT*>(I.TKh);
-    const TT* __restrict__ TV = reinterpret_cast<const TT*>(I.TV);
+    using VT = typename VabT<R>::T;
+    const VT* __restrict__ TV = reinterpret_cast<const VT*>(I.TV);
     const C* __restrict__ cn = reinterpret_cast<const C*>(I.cn);
-    const TT* __restrict__ TVs = reinterpret_cast<const TT*>(I.TVs);
+    const VT* __restrict__ TVs = reinterpret_cast<const VT*>(I.TVs);
     const int tid = threadIdx.x;
     const int nb = I.nb, blk0 = I.blk0;
     if (nsteps <= 0) return;
@@ -589,8 +603,8 @@ soft1d_kernel(const Inst1D* __restrict__ insts, void* __restrict__ psi_base, int
     for (int64_t step = -1; step < nsteps; ++step) {
         // ---- Crank-Nicolson on the strip block, then the second e^{-iU tau/2}
         if (step >= 0 && nb > 0) {
-            strip_cn_1d<C, TT, T, K::CMAX, N>(S, cn, TVs, nb, blk0, tid, scan, [&](int n, const TT& tv, C v) {
-                v = tmul(v, tv);
+            strip_cn_1d<C, VT, T, K::CMAX, N>(S, cn, TVs, nb, blk0, tid, scan, [&](int n, const VT& tv, C v) {
+                v = vmul(v, tv);
                 if (I.has_field) v = cmul(v, strip_field<R, C, E>(fr, al, I, n));
                 return v;
             });

@@ -58,7 +58,7 @@ size_t soft1d_smem_bytes(int prec, int logn, int loge, int logrm) {
         tw += 4 * (size_t(1) << (logl - lr));
         logl -= lr;
     }
-    return c * ((size_t(1) << logn) + tw + 64 + (size_t(1) << loge) + 16 + 4) + 64;
+    return c * ((size_t(1) << logn) + tw + 64 + (size_t(1) << loge) + 36) + 64;
 }
 
 int launch_soft1d(int prec, int logn, int loge, int logrm, const Inst1D* d_inst, int count,
