@@ -33,10 +33,11 @@ template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s)
 
 // XOR swizzle of a shared-memory complex array: 128-byte rows, the column
 // index is XORed with the row index so that strided butterfly accesses of
-// every stride spread over all banks.
-template <typename C> __device__ __forceinline__ int swz(int i) {
-    if (sizeof(C) == 8) return i ^ ((i >> 4) & 15);
-    return i ^ ((i >> 3) & 7);
+// every stride spread over all banks.  The map is linear over XOR, so for a
+// butterfly whose element offsets j*s share no bits with its base,
+// swz(base + j*s) = swz(base) ^ swz(j*s) with the second term a constant.
+template <typename C> __host__ __device__ __forceinline__ constexpr int swz(int i) {
+    return sizeof(C) == 8 ? (i ^ ((i >> 4) & 15)) : (i ^ ((i >> 3) & 7));
 }
 
 // ---------------------------------------------------------------------------

@@ -91,31 +91,33 @@ __device__ __forceinline__ C tw_pow(const C* b) {
     }
 }
 
-template <typename C, int RR, int M>
+// The element M of a butterfly lives at base + M s; the callers pass
+// sb = swz(base) and the offset of element M is the constant swz(M s).
+template <typename C, int RR, int SS, int M>
 struct StoreFwd {   // y_M = v[bitrev(M)] * W^{M off}, stored at base + M s
-    __device__ __forceinline__ static void run(C* S, const C* v, const C* b, int base, int s, bool tw) {
+    __device__ __forceinline__ static void run(C* S, const C* v, const C* b, int sb, bool tw) {
         constexpr int LOGR = (RR == 16) ? 4 : (RR == 8) ? 3 : (RR == 4) ? 2 : (RR == 2) ? 1 : 0;
         C y = v[bitrev_c(M, LOGR)];
         if constexpr (M > 0) { if (tw) y = cmul(y, tw_pow<C, M>(b)); }
-        S[swz<C>(base + M * s)] = y;
-        if constexpr (M + 1 < RR) StoreFwd<C, RR, M + 1>::run(S, v, b, base, s, tw);
+        S[sb ^ swz<C>(M * SS)] = y;
+        if constexpr (M + 1 < RR) StoreFwd<C, RR, SS, M + 1>::run(S, v, b, sb, tw);
     }
 };
-template <typename C, int RR, int M>
+template <typename C, int RR, int SS, int M>
 struct LoadInv {    // v_M = S[base + M s] * conj(W^{M off})
-    __device__ __forceinline__ static void run(const C* S, C* v, const C* b, int base, int s, bool tw) {
-        C y = S[swz<C>(base + M * s)];
+    __device__ __forceinline__ static void run(const C* S, C* v, const C* b, int sb, bool tw) {
+        C y = S[sb ^ swz<C>(M * SS)];
         if constexpr (M > 0) { if (tw) y = cmulc(y, tw_pow<C, M>(b)); }
         v[M] = y;
-        if constexpr (M + 1 < RR) LoadInv<C, RR, M + 1>::run(S, v, b, base, s, tw);
+        if constexpr (M + 1 < RR) LoadInv<C, RR, SS, M + 1>::run(S, v, b, sb, tw);
     }
 };
-template <typename C, int RR, int M>
+template <typename C, int RR, int SS, int M>
 struct StoreNat {   // x_M = v[bitrev(M)] stored at base + M s
-    __device__ __forceinline__ static void run(C* S, const C* v, int base, int s) {
+    __device__ __forceinline__ static void run(C* S, const C* v, int sb) {
         constexpr int LOGR = (RR == 16) ? 4 : (RR == 8) ? 3 : (RR == 4) ? 2 : (RR == 2) ? 1 : 0;
-        S[swz<C>(base + M * s)] = v[bitrev_c(M, LOGR)];
-        if constexpr (M + 1 < RR) StoreNat<C, RR, M + 1>::run(S, v, base, s);
+        S[sb ^ swz<C>(M * SS)] = v[bitrev_c(M, LOGR)];
+        if constexpr (M + 1 < RR) StoreNat<C, RR, SS, M + 1>::run(S, v, sb);
     }
 };
 
@@ -149,14 +151,14 @@ __device__ __forceinline__ void fwd_pass(typename CT<R>::C* S, const typename CT
     for (int u = 0; u < K::E / RR; ++u) {      // one butterfly live at a time
         const int b = tid + u * K::T;
         const int blk = b / s, off = b & (s - 1);
-        const int base = blk * L + off;
+        const int sb = swz<C>(blk * L + off);
         C v[RR];
 #pragma unroll
-        for (int j = 0; j < RR; ++j) v[j] = S[swz<C>(base + j * s)];
+        for (int j = 0; j < RR; ++j) v[j] = S[sb ^ swz<C>(j * s)];
         dft_reg<C, RR, -1>(v);
         C tb[4];
         if constexpr (s > 1) load_tw<C, NB, s, SH>(tb, W + G::TOFF + off);
-        StoreFwd<C, RR, 0>::run(S, v, tb, base, s, s > 1);
+        StoreFwd<C, RR, s, 0>::run(S, v, tb, sb, s > 1);
     }
 }
 
@@ -175,13 +177,13 @@ __device__ __forceinline__ void inv_pass(typename CT<R>::C* S, const typename CT
     for (int u = 0; u < K::E / RR; ++u) {      // one butterfly live at a time
         const int b = tid + u * K::T;
         const int blk = b / s, off = b & (s - 1);
-        const int base = blk * L + off;
+        const int sb = swz<C>(blk * L + off);
         C v[RR];
         C tb[4];
         if constexpr (s > 1) load_tw<C, NB, s, SH>(tb, W + G::TOFF + off);
-        LoadInv<C, RR, 0>::run(S, v, tb, base, s, s > 1);
+        LoadInv<C, RR, s, 0>::run(S, v, tb, sb, s > 1);
         dft_reg<C, RR, +1>(v);
-        StoreNat<C, RR, 0>::run(S, v, base, s);
+        StoreNat<C, RR, s, 0>::run(S, v, sb);
     }
 }
 
@@ -429,16 +431,17 @@ __device__ __forceinline__ void kcenter(typename CT<R>::C* S, const typename Tab
 #pragma unroll
             for (int m = 0; m < RR; ++m) tc[m] = __ldg(&tab[m * (K::N / RR) + tid + u * K::T]);
         }
+        const int sb = swz<C>(base);
         C v[RR];
 #pragma unroll
-        for (int j = 0; j < RR; ++j) v[j] = S[swz<C>(base + j)];
+        for (int j = 0; j < RR; ++j) v[j] = S[sb ^ swz<C>(j)];
         dft_reg<C, RR, -1>(v);
         C w[RR];
 #pragma unroll
         for (int m = 0; m < RR; ++m) w[m] = tmul(v[bitrev_c(m, LOGR)], tc[m]);
         dft_reg<C, RR, +1>(w);
 #pragma unroll
-        for (int m = 0; m < RR; ++m) S[swz<C>(base + m)] = w[bitrev_c(m, LOGR)];
+        for (int m = 0; m < RR; ++m) S[sb ^ swz<C>(m)] = w[bitrev_c(m, LOGR)];
     }
 }
 
@@ -504,13 +507,14 @@ __device__ __forceinline__ void inv_pass0_v(typename CT<R>::C* S, const typename
 #pragma unroll 1
     for (int u = 0; u < K::E / RR; ++u) {
         const int off = tid + u * K::T;        // L = N: a single block
+        const int sb = swz<C>(off);
         C v[RR];
         C tb[4];
         if constexpr (s > 1) load_tw<C, NB, s, true>(tb, Ws + G::TOFF + off);
-        LoadInv<C, RR, 0>::run(S, v, tb, off, s, s > 1);
+        LoadInv<C, RR, s, 0>::run(S, v, tb, sb, s > 1);
         dft_reg<C, RR, +1>(v);
         if (!V) {
-            StoreNat<C, RR, 0>::run(S, v, off, s);
+            StoreNat<C, RR, s, 0>::run(S, v, sb);
             continue;
         }
         C fb = ft;
@@ -526,7 +530,7 @@ __device__ __forceinline__ void inv_pass0_v(typename CT<R>::C* S, const typename
                 const C fk = n >= iR ? fcR : (n < iL ? fcL : fh);
                 x = cmul(x, inb ? fk : ff);
             }
-            S[swz<C>(n)] = x;
+            S[sb ^ swz<C>(m * s)] = x;
         }
     }
 }
