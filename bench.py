@@ -52,6 +52,35 @@ def _hbm_peak(d):
     return 6800.0
 
 
+# DRAM bytes (read + write) of one launch of the dominant kernel, from an
+# ncu capture of that launch (dram__bytes_read.sum + dram__bytes_write.sum;
+# summary and command in profiles/soft1d_kernel_laser_batch_c64.md), valid
+# only while the kernel sources hash to the same value and the launch has the
+# same instances and steps.
+TRAFFIC_MEASURED = {
+    "c64": {"src_sha1": "fc86826ff314099811b48c69840620fc491d6db8", "n": 16384, "instances": 988,
+            "steps": 256, "bytes": 133035776 + 78681088},
+}
+
+
+def _kernel_src_sha1():
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("soft1d.cuh", "device_common.cuh"):
+        with open(os.path.join(ROOT, "paper_1505_06707_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def _traffic(prec, n, instances, steps):
+    t = TRAFFIC_MEASURED.get(prec)
+    if not t or t["src_sha1"] != _kernel_src_sha1():
+        return None
+    if (t["n"], t["instances"], t["steps"]) != (n, instances, steps):
+        return None
+    return float(t["bytes"])
+
+
 # FP32 SIMT peak derived from the unit counts and the maximum clock:
 # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -345,9 +374,19 @@ def main():
     ap.add_argument("--steps-per-call", type=int, default=STEPS_PER_CALL)
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the 2D step and stationary-solver measurements")
+    ap.add_argument("--only", choices=["2d", "pcg", "learned"], default=None,
+                    help="run one of the extra measurements alone (for profiling captures; not a bench line)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        import torch
+        import paper_1505_06707_gb300 as S
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        fn = {"2d": bench_2d, "pcg": bench_pcg, "learned": bench_learned}[args.only]
+        print(json.dumps({"only": args.only, "result": fn(S, torch, dev, args)}))
+        return
 
     import numpy as np
     import torch
@@ -494,7 +533,9 @@ def main():
            .replace("c128", "c128 (f64)"), "data": "synthetic", "config": config(args.prec, args.instances, spc)}
     peak = FP32_PEAK_TFLOPS if prec == S.SOFT_C64 else FP64_PEAK_TFLOPS
     out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                       "frac": achieved / peak, "traffic": None,
+                       "frac": achieved / peak,
+                       "traffic": _traffic(args.prec, sizes[0], len(groups[sizes[0]]), spc),
+                       "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
                        "kernel": "soft1d_kernel, N = %d group (%d instances, %d steps per launch), "
                                  "%.3f ms per launch, timed alone" % (sizes[0], len(groups[sizes[0]]), spc, kms),
                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"

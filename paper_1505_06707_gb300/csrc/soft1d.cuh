@@ -60,6 +60,10 @@ struct Cfg1D {
     static constexpr int CMAX = E / 4 + 2;   // strip rows per thread
     static constexpr int NW = (T + 31) / 32;
     static constexpr int MINB = T >= 512 ? 1 : 512 / T;   // CTAs per SM the registers must allow (128 regs)
+    // state larger than a CTA's shared memory (complex128, N = 16384): the
+    // step kernel works on the instance's own buffer in global memory (L2
+    // resident while the CTA runs; such plans are bound by FP64 arithmetic)
+    static constexpr bool GM = sizeof(C) * N > 160 * 1024;
 };
 
 // Twiddle tables: for pass P (sub-transform length L, stride s = L/R) four
@@ -374,7 +378,8 @@ struct Step1D {
 template <typename R, int LOGN, int LOGE, int LOGRM>
 __host__ __device__ constexpr size_t soft1d_smem() {
     return sizeof(typename CT<R>::C) *
-               ((size_t(1) << LOGN) + TwCount<LOGN, LOGRM>::value + 64 + (size_t(1) << LOGE) + 36) + 64;
+               ((Cfg1D<R, LOGN, LOGE, LOGRM>::GM ? 0 : (size_t(1) << LOGN)) + TwCount<LOGN, LOGRM>::value + 64 +
+                (size_t(1) << LOGE) + 36) + 64;
 }
 
 template <typename R, int LOGN, int LOGE, int LOGRM, int P, int PEND>
@@ -568,13 +573,14 @@ soft1d_kernel(const Inst1D* __restrict__ insts, void* __restrict__ psi_base, int
     static_assert(Q::R0 <= 16, "pass radix <= 16");
     static_assert(soft1d_smem<R, LOGN, LOGE, LOGRM>() <= 227 * 1024, "shared memory");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* S = reinterpret_cast<C*>(smem_raw);
-    C* Ws = S + N;                   // twiddles, TWN complex
+    C* Ws = reinterpret_cast<C*>(smem_raw) + (K::GM ? 0 : N);   // twiddles, TWN complex
     C* scan = Ws + Q::TWN;           // 2*32 complex
     C* fr = scan + 64;               // E + 36 complex: field phases (field_setup)
 
     const Inst1D I = insts[blockIdx.x];
     C* __restrict__ g_psi = reinterpret_cast<C*>(psi_base) + I.off;
+    // the state: shared memory, or (GM) the instance's buffer itself
+    C* S = K::GM ? g_psi : reinterpret_cast<C*>(smem_raw);
     const C* __restrict__ W = reinterpret_cast<const C*>(I.W);
     using TT = typename K::TT;
     const TT* __restrict__ TK = reinterpret_cast<const TT*>(I.TK);
@@ -587,11 +593,19 @@ soft1d_kernel(const Inst1D* __restrict__ insts, void* __restrict__ psi_base, int
     const int nb = I.nb, blk0 = I.blk0;
     if (nsteps <= 0) return;
 
-    // load the state and the twiddles
+    // load the state (GM: permute the buffer into the swizzled order in place;
+    // swz is an involution, so it is a product of disjoint swaps) and the twiddles
+    if constexpr (K::GM) {
+        for (int j = 0; j < E; ++j) {
+            const int n = tid + j * T, p = swz<C>(n);
+            if (n < p) { const C a = S[n]; S[n] = S[p]; S[p] = a; }
+        }
+    } else {
 #pragma unroll
-    for (int j = 0; j < E; ++j) {
-        const int n = tid + j * T;
-        S[swz<C>(n)] = g_psi[n];
+        for (int j = 0; j < E; ++j) {
+            const int n = tid + j * T;
+            S[swz<C>(n)] = g_psi[n];
+        }
     }
     for (int i = tid; i < Q::TWN; i += T) Ws[i] = __ldg(&W[i]);
     __syncthreads();
@@ -630,10 +644,17 @@ soft1d_kernel(const Inst1D* __restrict__ insts, void* __restrict__ psi_base, int
     }
 
     // store
+    if constexpr (K::GM) {
+        for (int j = 0; j < E; ++j) {
+            const int n = tid + j * T, p = swz<C>(n);
+            if (n < p) { const C a = S[n]; S[n] = S[p]; S[p] = a; }
+        }
+    } else {
 #pragma unroll
-    for (int j = 0; j < E; ++j) {
-        const int n = tid + j * T;
-        g_psi[n] = S[swz<C>(n)];
+        for (int j = 0; j < E; ++j) {
+            const int n = tid + j * T;
+            g_psi[n] = S[swz<C>(n)];
+        }
     }
     if (tid == 0 && status) {
         const C v = S[0];

@@ -33,7 +33,7 @@ void soft1d_default_cfg(int prec, int logn, int* loge, int* logrm) {
     else if (logn == 7) e = 2;
     else if (logn <= 9) e = 3;
     else if (prec == SOFT_C64) e = logn >= 13 ? 5 : 4;
-    else e = logn >= 12 ? 4 : 3;
+    else e = logn >= 14 ? 5 : logn >= 12 ? 4 : 3;   // N = 16384: state in global memory, 512 threads
     *loge = e;
     *logrm = e > 4 ? 4 : e;
     if (prec == SOFT_C128 && *logrm > 3) *logrm = 3;   // radix 16 in FP64 does not fit 128 registers
@@ -58,7 +58,8 @@ size_t soft1d_smem_bytes(int prec, int logn, int loge, int logrm) {
         tw += 4 * (size_t(1) << (logl - lr));
         logl -= lr;
     }
-    return c * ((size_t(1) << logn) + tw + 64 + (size_t(1) << loge) + 36) + 64;
+    const bool gm = c * (size_t(1) << logn) > 160 * 1024;   // Cfg1D::GM: state stays in global memory
+    return c * ((gm ? 0 : (size_t(1) << logn)) + tw + 64 + (size_t(1) << loge) + 36) + 64;
 }
 
 int launch_soft1d(int prec, int logn, int loge, int logrm, const Inst1D* d_inst, int count,

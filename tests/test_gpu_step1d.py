@@ -107,8 +107,6 @@ def test_free_gaussian_closed_form_c128():
 def test_random_state_all_sizes(n, prec):
     """Every built size and both precisions, random complex state, sharp ECS
     (strip = 1/8 of the box per side plus the coupled neighbours), 7 steps."""
-    if prec == S.SOFT_C128 and n == 16384:
-        pytest.skip("complex128 N=16384 exceeds one CTA's shared memory")
     rng = np.random.default_rng(n + prec)
     psi0 = rng.standard_normal(n) + 1j * rng.standard_normal(n)
     hw = 8.0 * n / 1024
