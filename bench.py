@@ -249,7 +249,7 @@ def bench_2d(S, torch, dev, args):
         sec = e0.elapsed_time(e1) / 1e3
         steps = nst * reps
         Sb = 8 if prec == S.SOFT_C64 else 16
-        tab = 16                                          # e^{-iU tau/2} per point, read ~1.25x
+        tab = 8 if prec == S.SOFT_C64 else 16             # e^{-iU tau/2} per point (c64: minus 1, float2), read ~1.25x
         bytes_pt = 5 * Sb + 1.25 * tab
         gps = n * n * steps / sec
         res[name] = {"grid_point_steps_per_s": gps, "ms_per_step": 1e3 * sec / steps,

@@ -86,6 +86,8 @@ int create_2d(const soft_grid* grid, const double* box, double R0, double theta,
     Q->lx = lx; Q->ly = ly;
     soft1d_default_cfg(o.prec, lx, &Q->lex, &Q->lrx);
     soft1d_default_cfg(o.prec, ly, &Q->ley, &Q->lry);
+    // column pass: 32 elements per thread in complex64 (two CTAs of 4 columns per SM)
+    if (o.prec == SOFT_C64 && ly >= 10) Q->ley = 5;
     Q->R0 = R0; Q->theta = theta; Q->tau = dt;
     Q->band_width = o.band_width;
     ContourFn cx(o.contour, R0, box[1], theta, o.tfecs_alpha);
@@ -110,13 +112,18 @@ int create_2d(const soft_grid* grid, const double* box, double R0, double theta,
             Q->U[yy * nx + xx] = u;
             tvh[yy * nx + xx] = std::exp(cd(0.0, -0.5 * dt) * u);
         }
-    // kinetic factors per axis, in each FFT's output order, 1/n folded in
-    auto ktab = [&](const Axis1D& A, int logn, int logrm, double frac) {
+    // kinetic factors per axis, in each FFT's output order, 1/n folded in; the
+    // column pass reads its table in the last forward pass (butterflies of R
+    // consecutive positions b*R + m, stored at m*(n/R) + b)
+    auto ktab = [&](const Axis1D& A, int logn, int logrm, double frac, bool center) {
         const std::vector<int> perm = dif_output_order(logn, logrm);
+        const int lrl = (logn % logrm) ? logn % logrm : logrm;
+        const int Rl = 1 << lrl, nbf = A.n >> lrl;
         std::vector<cd> t(A.n);
         for (int p = 0; p < A.n; ++p) {
             const double k = A.k[perm[p]];
-            t[p] = std::polar(1.0 / A.n, -0.5 * k * k * dt * frac);
+            const int q = center ? (p % Rl) * nbf + p / Rl : p;
+            t[q] = std::polar(1.0 / A.n, -0.5 * k * k * dt * frac);
         }
         return t;
     };
@@ -133,11 +140,11 @@ int create_2d(const soft_grid* grid, const double* box, double R0, double theta,
     const int pr = o.prec;
     if ((rc = upload_c(&Q->Wx, pass_twiddles(lx, Q->lrx), pr))) return rc;
     if ((rc = upload_c(&Q->Wy, pass_twiddles(ly, Q->lry), pr))) return rc;
-    if ((rc = upload_tab(&Q->TKx, ktab(Q->ax, lx, Q->lrx, 1.0), pr))) return rc;
-    if ((rc = upload_tab(&Q->TKhx, ktab(Q->ax, lx, Q->lrx, 0.5), pr))) return rc;
-    if ((rc = upload_tab(&Q->TKy, ktab(Q->ay, ly, Q->lry, 1.0), pr))) return rc;
-    if ((rc = upload_tab(&Q->TKhy, ktab(Q->ay, ly, Q->lry, 0.5), pr))) return rc;
-    if ((rc = upload_tab(&Q->TVh, tvh, pr))) return rc;
+    if ((rc = upload_tab(&Q->TKx, ktab(Q->ax, lx, Q->lrx, 1.0, false), pr))) return rc;
+    if ((rc = upload_tab(&Q->TKhx, ktab(Q->ax, lx, Q->lrx, 0.5, false), pr))) return rc;
+    if ((rc = upload_tab(&Q->TKy, ktab(Q->ay, ly, Q->lry, 1.0, true), pr))) return rc;
+    if ((rc = upload_tab(&Q->TKhy, ktab(Q->ay, ly, Q->lry, 0.5, true), pr))) return rc;
+    if ((rc = upload_vtab(&Q->TVh, tvh, pr))) return rc;
     if ((rc = upload_c(&Q->cnx, cnx, pr))) return rc;
     if ((rc = upload_c(&Q->cny, cny, pr))) return rc;
     Geo2D& g = Q->geo;

@@ -10,6 +10,7 @@ int cuda_status(cudaError_t e);
 int upload(void** dst, const void* src, size_t bytes);
 int upload_c(void** dst, const std::vector<cd>& v, int prec);
 int upload_tab(void** dst, const std::vector<cd>& v, int prec);
+int upload_vtab(void** dst, const std::vector<cd>& v, int prec);
 int make_tables_1d(Tables1D* T, int n, double a, double b, double R0, double theta, double tau,
                    const soft_options& o, int loge, int logrm);
 

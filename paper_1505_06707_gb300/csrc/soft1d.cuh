@@ -203,12 +203,12 @@ __device__ __forceinline__ void fwd_fft(typename CT<R>::C* S, const typename CT<
         fwd_fft<R, LOGN, LOGE, LOGRM, P + 1>(S, W, tid);
     }
 }
-template <typename R, int LOGN, int LOGE, int LOGRM, int P>
+template <typename R, int LOGN, int LOGE, int LOGRM, int P, int PSTOP = 0>
 __device__ __forceinline__ void inv_fft(typename CT<R>::C* S, const typename CT<R>::C* W, int tid) {
-    if constexpr (P >= 0) {
+    if constexpr (P >= PSTOP) {
         inv_pass<R, LOGN, LOGE, LOGRM, P>(S, W, tid);
         __syncthreads();
-        inv_fft<R, LOGN, LOGE, LOGRM, P - 1>(S, W, tid);
+        inv_fft<R, LOGN, LOGE, LOGRM, P - 1, PSTOP>(S, W, tid);
     }
 }
 

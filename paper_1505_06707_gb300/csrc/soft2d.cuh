@@ -24,7 +24,33 @@ struct Cfg2DRow : Cfg1D<R, LOGN, LOGE, LOGRM> {
     static constexpr size_t SMEM2 = sizeof(typename CT<R>::C) * ((1 << LOGN) + 64) + 64;
 };
 
-// One CTA per row.  rows are (row0 + blockIdx.x) mod ny.
+// Inverse pass 0 with post(n, v) applied to every output as it is stored.
+template <typename R, int LOGN, int LOGE, int LOGRM, class Post>
+__device__ __forceinline__ void inv_pass0_post(typename CT<R>::C* S, const typename CT<R>::C* __restrict__ W,
+                                               int tid, Post post) {
+    using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
+    using C = typename K::C;
+    using G = PassGeom<LOGN, LOGRM, 0>;
+    constexpr int LOGR = G::LOGR, RR = 1 << LOGR;
+    constexpr int s = G::S;
+    constexpr int NB = G::LOGR;
+#pragma unroll 1
+    for (int u = 0; u < K::E / RR; ++u) {
+        const int off = tid + u * K::T;
+        const int sb = swz<C>(off);
+        C v[RR];
+        C tb[4];
+        if constexpr (s > 1) load_tw<C, NB, s, false>(tb, W + G::TOFF + off);
+        LoadInv<C, RR, s, 0>::run(S, v, tb, sb, s > 1);
+        dft_reg<C, RR, +1>(v);
+#pragma unroll
+        for (int m = 0; m < RR; ++m) S[sb ^ swz<C>(m * s)] = post(off + m * s, v[bitrev_c(m, LOGR)]);
+    }
+}
+
+// One CTA per row.  rows are (row0 + blockIdx.x) mod ny.  The potential
+// factor is applied as the last inverse pass stores, the x kinetic factor as
+// the row is written back.
 template <typename R, int LOGN, int LOGE, int LOGRM, int MODE>
 __global__ void __launch_bounds__(Cfg1D<R, LOGN, LOGE, LOGRM>::T, Cfg1D<R, LOGN, LOGE, LOGRM>::MINB)
 row_pass_kernel(Geo2D g, void* __restrict__ psi_v, int row0, const void* __restrict__ tkx_v)
@@ -32,6 +58,7 @@ row_pass_kernel(Geo2D g, void* __restrict__ psi_v, int row0, const void* __restr
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
     using C = typename K::C;
     using TT = typename K::TT;
+    using VT = typename VabT<R>::T;
     constexpr int N = K::N, T = K::T, E = K::E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* S = reinterpret_cast<C*>(smem_raw);
@@ -40,33 +67,35 @@ row_pass_kernel(Geo2D g, void* __restrict__ psi_v, int row0, const void* __restr
     const int y = (row0 + (int)blockIdx.x) % g.ny;
     C* __restrict__ row = reinterpret_cast<C*>(psi_v) + (int64_t)y * N;
     const C* __restrict__ W = reinterpret_cast<const C*>(g.Wx);
-    const TT* __restrict__ tv = reinterpret_cast<const TT*>(g.TVh) + (int64_t)y * N;
+    const VT* __restrict__ tv = reinterpret_cast<const VT*>(g.TVh) + (int64_t)y * N;
     const TT* __restrict__ tkx = reinterpret_cast<const TT*>(tkx_v);
 
 #pragma unroll 4
     for (int j = 0; j < E; ++j) {
         const int n = tid + j * T;
         C v = row[n];
-        if (MODE == ROW_B) v = tmul(v, __ldg(&tv[n]));
+        if (MODE == ROW_B) v = vmul(v, __ldg(&tv[n]));
         S[swz<C>(n)] = v;
     }
     __syncthreads();
-    if (MODE == ROW_FULL || MODE == ROW_A || MODE == ROW_INV) inv_fft<R, LOGN, LOGE, LOGRM, K::NPASS - 1>(S, W, tid);
-    if (MODE == ROW_FULL || MODE == ROW_A) {
-#pragma unroll 4
-        for (int j = 0; j < E; ++j) {
-            const int n = tid + j * T;
-            const TT t = __ldg(&tv[n]);
-            C v = tmul(S[swz<C>(n)], t);
-            if (MODE == ROW_FULL && ((n - g.blk0x) & (N - 1)) >= g.nbx) v = tmul(v, t);
-            S[swz<C>(n)] = v;
-        }
+    if (MODE == ROW_INV) {
+        inv_fft<R, LOGN, LOGE, LOGRM, K::NPASS - 1>(S, W, tid);
+    } else if (MODE == ROW_FULL || MODE == ROW_A) {
+        inv_fft<R, LOGN, LOGE, LOGRM, K::NPASS - 1, 1>(S, W, tid);
+        // e^{-iU tau/2}; off the x-strip block of a full row pass the second
+        // half factor too
+        inv_pass0_post<R, LOGN, LOGE, LOGRM>(S, W, tid, [&](int n, C v) {
+            const VT t = __ldg(&tv[n]);
+            v = vmul(v, t);
+            if (MODE == ROW_FULL && ((n - g.blk0x) & (N - 1)) >= g.nbx) v = vmul(v, t);
+            return v;
+        });
         __syncthreads();
         if (g.nbx > 0) {
             const C* cn = reinterpret_cast<const C*>(g.cnx);
             if (MODE == ROW_FULL)
                 strip_cn<C, T, K::CMAX, N>(S, cn, g.nbx, g.blk0x, tid, scan,
-                                           [&](int n, C v) { return tmul(v, __ldg(&tv[n])); });
+                                           [&](int n, C v) { return vmul(v, __ldg(&tv[n])); });
             else
                 strip_cn<C, T, K::CMAX, N>(S, cn, g.nbx, g.blk0x, tid, scan, [](int, C v) { return v; });
             __syncthreads();
@@ -74,41 +103,60 @@ row_pass_kernel(Geo2D g, void* __restrict__ psi_v, int row0, const void* __restr
     }
     if (MODE == ROW_FULL || MODE == ROW_B || MODE == ROW_FWD) {
         fwd_fft<R, LOGN, LOGE, LOGRM, 0>(S, W, tid);
-        kmul<R, LOGN, LOGE, LOGRM>(S, tkx, tid);
-    }
 #pragma unroll 4
-    for (int j = 0; j < E; ++j) {
-        const int n = tid + j * T;
-        row[n] = S[swz<C>(n)];
+        for (int j = 0; j < E; ++j) {
+            const int n = tid + j * T;
+            row[n] = tmul(S[swz<C>(n)], __ldg(&tkx[n]));
+        }
+    } else {
+#pragma unroll 4
+        for (int j = 0; j < E; ++j) {
+            const int n = tid + j * T;
+            row[n] = S[swz<C>(n)];
+        }
     }
 }
 
 // Column pass: TW columns per CTA, each transformed by T = ny/E threads:
-// F_y, e^{-i ky^2 tau/2}/ny (table in the column FFT's output order), F_y^-1.
+// F_y, e^{-i ky^2 tau/2}/ny, F_y^-1, with the last forward pass, the factor
+// and the first inverse pass fused (kcenter; table in its transposed order)
+// and the twiddles in shared memory.
 template <typename R, int LOGN, int LOGE, int LOGRM, int TW>
-__global__ void __launch_bounds__(TW * Cfg1D<R, LOGN, LOGE, LOGRM>::T, 1)
+struct ColCfg {
+    using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
+    static constexpr int THREADS = TW * K::T;
+    static constexpr int MINB = THREADS >= 512 ? 1 : 512 / THREADS;   // <= 128 registers
+    static constexpr size_t SMEM = sizeof(typename K::C) * ((size_t)TW * K::N + TwCount<LOGN, LOGRM>::value);
+};
+
+template <typename R, int LOGN, int LOGE, int LOGRM, int TW>
+__global__ void __launch_bounds__(ColCfg<R, LOGN, LOGE, LOGRM, TW>::THREADS, ColCfg<R, LOGN, LOGE, LOGRM, TW>::MINB)
 col_pass_kernel(Geo2D g, void* __restrict__ psi_v, const void* __restrict__ tky_v)
 {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
     using C = typename K::C;
     using TT = typename K::TT;
     constexpr int N = K::N, T = K::T;
+    constexpr int TWN = TwCount<LOGN, LOGRM>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* S = reinterpret_cast<C*>(smem_raw);
+    C* Ws = S + TW * N;
     C* __restrict__ psi = reinterpret_cast<C*>(psi_v);
+    const C* __restrict__ W = reinterpret_cast<const C*>(g.Wy);
     const int c0 = blockIdx.x * TW;
     const int nx = g.nx;
     for (int idx = threadIdx.x; idx < TW * N; idx += TW * T) {
         const int yy = idx / TW, j = idx % TW;
         S[j * N + swz<C>(yy)] = psi[(int64_t)yy * nx + c0 + j];
     }
+    for (int i = threadIdx.x; i < TWN; i += TW * T) Ws[i] = __ldg(&W[i]);
     __syncthreads();
     const int col = threadIdx.x / T, tid = threadIdx.x % T;
     C* Sc = S + col * N;
-    const C* W = reinterpret_cast<const C*>(g.Wy);
-    fwd_fft<R, LOGN, LOGE, LOGRM, 0>(Sc, W, tid);
-    kmul<R, LOGN, LOGE, LOGRM>(Sc, reinterpret_cast<const TT*>(tky_v), tid);
-    inv_fft<R, LOGN, LOGE, LOGRM, K::NPASS - 1>(Sc, W, tid);
+    fwd_passes<R, LOGN, LOGE, LOGRM, 0, K::NPASS - 1>(Sc, Ws, tid);
+    kcenter<R, LOGN, LOGE, LOGRM>(Sc, reinterpret_cast<const TT*>(tky_v), tid);
+    __syncthreads();
+    inv_passes<R, LOGN, LOGE, LOGRM, K::NPASS - 2, 0>(Sc, Ws, tid);
     for (int idx = threadIdx.x; idx < TW * N; idx += TW * T) {
         const int yy = idx / TW, j = idx % TW;
         psi[(int64_t)yy * nx + c0 + j] = S[j * N + swz<C>(yy)];
@@ -223,14 +271,14 @@ int launch_row_t(int mode, const Geo2D& g, void* psi, int row0, int nrows, const
 
 template <typename R, int LOGN, int LOGE, int LOGRM, int TW>
 int launch_col_t(const Geo2D& g, void* psi, const void* tky, cudaStream_t st) {
-    using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
-    const size_t smem = sizeof(typename K::C) * TW * K::N;
+    using CC = ColCfg<R, LOGN, LOGE, LOGRM, TW>;
+    const size_t smem = CC::SMEM;
     auto k = col_pass_kernel<R, LOGN, LOGE, LOGRM, TW>;
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return SOFT_ERR_CUDA;
     if (!psi) return SOFT_OK;             // attribute set only
-    k<<<g.nx / TW, TW * K::T, smem, st>>>(g, psi, tky);
+    k<<<g.nx / TW, CC::THREADS, smem, st>>>(g, psi, tky);
     return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
 }
 

@@ -16,7 +16,7 @@ int soft2d_col_c64(int logn, int loge, int logrm, const Geo2D& g, void* psi, con
                     cudaStream_t st) {
 #define COLCASE(LN, LE, LR) \
     if (logn == LN && loge == LE && logrm == LR) return launch_col_t<float, LN, LE, LR, 4>(g, psi, tky, st);
-    COLCASE(8, 3, 3) COLCASE(9, 3, 3) COLCASE(10, 4, 4) COLCASE(11, 4, 4)
+    COLCASE(8, 3, 3) COLCASE(9, 3, 3) COLCASE(10, 5, 4) COLCASE(11, 5, 4)
 #undef COLCASE
     return SOFT_ERR_UNSUPPORTED;
 }

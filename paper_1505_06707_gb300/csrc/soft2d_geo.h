@@ -6,7 +6,7 @@ namespace soft {
 struct Geo2D {              // passed by value to every 2D kernel
     const void* Wx;         // pass twiddles of the row FFT (length nx)
     const void* Wy;         // pass twiddles of the column FFT (length ny)
-    const void* TVh;        // e^{-iU tau/2}, [ny][nx], phase-table format
+    const void* TVh;        // e^{-iU tau/2}, [ny][nx] (minus 1, float2, for complex64)
     const void* cnx;        // x-strip LU (mf, mb, g) for the row pass
     const void* cny;        // y-strip LU (mf, mb, g) for the y-block pass
     int nx, ny;
