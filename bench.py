@@ -278,18 +278,23 @@ def bench_pcg(S, torch, dev, args):
     st = torch.cuda.current_stream(dev)
     S.sse_pcg_solve(plan, E[:2], f, out, tol=w["tol"], maxit=4, precond=1, stream=st)   # warm-up
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    rc, its, rr = S.sse_pcg_solve(plan, E, f, out, tol=w["tol"], maxit=3000, precond=1, stream=st)
-    e1.record(st)
-    torch.cuda.synchronize()
-    sec = e0.elapsed_time(e1) / 1e3
+    res = {}
+    for pc, name in ((1, "band_fp64"), (4, "band_fp32")):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        rc, its, rr = S.sse_pcg_solve(plan, E, f, out, tol=w["tol"], maxit=3000, precond=pc, stream=st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        res[name] = {"solves_per_s": len(E) / sec, "seconds": sec, "status": rc,
+                     "iterations_mean": float(np.mean(its)), "iterations_max": int(np.max(its)),
+                     "max_relres": float(np.max(rr))}
     S.soft_destroy(plan)
     del out
-    return {"solves_per_s": len(E) / sec, "seconds": sec, "energies": len(E), "status": rc,
-            "iterations_mean": float(np.mean(its)), "iterations_max": int(np.max(its)),
-            "max_relres": float(np.max(rr)), "precond": "banded ECS (N_BW = 10)",
-            "precision": "c128 state, FP64 dots",
+    best = max(res.values(), key=lambda r: r["solves_per_s"] if r["status"] == 0 else 0)
+    return {"solves_per_s": best["solves_per_s"], "energies": len(E), **res,
+            "precond": "banded ECS (N_BW = 10): FP64 (precond 1) and FP32 arithmetic (precond 4)",
+            "precision": "c128 state, FP64 A, residual and dots",
             "workload": "1024^2 on [-200,200]^2, sharp ECS R0=150 theta=0.4, 64 energies in [0.05,2]"}
 
 

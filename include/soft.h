@@ -173,13 +173,17 @@ int soft_observe(const soft_plan* plan, const void* psi, double* norm_in, double
  *               Hermitian inner products: valid for a preconditioner that
  *               changes between iterations); grids with nx % 128 == 0;
  *            3: the banded preconditioner alone inside the same flexible GCR
- *               (the reference for what the learned correction gains).
+ *               (the reference for what the learned correction gains);
+ *            4: the banded preconditioner computing in FP32 (its FFTs, band
+ *               products and tables; r in and z out stay complex128, and
+ *               A, the residual and the dots stay FP64), in COCG with the
+ *               flexible beta = z'^T (r' - r) / r^T z (FP32 rounding leaves
+ *               the preconditioner not exactly symmetric).
  *   iters_out, relres_out: host int[nE], double[nE]; may be NULL.
  * Returns SOFT_ERR_NOT_CONVERGED if any energy stopped at maxit (its last
  * iterate is written), SOFT_ERR_BREAKDOWN on a vanishing CG denominator.
  * Workspace (and, for precond 2/3, 32 direction vectors per energy) is
- * allocated by the plan on first use.
- * C128 plans only.  Workspace is allocated by the plan on first use. */
+ * allocated by the plan on first use.  C128 plans only. */
 int sse_pcg_solve(soft_plan* plan, const double* E, int nE, const void* rhs, void* psi_out,
                   double tol, int maxit, int precond, int* iters_out, double* relres_out,
                   void* stream);
@@ -187,7 +191,7 @@ int sse_pcg_solve(soft_plan* plan, const double* E, int nE, const void* rhs, voi
 /* sse_apply_A / sse_apply_precond -- one application of A (Sec. III under
  * Eq. linsys) or of the chosen preconditioner, for one energy, device in
  * and out (x and y must not alias).  Exposed for testing and for callers
- * that run their own Krylov method. */
+ * that run their own Krylov method; precond 0, 1 or 4 (as in sse_pcg_solve). */
 int sse_apply_A(soft_plan* plan, double E, const void* x, void* y, void* stream);
 int sse_apply_precond(soft_plan* plan, double E, int precond, const void* x, void* y,
                       void* stream);

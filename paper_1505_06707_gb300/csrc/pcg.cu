@@ -17,7 +17,7 @@ namespace soft {
 
 struct PcgTables {               // one preconditioner type
     PcgGeo geo{};
-    void* bufs[16] = {nullptr};
+    void* bufs[20] = {nullptr};
     int nb = 0;
 };
 
@@ -33,9 +33,9 @@ struct Pcg {
     double2 *rho = nullptr, *alpha = nullptr, *beta = nullptr;
     double *relres = nullptr, *fnorm2 = nullptr;
     int *active = nullptr, *iters = nullptr, *status = nullptr, *nactive = nullptr;
-    // shared A tables and the two preconditioners
+    // shared A tables and the preconditioners
     void *U = nullptr, *Cx = nullptr, *Cy = nullptr, *Kx = nullptr, *Ky = nullptr;
-    PcgTables pc[2];
+    PcgTables pc[3];             // simple, banded, banded with FP32 tables
     bool tables = false;
     // flexible GCR: GCR_M stored direction pairs per energy
     static constexpr int GCR_M = 16;
@@ -67,7 +67,7 @@ static std::vector<cd> ksq_tab(const Axis1D& A, int logn, int logrm) {
     return t;
 }
 
-static int build_pc(Plan2D* Q, int type, PcgTables& T) {
+static int build_pc(Plan2D* Q, int type, PcgTables& T, int prec = SOFT_C128) {
     const bool simple = type == 0;
     BandAxis bx, by;
     double chk;
@@ -90,7 +90,7 @@ static int build_pc(Plan2D* Q, int type, PcgTables& T) {
     };
     auto uc = [&](const std::vector<cd>& v) -> const void* {
         void* d = nullptr;
-        if (upload_c(&d, v, SOFT_C128)) return nullptr;
+        if (upload_c(&d, v, prec)) return nullptr;
         T.bufs[i++] = d;
         return d;
     };
@@ -103,6 +103,10 @@ static int build_pc(Plan2D* Q, int type, PcgTables& T) {
     g.xfx = uc(bx.xf); g.xfy = uc(by.xf);
     g.xbx = uc(bx.xb); g.xby = uc(by.xb);
     g.lamx = uc(bx.lam); g.lamy = uc(by.lam);
+    if (prec == SOFT_C64) {      // FFT twiddles of the FP32 passes
+        g.Wx = uc(pass_twiddles(Q->lx, Q->lrx));
+        g.Wy = uc(pass_twiddles(Q->ly, Q->lry));
+    }
     for (int k = 0; k < i; ++k)
         if (!T.bufs[k]) return SOFT_ERR_OOM;
     T.nb = i;
@@ -126,11 +130,13 @@ static int ensure_tables(Plan2D* Q) {
     if ((rc = upload_c(&S->Cy, cat(Q->ay), SOFT_C128))) return rc;
     if ((rc = upload_tab(&S->Kx, ksq_tab(Q->ax, Q->lx, Q->lrx), SOFT_C128))) return rc;
     if ((rc = upload_tab(&S->Ky, ksq_tab(Q->ay, Q->ly, Q->lry), SOFT_C128))) return rc;
-    for (int type = 0; type < 2; ++type) {
-        if ((rc = build_pc(Q, type, S->pc[type]))) return rc;
+    for (int type = 0; type < 3; ++type) {
+        const bool f32 = type == 2;
+        if ((rc = build_pc(Q, f32 ? 1 : type, S->pc[type], f32 ? SOFT_C64 : SOFT_C128))) return rc;
         PcgGeo& g = S->pc[type].geo;
         g.nx = Q->nx; g.ny = Q->ny; g.N = S->N;
-        g.Wx = Q->Wx; g.Wy = Q->Wy; g.Kx = S->Kx; g.Ky = S->Ky; g.U = S->U;
+        if (!f32) { g.Wx = Q->Wx; g.Wy = Q->Wy; }
+        g.Kx = S->Kx; g.Ky = S->Ky; g.U = S->U;
         g.Cx = S->Cx; g.Cy = S->Cy;
         g.nbx = Q->geo.nbx; g.blk0x = Q->geo.blk0x; g.nby = Q->geo.nby; g.blk0y = Q->geo.blk0y;
     }
@@ -142,6 +148,10 @@ static int ensure_tables(Plan2D* Q) {
     for (int which = 0; which < 2; ++which)
         if ((rc = pcg_col(Q->ly, which, S->pc[0].geo, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0)))
             return rc;
+    for (int which = 1; which < 3; ++which)
+        if ((rc = pcg_pc32_row(Q->lx, which, S->pc[2].geo, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0)))
+            return rc;
+    if ((rc = pcg_pc32_col(Q->ly, S->pc[2].geo, nullptr, nullptr, nullptr, 0, 0))) return rc;
     S->tables = true;
     return SOFT_OK;
 }
@@ -179,11 +189,19 @@ static int ensure_workspace(Plan2D* Q, int nE) {
 }
 
 // z = P^-1 r for nE energies; with part, the per-row partials of r^T z
+// type: 0 simple, 1 banded, 4 banded computing in FP32 (r, z complex128)
 static int apply_pc(Plan2D* Q, int type, const void* r, void* z, const double* dE, const int* act,
                     double2* part, int nE, cudaStream_t st) {
     Pcg* S = Q->pcg;
-    const PcgGeo& g = S->pc[type].geo;
     int rc;
+    if (type == 4) {
+        const PcgGeo& g = S->pc[2].geo;
+        if ((rc = pcg_pc32_row(Q->lx, 1, g, r, S->t, nullptr, act, nullptr, nE, st))) return rc;
+        if ((rc = pcg_pc32_col(Q->ly, g, S->t, dE, act, nE, st))) return rc;
+        Q->launches += 3;
+        return pcg_pc32_row(Q->lx, 2, g, S->t, z, part ? r : nullptr, act, part, nE, st);
+    }
+    const PcgGeo& g = S->pc[type].geo;
     if ((rc = pcg_row(Q->lx, 1, g, r, S->t, nullptr, dE, act, nullptr, nE, st))) return rc;
     if ((rc = pcg_col(Q->ly, 1, g, nullptr, S->t, dE, act, nullptr, nE, st))) return rc;
     Q->launches += 3;
@@ -243,7 +261,7 @@ int sse_apply_A(soft_plan* P, double E, const void* x, void* y, void* stream) {
 
 int sse_apply_precond(soft_plan* P, double E, int precond, const void* x, void* y, void* stream) {
     if (!P || !x || !y || P->kind != 2 || !std::isfinite(E)) return SOFT_ERR_INVALID_ARG;
-    if (precond != 0 && precond != 1) return SOFT_ERR_INVALID_ARG;
+    if (precond != 0 && precond != 1 && precond != 4) return SOFT_ERR_INVALID_ARG;
     if (P->prec != SOFT_C128) return SOFT_ERR_UNSUPPORTED;
     Plan2D* Q = P->p2;
     int rc = ensure_workspace(Q, 1);
@@ -260,8 +278,8 @@ int sse_apply_precond(soft_plan* P, double E, int precond, const void* x, void* 
 int sse_pcg_solve(soft_plan* P, const double* E, int nE, const void* rhs, void* psi_out, double tol,
                   int maxit, int precond, int* iters_out, double* relres_out, void* stream) {
     if (!P || !E || nE <= 0 || !rhs || !psi_out || !(tol > 0) || maxit <= 0) return SOFT_ERR_INVALID_ARG;
-    if (precond < 0 || precond > 3) return SOFT_ERR_INVALID_ARG;
-    const bool flexible = precond >= 2;
+    if (precond < 0 || precond > 4) return SOFT_ERR_INVALID_ARG;
+    const bool flexible = precond == 2 || precond == 3;
     const bool learned = precond == 2;
     if (learned) {
         if (!P->p2 || P->p2->nx % 128) return SOFT_ERR_UNSUPPORTED;
@@ -317,8 +335,17 @@ int sse_pcg_solve(soft_plan* P, const double* E, int nE, const void* rhs, void* 
                 if (na <= 0) break;
             }
             if (it == maxit) break;
-            if ((rc = apply_pc(Q, precond, S->r, S->z, S->dE, S->active, S->part, nE, st))) return rc;
-            if ((rc = pcg_scalars(STAGE_BETA, nE, S->part, np_row, s, st))) return rc;
+            if (precond == 4) {
+                // FP32 preconditioner: not exactly symmetric, so the flexible
+                // beta = z'^T (r' - r) / rho = -alpha z'^T w / rho
+                if ((rc = apply_pc(Q, precond, S->r, S->z, S->dE, S->active, nullptr, nE, st))) return rc;
+                if ((rc = vec_dot2(S->r, S->z, S->w, S->active, N, nE, S->part, S->part2, np_vec, st))) return rc;
+                if ((rc = pcg_scalars(STAGE_BETA_FLEX, nE, S->part, np_vec, s, st, S->part2))) return rc;
+                Q->launches += 1;
+            } else {
+                if ((rc = apply_pc(Q, precond, S->r, S->z, S->dE, S->active, S->part, nE, st))) return rc;
+                if ((rc = pcg_scalars(STAGE_BETA, nE, S->part, np_row, s, st))) return rc;
+            }
             if ((rc = vec_p(S->p, S->z, S->beta, S->active, N, nE, 0, st))) return rc;
             Q->launches += 5;
         }

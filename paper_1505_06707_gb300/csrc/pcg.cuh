@@ -41,6 +41,10 @@ struct PcgGeo {
 template <typename C>
 __device__ __forceinline__ C cconj(C a) { return cmk<C>(a.x, -a.y); }
 
+// complex value in another precision
+template <typename C, typename D>
+__device__ __forceinline__ C cto(D a) { return cmk<C>((decltype(C::x))a.x, (decltype(C::x))a.y); }
+
 // block reduction of a complex FP64 value; returns the total in thread 0
 __device__ __forceinline__ double2 block_sum2(double2 v, double2* red) {
     for (int o = 16; o > 0; o >>= 1) {
@@ -173,6 +177,7 @@ __device__ __forceinline__ C band_row(int nu, const int* __restrict__ bs, const 
 }
 
 // row pass 1: t = X_x F_x r (F with e^{+ikx}), natural nu order
+// (r is complex128; the pass computes in R: t and the tables are in R)
 template <typename R, int LOGN, int LOGE, int LOGRM>
 __global__ void __launch_bounds__(Cfg1D<R, LOGN, LOGE, LOGRM>::T, Cfg1D<R, LOGN, LOGE, LOGRM>::MINB)
 pc_row1_kernel(PcgGeo g, const void* __restrict__ r_v, void* __restrict__ t_v,
@@ -187,11 +192,11 @@ pc_row1_kernel(PcgGeo g, const void* __restrict__ r_v, void* __restrict__ t_v,
     C* S = reinterpret_cast<C*>(smem_raw);
     const int tid = threadIdx.x;
     const int64_t base = (int64_t)e * g.N + (int64_t)y * N;
-    const C* __restrict__ r = reinterpret_cast<const C*>(r_v) + base;
+    const double2* __restrict__ r = reinterpret_cast<const double2*>(r_v) + base;
     C* __restrict__ t = reinterpret_cast<C*>(t_v) + base;
     for (int j = 0; j < E_; ++j) {
         const int n = tid + j * T;
-        S[swz<C>(n)] = cconj(r[n]);
+        S[swz<C>(n)] = cconj(cto<C>(r[n]));
     }
     __syncthreads();
     fwd_fft<R, LOGN, LOGE, LOGRM, 0>(S, reinterpret_cast<const C*>(g.Wx), tid);
@@ -258,7 +263,8 @@ pc_col_kernel(PcgGeo g, void* __restrict__ t_v, const double* __restrict__ E,
     }
 }
 
-// row pass 2: z = F_x^-1 X_x^T t; partial of r^T z per CTA
+// row pass 2: z = F_x^-1 X_x^T t; partial of r^T z per CTA (z and r are
+// complex128, the pass computes in R)
 template <typename R, int LOGN, int LOGE, int LOGRM>
 __global__ void __launch_bounds__(Cfg1D<R, LOGN, LOGE, LOGRM>::T, Cfg1D<R, LOGN, LOGE, LOGRM>::MINB)
 pc_row2_kernel(PcgGeo g, const void* __restrict__ t_v, void* __restrict__ z_v,
@@ -277,7 +283,7 @@ pc_row2_kernel(PcgGeo g, const void* __restrict__ t_v, void* __restrict__ z_v,
     const int tid = threadIdx.x;
     const int64_t base = (int64_t)e * g.N + (int64_t)y * N;
     const C* __restrict__ t = reinterpret_cast<const C*>(t_v) + base;
-    C* __restrict__ z = reinterpret_cast<C*>(z_v) + base;
+    double2* __restrict__ z = reinterpret_cast<double2*>(z_v) + base;     // complex128 out
     for (int j = 0; j < E_; ++j) {
         const int n = tid + j * T;
         Tn[n] = t[n];
@@ -292,13 +298,13 @@ pc_row2_kernel(PcgGeo g, const void* __restrict__ t_v, void* __restrict__ z_v,
     __syncthreads();
     inv_fft<R, LOGN, LOGE, LOGRM, K::NPASS - 1>(S, reinterpret_cast<const C*>(g.Wx), tid);
     double2 acc = make_double2(0.0, 0.0);
-    const C* r = r_v ? reinterpret_cast<const C*>(r_v) + base : nullptr;
+    const double2* r = r_v ? reinterpret_cast<const double2*>(r_v) + base : nullptr;
     for (int j = 0; j < E_; ++j) {
         const int n = tid + j * T;
-        const C zv = cconj(S[swz<C>(n)]);
+        const double2 zv = cto<double2>(cconj(S[swz<C>(n)]));
         z[n] = zv;
         if (r) {
-            const C rv = r[n];
+            const double2 rv = r[n];
             acc.x += (double)rv.x * zv.x - (double)rv.y * zv.y;
             acc.y += (double)rv.x * zv.y + (double)rv.y * zv.x;
         }

@@ -50,7 +50,61 @@ int col_kernels(int which, const PcgGeo& g, const void* a, void* b, const double
     return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
 }
 
+// preconditioner passes computing in FP32 (complex128 r in, complex128 z out)
+constexpr int TWP32 = 4;  // columns per CTA of the FP32 column pass
+
+template <int LN, int LE, int LR>
+int pc32_row(int which, const PcgGeo& g, const void* a, void* b, const void* c, const int* act,
+             double2* part, int nE, cudaStream_t st) {
+    using K = Cfg1D<float, LN, LE, LR>;
+    const size_t smem = sizeof(float2) * 2 * K::N + 64;
+    dim3 grid(g.ny, nE);
+    if (which == 1) {
+        auto k = pc_row1_kernel<float, LN, LE, LR>;
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return SOFT_ERR_CUDA;
+        if (nE > 0) k<<<grid, K::T, smem, st>>>(g, a, b, act);
+    } else {
+        auto k = pc_row2_kernel<float, LN, LE, LR>;
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return SOFT_ERR_CUDA;
+        if (nE > 0) k<<<grid, K::T, smem, st>>>(g, a, b, c, act, part);
+    }
+    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+}
+
+template <int LN, int LE, int LR>
+int pc32_col(const PcgGeo& g, void* b, const double* E, const int* act, int nE, cudaStream_t st) {
+    using K = Cfg1D<float, LN, LE, LR>;
+    const size_t smem = sizeof(float2) * 2 * TWP32 * K::N + 64;
+    dim3 grid(g.nx / TWP32, nE);
+    auto k = pc_col_kernel<float, LN, LE, LR, TWP32>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return SOFT_ERR_CUDA;
+    if (nE > 0) k<<<grid, TWP32 * K::T, smem, st>>>(g, b, E, act);
+    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+}
+
 }  // namespace
+
+int pcg_pc32_row(int logn, int which, const PcgGeo& g, const void* a, void* b, const void* c,
+                 const int* act, double2* part, int nE, cudaStream_t st) {
+    switch (logn) {
+    case 8: return pc32_row<8, 3, 3>(which, g, a, b, c, act, part, nE, st);
+    case 9: return pc32_row<9, 3, 3>(which, g, a, b, c, act, part, nE, st);
+    case 10: return pc32_row<10, 3, 3>(which, g, a, b, c, act, part, nE, st);
+    case 11: return pc32_row<11, 3, 3>(which, g, a, b, c, act, part, nE, st);
+    }
+    return SOFT_ERR_UNSUPPORTED;
+}
+
+int pcg_pc32_col(int logn, const PcgGeo& g, void* b, const double* E, const int* act, int nE,
+                 cudaStream_t st) {
+    switch (logn) {
+    case 8: return pc32_col<8, 3, 3>(g, b, E, act, nE, st);
+    case 9: return pc32_col<9, 3, 3>(g, b, E, act, nE, st);
+    case 10: return pc32_col<10, 3, 3>(g, b, E, act, nE, st);
+    case 11: return pc32_col<11, 3, 3>(g, b, E, act, nE, st);
+    }
+    return SOFT_ERR_UNSUPPORTED;
+}
 
 int pcg_row(int logn, int which, const PcgGeo& g, const void* a, void* b, const void* c,
             const double* E, const int* act, double2* part, int nE, cudaStream_t st) {

@@ -33,6 +33,13 @@ int pcg_row(int logn, int which, const PcgGeo& g, const void* a, void* b, const 
 int pcg_col(int logn, int which, const PcgGeo& g, const void* a, void* b, const double* E,
             const int* act, double2* part, int nE, cudaStream_t st);
 int pcg_col_blocks(int nx);
+// the banded preconditioner computing in FP32: which 1 = row pass 1 (a = r,
+// b = t), 2 = row pass 2 (a = t, b = z, c = r for r^T z); r and z complex128,
+// t complex64; column pass on t in place
+int pcg_pc32_row(int logn, int which, const PcgGeo& g, const void* a, void* b, const void* c,
+                 const int* act, double2* part, int nE, cudaStream_t st);
+int pcg_pc32_col(int logn, const PcgGeo& g, void* b, const double* E, const int* act, int nE,
+                 cudaStream_t st);
 
 int vec_init(const void* f, void* x, void* r, int64_t N, int nE, cudaStream_t st);
 int vec_norm2(const void* f, int64_t N, double2* part, int nparts, cudaStream_t st);

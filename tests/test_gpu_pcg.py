@@ -56,6 +56,37 @@ def test_apply_A_and_preconditioners_match_oracle():
             assert relerr(host(dy), st.precond_simple(x, E)) < 1e-11
             S.sse_apply_precond(plan, E, 1, dx, dy)
             assert relerr(host(dy), st.precond_band(x, E)) < 1e-11
+            # the same operator computing in FP32: rounding of 2^-24 per operation
+            # over the ~20 FFT stages and band products of the three passes
+            S.sse_apply_precond(plan, E, 4, dx, dy)
+            assert relerr(host(dy), st.precond_band(x, E)) < 2e-5
+    finally:
+        S.soft_destroy(plan)
+
+
+def test_pcg_fp32_preconditioner():
+    """COCG (flexible beta) with the banded preconditioner computing in FP32
+    (A, the residual and the dots stay FP64): every energy reaches the
+    tolerance, checked with the oracle's A, in about the iterations of the
+    FP64 preconditioner."""
+    plan, p2, st = setup()
+    try:
+        n = 256
+        xg = -40.0 + 80.0 / n * (np.arange(n) + 0.5)
+        f = -np.exp(-(xg[None, :] ** 2 + (xg[:, None] - 3.0) ** 2) / 32.0).astype(np.complex128)
+        Es = [0.2, 0.55, 1.1, 1.9]
+        out = torch.zeros((len(Es), n, n), dtype=torch.complex128, device="cuda")
+        rc1, its1, _ = S.sse_pcg_solve(plan, Es, dev(f), out, tol=1e-8, maxit=2000, precond=1)
+        rc4, its4, rr4 = S.sse_pcg_solve(plan, Es, dev(f), out, tol=1e-8, maxit=2000, precond=4)
+        assert rc1 == 0 and rc4 == 0, (rc4, its4, rr4)
+        xs = host(out)
+        for e, E in enumerate(Es):
+            res = np.linalg.norm(st.apply_A(xs[e], E) - f) / np.linalg.norm(f)
+            assert res < 2e-8, (E, res, its4[e])
+            # FP32 rounding leaves the preconditioner inexact and not exactly
+            # symmetric; measured cost up to ~25 % more iterations
+            assert its4[e] <= 1.3 * its1[e] + 5, (its1, its4)
+        print("iterations FP64 band", its1, "FP32 band", its4)
     finally:
         S.soft_destroy(plan)
 
@@ -135,13 +166,14 @@ def test_w4_full_size_sampled_energies():
         st = ST.Stationary2D(p2, nbw=10, kind=T.SHARP, R0=w["R0"], theta=w["theta"])
         Es = list(w["E"][[0, 21, 42, 63]])
         out = torch.zeros((len(Es), n, n), dtype=torch.complex128, device="cuda")
-        rc, its, rr = S.sse_pcg_solve(plan, Es, dev(w["f"]), out, tol=w["tol"], maxit=3000,
-                                      precond=1)
-        assert rc == 0, (rc, its, rr)
-        xs = host(out)
-        for e, E in enumerate(Es):
-            res = np.linalg.norm(st.apply_A(xs[e], E) - w["f"]) / np.linalg.norm(w["f"])
-            assert res < 2 * w["tol"], (E, res)
-        print("W4 iterations (band):", its)
+        for pc in (1, 4):
+            rc, its, rr = S.sse_pcg_solve(plan, Es, dev(w["f"]), out, tol=w["tol"], maxit=3000,
+                                          precond=pc)
+            assert rc == 0, (pc, rc, its, rr)
+            xs = host(out)
+            for e, E in enumerate(Es):
+                res = np.linalg.norm(st.apply_A(xs[e], E) - w["f"]) / np.linalg.norm(w["f"])
+                assert res < 2 * w["tol"], (pc, E, res)
+            print("W4 iterations (band, precond %d):" % pc, its)
     finally:
         S.soft_destroy(plan)
