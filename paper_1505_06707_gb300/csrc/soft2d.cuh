@@ -126,7 +126,10 @@ struct ColCfg {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
     static constexpr int THREADS = TW * K::T;
     static constexpr int MINB = THREADS >= 512 ? 1 : 512 / THREADS;   // <= 128 registers
-    static constexpr size_t SMEM = sizeof(typename K::C) * ((size_t)TW * K::N + TwCount<LOGN, LOGRM>::value);
+    // column pitch: N + 64 bytes, so that the TW columns of one row fall in
+    // different banks when the tile is filled and drained row by row
+    static constexpr int PITCH = K::N + 64 / (int)sizeof(typename K::C);
+    static constexpr size_t SMEM = sizeof(typename K::C) * ((size_t)TW * PITCH + TwCount<LOGN, LOGRM>::value);
 };
 
 template <typename R, int LOGN, int LOGE, int LOGRM, int TW>
@@ -138,28 +141,34 @@ col_pass_kernel(Geo2D g, void* __restrict__ psi_v, const void* __restrict__ tky_
     using TT = typename K::TT;
     constexpr int N = K::N, T = K::T;
     constexpr int TWN = TwCount<LOGN, LOGRM>::value;
+    constexpr int PITCH = ColCfg<R, LOGN, LOGE, LOGRM, TW>::PITCH;
+    constexpr int NIT = N / T;                      // tile elements per thread
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* S = reinterpret_cast<C*>(smem_raw);
-    C* Ws = S + TW * N;
+    C* Ws = S + TW * PITCH;
     C* __restrict__ psi = reinterpret_cast<C*>(psi_v);
     const C* __restrict__ W = reinterpret_cast<const C*>(g.Wy);
     const int c0 = blockIdx.x * TW;
     const int nx = g.nx;
-    for (int idx = threadIdx.x; idx < TW * N; idx += TW * T) {
+#pragma unroll 8
+    for (int it = 0; it < NIT; ++it) {              // row by row: the TW columns of a row are adjacent
+        const int idx = threadIdx.x + it * TW * T;
         const int yy = idx / TW, j = idx % TW;
-        S[j * N + swz<C>(yy)] = psi[(int64_t)yy * nx + c0 + j];
+        S[j * PITCH + swz<C>(yy)] = psi[(int64_t)yy * nx + c0 + j];
     }
     for (int i = threadIdx.x; i < TWN; i += TW * T) Ws[i] = __ldg(&W[i]);
     __syncthreads();
     const int col = threadIdx.x / T, tid = threadIdx.x % T;
-    C* Sc = S + col * N;
+    C* Sc = S + col * PITCH;
     fwd_passes<R, LOGN, LOGE, LOGRM, 0, K::NPASS - 1>(Sc, Ws, tid);
     kcenter<R, LOGN, LOGE, LOGRM>(Sc, reinterpret_cast<const TT*>(tky_v), tid);
     __syncthreads();
     inv_passes<R, LOGN, LOGE, LOGRM, K::NPASS - 2, 0>(Sc, Ws, tid);
-    for (int idx = threadIdx.x; idx < TW * N; idx += TW * T) {
+#pragma unroll 8
+    for (int it = 0; it < NIT; ++it) {
+        const int idx = threadIdx.x + it * TW * T;
         const int yy = idx / TW, j = idx % TW;
-        psi[(int64_t)yy * nx + c0 + j] = S[j * N + swz<C>(yy)];
+        psi[(int64_t)yy * nx + c0 + j] = S[j * PITCH + swz<C>(yy)];
     }
 }
 
