@@ -69,7 +69,7 @@ class Problem1D:
     the scaled strips, where continuing x to z would make it grow)."""
 
     def __init__(self, n, a, b, R0, theta=0.5, kind=T.SHARP, alpha=0.5, a2=2.0,
-                 charge=1.0, dt=0.05, potential=True):
+                 charge=1.0, dt=0.05, potential=True, e_cap=2.0, kmin=0.25):
         self.n, self.a, self.b, self.R0, self.theta = n, a, b, R0, theta
         self.kind, self.alpha, self.dt = kind, alpha, dt
         self.x, self.h = T.grid(n, a, b)
@@ -80,6 +80,8 @@ class Problem1D:
             self.U0 = T.soft_coulomb([self.z], a2, charge)
         else:
             self.U0 = np.zeros(n, dtype=np.complex128)
+        # CAP / TFAP comparison absorbers (Sec. IV): a complex potential
+        self.U0 = self.U0 + T.absorbing_potential(self.x, kind, R0, b, theta, e_cap, kmin)
         self.xc = np.clip(self.x, -R0, R0)
         self.Cs, self.Cd, self.Cu = T.c_tridiag(n, a, b, kind, R0, theta, alpha)
 
@@ -130,7 +132,7 @@ class Problem2D:
     Same contour kind on both axes; U = -Z/sqrt(z_x^2 + z_y^2 + a2)."""
 
     def __init__(self, nx, ny, box, R0, theta=0.4, kind=T.SHARP, alpha=0.5, a2=1.0,
-                 charge=1.0, dt=0.02, potential=True):
+                 charge=1.0, dt=0.02, potential=True, e_cap=2.0, kmin=0.25):
         ax, bx, ay, by = box
         self.nx, self.ny, self.box, self.dt = nx, ny, box, dt
         self.x, self.hx = T.grid(nx, ax, bx)
@@ -142,6 +144,9 @@ class Problem2D:
             self.U = T.soft_coulomb([zx[None, :], zy[:, None]], a2, charge)
         else:
             self.U = np.zeros((ny, nx), dtype=np.complex128)
+        # comparison absorbers: U_a(x) + U_a(y)
+        self.U = (self.U + T.absorbing_potential(self.x, kind, R0, bx, theta, e_cap, kmin)[None, :]
+                  + T.absorbing_potential(self.y, kind, R0, by, theta, e_cap, kmin)[:, None])
         self.U = np.ascontiguousarray(self.U, dtype=np.complex128)
         self.Cx = T.c_tridiag(nx, ax, bx, kind, R0, theta, alpha)
         self.Cy = T.c_tridiag(ny, ay, by, kind, R0, theta, alpha)

@@ -20,8 +20,12 @@ __all__ = [
     "strip_block", "field_E",
 ]
 
-# contour kinds
-SHARP, SECS, TFECS = 0, 1, 2
+# contour kinds; CAP and TFAP are the comparison absorbers of Sec. IV: the
+# contour stays real (q = 1, z = x) and a complex potential absorbs instead
+SHARP, SECS, TFECS, CAP, TFAP = 0, 1, 2, 3, 4
+
+# c of Eq. yTFAP (the value the paper quotes)
+TFAP_C = 2.622057
 
 
 def grid(n: int, a: float, b: float):
@@ -76,6 +80,8 @@ def q_contour(x, kind: int, R0: float, rmax: float, theta: float = 0.0,
         s = (ax[out] - R0) / (rmax - R0)
         with np.errstate(divide="ignore", invalid="ignore"):
             q[out] = np.sqrt(1.0 + 1j * _tfecs_ytilde(s, alpha))
+    elif kind in (CAP, TFAP):
+        pass                                # unscaled: the absorber is a potential
     else:
         raise ValueError("unknown contour kind")
     return q
@@ -118,9 +124,40 @@ def z_contour(x, kind: int, R0: float, rmax: float, theta: float = 0.0,
             im = quad(f_im, 0.0, dd, limit=200, epsabs=1e-14, epsrel=1e-13)[0]
             vals.append(R0 + re + 1j * im)
         z[out] = sg[out] * np.array(vals, dtype=np.complex128)
+    elif kind in (CAP, TFAP):
+        pass
     else:
         raise ValueError("unknown contour kind")
     return z
+
+
+def tfap_y(s):
+    """y(s) of Eq. yTFAP: [a s - b s^3 + 4/(1-s)^2 - 4/(1+s)^2] / c^2 with
+    a = c^3 - 16, b = c^3 - 17."""
+    c = TFAP_C
+    a, b = c ** 3 - 16.0, c ** 3 - 17.0
+    s = np.asarray(s, dtype=np.float64)
+    return (a * s - b * s ** 3 + 4.0 / (1.0 - s) ** 2 - 4.0 / (1.0 + s) ** 2) / (c * c)
+
+
+def absorbing_potential(x, kind: int, R0: float, rmax: float, theta: float = np.pi / 4,
+                        e_cap: float = 2.0, kmin: float = 0.25):
+    """Complex absorbing potential U_a(x) of the comparison absorbers of
+    Sec. IV, zero for |x| <= R0 (= r_s), dx_CS = rmax - R0:
+      CAP:  U_a = E_CAP [1 - q(x)^2] with q of Eq. qSECS (final angle theta)
+            -- Eq. CAP_via_q, the CAP equivalent to ECS at energy E_CAP;
+      TFAP: U_a = -i (k_min^2 / 2) y((|x| - r_s)/dx_CS)  -- Eqs. TFAP, yTFAP.
+    Other kinds have none (zeros)."""
+    x = np.asarray(x, dtype=np.float64)
+    ax = np.abs(x)
+    u = np.zeros(x.shape, dtype=np.complex128)
+    out = ax > R0
+    if kind == CAP:
+        q = np.exp(1j * theta * (ax[out] - R0) / (rmax - R0))
+        u[out] = e_cap * (1.0 - q * q)
+    elif kind == TFAP:
+        u[out] = -0.5j * kmin * kmin * tfap_y((ax[out] - R0) / (rmax - R0))
+    return u
 
 
 def soft_coulomb(z_list, a2: float, charge: float = 1.0):
