@@ -66,8 +66,19 @@ typedef enum { SOFT_C64 = 1, SOFT_C128 = 2 } soft_prec;
  *   SECS:  q = exp[i theta (|x| - R0)/(b - R0)] beyond R0: Eq. qSECS (Sec. IV)
  *          with its final angle pi/4 made the parameter theta.
  *   TFECS: q = sqrt(1 + i y~(s)), y~ = alpha[(1-s)^-2 - (1+s)^-2 - 4s],
- *          s = (|x| - R0)/(b - R0) (Sec. IV, Eq. qTFECS).                   */
-typedef enum { SOFT_CONTOUR_SHARP = 0, SOFT_CONTOUR_SECS = 1, SOFT_CONTOUR_TFECS = 2 } soft_contour;
+ *          s = (|x| - R0)/(b - R0) (Sec. IV, Eq. qTFECS).
+ * The comparison absorbers of Sec. IV keep the contour real (q = 1, z = x,
+ * so C = 0 and no strip) and add a complex potential beyond R0 = r_s:
+ *   CAP:   U_a = E_CAP [1 - q^2] with the SECS q (final angle theta),
+ *          Eq. CAP_via_q;
+ *   TFAP:  U_a = -i (k_min^2/2) y(s), y(s) = [a s - b s^3 + 4/(1-s)^2
+ *          - 4/(1+s)^2]/c^2, a = c^3 - 16, b = c^3 - 17, c = 2.622057
+ *          (Eqs. TFAP, yTFAP).
+ * Plans with an absorber take no laser field (SOFT_ERR_UNSUPPORTED).      */
+typedef enum {
+    SOFT_CONTOUR_SHARP = 0, SOFT_CONTOUR_SECS = 1, SOFT_CONTOUR_TFECS = 2,
+    SOFT_ABSORB_CAP = 3, SOFT_ABSORB_TFAP = 4
+} soft_contour;
 
 typedef struct {
     int ndim;        /* 1 or 2                                             */
@@ -84,6 +95,8 @@ typedef struct {
     int band_width;      /* N_BW of the banded preconditioner [10]           */
     int autotune;        /* 1: time the built kernel variants of every 1D size
                             at plan creation and keep the fastest [0]       */
+    double cap_energy;   /* E_CAP of the linear CAP [2.0]                    */
+    double tfap_kmin;    /* k_min of TFAP [0.25]                             */
 } soft_options;
 
 /* Laser pulse (length gauge, x-polarised), E(t) = E0 sin^2(pi t/T) sin(omega t)

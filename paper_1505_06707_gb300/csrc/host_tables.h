@@ -12,10 +12,13 @@ using cd = std::complex<double>;
 struct ContourFn {
     int kind;
     double R0, rmax, theta, alpha;
-    ContourFn(int kind, double R0, double rmax, double theta, double alpha);
+    double e_cap, kmin;           // comparison absorbers (kinds SOFT_ABSORB_*)
+    ContourFn(int kind, double R0, double rmax, double theta, double alpha, double e_cap = 2.0,
+              double kmin = 0.25);
     bool q(double x, cd* out) const;
     cd inv_q(double x) const;
     cd z(double x) const;
+    cd absorber(double x) const;  // U_a(x); 0 for the contours
 };
 
 // One grid axis: grid, momenta, contour and the periodic tridiagonal C.

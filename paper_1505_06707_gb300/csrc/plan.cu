@@ -86,7 +86,7 @@ int make_tables_1d(Tables1D* T, int n, double a, double b, double R0, double the
     const int logn = ilog2(n);
     T->prec = o.prec; T->logn = logn; T->loge = loge; T->logrm = logrm;
     T->R0 = R0; T->theta = theta;
-    ContourFn cf(o.contour, R0, b, theta, o.tfecs_alpha);
+    ContourFn cf(o.contour, R0, b, theta, o.tfecs_alpha, o.cap_energy, o.tfap_kmin);
     build_axis(T->ax, n, a, b, cf, tau);
     const Axis1D& A = T->ax;
     int rc = find_block(A, &T->blk0, &T->nb);
@@ -97,7 +97,7 @@ int make_tables_1d(Tables1D* T, int n, double a, double b, double R0, double the
         if (A.x[j] < R0) T->iR = j + 1;
     }
     T->U0.resize(n);
-    for (int j = 0; j < n; ++j) T->U0[j] = soft_coulomb(&A.z[j], 1, o.soft_a2, o.charge);
+    for (int j = 0; j < n; ++j) T->U0[j] = soft_coulomb(&A.z[j], 1, o.soft_a2, o.charge) + cf.absorber(A.x[j]);
     // kinetic tables in the forward FFT's output order, 1/N folded in
     const std::vector<int> perm = dif_output_order(logn, logrm);
     std::vector<cd> tk(n), tkh(n), tv(n);
@@ -166,6 +166,9 @@ void soft_default_options(soft_options* opt) {
     opt->soft_a2 = 2.0;
     opt->charge = 1.0;
     opt->band_width = 10;
+    opt->autotune = 0;
+    opt->cap_energy = 2.0;
+    opt->tfap_kmin = 0.25;
 }
 
 const char* soft_strerror(int s) {
@@ -190,7 +193,10 @@ static int check_opts(const soft_options* opt, soft_options* o) {
     soft_default_options(o);
     if (opt) *o = *opt;
     if (o->prec != SOFT_C64 && o->prec != SOFT_C128) return SOFT_ERR_INVALID_ARG;
-    if (o->contour < 0 || o->contour > 2) return SOFT_ERR_INVALID_ARG;
+    if (o->contour < 0 || o->contour > SOFT_ABSORB_TFAP) return SOFT_ERR_INVALID_ARG;
+    if (!(o->cap_energy >= 0) || !(o->tfap_kmin >= 0) || !std::isfinite(o->cap_energy) ||
+        !std::isfinite(o->tfap_kmin))
+        return SOFT_ERR_INVALID_ARG;
     if (!(o->soft_a2 > 0) && o->charge != 0) return SOFT_ERR_INVALID_ARG;
     if (o->band_width < 1) return SOFT_ERR_INVALID_ARG;
     return SOFT_OK;
@@ -329,6 +335,7 @@ static int create_1d(int count, const soft_grid* grids, const double* boxes, con
                 } else {
                     ih.fcls = c->second;
                 }
+                if (o.contour >= SOFT_ABSORB_CAP) return SOFT_ERR_UNSUPPORTED;   // absorbers: no field
                 ih.has_field = 1;
                 ih.E0 = f.E0;
             }
@@ -499,6 +506,7 @@ int soft_plan::set_single_field(const soft_field* f) {
     double E0 = 0;
     if (f && f->E0 != 0.0) {
         if (!(f->omega > 0 && f->ncycles > 0)) return SOFT_ERR_INVALID_ARG;
+        if (opt.contour >= SOFT_ABSORB_CAP) return SOFT_ERR_UNSUPPORTED;   // absorbers: no field
         const double Tp = f->ncycles * 2 * 3.14159265358979323846 / f->omega;
         if (call_cls[0] != f->omega || call_cls[1] != Tp) {
             call_cls[0] = f->omega;

@@ -90,8 +90,8 @@ int create_2d(const soft_grid* grid, const double* box, double R0, double theta,
     if (o.prec == SOFT_C64 && ly >= 10) Q->ley = 5;
     Q->R0 = R0; Q->theta = theta; Q->tau = dt;
     Q->band_width = o.band_width;
-    ContourFn cx(o.contour, R0, box[1], theta, o.tfecs_alpha);
-    ContourFn cy(o.contour, R0, box[3], theta, o.tfecs_alpha);
+    ContourFn cx(o.contour, R0, box[1], theta, o.tfecs_alpha, o.cap_energy, o.tfap_kmin);
+    ContourFn cy(o.contour, R0, box[3], theta, o.tfecs_alpha, o.cap_energy, o.tfap_kmin);
     build_axis(Q->ax, (int)nx, box[0], box[1], cx, dt);
     build_axis(Q->ay, (int)ny, box[2], box[3], cy, dt);
     int rc;
@@ -108,7 +108,8 @@ int create_2d(const soft_grid* grid, const double* box, double R0, double theta,
     for (int64_t yy = 0; yy < ny; ++yy)
         for (int64_t xx = 0; xx < nx; ++xx) {
             const cd z[2] = {Q->ax.z[xx], Q->ay.z[yy]};
-            const cd u = soft_coulomb(z, 2, o.soft_a2, o.charge);
+            const cd u = soft_coulomb(z, 2, o.soft_a2, o.charge) + cx.absorber(Q->ax.x[xx]) +
+                         cy.absorber(Q->ay.x[yy]);
             Q->U[yy * nx + xx] = u;
             tvh[yy * nx + xx] = std::exp(cd(0.0, -0.5 * dt) * u);
         }

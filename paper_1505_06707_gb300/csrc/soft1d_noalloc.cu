@@ -79,6 +79,7 @@ extern "C" int soft_step_noalloc(const soft_plan* P, void* psi, int64_t nsteps,
     d.has_field = 0; d.fcls = 0; d.E0 = 0.0;
     if (field && field->E0 != 0.0) {
         if (!(field->omega > 0 && field->ncycles > 0)) return SOFT_ERR_INVALID_ARG;
+        if (P->opt.contour >= SOFT_ABSORB_CAP) return SOFT_ERR_UNSUPPORTED;   // absorbers: no field
         cls[0] = field->omega;
         cls[1] = field->ncycles * 2 * 3.14159265358979323846 / field->omega;
         d.has_field = 1;

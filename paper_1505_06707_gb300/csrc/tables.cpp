@@ -12,13 +12,33 @@ namespace soft {
 
 static const double PI = 3.14159265358979323846;
 
-ContourFn::ContourFn(int kind, double R0, double rmax, double theta, double alpha)
-    : kind(kind), R0(R0), rmax(rmax), theta(theta), alpha(alpha) {}
+ContourFn::ContourFn(int kind, double R0, double rmax, double theta, double alpha, double e_cap,
+                     double kmin)
+    : kind(kind), R0(R0), rmax(rmax), theta(theta), alpha(alpha), e_cap(e_cap), kmin(kmin) {}
+
+// comparison absorbers of Sec. IV (the contour stays real): the linear CAP
+// U_a = E_CAP [1 - q^2] with the SECS q (Eq. CAP_via_q) and TFAP
+// U_a = -i (k_min^2/2) y(s) (Eqs. TFAP, yTFAP), zero for |x| <= R0
+cd ContourFn::absorber(double x) const {
+    const double ax = std::fabs(x);
+    if (ax <= R0) return 0.0;
+    const double s = (ax - R0) / (rmax - R0);
+    if (kind == SOFT_ABSORB_CAP) {
+        const cd qq = std::polar(1.0, theta * s);
+        return e_cap * (1.0 - qq * qq);
+    }
+    if (kind == SOFT_ABSORB_TFAP) {
+        const double c = 2.622057, a = c * c * c - 16.0, b = c * c * c - 17.0;
+        const double y = (a * s - b * s * s * s + 4.0 / ((1 - s) * (1 - s)) - 4.0 / ((1 + s) * (1 + s))) / (c * c);
+        return cd(0.0, -0.5 * kmin * kmin * y);
+    }
+    return 0.0;
+}
 
 // q(x); returns false where q is infinite (TFECS at |x| = rmax)
 bool ContourFn::q(double x, cd* out) const {
     const double ax = std::fabs(x);
-    if (ax <= R0) { *out = 1.0; return true; }
+    if (ax <= R0 || kind == SOFT_ABSORB_CAP || kind == SOFT_ABSORB_TFAP) { *out = 1.0; return true; }
     const double s = (ax - R0) / (rmax - R0);
     switch (kind) {
     case SOFT_CONTOUR_SHARP: *out = std::polar(1.0, theta); return true;
@@ -50,7 +70,7 @@ static const double GL_W[8] = {0.1894506104550685, 0.1826034150449236, 0.1691565
 // z(x) = int_0^x q (Eq. ECSintdef)
 cd ContourFn::z(double x) const {
     const double ax = std::fabs(x), sg = x < 0 ? -1.0 : 1.0;
-    if (ax <= R0) return x;
+    if (ax <= R0 || kind == SOFT_ABSORB_CAP || kind == SOFT_ABSORB_TFAP) return x;
     const double d = ax - R0;
     switch (kind) {
     case SOFT_CONTOUR_SHARP: return sg * (R0 + std::polar(1.0, theta) * d);

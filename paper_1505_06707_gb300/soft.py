@@ -12,6 +12,7 @@ import os
 
 __all__ = [
     "SoftError", "SOFT_C64", "SOFT_C128", "CONTOUR_SHARP", "CONTOUR_SECS", "CONTOUR_TFECS",
+    "ABSORB_CAP", "ABSORB_TFAP",
     "load", "lib_path", "exported_symbols", "Options", "Field", "soft_create", "soft_create_batch",
     "soft_batch_layout", "soft_step", "soft_step_batch", "soft_step_noalloc", "soft_observe", "sse_pcg_solve",
     "sse_apply_A", "sse_apply_precond", "soft_destroy", "sse_nn_set_weights", "sse_nn_get_weights",
@@ -21,6 +22,7 @@ __all__ = [
 
 SOFT_C64, SOFT_C128 = 1, 2
 CONTOUR_SHARP, CONTOUR_SECS, CONTOUR_TFECS = 0, 1, 2
+ABSORB_CAP, ABSORB_TFAP = 3, 4
 ERR_NOT_CONVERGED = -5
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -51,7 +53,7 @@ class Grid(C.Structure):
 class Options(C.Structure):
     _fields_ = [("prec", C.c_int), ("contour", C.c_int), ("tfecs_alpha", C.c_double),
                 ("soft_a2", C.c_double), ("charge", C.c_double), ("band_width", C.c_int),
-                ("autotune", C.c_int)]
+                ("autotune", C.c_int), ("cap_energy", C.c_double), ("tfap_kmin", C.c_double)]
 
 
 class Field(C.Structure):
@@ -138,12 +140,13 @@ def _check(rc, where):
 
 
 def _options(prec=SOFT_C128, contour=CONTOUR_SHARP, tfecs_alpha=0.5, soft_a2=2.0, charge=1.0,
-             band_width=10, autotune=0):
+             band_width=10, autotune=0, cap_energy=2.0, tfap_kmin=0.25):
     o = Options()
     load().soft_default_options(C.byref(o))
     o.prec, o.contour, o.tfecs_alpha = prec, contour, tfecs_alpha
     o.soft_a2, o.charge, o.band_width = soft_a2, charge, band_width
     o.autotune = autotune
+    o.cap_energy, o.tfap_kmin = cap_energy, tfap_kmin
     return o
 
 

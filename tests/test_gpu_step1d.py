@@ -135,6 +135,33 @@ def test_smooth_contours(contour, prec):
 
 
 @pytest.mark.parametrize("prec", [S.SOFT_C128, S.SOFT_C64])
+@pytest.mark.parametrize("kind", [S.ABSORB_CAP, S.ABSORB_TFAP])
+def test_comparison_absorbers(kind, prec):
+    """The linear CAP (Eq. CAP_via_q, E_CAP = 2) and TFAP (Eqs. TFAP, yTFAP,
+    k_min = 0.25) on the paper's test grid (b = -a = 51.2, r_s = 40,
+    N = 1024, tau = h^2): real contour, complex potential, no strip."""
+    n, b, rs = 1024, 51.2, 40.0
+    h = 2 * b / n
+    x = -b + h * (np.arange(n) + 0.5)
+    psi0 = math.pi ** -0.25 * np.exp(-x ** 2 / 2 + 2j * x)
+    okind = T.CAP if kind == S.ABSORB_CAP else T.TFAP
+    nst = 2000                  # t_max = 20: half the packet is inside the absorber
+    ref = P.Problem1D(n, -b, b, rs, theta=math.pi / 4, kind=okind, dt=h * h, potential=False,
+                      e_cap=2.0, kmin=0.25).step(psi0, nst)
+    assert np.linalg.norm(ref) < 0.95 * np.linalg.norm(psi0)        # the absorber has acted
+    got = gpu_run(n, (-b, b), rs, math.pi / 4, h * h, psi0, nst, prec=prec, contour=kind, charge=0.0,
+                  cap_energy=2.0, tfap_kmin=0.25)
+    assert relerr(got, ref) < tol(prec, nst, n)
+    plan = S.soft_create(n, (-b, b), rs, 0.5, h * h, prec=prec, contour=kind)
+    try:
+        d = torch.tensor(psi0, dtype=CT[prec], device="cuda")
+        with pytest.raises(S.SoftError):                                # absorbers take no field
+            S.soft_step(plan, d, 1, 0.0, field=(0.05, 0.057, 4.0))
+    finally:
+        S.soft_destroy(plan)
+
+
+@pytest.mark.parametrize("prec", [S.SOFT_C128, S.SOFT_C64])
 def test_laser_field_single(prec):
     """One laser-batch instance (N = 2048, h = 1/64, SECS contour reaching
     theta = 0.5, pulse E0 sin^2 sin) for 300 steps from mid-pulse, split over

@@ -79,6 +79,24 @@ def test_small_grids_match_oracle(shape, prec):
     assert launches >= 5 * 40
 
 
+@pytest.mark.parametrize("prec", [S.SOFT_C128, S.SOFT_C64])
+@pytest.mark.parametrize("kind", [S.ABSORB_CAP, S.ABSORB_TFAP])
+def test_comparison_absorbers_2d(kind, prec):
+    """The Sec. IV comparison absorbers on both axes, U_a(x) + U_a(y) on a
+    real contour (no strips): 256^2, 40 steps."""
+    from oracle import tables as T
+    n = 256
+    box = (-40.0, 40.0, -40.0, 40.0)
+    R0 = 30.0
+    psi0 = packet2d(n, n, box, 31 + kind)
+    okind = T.CAP if kind == S.ABSORB_CAP else T.TFAP
+    ref = P.Problem2D(n, n, box, R0, theta=0.4, kind=okind, a2=1.0, dt=0.02, e_cap=2.0,
+                      kmin=0.25).step(psi0, 40)
+    got, _ = run2d(n, n, box, R0, 0.4, 0.02, psi0, 40, prec, soft_a2=1.0, contour=kind,
+                   cap_energy=2.0, tfap_kmin=0.25)
+    assert relerr(got, ref) < tol(prec, 40, n)
+
+
 def test_free_gaussian_closed_form_2d():
     """theta = 0, U = 0: the 2D step must reproduce the separable closed-form
     free Gaussian (summed over periodic images)."""
