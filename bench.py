@@ -159,6 +159,24 @@ def config(prec, instances=N_INST, spc=STEPS_PER_CALL):
             "l2": "inputs larger than L2 (packed state %s)" % ("252 MB c64" if prec == "c64" else "504 MB c128")}
 
 
+def max_over_ranks(ms, world, device="cpu"):
+    """The slowest rank's time sets the whole-job rate: the maximum of every
+    rank's timed region (an all-reduce on the default process group)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank_step, steps, world, ms):
+    """Units all ranks processed (each rank runs its own batch: weak
+    scaling) over the slowest rank's time."""
+    return units_per_rank_step * steps * world / (ms / 1e3)
+
+
 def run_reference(args):
     """The FP64 CPU oracle on a bounded, stratified sample of the workload."""
     import numpy as np
@@ -175,10 +193,9 @@ def run_reference(args):
                          a2=w["a2"], dt=w["dt"]) for w in sample]
     psis = [w["psi0"] for w in sample]
     fields = [(w["E0"], w["omega"], w["ncyc"]) for w in sample]
-    P.step_batch(probs, psis, 1, fields=fields)          # warm-up (page-in, threads)
+    for _ in range(max(1, args.warmup)):                 # untimed warm-up steps
+        P.step_batch(probs, psis, nst, fields=fields)
     times = []
-    for _ in range(max(1, args.warmup)):
-        pass
     for _ in range(max(1, args.steps)):
         t = time.perf_counter()
         P.step_batch(probs, psis, nst, fields=fields)
@@ -192,7 +209,7 @@ def run_reference(args):
            "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": config("c128"),
+           "config": config(args.prec, args.instances, args.steps_per_call),
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -481,13 +498,11 @@ def main():
     clocks = clk.stop()
     ms = ev0.elapsed_time(ev1)
     kms = sum(a.elapsed_time(b) for a, b in kev) / args.steps
+    ms = max_over_ranks(ms, world, dev)
     if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
         dist.barrier()
     sec = ms / 1e3
-    value = pts_call * args.steps * world / sec
+    value = whole_job_value(pts_call, args.steps, world, ms)
     # roofline of the dominant kernel: its size group alone on one stream,
     # timed with events around each launch (the shared timed region above
     # overlaps the groups, which would inflate its duration)
