@@ -70,7 +70,7 @@ row_pass_kernel(Geo2D g, void* __restrict__ psi_v, int row0, const void* __restr
     const VT* __restrict__ tv = reinterpret_cast<const VT*>(g.TVh) + (int64_t)y * N;
     const TT* __restrict__ tkx = reinterpret_cast<const TT*>(tkx_v);
 
-#pragma unroll 4
+#pragma unroll
     for (int j = 0; j < E; ++j) {
         const int n = tid + j * T;
         C v = row[n];
@@ -186,7 +186,8 @@ cny_kernel(Geo2D g, void* __restrict__ psi_v)
     const C* __restrict__ cn = reinterpret_cast<const C*>(g.cny);
     const int c0 = blockIdx.x * TWC;
     const int nb = g.nby, nx = g.nx, ny = g.ny;
-    for (int idx = threadIdx.x; idx < nb * TWC; idx += blockDim.x) {
+#pragma unroll 8
+    for (int idx = threadIdx.x; idx < nb * TWC; idx += blockDim.x) {   // several rows in flight
         const int r = idx / TWC, j = idx % TWC;
         const int yy = (g.blk0y + r) % ny;
         S[r * PITCH + j] = psi[(int64_t)yy * nx + c0 + j];
@@ -248,6 +249,7 @@ cny_kernel(Geo2D g, void* __restrict__ psi_v)
         }
     }
     __syncthreads();
+#pragma unroll 8
     for (int idx = threadIdx.x; idx < nb * TWC; idx += blockDim.x) {
         const int r = idx / TWC, j = idx % TWC;
         const int yy = (g.blk0y + r) % ny;
