@@ -186,6 +186,12 @@ cny_kernel(Geo2D g, void* __restrict__ psi_v)
     const C* __restrict__ cn = reinterpret_cast<const C*>(g.cny);
     const int c0 = blockIdx.x * TWC;
     const int nb = g.nby, nx = g.nx, ny = g.ny;
+    // the LU coefficients (mf, mb, g) are the same for every column: one
+    // copy in shared memory, read by each lane at its own row (a warp's
+    // rows are a chunk apart, which in global memory touched one cache
+    // line per lane)
+    C* Scn = S + nb * PITCH;
+    for (int i = threadIdx.x; i < 3 * nb; i += blockDim.x) Scn[i] = __ldg(&cn[i]);
 #pragma unroll 8
     for (int idx = threadIdx.x; idx < nb * TWC; idx += blockDim.x) {   // several rows in flight
         const int r = idx / TWC, j = idx % TWC;
@@ -203,7 +209,7 @@ cny_kernel(Geo2D g, void* __restrict__ psi_v)
     for (int c = 0; c < CH; ++c) {
         const int i = i0 + c;
         if (c < ch && i < nb) {
-            const C m = __ldg(&cn[i]);
+            const C m = Scn[i];
             yl = cfma(m, yl, S[i * PITCH + w]);
             Mp = cmul(m, Mp);
             yv[c] = yl;
@@ -216,7 +222,7 @@ cny_kernel(Geo2D g, void* __restrict__ psi_v)
         for (int c = 0; c < CH; ++c) {
             const int i = i0 + c;
             if (c < ch && i < nb) {
-                pr = cmul(__ldg(&cn[i]), pr);
+                pr = cmul(Scn[i], pr);
                 yv[c] = cfma(pr, carry, yv[c]);
             }
         }
@@ -227,8 +233,8 @@ cny_kernel(Geo2D g, void* __restrict__ psi_v)
     for (int c = CH - 1; c >= 0; --c) {
         const int i = i0 + c;
         if (c < ch && i < nb) {
-            const C m = __ldg(&cn[nb + i]);
-            const C gg = __ldg(&cn[2 * nb + i]);
+            const C m = Scn[nb + i];
+            const C gg = Scn[2 * nb + i];
             xl = cfma(m, xl, cmul(gg, yv[c]));
             Mp = cmul(m, Mp);
             yv[c] = xl;
@@ -241,7 +247,7 @@ cny_kernel(Geo2D g, void* __restrict__ psi_v)
         for (int c = CH - 1; c >= 0; --c) {
             const int i = i0 + c;
             if (c < ch && i < nb) {
-                pr = cmul(__ldg(&cn[nb + i]), pr);
+                pr = cmul(Scn[nb + i], pr);
                 const C xv = cfma(pr, carry, yv[c]);
                 const C rc = S[i * PITCH + w];
                 S[i * PITCH + w] = cmk<C>(2 * xv.x - rc.x, 2 * xv.y - rc.y);
@@ -295,7 +301,7 @@ int launch_col_t(const Geo2D& g, void* psi, const void* tky, cudaStream_t st) {
 
 template <typename C, int CH>
 int launch_cny_t(const Geo2D& g, void* psi, cudaStream_t st) {
-    const size_t smem = sizeof(C) * (size_t)g.nby * 17;
+    const size_t smem = sizeof(C) * (size_t)g.nby * (17 + 3);   // tile + LU coefficients
     auto k = cny_kernel<C, CH>;
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
