@@ -102,8 +102,8 @@ int create_2d(const soft_grid* grid, const double* box, double R0, double theta,
     const int thr = (int)(nx >> Q->lex);
     if ((nbx + thr - 1) / thr > (1 << Q->lex) / 4 + 2) return SOFT_ERR_UNSUPPORTED;
     if ((nby + 31) / 32 > 24) return SOFT_ERR_UNSUPPORTED;
-    // the y-strip pass holds a 16-column tile and the LU coefficients in shared memory
-    if ((o.prec == SOFT_C64 ? 8 : 16) * (size_t)nby * 20 > 227 * 1024) return SOFT_ERR_UNSUPPORTED;
+    // the y-strip pass holds an 8-column tile and the LU coefficients in shared memory
+    if ((o.prec == SOFT_C64 ? 8 : 16) * (size_t)nby * 12 > 227 * 1024) return SOFT_ERR_UNSUPPORTED;
     // potential at (z(x), z(y)) and e^{-iU tau/2}
     Q->U.resize((size_t)nx * ny);
     std::vector<cd> tvh((size_t)nx * ny);

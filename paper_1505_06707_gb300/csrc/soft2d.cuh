@@ -172,14 +172,16 @@ col_pass_kernel(Geo2D g, void* __restrict__ psi_v, const void* __restrict__ tky_
     }
 }
 
-// y-strip Crank-Nicolson: 16 columns per CTA, one warp per column, each lane a
-// contiguous chunk of the nby block rows; the tile is staged in shared memory
-// with a padded pitch so that the lanes' strided rows hit distinct banks.
-template <typename C, int CH>
-__global__ void __launch_bounds__(512, 1)
+// y-strip Crank-Nicolson: TWC columns per CTA, one warp per column, each lane
+// a contiguous chunk of the nby block rows; the tile is staged in shared
+// memory with a padded pitch so that the lanes' strided rows hit distinct
+// banks.  Small CTAs (two per SM) let one CTA's tile loads overlap another's
+// sweeps.
+template <typename C, int CH, int TWC>
+__global__ void __launch_bounds__(32 * TWC, 512 / (32 * TWC))
 cny_kernel(Geo2D g, void* __restrict__ psi_v)
 {
-    constexpr int TWC = 16, PITCH = TWC + 1;
+    constexpr int PITCH = TWC + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* S = reinterpret_cast<C*>(smem_raw);
     C* __restrict__ psi = reinterpret_cast<C*>(psi_v);
@@ -301,13 +303,14 @@ int launch_col_t(const Geo2D& g, void* psi, const void* tky, cudaStream_t st) {
 
 template <typename C, int CH>
 int launch_cny_t(const Geo2D& g, void* psi, cudaStream_t st) {
-    const size_t smem = sizeof(C) * (size_t)g.nby * (17 + 3);   // tile + LU coefficients
-    auto k = cny_kernel<C, CH>;
+    constexpr int TWC = 8;
+    const size_t smem = sizeof(C) * (size_t)g.nby * (TWC + 1 + 3);   // tile + LU coefficients
+    auto k = cny_kernel<C, CH, TWC>;
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return SOFT_ERR_CUDA;
     if (g.nby <= 0 || !psi) return SOFT_OK;
-    k<<<g.nx / 16, 512, smem, st>>>(g, psi);
+    k<<<g.nx / TWC, 32 * TWC, smem, st>>>(g, psi);
     return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
 }
 
