@@ -315,6 +315,43 @@ def bench_pcg(S, torch, dev, args):
             "workload": "1024^2 on [-200,200]^2, sharp ECS R0=150 theta=0.4, 64 energies in [0.05,2]"}
 
 
+def bench_conv(S, torch, dev, args, plan=None):
+    """The learned correction's forward pass alone (three 3x3 convolutions,
+    2 -> 32 -> 32 -> 2 channels, BF16 operands on the tensor cores, FP32
+    accumulate) on 16 fields of the stationary workload's 1024^2 grid,
+    against the BF16 tensor peak."""
+    import workloads as W
+    w = W.w4()
+    n = w["nx"]
+    own = plan is None
+    if own:
+        plan = S.soft_create((n, n), w["box"], w["R0"], w["theta"], 0.02, prec=S.SOFT_C128,
+                             soft_a2=w["a2"])
+    st = torch.cuda.current_stream(dev)
+    nf = 16
+    xf = torch.randn((nf, n, n), dtype=torch.complex64, device=dev)
+    yf = torch.zeros((nf, n, n, 2), dtype=torch.float32, device=dev)
+    for _ in range(3):
+        S.sse_nn_forward(plan, xf, yf, stream=st)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    for a_, b_ in ev:
+        a_.record(st)
+        S.sse_nn_forward(plan, xf, yf, stream=st)
+        b_.record(st)
+    torch.cuda.synchronize()
+    fms = sum(a_.elapsed_time(b_) for a_, b_ in ev) / len(ev)
+    if own:
+        S.soft_destroy(plan)
+    flops = 2.0 * 9 * (2 * 32 + 32 * 32 + 32 * 2) * nf * n * n
+    peaks, psrc = _peaks()
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    return {"fields": nf, "ms": fms, "tflops": flops / (fms / 1e3) / 1e12,
+            "peak_bf16_tflops": bf16, "frac": flops / (fms / 1e3) / 1e12 / bf16,
+            "peak_source": psrc, "flop_per_point": flops / (nf * n * n),
+            "path": "warp mma.sync m16n8k16 BF16, FP32 accumulate"}
+
+
 def bench_learned(S, torch, dev, args):
     """The learned correction on the stationary workload: errors of plain
     banded CG runs at 8 training energies are cut into 128^2 crops and the
@@ -367,6 +404,7 @@ def bench_learned(S, torch, dev, args):
            "harvest_s": t_harvest, "train_s": t_train, "train_steps": 400,
            "loss_first": float(np.mean(losses[:10])), "loss_last": float(np.mean(losses[-10:])),
            "test_energies": len(test_E), "gamma": gamma}
+    res["conv_forward"] = bench_conv(S, torch, dev, args, plan)
     out = torch.zeros((len(test_E), n, n), dtype=torch.complex128, device=dev)
     for name, pc in (("cocg_band", 1), ("fgcr_band", 3), ("fgcr_band_learned", 2)):
         out.zero_()
@@ -396,7 +434,7 @@ def main():
     ap.add_argument("--steps-per-call", type=int, default=STEPS_PER_CALL)
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the 2D step and stationary-solver measurements")
-    ap.add_argument("--only", choices=["2d", "pcg", "learned"], default=None,
+    ap.add_argument("--only", choices=["2d", "pcg", "learned", "conv"], default=None,
                     help="run one of the extra measurements alone (for profiling captures; not a bench line)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -406,7 +444,7 @@ def main():
         import paper_1505_06707_gb300 as S
         dev = torch.device("cuda", 0)
         torch.cuda.set_device(dev)
-        fn = {"2d": bench_2d, "pcg": bench_pcg, "learned": bench_learned}[args.only]
+        fn = {"2d": bench_2d, "pcg": bench_pcg, "learned": bench_learned, "conv": bench_conv}[args.only]
         print(json.dumps({"only": args.only, "result": fn(S, torch, dev, args)}))
         return
 
