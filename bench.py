@@ -315,6 +315,30 @@ def bench_pcg(S, torch, dev, args):
             "workload": "1024^2 on [-200,200]^2, sharp ECS R0=150 theta=0.4, 64 energies in [0.05,2]"}
 
 
+def bench_accuracy(S, torch, dev, args, sizes=(2048,)):
+    """Accuracy of the complex64 path: one laser-batch instance per size
+    propagated over the whole pulse (22046 steps of dt = 0.02) in complex64
+    and in complex128 on the GPU (complex128 matches the FP64 oracle to
+    1e-11 in the tests); rel-L2 of the difference at the end."""
+    import numpy as np
+    import workloads as W
+    out = {}
+    for n in sizes:
+        w = next(v for v in (W.w2_instance(j) for j in range(256)) if v["n"] == n)
+        nst = int(round(w["ncyc"] * 2 * math.pi / w["omega"] / w["dt"]))
+        res = {}
+        for prec, name, ct in ((S.SOFT_C64, "c64", torch.complex64), (S.SOFT_C128, "c128", torch.complex128)):
+            pl = S.soft_create(n, (w["a"], w["b"]), w["R0"], w["theta"], w["dt"], prec=prec,
+                               contour=w["contour"], soft_a2=w["a2"])
+            d = torch.tensor(w["psi0"], dtype=ct, device=dev)
+            S.soft_step(pl, d, nst, 0.0, field=(w["E0"], w["omega"], w["ncyc"]))
+            res[name] = d.cpu().numpy().astype(np.complex128)
+            S.soft_destroy(pl)
+        out[str(n)] = {"steps": nst, "rel_l2_c64_vs_c128":
+                       float(np.linalg.norm(res["c64"] - res["c128"]) / np.linalg.norm(res["c128"]))}
+    return out
+
+
 def bench_conv(S, torch, dev, args, plan=None):
     """The learned correction's forward pass alone (three 3x3 convolutions,
     2 -> 32 -> 32 -> 2 channels, BF16 operands on the tensor cores, FP32
@@ -434,7 +458,7 @@ def main():
     ap.add_argument("--steps-per-call", type=int, default=STEPS_PER_CALL)
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the 2D step and stationary-solver measurements")
-    ap.add_argument("--only", choices=["2d", "pcg", "learned", "conv"], default=None,
+    ap.add_argument("--only", choices=["2d", "pcg", "learned", "conv", "accuracy"], default=None,
                     help="run one of the extra measurements alone (for profiling captures; not a bench line)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -444,8 +468,12 @@ def main():
         import paper_1505_06707_gb300 as S
         dev = torch.device("cuda", 0)
         torch.cuda.set_device(dev)
-        fn = {"2d": bench_2d, "pcg": bench_pcg, "learned": bench_learned, "conv": bench_conv}[args.only]
-        print(json.dumps({"only": args.only, "result": fn(S, torch, dev, args)}))
+        if args.only == "accuracy":
+            r = bench_accuracy(S, torch, dev, args, sizes=(2048, 4096, 8192, 16384))
+        else:
+            fn = {"2d": bench_2d, "pcg": bench_pcg, "learned": bench_learned, "conv": bench_conv}[args.only]
+            r = fn(S, torch, dev, args)
+        print(json.dumps({"only": args.only, "result": r}))
         return
 
     import numpy as np
@@ -608,6 +636,7 @@ def main():
     out["gpu_launches"] = int(launches_per_call * args.steps)
     out["clocks"] = clocks
     if not args.no_extra:
+        out["fp32_accuracy"] = bench_accuracy(S, torch, dev, args)
         out["w3_2d"] = bench_2d(S, torch, dev, args)
         out["w4_pcg"] = bench_pcg(S, torch, dev, args)
         out["w5_learned"] = bench_learned(S, torch, dev, args)

@@ -104,8 +104,14 @@ static int build_pc(Plan2D* Q, int type, PcgTables& T, int prec = SOFT_C128) {
     g.xbx = uc(bx.xb); g.xby = uc(by.xb);
     g.lamx = uc(bx.lam); g.lamy = uc(by.lam);
     if (prec == SOFT_C64) {      // FFT twiddles of the FP32 passes
-        g.Wx = uc(pass_twiddles(Q->lx, Q->lrx));
-        g.Wy = uc(pass_twiddles(Q->ly, Q->lry));
+        auto ut = [&](const std::vector<cd>& v) -> const void* {
+            void* d = nullptr;
+            if (upload_tw(&d, v, prec)) return nullptr;
+            T.bufs[i++] = d;
+            return d;
+        };
+        g.Wx = ut(pass_twiddles(Q->lx, Q->lrx));
+        g.Wy = ut(pass_twiddles(Q->ly, Q->lry));
     }
     for (int k = 0; k < i; ++k)
         if (!T.bufs[k]) return SOFT_ERR_OOM;

@@ -141,8 +141,8 @@ int create_2d(const soft_grid* grid, const double* box, double R0, double theta,
         cny = mfy; cny.insert(cny.end(), mby.begin(), mby.end()); cny.insert(cny.end(), gy.begin(), gy.end());
     }
     const int pr = o.prec;
-    if ((rc = upload_c(&Q->Wx, pass_twiddles(lx, Q->lrx), pr))) return rc;
-    if ((rc = upload_c(&Q->Wy, pass_twiddles(ly, Q->lry), pr))) return rc;
+    if ((rc = upload_tw(&Q->Wx, pass_twiddles(lx, Q->lrx), pr))) return rc;
+    if ((rc = upload_tw(&Q->Wy, pass_twiddles(ly, Q->lry), pr))) return rc;
     if ((rc = upload_tab(&Q->TKx, ktab(Q->ax, lx, Q->lrx, 1.0, false), pr))) return rc;
     if ((rc = upload_tab(&Q->TKhx, ktab(Q->ax, lx, Q->lrx, 0.5, false), pr))) return rc;
     if ((rc = upload_tab(&Q->TKy, ktab(Q->ay, ly, Q->lry, 1.0, true), pr))) return rc;

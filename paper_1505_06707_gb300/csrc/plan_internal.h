@@ -11,6 +11,7 @@ int upload(void** dst, const void* src, size_t bytes);
 int upload_c(void** dst, const std::vector<cd>& v, int prec);
 int upload_tab(void** dst, const std::vector<cd>& v, int prec);
 int upload_vtab(void** dst, const std::vector<cd>& v, int prec);
+int upload_tw(void** dst, const std::vector<cd>& v, int prec);
 int make_tables_1d(Tables1D* T, int n, double a, double b, double R0, double theta, double tau,
                    const soft_options& o, int loge, int logrm);
 
