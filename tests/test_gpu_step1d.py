@@ -197,8 +197,6 @@ def test_batch_mixed_sizes_with_fields(prec):
     """A batch of instances of the laser workload (mixed N, own E0 each)
     advanced in one call; each compared with its own oracle run."""
     idx = [0, 1, 2, 3, 5, 8, 13, 21]
-    if prec == S.SOFT_C128:
-        idx = [j for j in idx if W.w2_instance(j)["n"] <= 8192]
     ws = [W.w2_instance(j) for j in idx]
     nst, t0 = 40, 50.0
     plan = S.soft_create_batch([w["n"] for w in ws], [(w["a"], w["b"]) for w in ws],
@@ -251,7 +249,7 @@ def test_autotuned_batch_matches_default(prec):
     """A batch plan whose kernel variants were chosen by timing (autotune)
     computes the same states as the default variants, and repeated calls
     (replayed from the captured graph) continue the propagation correctly."""
-    idx = [j for j in range(40) if prec == S.SOFT_C64 or W.w2_instance(j)["n"] <= 8192][:12]
+    idx = list(range(12))
     ws = [W.w2_instance(j) for j in idx]
     args = ([w["n"] for w in ws], [(w["a"], w["b"]) for w in ws], [w["R0"] for w in ws],
             [w["theta"] for w in ws], [(w["E0"], w["omega"], w["ncyc"]) for w in ws], W.W2_DT)
@@ -277,3 +275,42 @@ def test_autotuned_batch_matches_default(prec):
     for out in outs:
         for o, w, r in zip(offs, ws, refs):
             assert relerr(out[o:o + w["n"]], r) < tol(prec, 30, w["n"])
+
+
+@pytest.mark.parametrize("prec", [S.SOFT_C64, S.SOFT_C128])
+def test_w2_full_batch_sampled(prec):
+    """The whole laser batch (4096 instances, N = 2048 .. 16384) advanced by
+    one call of 256 steps, as the benchmark launches it (one plan per size,
+    autotuned kernels); 8 sampled instances, two per size, compared with
+    their own oracle runs."""
+    ws = [W.w2_instance(j) for j in range(4096)]
+    nst, t0 = 256, 0.0
+    sample = []
+    for n in W.W2_SIZES:
+        sample += [i for i, w in enumerate(ws) if w["n"] == n][:2]
+    got = {}
+    for n in W.W2_SIZES:
+        members = [i for i, w in enumerate(ws) if w["n"] == n]
+        g = [ws[i] for i in members]
+        plan = S.soft_create_batch([w["n"] for w in g], [(w["a"], w["b"]) for w in g],
+                                   [w["R0"] for w in g], [w["theta"] for w in g],
+                                   [(w["E0"], w["omega"], w["ncyc"]) for w in g], W.W2_DT,
+                                   prec=prec, contour=W.W2_CONTOUR, autotune=1)
+        try:
+            offs, tot = S.soft_batch_layout(plan)
+            d = torch.tensor(np.concatenate([w["psi0"] for w in g]), dtype=CT[prec], device="cuda")
+            S.soft_step_batch(plan, d, nst, t0)
+            torch.cuda.synchronize()
+            h = d.cpu().numpy().astype(np.complex128)
+        finally:
+            S.soft_destroy(plan)
+        for k, i in enumerate(members):
+            if i in sample:
+                got[i] = h[offs[k]:offs[k] + n]
+    sw = [ws[i] for i in sample]
+    probs = [P.Problem1D(w["n"], w["a"], w["b"], w["R0"], theta=w["theta"], kind=w["contour"],
+                         a2=w["a2"], dt=w["dt"]) for w in sw]
+    refs = P.step_batch(probs, [w["psi0"] for w in sw], nst, t0s=[t0] * len(sw),
+                        fields=[(w["E0"], w["omega"], w["ncyc"]) for w in sw])
+    for i, w, r in zip(sample, sw, refs):
+        assert relerr(got[i], r) < tol(prec, nst, w["n"]), (i, w["n"])
