@@ -54,7 +54,6 @@ struct Group1D {                  // instances sharing one kernel configuration
     int logn = 0, loge = 0, logrm = 0;
     std::vector<int> members;     // instance indices
     Inst1D* d_inst = nullptr;     // device descriptors
-    size_t smem = 0;
 };
 
 // kernel launchers (defined in soft1d_*.cu)
@@ -70,7 +69,6 @@ int soft1d_variants(int prec, int logn, int* loge, int* logrm, int maxv);
 int launch_advance_time(double* d_t, double dt, cudaStream_t st);
 bool soft1d_supported(int prec, int logn, int loge, int logrm);
 void soft1d_default_cfg(int prec, int logn, int* loge, int* logrm);
-size_t soft1d_smem_bytes(int prec, int logn, int loge, int logrm);
 
 int launch_observe1d(int prec, const Inst1D* d_inst, int count, const void* psi,
                      double* norm_in, double* flux, cudaStream_t st);

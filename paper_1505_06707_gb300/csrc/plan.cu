@@ -509,7 +509,6 @@ int soft_plan::build_1d_device() {
         std::vector<Inst1D> d;
         for (int i : g.members) d.push_back(descriptor(i));
         if ((rc = upload((void**)&g.d_inst, d.data(), d.size() * sizeof(Inst1D)))) return rc;
-        g.smem = soft1d_smem_bytes(prec, g.logn, g.loge, g.logrm);
     }
     h_obs.clear();
     for (size_t i = 0; i < inst.size(); ++i) h_obs.push_back(descriptor((int)i));

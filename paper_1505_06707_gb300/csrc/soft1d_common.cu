@@ -48,20 +48,6 @@ int soft1d_variants(int prec, int logn, int* loge, int* logrm, int maxv) {
     return k;
 }
 
-// shared memory of soft1d_kernel (state, twiddles of every pass, scan
-// scratch, field phases)
-size_t soft1d_smem_bytes(int prec, int logn, int loge, int logrm) {
-    const size_t c = prec == SOFT_C64 ? 8 : 16;
-    size_t tw = 0;
-    for (int logl = logn; logl > 0;) {
-        const int lr = logl >= logrm ? logrm : logl;
-        tw += 4 * (size_t(1) << (logl - lr));
-        logl -= lr;
-    }
-    const bool gm = c * (size_t(1) << logn) > 160 * 1024;   // Cfg1D::GM: state stays in global memory
-    return c * ((gm ? 0 : (size_t(1) << logn)) + tw + 64 + (size_t(1) << loge) + 36) + 64;
-}
-
 int launch_soft1d(int prec, int logn, int loge, int logrm, const Inst1D* d_inst, int count,
                   void* psi, int64_t nsteps, const double* ftab, int64_t ftab_stride, int* d_status,
                   cudaStream_t st, size_t* smem_out) {
