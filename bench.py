@@ -296,7 +296,9 @@ def bench_pcg(S, torch, dev, args):
     S.sse_pcg_solve(plan, E[:2], f, out, tol=w["tol"], maxit=4, precond=1, stream=st)   # warm-up
     torch.cuda.synchronize()
     res = {}
-    for pc, name in ((1, "band_fp64"), (4, "band_fp32")):
+    names = {1: "band_fp64", 4: "band_fp32", 5: "mixed_fp32_reliable"}
+    for pc in (int(v) for v in args.pcg_precond.split(",")):
+        name = names[pc]
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
         rc, its, rr = S.sse_pcg_solve(plan, E, f, out, tol=w["tol"], maxit=3000, precond=pc, stream=st)
@@ -310,8 +312,10 @@ def bench_pcg(S, torch, dev, args):
     del out
     best = max(res.values(), key=lambda r: r["solves_per_s"] if r["status"] == 0 else 0)
     return {"solves_per_s": best["solves_per_s"], "energies": len(E), **res,
-            "precond": "banded ECS (N_BW = 10): FP64 (precond 1) and FP32 arithmetic (precond 4)",
-            "precision": "c128 state, FP64 A, residual and dots",
+            "precond": "banded ECS (N_BW = 10): FP64 (precond 1), FP32 arithmetic (precond 4), "
+                       "FP32 A and preconditioner with FP64 reliable updates (precond 5)",
+            "precision": "c128 state, FP64 dots; FP64 A and residual (1, 4); FP32 A inside the "
+                         "iteration with the FP64 true residual deciding convergence (5)",
             "workload": "1024^2 on [-200,200]^2, sharp ECS R0=150 theta=0.4, 64 energies in [0.05,2]"}
 
 
@@ -460,6 +464,8 @@ def main():
                     help="skip the 2D step and stationary-solver measurements")
     ap.add_argument("--only", choices=["2d", "pcg", "learned", "conv", "accuracy"], default=None,
                     help="run one of the extra measurements alone (for profiling captures; not a bench line)")
+    ap.add_argument("--pcg-precond", default="1,4,5",
+                    help="stationary-solver modes to time (sse_pcg_solve precond values)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

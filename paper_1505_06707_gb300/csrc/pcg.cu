@@ -33,9 +33,12 @@ struct Pcg {
     double2 *rho = nullptr, *alpha = nullptr, *beta = nullptr;
     double *relres = nullptr, *fnorm2 = nullptr;
     int *active = nullptr, *iters = nullptr, *status = nullptr, *nactive = nullptr;
-    // shared A tables and the preconditioners
+    double* rref = nullptr;      // reliable updates of the FP32-A iteration
+    int *upd = nullptr, *lastu = nullptr, *mode = nullptr, *act32 = nullptr, *act64 = nullptr;
+    // A tables in FP64 and FP32, and the preconditioners
     void *U = nullptr, *Cx = nullptr, *Cy = nullptr, *Kx = nullptr, *Ky = nullptr;
-    PcgTables pc[3];             // simple, banded, banded with FP32 tables
+    void *U32 = nullptr, *Cx32 = nullptr, *Cy32 = nullptr, *Kx32 = nullptr, *Ky32 = nullptr;
+    PcgTables pc[3];             // simple, banded, banded with FP32 tables (and the FP32 A)
     bool tables = false;
     // flexible GCR: GCR_M stored direction pairs per energy
     static constexpr int GCR_M = 16;
@@ -45,7 +48,8 @@ struct Pcg {
     int gcap = 0;
     ~Pcg() {
         void* v[] = {r, z, p, w, t, dE, part, part2, rho, alpha, beta, relres, fnorm2, active, iters,
-                     status, nactive, U, Cx, Cy, Kx, Ky, gP, gQ, gbeta, gpart, gqn};
+                     status, nactive, rref, upd, lastu, mode, act32, act64, U, Cx, Cy, Kx, Ky, U32, Cx32, Cy32, Kx32, Ky32,
+                     gP, gQ, gbeta, gpart, gqn};
         for (void* b : v) cudaFree(b);
         for (auto& T : pc)
             for (void* b : T.bufs) cudaFree(b);
@@ -136,14 +140,19 @@ static int ensure_tables(Plan2D* Q) {
     if ((rc = upload_c(&S->Cy, cat(Q->ay), SOFT_C128))) return rc;
     if ((rc = upload_tab(&S->Kx, ksq_tab(Q->ax, Q->lx, Q->lrx), SOFT_C128))) return rc;
     if ((rc = upload_tab(&S->Ky, ksq_tab(Q->ay, Q->ly, Q->lry), SOFT_C128))) return rc;
+    if ((rc = upload_c(&S->U32, Q->U, SOFT_C64))) return rc;
+    if ((rc = upload_c(&S->Cx32, cat(Q->ax), SOFT_C64))) return rc;
+    if ((rc = upload_c(&S->Cy32, cat(Q->ay), SOFT_C64))) return rc;
+    if ((rc = upload_tab(&S->Kx32, ksq_tab(Q->ax, Q->lx, Q->lrx), SOFT_C64))) return rc;
+    if ((rc = upload_tab(&S->Ky32, ksq_tab(Q->ay, Q->ly, Q->lry), SOFT_C64))) return rc;
     for (int type = 0; type < 3; ++type) {
         const bool f32 = type == 2;
         if ((rc = build_pc(Q, f32 ? 1 : type, S->pc[type], f32 ? SOFT_C64 : SOFT_C128))) return rc;
         PcgGeo& g = S->pc[type].geo;
         g.nx = Q->nx; g.ny = Q->ny; g.N = S->N;
         if (!f32) { g.Wx = Q->Wx; g.Wy = Q->Wy; }
-        g.Kx = S->Kx; g.Ky = S->Ky; g.U = S->U;
-        g.Cx = S->Cx; g.Cy = S->Cy;
+        g.Kx = f32 ? S->Kx32 : S->Kx; g.Ky = f32 ? S->Ky32 : S->Ky; g.U = f32 ? S->U32 : S->U;
+        g.Cx = f32 ? S->Cx32 : S->Cx; g.Cy = f32 ? S->Cy32 : S->Cy;
         g.nbx = Q->geo.nbx; g.blk0x = Q->geo.blk0x; g.nby = Q->geo.nby; g.blk0y = Q->geo.blk0y;
     }
     // set the kernels' shared-memory attributes outside any capture
@@ -158,6 +167,8 @@ static int ensure_tables(Plan2D* Q) {
         if ((rc = pcg_pc32_row(Q->lx, which, S->pc[2].geo, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0)))
             return rc;
     if ((rc = pcg_pc32_col(Q->ly, S->pc[2].geo, nullptr, nullptr, nullptr, 0, 0))) return rc;
+    if ((rc = pcg_a32_row(Q->lx, S->pc[2].geo, nullptr, nullptr, nullptr, nullptr, 0, 0))) return rc;
+    if ((rc = pcg_a32_col(Q->ly, S->pc[2].geo, nullptr, nullptr, nullptr, nullptr, 0, 0, 0))) return rc;
     S->tables = true;
     return SOFT_OK;
 }
@@ -168,9 +179,14 @@ static int ensure_workspace(Plan2D* Q, int nE) {
     Pcg* S = Q->pcg;
     if (S->nEcap >= nE) return SOFT_OK;
     void* v[] = {S->r, S->z, S->p, S->w, S->t, S->dE, S->part, S->part2, S->rho, S->alpha, S->beta,
-                 S->relres, S->active, S->iters, S->status};
+                 S->relres, S->active, S->iters, S->status, S->rref, S->upd, S->lastu, S->mode,
+                 S->act32, S->act64};
     for (void* b : v) cudaFree(b);
     S->r = S->z = S->p = S->w = S->t = nullptr;
+    S->dE = S->relres = S->rref = nullptr;
+    S->part = S->part2 = S->rho = S->alpha = S->beta = nullptr;
+    S->active = S->iters = S->status = S->upd = S->lastu = S->mode = S->act32 = S->act64 = nullptr;
+    S->nEcap = 0;
     const size_t vb = sizeof(double2) * (size_t)S->N * nE;
     S->nparts_max = std::max(std::max(Q->ny, pcg_col_blocks(Q->nx)), 256);
     if ((rc = cuda_status(cudaMalloc(&S->r, vb)))) return rc;
@@ -188,6 +204,12 @@ static int ensure_workspace(Plan2D* Q, int nE) {
     if ((rc = cuda_status(cudaMalloc((void**)&S->active, sizeof(int) * nE)))) return rc;
     if ((rc = cuda_status(cudaMalloc((void**)&S->iters, sizeof(int) * nE)))) return rc;
     if ((rc = cuda_status(cudaMalloc((void**)&S->status, sizeof(int) * nE)))) return rc;
+    if ((rc = cuda_status(cudaMalloc((void**)&S->rref, sizeof(double) * nE)))) return rc;
+    if ((rc = cuda_status(cudaMalloc((void**)&S->upd, sizeof(int) * nE)))) return rc;
+    if ((rc = cuda_status(cudaMalloc((void**)&S->lastu, sizeof(int) * nE)))) return rc;
+    if ((rc = cuda_status(cudaMalloc((void**)&S->mode, sizeof(int) * nE)))) return rc;
+    if ((rc = cuda_status(cudaMalloc((void**)&S->act32, sizeof(int) * nE)))) return rc;
+    if ((rc = cuda_status(cudaMalloc((void**)&S->act64, sizeof(int) * nE)))) return rc;
     if (!S->fnorm2 && (rc = cuda_status(cudaMalloc((void**)&S->fnorm2, sizeof(double))))) return rc;
     if (!S->nactive && (rc = cuda_status(cudaMalloc((void**)&S->nactive, sizeof(int))))) return rc;
     S->nEcap = nE;
@@ -223,6 +245,17 @@ static int apply_A(Plan2D* Q, const void* p, void* w, const double* dE, const in
     if ((rc = pcg_row(Q->lx, 0, g, p, w, nullptr, dE, act, nullptr, nE, st))) return rc;
     Q->launches += 2;
     return pcg_col(Q->ly, 0, g, p, w, dE, act, part, nE, st);
+}
+
+// w = A p with A computing in FP32 (p, w complex128); partials of p^T w, at
+// the stride of the FP64 column pass
+static int apply_A32(Plan2D* Q, const void* p, void* w, const double* dE, const int* act,
+                     double2* part, int nE, cudaStream_t st) {
+    const PcgGeo& g = Q->pcg->pc[2].geo;
+    int rc;
+    if ((rc = pcg_a32_row(Q->lx, g, p, w, dE, act, nE, st))) return rc;
+    Q->launches += 2;
+    return pcg_a32_col(Q->ly, g, p, w, act, part, pcg_col_blocks(Q->nx), nE, st);
 }
 
 static int ensure_gcr(Pcg* S, int nE) {
@@ -265,6 +298,21 @@ int sse_apply_A(soft_plan* P, double E, const void* x, void* y, void* stream) {
     return rc;
 }
 
+int sse_apply_A32(soft_plan* P, double E, const void* x, void* y, void* stream) {
+    if (!P || !x || !y || P->kind != 2 || !std::isfinite(E)) return SOFT_ERR_INVALID_ARG;
+    if (P->prec != SOFT_C128) return SOFT_ERR_UNSUPPORTED;
+    Plan2D* Q = P->p2;
+    int rc = ensure_workspace(Q, 1);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    Q->launches = 0;
+    if ((rc = cuda_status(cudaMemcpyAsync(Q->pcg->dE, &E, sizeof(double), cudaMemcpyHostToDevice, st))))
+        return rc;
+    rc = apply_A32(Q, x, y, Q->pcg->dE, nullptr, Q->pcg->part, 1, st);
+    P->last_launches = Q->launches;
+    return rc;
+}
+
 int sse_apply_precond(soft_plan* P, double E, int precond, const void* x, void* y, void* stream) {
     if (!P || !x || !y || P->kind != 2 || !std::isfinite(E)) return SOFT_ERR_INVALID_ARG;
     if (precond != 0 && precond != 1 && precond != 4) return SOFT_ERR_INVALID_ARG;
@@ -284,8 +332,16 @@ int sse_apply_precond(soft_plan* P, double E, int precond, const void* x, void* 
 int sse_pcg_solve(soft_plan* P, const double* E, int nE, const void* rhs, void* psi_out, double tol,
                   int maxit, int precond, int* iters_out, double* relres_out, void* stream) {
     if (!P || !E || nE <= 0 || !rhs || !psi_out || !(tol > 0) || maxit <= 0) return SOFT_ERR_INVALID_ARG;
-    if (precond < 0 || precond > 4) return SOFT_ERR_INVALID_ARG;
+    if (precond < 0 || precond > 5) return SOFT_ERR_INVALID_ARG;
     const bool flexible = precond == 2 || precond == 3;
+    // precond 5: A and the banded preconditioner both computing in FP32, the
+    // vectors, dots and scalars in FP64, with reliable updates: the residual
+    // is replaced by the true f - A x (A in FP64) each time the recursive one
+    // has dropped by RU_DELTA, and only the true residual decides convergence
+    const bool mixed = precond == 5;
+    const double RU_DELTA = 0.1;
+    const int RU_MAXGAP = 200;
+    if (mixed) precond = 4;
     const bool learned = precond == 2;
     if (learned) {
         if (!P->p2 || P->p2->nx % 128) return SOFT_ERR_UNSUPPORTED;
@@ -309,14 +365,22 @@ int sse_pcg_solve(soft_plan* P, const double* E, int nE, const void* rhs, void* 
     const int64_t N = S->N;
     // state
     std::vector<int> ones(nE, 1), zeros(nE, 0), nconv(nE, SOFT_ERR_NOT_CONVERGED);
+    std::vector<double> rel1(nE, 1.0);
     if ((rc = cuda_status(cudaMemcpy(S->dE, E, sizeof(double) * nE, cudaMemcpyHostToDevice)))) return rc;
     if ((rc = cuda_status(cudaMemcpy(S->active, ones.data(), sizeof(int) * nE, cudaMemcpyHostToDevice)))) return rc;
     if ((rc = cuda_status(cudaMemcpy(S->iters, zeros.data(), sizeof(int) * nE, cudaMemcpyHostToDevice)))) return rc;
     if ((rc = cuda_status(cudaMemcpy(S->status, nconv.data(), sizeof(int) * nE, cudaMemcpyHostToDevice)))) return rc;
     if ((rc = cuda_status(cudaMemcpy(S->nactive, &nE, sizeof(int), cudaMemcpyHostToDevice)))) return rc;
+    if ((rc = cuda_status(cudaMemcpy(S->rref, rel1.data(), sizeof(double) * nE, cudaMemcpyHostToDevice)))) return rc;
+    if ((rc = cuda_status(cudaMemcpy(S->upd, zeros.data(), sizeof(int) * nE, cudaMemcpyHostToDevice)))) return rc;
+    if ((rc = cuda_status(cudaMemcpy(S->lastu, zeros.data(), sizeof(int) * nE, cudaMemcpyHostToDevice)))) return rc;
+    if ((rc = cuda_status(cudaMemcpy(S->mode, zeros.data(), sizeof(int) * nE, cudaMemcpyHostToDevice)))) return rc;
+    if ((rc = cuda_status(cudaMemcpy(S->act32, ones.data(), sizeof(int) * nE, cudaMemcpyHostToDevice)))) return rc;
+    if ((rc = cuda_status(cudaMemcpy(S->act64, zeros.data(), sizeof(int) * nE, cudaMemcpyHostToDevice)))) return rc;
     PcgState s{S->rho, S->alpha, S->beta, S->relres, S->fnorm2, S->active, S->iters, S->status,
-               S->nactive, tol};
-    const int np_row = Q->ny, np_col = pcg_col_blocks(Q->nx), np_vec = 256;
+               S->nactive, tol, S->rref, S->upd, RU_DELTA, RU_MAXGAP, S->lastu,
+               mixed ? S->mode : nullptr, mixed ? S->act32 : nullptr, mixed ? S->act64 : nullptr};
+    const int np_row = Q->ny, np_vec = 256, np_col = pcg_col_blocks(Q->nx);
     // x = 0, r = f, ||f||^2, z = P^-1 r, rho = r^T z, p = z
     if ((rc = vec_init(rhs, psi_out, S->r, N, nE, st))) return rc;
     if ((rc = vec_norm2(rhs, N, S->part, np_vec, st))) return rc;
@@ -329,11 +393,24 @@ int sse_pcg_solve(soft_plan* P, const double* E, int nE, const void* rhs, void* 
         Q->launches += 5;
         const int CHECK = 4;
         for (int it = 1; it <= maxit; ++it) {
-            if ((rc = apply_A(Q, S->p, S->w, S->dE, S->active, S->part, nE, st))) return rc;
+            if (mixed) {
+                // FP32 A for the energies still on it, FP64 A for the others
+                if ((rc = apply_A32(Q, S->p, S->w, S->dE, S->act32, S->part, nE, st))) return rc;
+                if ((rc = apply_A(Q, S->p, S->w, S->dE, S->act64, S->part, nE, st))) return rc;
+            } else if ((rc = apply_A(Q, S->p, S->w, S->dE, S->active, S->part, nE, st))) {
+                return rc;
+            }
             if ((rc = pcg_scalars(STAGE_ALPHA, nE, S->part, np_col, s, st))) return rc;
             if ((rc = vec_xr(psi_out, S->r, S->p, S->w, S->alpha, S->active, N, nE, S->part, np_vec, st))) return rc;
-            if ((rc = pcg_scalars(STAGE_RNORM, nE, S->part, np_vec, s, st))) return rc;
+            if ((rc = pcg_scalars(mixed ? STAGE_RNORM_RU : STAGE_RNORM, nE, S->part, np_vec, s, st))) return rc;
             Q->launches += 3;
+            if (mixed) {
+                // true residual for the flagged energies (t is free here)
+                if ((rc = apply_A(Q, psi_out, S->t, S->dE, S->upd, S->part2, nE, st))) return rc;
+                if ((rc = vec_res(rhs, S->t, S->r, S->upd, N, nE, S->part, np_vec, st))) return rc;
+                if ((rc = pcg_scalars(STAGE_TRUE, nE, S->part, np_vec, s, st))) return rc;
+                Q->launches += 2;
+            }
             if (it % CHECK == 0 || it == maxit) {
                 int na = 0;
                 if ((rc = cuda_status(cudaMemcpyAsync(&na, S->nactive, sizeof(int), cudaMemcpyDeviceToHost, st)))) return rc;

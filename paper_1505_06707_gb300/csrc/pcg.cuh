@@ -62,7 +62,8 @@ __device__ __forceinline__ double2 block_sum2(double2 v, double2* red) {
 }
 
 // --------------------------------------------------------------- A apply
-// w = F_x^-1 Kx F_x p + C_x p + (U - E) p, one CTA per (row, energy)
+// w = F_x^-1 Kx F_x p + C_x p + (U - E) p, one CTA per (row, energy); p and w
+// are complex128, the pass computes in R (with R = float the tables are FP32)
 template <typename R, int LOGN, int LOGE, int LOGRM>
 __global__ void __launch_bounds__(Cfg1D<R, LOGN, LOGE, LOGRM>::T, Cfg1D<R, LOGN, LOGE, LOGRM>::MINB)
 a_row_kernel(PcgGeo g, const void* __restrict__ p_v, void* __restrict__ w_v,
@@ -79,12 +80,12 @@ a_row_kernel(PcgGeo g, const void* __restrict__ p_v, void* __restrict__ w_v,
     C* P0 = S + N;                               // p row kept for C_x p and (U - E) p
     const int tid = threadIdx.x;
     const int64_t base = (int64_t)e * g.N + (int64_t)y * N;
-    const C* __restrict__ p = reinterpret_cast<const C*>(p_v) + base;
-    C* __restrict__ w = reinterpret_cast<C*>(w_v) + base;
+    const double2* __restrict__ p = reinterpret_cast<const double2*>(p_v) + base;
+    double2* __restrict__ w = reinterpret_cast<double2*>(w_v) + base;
     const C* W = reinterpret_cast<const C*>(g.Wx);
     for (int j = 0; j < E_; ++j) {
         const int n = tid + j * T;
-        const C v = p[n];
+        const C v = cto<C>(p[n]);
         S[swz<C>(n)] = v;
         P0[n] = v;
     }
@@ -106,15 +107,17 @@ a_row_kernel(PcgGeo g, const void* __restrict__ p_v, void* __restrict__ w_v,
             v = cfma(__ldg(&Cx[N + n]), pv, v);
             v = cfma(__ldg(&Cx[2 * N + n]), P0[(n + 1) & (N - 1)], v);
         }
-        w[n] = v;
+        w[n] = cto<double2>(v);
     }
 }
 
 // w += F_y^-1 Ky F_y p + C_y p, TW columns per CTA; partial of p^T w per CTA
+// at part[e * pstride + block], the entries from gridDim.x to pstride zeroed
+// (p and w complex128, the pass computes in R, the sum into w in FP64)
 template <typename R, int LOGN, int LOGE, int LOGRM, int TW>
 __global__ void __launch_bounds__(TW * Cfg1D<R, LOGN, LOGE, LOGRM>::T, 1)
 a_col_kernel(PcgGeo g, const void* __restrict__ p_v, void* __restrict__ w_v,
-             const int* __restrict__ active, double2* __restrict__ part)
+             const int* __restrict__ active, double2* __restrict__ part, int pstride)
 {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
     using C = typename K::C;
@@ -128,11 +131,11 @@ a_col_kernel(PcgGeo g, const void* __restrict__ p_v, void* __restrict__ w_v,
     __shared__ double2 red[32];
     const int c0 = blockIdx.x * TW, nx = g.nx;
     const int64_t eb = (int64_t)e * g.N;
-    const C* __restrict__ p = reinterpret_cast<const C*>(p_v) + eb;
-    C* __restrict__ w = reinterpret_cast<C*>(w_v) + eb;
+    const double2* __restrict__ p = reinterpret_cast<const double2*>(p_v) + eb;
+    double2* __restrict__ w = reinterpret_cast<double2*>(w_v) + eb;
     for (int idx = threadIdx.x; idx < TW * N; idx += blockDim.x) {
         const int yy = idx / TW, j = idx % TW;
-        const C v = p[(int64_t)yy * nx + c0 + j];
+        const C v = cto<C>(p[(int64_t)yy * nx + c0 + j]);
         S[j * N + swz<C>(yy)] = v;
         P0[j * N + yy] = v;
     }
@@ -155,14 +158,19 @@ a_col_kernel(PcgGeo g, const void* __restrict__ p_v, void* __restrict__ w_v,
             v = cfma(__ldg(&Cy[2 * N + yy]), Pj[(yy + 1) & (N - 1)], v);
         }
         const int64_t a = (int64_t)yy * nx + c0 + j;
-        const C wv = cadd(w[a], v);
+        const double2 w0 = w[a];
+        const double2 wv = make_double2(w0.x + (double)v.x, w0.y + (double)v.y);
         w[a] = wv;
         const C pv = Pj[yy];
         acc.x += (double)pv.x * wv.x - (double)pv.y * wv.y;      // bilinear p^T w
         acc.y += (double)pv.x * wv.y + (double)pv.y * wv.x;
     }
     const double2 t = block_sum2(acc, red);
-    if (threadIdx.x == 0) part[(int64_t)e * gridDim.x + blockIdx.x] = t;
+    if (threadIdx.x == 0) {
+        part[(int64_t)e * pstride + blockIdx.x] = t;
+        for (int k = blockIdx.x + gridDim.x; k < pstride; k += gridDim.x)
+            part[(int64_t)e * pstride + k] = make_double2(0.0, 0.0);
+    }
 }
 
 // --------------------------------------------------------- preconditioner

@@ -41,7 +41,7 @@ int col_kernels(int which, const PcgGeo& g, const void* a, void* b, const double
     if (which == 0) {
         auto k = a_col_kernel<double, LN, LE, LR, TWP>;
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return SOFT_ERR_CUDA;
-        if (nE > 0) k<<<grid, TWP * K::T, smem, st>>>(g, a, b, act, part);
+        if (nE > 0) k<<<grid, TWP * K::T, smem, st>>>(g, a, b, act, part, (int)grid.x);
     } else {
         auto k = pc_col_kernel<double, LN, LE, LR, TWP>;
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return SOFT_ERR_CUDA;
@@ -82,7 +82,57 @@ int pc32_col(const PcgGeo& g, void* b, const double* E, const int* act, int nE, 
     return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
 }
 
+// A computing in FP32
+constexpr int TWA32 = 4;  // columns per CTA of the FP32 A column pass
+
+template <int LN, int LE, int LR>
+int a32_row(const PcgGeo& g, const void* a, void* b, const double* E, const int* act, int nE,
+            cudaStream_t st) {
+    using K = Cfg1D<float, LN, LE, LR>;
+    const size_t smem = sizeof(float2) * 2 * K::N + 64;
+    auto k = a_row_kernel<float, LN, LE, LR>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return SOFT_ERR_CUDA;
+    if (nE > 0) k<<<dim3(g.ny, nE), K::T, smem, st>>>(g, a, b, E, act);
+    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+}
+
+template <int LN, int LE, int LR>
+int a32_col(const PcgGeo& g, const void* a, void* b, const int* act, double2* part, int pstride, int nE,
+            cudaStream_t st) {
+    using K = Cfg1D<float, LN, LE, LR>;
+    const size_t smem = sizeof(float2) * 2 * TWA32 * K::N + 64;
+    auto k = a_col_kernel<float, LN, LE, LR, TWA32>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return SOFT_ERR_CUDA;
+    const int nb = g.nx / TWA32;
+    if (nE > 0) k<<<dim3(nb, nE), TWA32 * K::T, smem, st>>>(g, a, b, act, part, pstride > nb ? pstride : nb);
+    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+}
+
 }  // namespace
+
+int pcg_a32_row(int logn, const PcgGeo& g, const void* p, void* w, const double* E, const int* act,
+                int nE, cudaStream_t st) {
+    switch (logn) {
+    case 8: return a32_row<8, 3, 3>(g, p, w, E, act, nE, st);
+    case 9: return a32_row<9, 3, 3>(g, p, w, E, act, nE, st);
+    case 10: return a32_row<10, 3, 3>(g, p, w, E, act, nE, st);
+    case 11: return a32_row<11, 3, 3>(g, p, w, E, act, nE, st);
+    }
+    return SOFT_ERR_UNSUPPORTED;
+}
+
+int pcg_a32_col(int logn, const PcgGeo& g, const void* p, void* w, const int* act, double2* part,
+                int pstride, int nE, cudaStream_t st) {
+    switch (logn) {
+    case 8: return a32_col<8, 3, 3>(g, p, w, act, part, pstride, nE, st);
+    case 9: return a32_col<9, 3, 3>(g, p, w, act, part, pstride, nE, st);
+    case 10: return a32_col<10, 3, 3>(g, p, w, act, part, pstride, nE, st);
+    case 11: return a32_col<11, 3, 3>(g, p, w, act, part, pstride, nE, st);
+    }
+    return SOFT_ERR_UNSUPPORTED;
+}
+
+int pcg_a32_col_blocks(int nx) { return nx / TWA32; }
 
 int pcg_pc32_row(int logn, int which, const PcgGeo& g, const void* a, void* b, const void* c,
                  const int* act, double2* part, int nE, cudaStream_t st) {
@@ -188,6 +238,26 @@ __global__ void vec_xr_kernel(double2* __restrict__ x, double2* __restrict__ r,
     if (threadIdx.x == 0) part[(int64_t)e * gridDim.x + blockIdx.x] = t;
 }
 
+// r = f - t (t = A x in FP64) for the energies with upd set; partial ||r||^2
+__global__ void vec_res_kernel(const double2* __restrict__ f, const double2* __restrict__ t,
+                               double2* __restrict__ r, const int* __restrict__ upd, int64_t N,
+                               double2* __restrict__ part) {
+    const int e = blockIdx.y;
+    if (!upd[e]) return;
+    __shared__ double2 red[32];
+    const int64_t o = (int64_t)e * N;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 fv = f[i], tv = t[o + i];
+        const double2 rv = make_double2(fv.x - tv.x, fv.y - tv.y);
+        r[o + i] = rv;
+        acc.x += rv.x * rv.x + rv.y * rv.y;
+    }
+    const double2 s = block_sum2(acc, red);
+    if (threadIdx.x == 0) part[(int64_t)e * gridDim.x + blockIdx.x] = s;
+}
+
 // p = z + beta p (beta = 0 with copy = 1: p = z)
 __global__ void vec_p_kernel(double2* __restrict__ p, const double2* __restrict__ z,
                              const double2* __restrict__ beta, const int* __restrict__ active,
@@ -204,6 +274,14 @@ __global__ void vec_p_kernel(double2* __restrict__ p, const double2* __restrict_
     }
 }
 
+// an energy leaves the iteration with status st
+__device__ __forceinline__ void retire(const PcgState& s, int e, int st) {
+    s.status[e] = st;
+    s.active[e] = 0;
+    if (s.act32) { s.act32[e] = 0; s.act64[e] = 0; }
+    atomicSub(s.nactive, 1);
+}
+
 // per-energy scalar updates of the iteration (one thread per energy; the
 // partial sums are added in a fixed order, so results are reproducible)
 __global__ void pcg_scalar_kernel(int stage, int nE, const double2* __restrict__ part, int nparts,
@@ -218,36 +296,70 @@ __global__ void pcg_scalar_kernel(int stage, int nE, const double2* __restrict__
         return;
     }
     if (e >= nE || !s.active[e]) return;
+    if (stage == STAGE_TRUE && !s.upd[e]) return;
     double2 t = make_double2(0.0, 0.0);
     for (int i = 0; i < nparts; ++i) { t.x += part[(int64_t)e * nparts + i].x; t.y += part[(int64_t)e * nparts + i].y; }
     if (stage == STAGE_RHO) {
         s.rho[e] = t;
-        if (!(fabs(t.x) + fabs(t.y) > 1e-300)) { s.status[e] = SOFT_ERR_BREAKDOWN; s.active[e] = 0; atomicSub(s.nactive, 1); }
+        if (!(fabs(t.x) + fabs(t.y) > 1e-300)) { retire(s, e, SOFT_ERR_BREAKDOWN); }
     } else if (stage == STAGE_ALPHA) {
         const double d = t.x * t.x + t.y * t.y;
-        if (!(d > 0.0) || !isfinite(d)) { s.status[e] = SOFT_ERR_BREAKDOWN; s.active[e] = 0; atomicSub(s.nactive, 1); return; }
+        if (!(d > 0.0) || !isfinite(d)) { retire(s, e, SOFT_ERR_BREAKDOWN); return; }
         const double2 rho = s.rho[e];                      // alpha = rho / (p^T w)
         s.alpha[e] = make_double2((rho.x * t.x + rho.y * t.y) / d, (rho.y * t.x - rho.x * t.y) / d);
     } else if (stage == STAGE_RNORM) {
         const double rel = sqrt(t.x / *s.fnorm2);
         s.relres[e] = rel;
         s.iters[e] += 1;
-        if (!isfinite(rel)) { s.status[e] = SOFT_ERR_NONFINITE; s.active[e] = 0; atomicSub(s.nactive, 1); }
-        else if (rel < s.tol) { s.status[e] = SOFT_OK; s.active[e] = 0; atomicSub(s.nactive, 1); }
+        if (!isfinite(rel)) { retire(s, e, SOFT_ERR_NONFINITE); }
+        else if (rel < s.tol) { retire(s, e, SOFT_OK); }
+    } else if (stage == STAGE_RNORM_RU) {
+        // recursive residual of the FP32-A iteration: flag a true-residual
+        // update once it has dropped by delta since the last one (or below tol)
+        const double rel = sqrt(t.x / *s.fnorm2);
+        s.relres[e] = rel;
+        s.iters[e] += 1;
+        s.upd[e] = 0;
+        if (!isfinite(rel)) { retire(s, e, SOFT_ERR_NONFINITE); }
+        else if (rel < fmax(s.tol, s.delta * s.rref[e]) || s.iters[e] - s.lastu[e] >= s.maxgap) s.upd[e] = 1;
+    } else if (stage == STAGE_TRUE) {
+        // true residual f - A x (A in FP64) replaces the recursive one; only
+        // it decides convergence.  If it has not halved since the last update
+        // (while the recursive one dropped by delta, or maxgap iterations
+        // passed), the FP32 A no longer drives this energy's iteration: A is
+        // applied in FP64 for it from here on, after a restart.
+        const double rel = sqrt(t.x / *s.fnorm2);
+        s.relres[e] = rel;
+        s.upd[e] = 0;
+        s.lastu[e] = s.iters[e];
+        if (!isfinite(rel)) { retire(s, e, SOFT_ERR_NONFINITE); return; }
+        if (rel < s.tol) { retire(s, e, SOFT_OK); return; }
+        if (!(rel < 0.5 * s.rref[e]) && !(s.mode[e] & 1)) {
+            s.mode[e] = 3;
+            s.act32[e] = 0;
+            s.act64[e] = 1;
+        }
+        s.rref[e] = rel;
     } else if (stage == STAGE_BETA_FLEX) {
         // flexible (Polak-Ribiere) beta = z'^T (r' - r) / rho = -alpha z'^T w / rho
         double2 u = make_double2(0.0, 0.0);
         for (int i = 0; i < nparts; ++i) { u.x += part2[(int64_t)e * nparts + i].x; u.y += part2[(int64_t)e * nparts + i].y; }
         const double2 rho = s.rho[e], al = s.alpha[e];
         const double d = rho.x * rho.x + rho.y * rho.y;
-        if (!(d > 0.0)) { s.status[e] = SOFT_ERR_BREAKDOWN; s.active[e] = 0; atomicSub(s.nactive, 1); return; }
+        if (!(d > 0.0)) { retire(s, e, SOFT_ERR_BREAKDOWN); return; }
         const double2 au = make_double2(al.x * u.x - al.y * u.y, al.x * u.y + al.y * u.x);
+        if (s.mode && (s.mode[e] & 2)) {                   // restart: p = z
+            s.mode[e] &= ~2;
+            s.beta[e] = make_double2(0.0, 0.0);
+            s.rho[e] = t;
+            return;
+        }
         s.beta[e] = make_double2(-(au.x * rho.x + au.y * rho.y) / d, -(au.y * rho.x - au.x * rho.y) / d);
         s.rho[e] = t;
     } else if (stage == STAGE_BETA) {
         const double2 rho = s.rho[e];
         const double d = rho.x * rho.x + rho.y * rho.y;
-        if (!(d > 0.0)) { s.status[e] = SOFT_ERR_BREAKDOWN; s.active[e] = 0; atomicSub(s.nactive, 1); return; }
+        if (!(d > 0.0)) { retire(s, e, SOFT_ERR_BREAKDOWN); return; }
         s.beta[e] = make_double2((t.x * rho.x + t.y * rho.y) / d, (t.y * rho.x - t.x * rho.y) / d);
         s.rho[e] = t;
     }
@@ -265,6 +377,12 @@ int vec_xr(void* x, void* r, const void* p, const void* w, const double2* alpha,
            int64_t N, int nE, double2* part, int nparts, cudaStream_t st) {
     vec_xr_kernel<<<dim3(nparts, nE), 256, 0, st>>>((double2*)x, (double2*)r, (const double2*)p,
                                                      (const double2*)w, alpha, act, N, part);
+    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+}
+int vec_res(const void* f, const void* t, void* r, const int* upd, int64_t N, int nE, double2* part,
+            int nparts, cudaStream_t st) {
+    vec_res_kernel<<<dim3(nparts, nE), 256, 0, st>>>((const double2*)f, (const double2*)t, (double2*)r, upd,
+                                                      N, part);
     return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
 }
 int vec_p(void* p, const void* z, const double2* beta, const int* act, int64_t N, int nE, int copy,
@@ -387,7 +505,7 @@ __global__ void gcr_alpha_kernel(const double2* __restrict__ p1, const double2* 
         c.y += p2[(int64_t)e * nparts + i].y;
     }
     if (!(n > 0.0) || !isfinite(n)) {
-        s.status[e] = SOFT_ERR_BREAKDOWN; s.active[e] = 0; atomicSub(s.nactive, 1);
+        retire(s, e, SOFT_ERR_BREAKDOWN);
         return;
     }
     qnorm[(int64_t)e * ld + slot] = n;

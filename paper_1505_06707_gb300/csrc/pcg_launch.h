@@ -9,7 +9,8 @@ namespace soft {
 
 struct PcgGeo;
 
-enum { STAGE_FNORM = 0, STAGE_RHO = 1, STAGE_ALPHA = 2, STAGE_RNORM = 3, STAGE_BETA = 4, STAGE_BETA_FLEX = 5 };
+enum { STAGE_FNORM = 0, STAGE_RHO = 1, STAGE_ALPHA = 2, STAGE_RNORM = 3, STAGE_BETA = 4, STAGE_BETA_FLEX = 5,
+       STAGE_RNORM_RU = 6, STAGE_TRUE = 7 };
 
 struct PcgState {                 // device pointers, per energy unless noted
     double2* rho;
@@ -22,6 +23,19 @@ struct PcgState {                 // device pointers, per energy unless noted
     int* status;
     int* nactive;                 // scalar
     double tol;
+    // reliable updates (A computing in FP32): relative residual at the last
+    // true-residual update, the update flags, the drop that triggers one and
+    // the most iterations between two; per energy the iteration of the last
+    // update, the mode (bit 0: A in FP64 from now on, bit 1: restart with
+    // beta = 0) and the launch masks of the FP32 and FP64 A passes
+    double* rref;
+    int* upd;
+    double delta;
+    int maxgap;
+    int* lastu;
+    int* mode;
+    int* act32;
+    int* act64;
 };
 
 // which: 0 = A row pass (a = p, b = w), 1 = preconditioner row pass 1
@@ -41,6 +55,15 @@ int pcg_pc32_row(int logn, int which, const PcgGeo& g, const void* a, void* b, c
 int pcg_pc32_col(int logn, const PcgGeo& g, void* b, const double* E, const int* act, int nE,
                  cudaStream_t st);
 
+// A computing in FP32 (complex128 p in, complex128 w out): row pass (w = ...)
+// then column pass (w += ..., partials of p^T w at part[e * pstride + b] for
+// its pcg_a32_col_blocks(nx) blocks b, zero up to pstride)
+int pcg_a32_row(int logn, const PcgGeo& g, const void* p, void* w, const double* E, const int* act,
+                int nE, cudaStream_t st);
+int pcg_a32_col(int logn, const PcgGeo& g, const void* p, void* w, const int* act, double2* part,
+                int pstride, int nE, cudaStream_t st);
+int pcg_a32_col_blocks(int nx);
+
 int vec_init(const void* f, void* x, void* r, int64_t N, int nE, cudaStream_t st);
 int vec_norm2(const void* f, int64_t N, double2* part, int nparts, cudaStream_t st);
 int vec_xr(void* x, void* r, const void* p, const void* w, const double2* alpha, const int* act,
@@ -54,6 +77,9 @@ int pcg_scalars(int stage, int nE, const double2* part, int nparts, const PcgSta
 int gcr_step(int phase, void* Pb, void* Q, int64_t slot_stride, int mu, int ld, int slot, double2* beta,
              double* qnorm, const void* r, const int* act, int64_t N, int nE, double2* gpart, double2* part,
              double2* part2, int nparts, const PcgState& s, cudaStream_t st);
+// r = f - t for the energies with upd set; partials of ||r||^2
+int vec_res(const void* f, const void* t, void* r, const int* upd, int64_t N, int nE, double2* part,
+            int nparts, cudaStream_t st);
 // partials of the bilinear forms r^T z and z^T w (flexible CG)
 int vec_dot2(const void* r, const void* z, const void* w, const int* act, int64_t N, int nE,
              double2* part1, double2* part2, int nparts, cudaStream_t st);

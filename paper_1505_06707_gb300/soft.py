@@ -15,7 +15,7 @@ __all__ = [
     "ABSORB_CAP", "ABSORB_TFAP",
     "load", "lib_path", "exported_symbols", "Options", "Field", "soft_create", "soft_create_batch",
     "soft_batch_layout", "soft_step", "soft_step_batch", "soft_step_noalloc", "soft_observe", "sse_pcg_solve",
-    "sse_apply_A", "sse_apply_precond", "soft_destroy", "sse_nn_set_weights", "sse_nn_get_weights",
+    "sse_apply_A", "sse_apply_A32", "sse_apply_precond", "soft_destroy", "sse_nn_set_weights", "sse_nn_get_weights",
     "sse_nn_forward", "sse_nn_grad", "sse_nn_train", "NN_PARAMS", "soft_plan_points", "soft_plan_count",
     "soft_last_launches", "Plan",
 ]
@@ -32,8 +32,8 @@ _lib = None
 # every symbol include/soft.h declares
 exported_symbols = [
     "soft_default_options", "soft_create", "soft_create_batch", "soft_batch_layout", "soft_step",
-    "soft_step_batch", "soft_observe", "sse_pcg_solve", "sse_apply_A", "sse_apply_precond",
-    "soft_destroy", "soft_strerror", "soft_plan_count", "soft_plan_points", "soft_plan_prec",
+    "soft_step_batch", "soft_observe", "sse_pcg_solve", "sse_apply_A", "sse_apply_A32",
+    "sse_apply_precond", "soft_destroy", "soft_strerror", "soft_plan_count", "soft_plan_points", "soft_plan_prec",
     "soft_last_launches", "soft_step_noalloc", "sse_nn_set_weights", "sse_nn_get_weights",
     "sse_nn_forward", "sse_nn_grad", "sse_nn_train",
 ]
@@ -90,6 +90,7 @@ def load():
     L.sse_pcg_solve.argtypes = [P, C.POINTER(dbl), C.c_int, P, P, dbl, C.c_int, C.c_int,
                                 C.POINTER(C.c_int), C.POINTER(dbl), P]
     L.sse_apply_A.argtypes = [P, dbl, P, P, P]
+    L.sse_apply_A32.argtypes = [P, dbl, P, P, P]
     L.sse_apply_precond.argtypes = [P, dbl, C.c_int, P, P, P]
     L.sse_nn_set_weights.argtypes = [P, P]
     L.sse_nn_get_weights.argtypes = [P, P]
@@ -246,6 +247,10 @@ def sse_pcg_solve(plan, E, rhs, psi_out, tol=1e-8, maxit=1000, precond=1, stream
 
 def sse_apply_A(plan, E, x, y, stream=None):
     _check(load().sse_apply_A(plan, E, _ptr(x), _ptr(y), _stream(stream)), "sse_apply_A")
+
+
+def sse_apply_A32(plan, E, x, y, stream=None):
+    _check(load().sse_apply_A32(plan, E, _ptr(x), _ptr(y), _stream(stream)), "sse_apply_A32")
 
 
 def sse_apply_precond(plan, E, precond, x, y, stream=None):

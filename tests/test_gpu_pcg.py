@@ -52,6 +52,9 @@ def test_apply_A_and_preconditioners_match_oracle():
         for E in (0.3, 1.7):
             S.sse_apply_A(plan, E, dx, dy)
             assert relerr(host(dy), st.apply_A(x, E)) < 1e-12
+            # A computing in FP32: 2^-24 per operation over the two FFT pairs
+            S.sse_apply_A32(plan, E, dx, dy)
+            assert relerr(host(dy), st.apply_A(x, E)) < 5e-6
             S.sse_apply_precond(plan, E, 0, dx, dy)
             assert relerr(host(dy), st.precond_simple(x, E)) < 1e-11
             S.sse_apply_precond(plan, E, 1, dx, dy)
@@ -87,6 +90,34 @@ def test_pcg_fp32_preconditioner():
             # symmetric; measured cost up to ~25 % more iterations
             assert its4[e] <= 1.3 * its1[e] + 5, (its1, its4)
         print("iterations FP64 band", its1, "FP32 band", its4)
+    finally:
+        S.soft_destroy(plan)
+
+
+def test_pcg_mixed_precision_reliable_updates():
+    """precond 5: A and the banded preconditioner computing in FP32, the
+    residual replaced by the true FP64 one each time it has dropped tenfold.
+    Every energy must reach the tolerance on the oracle's A (so the reported
+    residual is the true one), in about the iterations of the FP64 solve."""
+    plan, p2, st = setup()
+    try:
+        n = 256
+        xg = -40.0 + 80.0 / n * (np.arange(n) + 0.5)
+        f = -np.exp(-(xg[None, :] ** 2 + (xg[:, None] - 3.0) ** 2) / 32.0).astype(np.complex128)
+        Es = [0.2, 0.55, 1.1, 1.9]
+        out = torch.zeros((len(Es), n, n), dtype=torch.complex128, device="cuda")
+        rc1, its1, _ = S.sse_pcg_solve(plan, Es, dev(f), out, tol=1e-8, maxit=2000, precond=1)
+        for tol in (1e-8, 1e-10):
+            rc5, its5, rr5 = S.sse_pcg_solve(plan, Es, dev(f), out, tol=tol, maxit=2000, precond=5)
+            assert rc5 == 0, (tol, rc5, its5, rr5)
+            xs = host(out)
+            for e, E in enumerate(Es):
+                res = np.linalg.norm(st.apply_A(xs[e], E) - f) / np.linalg.norm(f)
+                assert res < 1.05 * tol and rr5[e] < tol, (tol, E, res, rr5[e], its5[e])
+                assert abs(res - rr5[e]) < 1e-3 * tol + 1e-2 * res, (res, rr5[e])
+            if tol == 1e-8:
+                assert all(b <= 1.5 * a + 10 for a, b in zip(its1, its5)), (its1, its5)
+            print("tol", tol, "iterations FP64", its1, "mixed", its5)
     finally:
         S.soft_destroy(plan)
 
@@ -166,7 +197,7 @@ def test_w4_full_size_sampled_energies():
         st = ST.Stationary2D(p2, nbw=10, kind=T.SHARP, R0=w["R0"], theta=w["theta"])
         Es = list(w["E"][[0, 21, 42, 63]])
         out = torch.zeros((len(Es), n, n), dtype=torch.complex128, device="cuda")
-        for pc in (1, 4):
+        for pc in (1, 4, 5):
             rc, its, rr = S.sse_pcg_solve(plan, Es, dev(w["f"]), out, tol=w["tol"], maxit=3000,
                                           precond=pc)
             assert rc == 0, (pc, rc, its, rr)
