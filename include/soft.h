@@ -192,14 +192,19 @@ int soft_observe(const soft_plan* plan, const void* psi, double* norm_in, double
  *               A, the residual and the dots stay FP64), in COCG with the
  *               flexible beta = z'^T (r' - r) / r^T z (FP32 rounding leaves
  *               the preconditioner not exactly symmetric);
- *            5: as 4, with A also computing in FP32 inside the iteration
- *               (vectors, dots and scalars stay FP64), plus reliable
- *               updates: once the recursive residual has dropped tenfold
- *               since the last update (or below tol), it is replaced by
- *               the true residual f - A psi with A in FP64, and only that
- *               true residual decides convergence, so the stopping test
- *               means the same as for 0-4.  iters_out counts the FP32
- *               iterations.
+ *            5: mixed precision: A and the banded preconditioner compute
+ *               in FP32 on complex64 r, p, z, w inside the iteration (FP32
+ *               products, FP64 sums for the dots); the solution increment
+ *               accumulates in double-float.  Reliable updates: once the
+ *               recursive residual has dropped tenfold since the last
+ *               update (or below tol, or after 200 iterations), the
+ *               increment is folded into the complex128 psi and the
+ *               residual replaced by the true f - A psi with A in FP64;
+ *               only that true residual decides convergence, so the
+ *               stopping test means the same as for 0-4.  An energy whose
+ *               true residual has not halved between two updates
+ *               continues with the FP64 A, after a restart.  iters_out
+ *               counts the iterations.
  *   iters_out, relres_out: host int[nE], double[nE]; may be NULL.
  * Returns SOFT_ERR_NOT_CONVERGED if any energy stopped at maxit (its last
  * iterate is written), SOFT_ERR_BREAKDOWN on a vanishing CG denominator.
@@ -210,11 +215,12 @@ int sse_pcg_solve(soft_plan* plan, const double* E, int nE, const void* rhs, voi
                   void* stream);
 
 /* sse_apply_A / sse_apply_A32 / sse_apply_precond -- one application of A
- * (Sec. III under Eq. linsys; sse_apply_A32 computes it in FP32, with
- * complex128 x and y, as precond 5 does inside its iteration) or of the
- * chosen preconditioner, for one energy, device in and out (x and y must
- * not alias).  Exposed for testing and for callers that run their own
- * Krylov method; precond 0, 1 or 4 (as in sse_pcg_solve). */
+ * (Sec. III under Eq. linsys) or of the chosen preconditioner, for one
+ * energy, device in and out (x and y must not alias).  sse_apply_A32
+ * computes A in FP32 on complex64 x and y, as precond 5 does inside its
+ * iteration; the others take complex128.  Exposed for testing and for
+ * callers that run their own Krylov method; precond 0, 1 or 4 (as in
+ * sse_pcg_solve). */
 int sse_apply_A(soft_plan* plan, double E, const void* x, void* y, void* stream);
 int sse_apply_A32(soft_plan* plan, double E, const void* x, void* y, void* stream);
 int sse_apply_precond(soft_plan* plan, double E, int precond, const void* x, void* y,

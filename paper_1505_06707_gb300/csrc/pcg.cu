@@ -247,15 +247,91 @@ static int apply_A(Plan2D* Q, const void* p, void* w, const double* dE, const in
     return pcg_col(Q->ly, 0, g, p, w, dE, act, part, nE, st);
 }
 
-// w = A p with A computing in FP32 (p, w complex128); partials of p^T w, at
-// the stride of the FP64 column pass
-static int apply_A32(Plan2D* Q, const void* p, void* w, const double* dE, const int* act,
-                     double2* part, int nE, cudaStream_t st) {
-    const PcgGeo& g = Q->pcg->pc[2].geo;
+// w = A p on complex64 vectors (mixed iteration): A computing in FP32 for
+// the energies in act32 (all if null), in FP64 for those in act64 (none if
+// null); partials of p^T w at the stride of the FP64 column pass
+static int apply_A_mixed(Plan2D* Q, const void* p, void* w, const double* dE, const int* act32,
+                         const int* act64, double2* part, int nE, cudaStream_t st) {
+    Pcg* S = Q->pcg;
+    const int ps = pcg_col_blocks(Q->nx);
     int rc;
-    if ((rc = pcg_a32_row(Q->lx, g, p, w, dE, act, nE, st))) return rc;
+    if ((rc = pcg_a32_row(Q->lx, S->pc[2].geo, p, w, dE, act32, nE, st))) return rc;
+    if ((rc = pcg_a32_col(Q->ly, S->pc[2].geo, p, w, act32, part, ps, nE, st))) return rc;
     Q->launches += 2;
-    return pcg_a32_col(Q->ly, g, p, w, act, part, pcg_col_blocks(Q->nx), nE, st);
+    if (!act64) return SOFT_OK;
+    if ((rc = pcg_a64f_row(Q->lx, S->pc[0].geo, p, w, dE, act64, nE, st))) return rc;
+    Q->launches += 2;
+    return pcg_a64f_col(Q->ly, S->pc[0].geo, p, w, act64, part, ps, nE, st);
+}
+
+// z = P^-1 r, banded preconditioner in FP32 on complex64 vectors; with part
+// the per-row partials of r^T z, with w also those of z^T w in part2
+static int apply_pc_mixed(Plan2D* Q, const void* r, void* z, const void* w, const double* dE,
+                          const int* act, double2* part, double2* part2, int nE, cudaStream_t st) {
+    Pcg* S = Q->pcg;
+    const PcgGeo& g = S->pc[2].geo;
+    int rc;
+    if ((rc = pcg_pc32f_row(Q->lx, 1, g, r, S->t, nullptr, nullptr, act, nullptr, nullptr, nE, st))) return rc;
+    if ((rc = pcg_pc32_col(Q->ly, g, S->t, dE, act, nE, st))) return rc;
+    Q->launches += 3;
+    return pcg_pc32f_row(Q->lx, 2, g, S->t, z, part ? r : nullptr, w, act, part, part2, nE, st);
+}
+
+// The mixed iteration (precond 5): COCG with the flexible beta in which A
+// and the banded preconditioner compute in FP32 on complex64 r, p, z, w, and
+// the solution increment since the last update accumulates in double-float.
+// Reliable updates: once an energy's recursive residual has dropped by delta
+// (or below tol, or maxgap iterations passed) the increment is folded into
+// the complex128 x and the residual replaced by f - A x with A in FP64; only
+// that true residual decides convergence.  An energy whose true residual has
+// not halved since its previous update switches to the FP64 A (on the same
+// complex64 vectors) after a restart.
+static int solve_mixed(Plan2D* Q, const PcgState& s, const void* rhs, void* psi_out, int maxit, int nE,
+                       cudaStream_t st) {
+    Pcg* S = Q->pcg;
+    const int64_t N = S->N, NE = N * nE;
+    float2* r = (float2*)S->r;             // each complex128 buffer holds two complex64 vectors
+    float2* xh = r + NE;
+    float2* z = (float2*)S->z;
+    float2* xl = z + NE;
+    float2* p = (float2*)S->p;
+    float2* w = (float2*)S->w;
+    const int np_row = Q->ny, np_vec = 256, np_col = pcg_col_blocks(Q->nx);
+    int rc;
+    // x = 0, r = f, ||f||^2, z = P^-1 r, rho = r^T z, p = z
+    if ((rc = vec_init32(rhs, psi_out, r, xh, xl, N, nE, st))) return rc;
+    if ((rc = vec_norm2(rhs, N, S->part, np_vec, st))) return rc;
+    if ((rc = pcg_scalars(STAGE_FNORM, nE, S->part, np_vec, s, st))) return rc;
+    if ((rc = apply_pc_mixed(Q, r, z, nullptr, S->dE, S->active, S->part, nullptr, nE, st))) return rc;
+    if ((rc = pcg_scalars(STAGE_RHO, nE, S->part, np_row, s, st))) return rc;
+    if ((rc = vec_p32(p, z, S->beta, S->active, N, nE, 1, st))) return rc;
+    Q->launches += 5;
+    const int CHECK = 4;
+    for (int it = 1; it <= maxit; ++it) {
+        if ((rc = apply_A_mixed(Q, p, w, S->dE, S->act32, S->act64, S->part, nE, st))) return rc;
+        if ((rc = pcg_scalars(STAGE_ALPHA, nE, S->part, np_col, s, st))) return rc;
+        if ((rc = vec_xr32(xh, xl, r, p, w, S->alpha, S->active, N, nE, S->part, np_vec, st))) return rc;
+        if ((rc = pcg_scalars(STAGE_RNORM_RU, nE, S->part, np_vec, s, st))) return rc;
+        // reliable update of the flagged energies (t is free here)
+        if ((rc = vec_fold(psi_out, xh, xl, S->upd, N, nE, st))) return rc;
+        if ((rc = apply_A(Q, psi_out, S->t, S->dE, S->upd, S->part2, nE, st))) return rc;
+        if ((rc = vec_res32(rhs, S->t, r, S->upd, N, nE, S->part, np_vec, st))) return rc;
+        if ((rc = pcg_scalars(STAGE_TRUE, nE, S->part, np_vec, s, st))) return rc;
+        Q->launches += 6;
+        if (it % CHECK == 0 || it == maxit) {
+            int na = 0;
+            if ((rc = cuda_status(cudaMemcpyAsync(&na, S->nactive, sizeof(int), cudaMemcpyDeviceToHost, st)))) return rc;
+            if ((rc = cuda_status(cudaStreamSynchronize(st)))) return rc;
+            if (na <= 0) break;
+        }
+        if (it == maxit) break;
+        if ((rc = apply_pc_mixed(Q, r, z, w, S->dE, S->active, S->part, S->part2, nE, st))) return rc;
+        if ((rc = pcg_scalars(STAGE_BETA_FLEX, nE, S->part, np_row, s, st, S->part2))) return rc;
+        if ((rc = vec_p32(p, z, S->beta, S->active, N, nE, 0, st))) return rc;
+        Q->launches += 2;
+    }
+    Q->launches += 1;
+    return vec_fold(psi_out, xh, xl, nullptr, N, nE, st);     // energies stopped at maxit
 }
 
 static int ensure_gcr(Pcg* S, int nE) {
@@ -308,7 +384,7 @@ int sse_apply_A32(soft_plan* P, double E, const void* x, void* y, void* stream) 
     Q->launches = 0;
     if ((rc = cuda_status(cudaMemcpyAsync(Q->pcg->dE, &E, sizeof(double), cudaMemcpyHostToDevice, st))))
         return rc;
-    rc = apply_A32(Q, x, y, Q->pcg->dE, nullptr, Q->pcg->part, 1, st);
+    rc = apply_A_mixed(Q, x, y, Q->pcg->dE, nullptr, nullptr, Q->pcg->part, 1, st);
     P->last_launches = Q->launches;
     return rc;
 }
@@ -334,14 +410,11 @@ int sse_pcg_solve(soft_plan* P, const double* E, int nE, const void* rhs, void* 
     if (!P || !E || nE <= 0 || !rhs || !psi_out || !(tol > 0) || maxit <= 0) return SOFT_ERR_INVALID_ARG;
     if (precond < 0 || precond > 5) return SOFT_ERR_INVALID_ARG;
     const bool flexible = precond == 2 || precond == 3;
-    // precond 5: A and the banded preconditioner both computing in FP32, the
-    // vectors, dots and scalars in FP64, with reliable updates: the residual
-    // is replaced by the true f - A x (A in FP64) each time the recursive one
-    // has dropped by RU_DELTA, and only the true residual decides convergence
+    // precond 5: the mixed iteration (solve_mixed); reliable updates after a
+    // tenfold drop of the recursive residual, or after 200 iterations
     const bool mixed = precond == 5;
     const double RU_DELTA = 0.1;
     const int RU_MAXGAP = 200;
-    if (mixed) precond = 4;
     const bool learned = precond == 2;
     if (learned) {
         if (!P->p2 || P->p2->nx % 128) return SOFT_ERR_UNSUPPORTED;
@@ -381,84 +454,75 @@ int sse_pcg_solve(soft_plan* P, const double* E, int nE, const void* rhs, void* 
                S->nactive, tol, S->rref, S->upd, RU_DELTA, RU_MAXGAP, S->lastu,
                mixed ? S->mode : nullptr, mixed ? S->act32 : nullptr, mixed ? S->act64 : nullptr};
     const int np_row = Q->ny, np_vec = 256, np_col = pcg_col_blocks(Q->nx);
-    // x = 0, r = f, ||f||^2, z = P^-1 r, rho = r^T z, p = z
-    if ((rc = vec_init(rhs, psi_out, S->r, N, nE, st))) return rc;
-    if ((rc = vec_norm2(rhs, N, S->part, np_vec, st))) return rc;
-    if ((rc = pcg_scalars(STAGE_FNORM, nE, S->part, np_vec, s, st))) return rc;
-    if (!flexible) {
-        // COCG (Sec. III): z = P^-1 r, rho = r^T z, p = z
-        if ((rc = apply_pc(Q, precond, S->r, S->z, S->dE, S->active, S->part, nE, st))) return rc;
-        if ((rc = pcg_scalars(STAGE_RHO, nE, S->part, np_row, s, st))) return rc;
-        if ((rc = vec_p(S->p, S->z, S->beta, S->active, N, nE, 1, st))) return rc;
-        Q->launches += 5;
-        const int CHECK = 4;
-        for (int it = 1; it <= maxit; ++it) {
-            if (mixed) {
-                // FP32 A for the energies still on it, FP64 A for the others
-                if ((rc = apply_A32(Q, S->p, S->w, S->dE, S->act32, S->part, nE, st))) return rc;
-                if ((rc = apply_A(Q, S->p, S->w, S->dE, S->act64, S->part, nE, st))) return rc;
-            } else if ((rc = apply_A(Q, S->p, S->w, S->dE, S->active, S->part, nE, st))) {
-                return rc;
-            }
-            if ((rc = pcg_scalars(STAGE_ALPHA, nE, S->part, np_col, s, st))) return rc;
-            if ((rc = vec_xr(psi_out, S->r, S->p, S->w, S->alpha, S->active, N, nE, S->part, np_vec, st))) return rc;
-            if ((rc = pcg_scalars(mixed ? STAGE_RNORM_RU : STAGE_RNORM, nE, S->part, np_vec, s, st))) return rc;
-            Q->launches += 3;
-            if (mixed) {
-                // true residual for the flagged energies (t is free here)
-                if ((rc = apply_A(Q, psi_out, S->t, S->dE, S->upd, S->part2, nE, st))) return rc;
-                if ((rc = vec_res(rhs, S->t, S->r, S->upd, N, nE, S->part, np_vec, st))) return rc;
-                if ((rc = pcg_scalars(STAGE_TRUE, nE, S->part, np_vec, s, st))) return rc;
-                Q->launches += 2;
-            }
-            if (it % CHECK == 0 || it == maxit) {
-                int na = 0;
-                if ((rc = cuda_status(cudaMemcpyAsync(&na, S->nactive, sizeof(int), cudaMemcpyDeviceToHost, st)))) return rc;
-                if ((rc = cuda_status(cudaStreamSynchronize(st)))) return rc;
-                if (na <= 0) break;
-            }
-            if (it == maxit) break;
-            if (precond == 4) {
-                // FP32 preconditioner: not exactly symmetric, so the flexible
-                // beta = z'^T (r' - r) / rho = -alpha z'^T w / rho
-                if ((rc = apply_pc(Q, precond, S->r, S->z, S->dE, S->active, nullptr, nE, st))) return rc;
-                if ((rc = vec_dot2(S->r, S->z, S->w, S->active, N, nE, S->part, S->part2, np_vec, st))) return rc;
-                if ((rc = pcg_scalars(STAGE_BETA_FLEX, nE, S->part, np_vec, s, st, S->part2))) return rc;
-                Q->launches += 1;
-            } else {
-                if ((rc = apply_pc(Q, precond, S->r, S->z, S->dE, S->active, S->part, nE, st))) return rc;
-                if ((rc = pcg_scalars(STAGE_BETA, nE, S->part, np_row, s, st))) return rc;
-            }
-            if ((rc = vec_p(S->p, S->z, S->beta, S->active, N, nE, 0, st))) return rc;
-            Q->launches += 5;
-        }
+    if (mixed) {
+        if ((rc = solve_mixed(Q, s, rhs, psi_out, maxit, nE, st))) return rc;
     } else {
-        // flexible GCR with the last GCR_M direction pairs (minimal residual,
-        // valid for a preconditioner that changes from one iteration to the
-        // next, e.g. the learned correction)
-        if ((rc = ensure_gcr(S, nE))) return rc;
-        const int M = Pcg::GCR_M;
-        const int64_t ss = N * nE;
-        double2* gPb = (double2*)S->gP;
-        double2* gQb = (double2*)S->gQ;
-        const int CHECK = 4;
-        for (int it = 1; it <= maxit; ++it) {
-            const int slot = (it - 1) % M, mu = std::min(it, M);
-            double2* Ps = gPb + slot * ss;
-            double2* Qs = gQb + slot * ss;
-            if ((rc = apply_pc(Q, precond, S->r, Ps, S->dE, S->active, nullptr, nE, st))) return rc;
-            if (learned && (rc = P->nn->correct_c128(Ps, nE, Q->ny, Q->nx, S->active, st))) return rc;
-            if ((rc = apply_A(Q, Ps, Qs, S->dE, S->active, S->part, nE, st))) return rc;
-            if ((rc = gcr_step(0, gPb, gQb, ss, mu, M, slot, S->gbeta, S->gqn, S->r, S->active, N, nE,
-                               S->gpart, S->part, S->part2, np_vec, s, st))) return rc;
-            if ((rc = vec_xr(psi_out, S->r, Ps, Qs, S->alpha, S->active, N, nE, S->part, np_vec, st))) return rc;
-            if ((rc = pcg_scalars(STAGE_RNORM, nE, S->part, np_vec, s, st))) return rc;
-            Q->launches += (learned ? 4 : 0) + 3 + 2 + 4 + 2;
-            if (it % CHECK == 0 || it == maxit) {
-                int na = 0;
-                if ((rc = cuda_status(cudaMemcpyAsync(&na, S->nactive, sizeof(int), cudaMemcpyDeviceToHost, st)))) return rc;
-                if ((rc = cuda_status(cudaStreamSynchronize(st)))) return rc;
-                if (na <= 0) break;
+        // x = 0, r = f, ||f||^2, z = P^-1 r, rho = r^T z, p = z
+        if ((rc = vec_init(rhs, psi_out, S->r, N, nE, st))) return rc;
+        if ((rc = vec_norm2(rhs, N, S->part, np_vec, st))) return rc;
+        if ((rc = pcg_scalars(STAGE_FNORM, nE, S->part, np_vec, s, st))) return rc;
+        if (!flexible) {
+            // COCG (Sec. III): z = P^-1 r, rho = r^T z, p = z
+            if ((rc = apply_pc(Q, precond, S->r, S->z, S->dE, S->active, S->part, nE, st))) return rc;
+            if ((rc = pcg_scalars(STAGE_RHO, nE, S->part, np_row, s, st))) return rc;
+            if ((rc = vec_p(S->p, S->z, S->beta, S->active, N, nE, 1, st))) return rc;
+            Q->launches += 5;
+            const int CHECK = 4;
+            for (int it = 1; it <= maxit; ++it) {
+                if ((rc = apply_A(Q, S->p, S->w, S->dE, S->active, S->part, nE, st))) return rc;
+                if ((rc = pcg_scalars(STAGE_ALPHA, nE, S->part, np_col, s, st))) return rc;
+                if ((rc = vec_xr(psi_out, S->r, S->p, S->w, S->alpha, S->active, N, nE, S->part, np_vec, st))) return rc;
+                if ((rc = pcg_scalars(STAGE_RNORM, nE, S->part, np_vec, s, st))) return rc;
+                Q->launches += 3;
+                if (it % CHECK == 0 || it == maxit) {
+                    int na = 0;
+                    if ((rc = cuda_status(cudaMemcpyAsync(&na, S->nactive, sizeof(int), cudaMemcpyDeviceToHost, st)))) return rc;
+                    if ((rc = cuda_status(cudaStreamSynchronize(st)))) return rc;
+                    if (na <= 0) break;
+                }
+                if (it == maxit) break;
+                if (precond == 4) {
+                    // FP32 preconditioner: not exactly symmetric, so the flexible
+                    // beta = z'^T (r' - r) / rho = -alpha z'^T w / rho
+                    if ((rc = apply_pc(Q, precond, S->r, S->z, S->dE, S->active, nullptr, nE, st))) return rc;
+                    if ((rc = vec_dot2(S->r, S->z, S->w, S->active, N, nE, S->part, S->part2, np_vec, st))) return rc;
+                    if ((rc = pcg_scalars(STAGE_BETA_FLEX, nE, S->part, np_vec, s, st, S->part2))) return rc;
+                    Q->launches += 1;
+                } else {
+                    if ((rc = apply_pc(Q, precond, S->r, S->z, S->dE, S->active, S->part, nE, st))) return rc;
+                    if ((rc = pcg_scalars(STAGE_BETA, nE, S->part, np_row, s, st))) return rc;
+                }
+                if ((rc = vec_p(S->p, S->z, S->beta, S->active, N, nE, 0, st))) return rc;
+                Q->launches += 5;
+            }
+        } else {
+            // flexible GCR with the last GCR_M direction pairs (minimal residual,
+            // valid for a preconditioner that changes from one iteration to the
+            // next, e.g. the learned correction)
+            if ((rc = ensure_gcr(S, nE))) return rc;
+            const int M = Pcg::GCR_M;
+            const int64_t ss = N * nE;
+            double2* gPb = (double2*)S->gP;
+            double2* gQb = (double2*)S->gQ;
+            const int CHECK = 4;
+            for (int it = 1; it <= maxit; ++it) {
+                const int slot = (it - 1) % M, mu = std::min(it, M);
+                double2* Ps = gPb + slot * ss;
+                double2* Qs = gQb + slot * ss;
+                if ((rc = apply_pc(Q, precond, S->r, Ps, S->dE, S->active, nullptr, nE, st))) return rc;
+                if (learned && (rc = P->nn->correct_c128(Ps, nE, Q->ny, Q->nx, S->active, st))) return rc;
+                if ((rc = apply_A(Q, Ps, Qs, S->dE, S->active, S->part, nE, st))) return rc;
+                if ((rc = gcr_step(0, gPb, gQb, ss, mu, M, slot, S->gbeta, S->gqn, S->r, S->active, N, nE,
+                                   S->gpart, S->part, S->part2, np_vec, s, st))) return rc;
+                if ((rc = vec_xr(psi_out, S->r, Ps, Qs, S->alpha, S->active, N, nE, S->part, np_vec, st))) return rc;
+                if ((rc = pcg_scalars(STAGE_RNORM, nE, S->part, np_vec, s, st))) return rc;
+                Q->launches += (learned ? 4 : 0) + 3 + 2 + 4 + 2;
+                if (it % CHECK == 0 || it == maxit) {
+                    int na = 0;
+                    if ((rc = cuda_status(cudaMemcpyAsync(&na, S->nactive, sizeof(int), cudaMemcpyDeviceToHost, st)))) return rc;
+                    if ((rc = cuda_status(cudaStreamSynchronize(st)))) return rc;
+                    if (na <= 0) break;
+                }
             }
         }
     }

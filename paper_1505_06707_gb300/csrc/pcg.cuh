@@ -61,10 +61,17 @@ __device__ __forceinline__ double2 block_sum2(double2 v, double2* red) {
     return t;
 }
 
+// shared-memory pitch of one column in the column passes: N + 64 bytes, so
+// that the TW columns of one row fall in different banks when the tile is
+// filled and drained row by row
+template <typename C, int N>
+struct ColPitch { static constexpr int value = N + 64 / (int)sizeof(C); };
+
 // --------------------------------------------------------------- A apply
 // w = F_x^-1 Kx F_x p + C_x p + (U - E) p, one CTA per (row, energy); p and w
-// are complex128, the pass computes in R (with R = float the tables are FP32)
-template <typename R, int LOGN, int LOGE, int LOGRM>
+// are IO (complex128 or complex64), the pass computes in R (with R = float
+// the tables are FP32)
+template <typename R, typename IO, int LOGN, int LOGE, int LOGRM>
 __global__ void __launch_bounds__(Cfg1D<R, LOGN, LOGE, LOGRM>::T, Cfg1D<R, LOGN, LOGE, LOGRM>::MINB)
 a_row_kernel(PcgGeo g, const void* __restrict__ p_v, void* __restrict__ w_v,
              const double* __restrict__ E, const int* __restrict__ active)
@@ -80,8 +87,8 @@ a_row_kernel(PcgGeo g, const void* __restrict__ p_v, void* __restrict__ w_v,
     C* P0 = S + N;                               // p row kept for C_x p and (U - E) p
     const int tid = threadIdx.x;
     const int64_t base = (int64_t)e * g.N + (int64_t)y * N;
-    const double2* __restrict__ p = reinterpret_cast<const double2*>(p_v) + base;
-    double2* __restrict__ w = reinterpret_cast<double2*>(w_v) + base;
+    const IO* __restrict__ p = reinterpret_cast<const IO*>(p_v) + base;
+    IO* __restrict__ w = reinterpret_cast<IO*>(w_v) + base;
     const C* W = reinterpret_cast<const C*>(g.Wx);
     for (int j = 0; j < E_; ++j) {
         const int n = tid + j * T;
@@ -107,65 +114,69 @@ a_row_kernel(PcgGeo g, const void* __restrict__ p_v, void* __restrict__ w_v,
             v = cfma(__ldg(&Cx[N + n]), pv, v);
             v = cfma(__ldg(&Cx[2 * N + n]), P0[(n + 1) & (N - 1)], v);
         }
-        w[n] = cto<double2>(v);
+        w[n] = cto<IO>(v);
     }
 }
 
 // w += F_y^-1 Ky F_y p + C_y p, TW columns per CTA; partial of p^T w per CTA
 // at part[e * pstride + block], the entries from gridDim.x to pstride zeroed
-// (p and w complex128, the pass computes in R, the sum into w in FP64)
-template <typename R, int LOGN, int LOGE, int LOGRM, int TW>
-__global__ void __launch_bounds__(TW * Cfg1D<R, LOGN, LOGE, LOGRM>::T, 1)
+// (p and w IO, the pass computes in R; each thread sums its terms of p^T w
+// in IO precision, the block sum is FP64)
+template <typename R, typename IO, int LOGN, int LOGE, int LOGRM, int TW, int MINB = 1>
+__global__ void __launch_bounds__(TW * Cfg1D<R, LOGN, LOGE, LOGRM>::T, MINB)
 a_col_kernel(PcgGeo g, const void* __restrict__ p_v, void* __restrict__ w_v,
              const int* __restrict__ active, double2* __restrict__ part, int pstride)
 {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
     using C = typename K::C;
     using TT = typename K::TT;
-    constexpr int N = K::N, T = K::T;
+    constexpr int N = K::N, T = K::T, NIT = N / T, PITCH = ColPitch<C, N>::value;
     const int e = blockIdx.y;
     if (active && !active[e]) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* S = reinterpret_cast<C*>(smem_raw);
-    C* P0 = S + TW * N;
+    C* P0 = S + TW * PITCH;
     __shared__ double2 red[32];
     const int c0 = blockIdx.x * TW, nx = g.nx;
     const int64_t eb = (int64_t)e * g.N;
-    const double2* __restrict__ p = reinterpret_cast<const double2*>(p_v) + eb;
-    double2* __restrict__ w = reinterpret_cast<double2*>(w_v) + eb;
-    for (int idx = threadIdx.x; idx < TW * N; idx += blockDim.x) {
+    const IO* __restrict__ p = reinterpret_cast<const IO*>(p_v) + eb;
+    IO* __restrict__ w = reinterpret_cast<IO*>(w_v) + eb;
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {              // row by row: the TW columns of a row are adjacent
+        const int idx = threadIdx.x + it * TW * T;
         const int yy = idx / TW, j = idx % TW;
         const C v = cto<C>(p[(int64_t)yy * nx + c0 + j]);
-        S[j * N + swz<C>(yy)] = v;
-        P0[j * N + yy] = v;
+        S[j * PITCH + swz<C>(yy)] = v;
+        P0[j * PITCH + yy] = v;
     }
     __syncthreads();
     const int col = threadIdx.x / T, tid = threadIdx.x % T;
-    C* Sc = S + col * N;
+    C* Sc = S + col * PITCH;
     const C* W = reinterpret_cast<const C*>(g.Wy);
     fwd_fft<R, LOGN, LOGE, LOGRM, 0>(Sc, W, tid);
     kmul<R, LOGN, LOGE, LOGRM>(Sc, reinterpret_cast<const TT*>(g.Ky), tid);
     inv_fft<R, LOGN, LOGE, LOGRM, K::NPASS - 1>(Sc, W, tid);
     const C* __restrict__ Cy = reinterpret_cast<const C*>(g.Cy);
-    double2 acc = make_double2(0.0, 0.0);
-    for (int idx = threadIdx.x; idx < TW * N; idx += blockDim.x) {
+    IO acc = cmk<IO>(0, 0);
+#pragma unroll 4
+    for (int it = 0; it < NIT; ++it) {
+        const int idx = threadIdx.x + it * TW * T;
         const int yy = idx / TW, j = idx % TW;
-        const C* Pj = P0 + j * N;
-        C v = S[j * N + swz<C>(yy)];
+        const C* Pj = P0 + j * PITCH;
+        C v = S[j * PITCH + swz<C>(yy)];
         if (((yy - g.blk0y) & (N - 1)) < g.nby) {
             v = cfma(__ldg(&Cy[yy]), Pj[(yy + N - 1) & (N - 1)], v);
             v = cfma(__ldg(&Cy[N + yy]), Pj[yy], v);
             v = cfma(__ldg(&Cy[2 * N + yy]), Pj[(yy + 1) & (N - 1)], v);
         }
         const int64_t a = (int64_t)yy * nx + c0 + j;
-        const double2 w0 = w[a];
-        const double2 wv = make_double2(w0.x + (double)v.x, w0.y + (double)v.y);
+        const IO wv = cto<IO>(cadd(cto<C>(w[a]), v));
         w[a] = wv;
-        const C pv = Pj[yy];
-        acc.x += (double)pv.x * wv.x - (double)pv.y * wv.y;      // bilinear p^T w
-        acc.y += (double)pv.x * wv.y + (double)pv.y * wv.x;
+        const IO pv = cto<IO>(Pj[yy]);
+        acc.x += pv.x * wv.x - pv.y * wv.y;      // bilinear p^T w
+        acc.y += pv.x * wv.y + pv.y * wv.x;
     }
-    const double2 t = block_sum2(acc, red);
+    const double2 t = block_sum2(cto<double2>(acc), red);
     if (threadIdx.x == 0) {
         part[(int64_t)e * pstride + blockIdx.x] = t;
         for (int k = blockIdx.x + gridDim.x; k < pstride; k += gridDim.x)
@@ -185,8 +196,8 @@ __device__ __forceinline__ C band_row(int nu, const int* __restrict__ bs, const 
 }
 
 // row pass 1: t = X_x F_x r (F with e^{+ikx}), natural nu order
-// (r is complex128; the pass computes in R: t and the tables are in R)
-template <typename R, int LOGN, int LOGE, int LOGRM>
+// (r is IO; the pass computes in R: t and the tables are in R)
+template <typename R, typename IO, int LOGN, int LOGE, int LOGRM>
 __global__ void __launch_bounds__(Cfg1D<R, LOGN, LOGE, LOGRM>::T, Cfg1D<R, LOGN, LOGE, LOGRM>::MINB)
 pc_row1_kernel(PcgGeo g, const void* __restrict__ r_v, void* __restrict__ t_v,
                const int* __restrict__ active)
@@ -200,7 +211,7 @@ pc_row1_kernel(PcgGeo g, const void* __restrict__ r_v, void* __restrict__ t_v,
     C* S = reinterpret_cast<C*>(smem_raw);
     const int tid = threadIdx.x;
     const int64_t base = (int64_t)e * g.N + (int64_t)y * N;
-    const double2* __restrict__ r = reinterpret_cast<const double2*>(r_v) + base;
+    const IO* __restrict__ r = reinterpret_cast<const IO*>(r_v) + base;
     C* __restrict__ t = reinterpret_cast<C*>(t_v) + base;
     for (int j = 0; j < E_; ++j) {
         const int n = tid + j * T;
@@ -217,29 +228,31 @@ pc_row1_kernel(PcgGeo g, const void* __restrict__ r_v, void* __restrict__ t_v,
 }
 
 // column pass: F_y, X_y, / (lambda_x + lambda_y - E), X_y^T, F_y^-1 (in place on t)
-template <typename R, int LOGN, int LOGE, int LOGRM, int TW>
-__global__ void __launch_bounds__(TW * Cfg1D<R, LOGN, LOGE, LOGRM>::T, 1)
+template <typename R, int LOGN, int LOGE, int LOGRM, int TW, int MINB = 1>
+__global__ void __launch_bounds__(TW * Cfg1D<R, LOGN, LOGE, LOGRM>::T, MINB)
 pc_col_kernel(PcgGeo g, void* __restrict__ t_v, const double* __restrict__ E,
               const int* __restrict__ active)
 {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
     using C = typename K::C;
-    constexpr int N = K::N, T = K::T, E_ = K::E;
+    constexpr int N = K::N, T = K::T, E_ = K::E, PITCH = ColPitch<C, N>::value;
     const int e = blockIdx.y;
     if (active && !active[e]) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* S = reinterpret_cast<C*>(smem_raw);
-    C* S2 = S + TW * N;
+    C* S2 = S + TW * PITCH;
     const int c0 = blockIdx.x * TW, nx = g.nx;
     C* __restrict__ t = reinterpret_cast<C*>(t_v) + (int64_t)e * g.N;
-    for (int idx = threadIdx.x; idx < TW * N; idx += blockDim.x) {
+#pragma unroll
+    for (int it = 0; it < E_; ++it) {
+        const int idx = threadIdx.x + it * TW * T;
         const int yy = idx / TW, j = idx % TW;
-        S[j * N + swz<C>(yy)] = cconj(t[(int64_t)yy * nx + c0 + j]);
+        S[j * PITCH + swz<C>(yy)] = cconj(t[(int64_t)yy * nx + c0 + j]);
     }
     __syncthreads();
     const int col = threadIdx.x / T, tid = threadIdx.x % T;
-    C* Sc = S + col * N;
-    C* S2c = S2 + col * N;
+    C* Sc = S + col * PITCH;
+    C* S2c = S2 + col * PITCH;
     const C* W = reinterpret_cast<const C*>(g.Wy);
     fwd_fft<R, LOGN, LOGE, LOGRM, 0>(Sc, W, tid);
     const int nu = c0 + col;
@@ -265,19 +278,23 @@ pc_col_kernel(PcgGeo g, void* __restrict__ t_v, const double* __restrict__ E,
     }
     __syncthreads();
     inv_fft<R, LOGN, LOGE, LOGRM, K::NPASS - 1>(Sc, W, tid);
-    for (int idx = threadIdx.x; idx < TW * N; idx += blockDim.x) {
+#pragma unroll
+    for (int it = 0; it < E_; ++it) {
+        const int idx = threadIdx.x + it * TW * T;
         const int yy = idx / TW, j = idx % TW;
-        t[(int64_t)yy * nx + c0 + j] = cconj(S[j * N + swz<C>(yy)]);
+        t[(int64_t)yy * nx + c0 + j] = cconj(S[j * PITCH + swz<C>(yy)]);
     }
 }
 
-// row pass 2: z = F_x^-1 X_x^T t; partial of r^T z per CTA (z and r are
-// complex128, the pass computes in R)
-template <typename R, int LOGN, int LOGE, int LOGRM>
+// row pass 2: z = F_x^-1 X_x^T t; with r, the partial of r^T z per CTA in
+// part, and with w also that of z^T w in part2 (z, r and w are IO, the pass
+// computes in R; each thread sums its terms in IO precision, the block sum
+// is FP64)
+template <typename R, typename IO, int LOGN, int LOGE, int LOGRM>
 __global__ void __launch_bounds__(Cfg1D<R, LOGN, LOGE, LOGRM>::T, Cfg1D<R, LOGN, LOGE, LOGRM>::MINB)
 pc_row2_kernel(PcgGeo g, const void* __restrict__ t_v, void* __restrict__ z_v,
-               const void* __restrict__ r_v, const int* __restrict__ active,
-               double2* __restrict__ part)
+               const void* __restrict__ r_v, const void* __restrict__ w_v, const int* __restrict__ active,
+               double2* __restrict__ part, double2* __restrict__ part2)
 {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
     using C = typename K::C;
@@ -291,7 +308,7 @@ pc_row2_kernel(PcgGeo g, const void* __restrict__ t_v, void* __restrict__ z_v,
     const int tid = threadIdx.x;
     const int64_t base = (int64_t)e * g.N + (int64_t)y * N;
     const C* __restrict__ t = reinterpret_cast<const C*>(t_v) + base;
-    double2* __restrict__ z = reinterpret_cast<double2*>(z_v) + base;     // complex128 out
+    IO* __restrict__ z = reinterpret_cast<IO*>(z_v) + base;
     for (int j = 0; j < E_; ++j) {
         const int n = tid + j * T;
         Tn[n] = t[n];
@@ -305,21 +322,31 @@ pc_row2_kernel(PcgGeo g, const void* __restrict__ t_v, void* __restrict__ z_v,
     }
     __syncthreads();
     inv_fft<R, LOGN, LOGE, LOGRM, K::NPASS - 1>(S, reinterpret_cast<const C*>(g.Wx), tid);
-    double2 acc = make_double2(0.0, 0.0);
-    const double2* r = r_v ? reinterpret_cast<const double2*>(r_v) + base : nullptr;
+    IO acc = cmk<IO>(0, 0), acc2 = cmk<IO>(0, 0);
+    const IO* r = r_v ? reinterpret_cast<const IO*>(r_v) + base : nullptr;
+    const IO* w = w_v ? reinterpret_cast<const IO*>(w_v) + base : nullptr;
     for (int j = 0; j < E_; ++j) {
         const int n = tid + j * T;
-        const double2 zv = cto<double2>(cconj(S[swz<C>(n)]));
+        const IO zv = cto<IO>(cconj(S[swz<C>(n)]));
         z[n] = zv;
         if (r) {
-            const double2 rv = r[n];
-            acc.x += (double)rv.x * zv.x - (double)rv.y * zv.y;
-            acc.y += (double)rv.x * zv.y + (double)rv.y * zv.x;
+            const IO rv = r[n];
+            acc.x += rv.x * zv.x - rv.y * zv.y;
+            acc.y += rv.x * zv.y + rv.y * zv.x;
+        }
+        if (w) {
+            const IO wv = w[n];
+            acc2.x += zv.x * wv.x - zv.y * wv.y;
+            acc2.y += zv.x * wv.y + zv.y * wv.x;
         }
     }
     if (part) {
-        const double2 s = block_sum2(acc, red);
+        const double2 s = block_sum2(cto<double2>(acc), red);
         if (threadIdx.x == 0) part[(int64_t)e * gridDim.x + blockIdx.x] = s;
+    }
+    if (part2) {
+        const double2 s = block_sum2(cto<double2>(acc2), red);
+        if (threadIdx.x == 0) part2[(int64_t)e * gridDim.x + blockIdx.x] = s;
     }
 }
 

@@ -1,6 +1,13 @@
 // Complex-symmetric CG (Sec. III) for the 2D stationary ECS equation:
-// instantiations of the A-apply and preconditioner passes (complex128) and the
-// vector / scalar kernels of the iteration.
+// instantiations of the A-apply and preconditioner passes and the vector /
+// scalar kernels of the iteration.
+//
+// Pass precisions (compute R, vector I/O IO):
+//   FP64 path (precond 0, 1)          A and P^-1: R double, IO complex128
+//   FP32 preconditioner (precond 4)   P^-1: R float, IO complex128
+//   mixed iteration (precond 5)       A and P^-1: R float, IO complex64; the
+//                                     energies that fall back: A with R double,
+//                                     IO complex64
 #include "pcg.cuh"
 #include "pcg_launch.h"
 
@@ -8,177 +15,155 @@ namespace soft {
 
 namespace {
 
-constexpr int TWP = 2;    // columns per CTA in the column passes (complex128)
+constexpr int TWP = 2;    // columns per CTA of the FP64 column passes
+constexpr int TW32 = 4;   // columns per CTA of the FP32 column passes
 
-template <int LN, int LE, int LR>
-int row_kernels(int which, const PcgGeo& g, const void* a, void* b, const void* c, const double* E,
-                const int* act, double2* part, int nE, cudaStream_t st) {
-    using K = Cfg1D<double, LN, LE, LR>;
-    const size_t smem = sizeof(double2) * 2 * K::N + 64;
-    dim3 grid(g.ny, nE);
-    if (which == 0) {
-        auto k = a_row_kernel<double, LN, LE, LR>;
-        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return SOFT_ERR_CUDA;
-        if (nE > 0) k<<<grid, K::T, smem, st>>>(g, a, b, E, act);
-    } else if (which == 1) {
-        auto k = pc_row1_kernel<double, LN, LE, LR>;
-        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return SOFT_ERR_CUDA;
-        if (nE > 0) k<<<grid, K::T, smem, st>>>(g, a, b, act);
-    } else {
-        auto k = pc_row2_kernel<double, LN, LE, LR>;
-        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return SOFT_ERR_CUDA;
-        if (nE > 0) k<<<grid, K::T, smem, st>>>(g, a, b, c, act, part);
-    }
-    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+// CTAs per SM: 1024 threads per SM, <= 64 registers (FP32 column passes)
+template <int THREADS>
+struct MinB32 { static constexpr int value = THREADS >= 1024 ? 1 : 1024 / THREADS; };
+
+inline int done() { return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA; }
+
+template <class Kern>
+inline bool set_smem(Kern k, size_t smem) {
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
 }
 
-template <int LN, int LE, int LR>
-int col_kernels(int which, const PcgGeo& g, const void* a, void* b, const double* E,
-                const int* act, double2* part, int nE, cudaStream_t st) {
-    using K = Cfg1D<double, LN, LE, LR>;
-    const size_t smem = sizeof(double2) * 2 * TWP * K::N + 64;
-    dim3 grid(g.nx / TWP, nE);
-    if (which == 0) {
-        auto k = a_col_kernel<double, LN, LE, LR, TWP>;
-        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return SOFT_ERR_CUDA;
-        if (nE > 0) k<<<grid, TWP * K::T, smem, st>>>(g, a, b, act, part, (int)grid.x);
-    } else {
-        auto k = pc_col_kernel<double, LN, LE, LR, TWP>;
-        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return SOFT_ERR_CUDA;
-        if (nE > 0) k<<<grid, TWP * K::T, smem, st>>>(g, b, E, act);
-    }
-    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+template <typename R, typename IO, int LN, int LE, int LR>
+int a_row(const PcgGeo& g, const void* p, void* w, const double* E, const int* act, int nE,
+          cudaStream_t st) {
+    using K = Cfg1D<R, LN, LE, LR>;
+    const size_t smem = sizeof(typename K::C) * 2 * K::N + 64;
+    auto k = a_row_kernel<R, IO, LN, LE, LR>;
+    if (!set_smem(k, smem)) return SOFT_ERR_CUDA;
+    if (nE > 0) k<<<dim3(g.ny, nE), K::T, smem, st>>>(g, p, w, E, act);
+    return done();
 }
 
-// preconditioner passes computing in FP32 (complex128 r in, complex128 z out)
-constexpr int TWP32 = 4;  // columns per CTA of the FP32 column pass
+template <typename R, typename IO, int LN, int LE, int LR, int TW, int MB>
+int a_col(const PcgGeo& g, const void* p, void* w, const int* act, double2* part, int pstride, int nE,
+          cudaStream_t st) {
+    using K = Cfg1D<R, LN, LE, LR>;
+    using C = typename K::C;
+    const size_t smem = sizeof(C) * 2 * TW * ColPitch<C, K::N>::value + 64;
+    auto k = a_col_kernel<R, IO, LN, LE, LR, TW, MB>;
+    if (!set_smem(k, smem)) return SOFT_ERR_CUDA;
+    const int nb = g.nx / TW;
+    if (nE > 0) k<<<dim3(nb, nE), TW * K::T, smem, st>>>(g, p, w, act, part, pstride > nb ? pstride : nb);
+    return done();
+}
 
-template <int LN, int LE, int LR>
-int pc32_row(int which, const PcgGeo& g, const void* a, void* b, const void* c, const int* act,
-             double2* part, int nE, cudaStream_t st) {
-    using K = Cfg1D<float, LN, LE, LR>;
-    const size_t smem = sizeof(float2) * 2 * K::N + 64;
-    dim3 grid(g.ny, nE);
+// which 1: t = X_x F_x a; which 2: b = F_x^-1 X_x^T a, partials r^T b, b^T w
+template <typename R, typename IO, int LN, int LE, int LR>
+int pc_row(int which, const PcgGeo& g, const void* a, void* b, const void* r, const void* w, const int* act,
+           double2* part, double2* part2, int nE, cudaStream_t st) {
+    using K = Cfg1D<R, LN, LE, LR>;
+    const size_t smem = sizeof(typename K::C) * 2 * K::N + 64;
+    const dim3 grid(g.ny, nE);
     if (which == 1) {
-        auto k = pc_row1_kernel<float, LN, LE, LR>;
-        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return SOFT_ERR_CUDA;
+        auto k = pc_row1_kernel<R, IO, LN, LE, LR>;
+        if (!set_smem(k, smem)) return SOFT_ERR_CUDA;
         if (nE > 0) k<<<grid, K::T, smem, st>>>(g, a, b, act);
     } else {
-        auto k = pc_row2_kernel<float, LN, LE, LR>;
-        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return SOFT_ERR_CUDA;
-        if (nE > 0) k<<<grid, K::T, smem, st>>>(g, a, b, c, act, part);
+        auto k = pc_row2_kernel<R, IO, LN, LE, LR>;
+        if (!set_smem(k, smem)) return SOFT_ERR_CUDA;
+        if (nE > 0) k<<<grid, K::T, smem, st>>>(g, a, b, r, w, act, part, part2);
     }
-    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+    return done();
 }
 
-template <int LN, int LE, int LR>
-int pc32_col(const PcgGeo& g, void* b, const double* E, const int* act, int nE, cudaStream_t st) {
-    using K = Cfg1D<float, LN, LE, LR>;
-    const size_t smem = sizeof(float2) * 2 * TWP32 * K::N + 64;
-    dim3 grid(g.nx / TWP32, nE);
-    auto k = pc_col_kernel<float, LN, LE, LR, TWP32>;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return SOFT_ERR_CUDA;
-    if (nE > 0) k<<<grid, TWP32 * K::T, smem, st>>>(g, b, E, act);
-    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
-}
-
-// A computing in FP32
-constexpr int TWA32 = 4;  // columns per CTA of the FP32 A column pass
-
-template <int LN, int LE, int LR>
-int a32_row(const PcgGeo& g, const void* a, void* b, const double* E, const int* act, int nE,
-            cudaStream_t st) {
-    using K = Cfg1D<float, LN, LE, LR>;
-    const size_t smem = sizeof(float2) * 2 * K::N + 64;
-    auto k = a_row_kernel<float, LN, LE, LR>;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return SOFT_ERR_CUDA;
-    if (nE > 0) k<<<dim3(g.ny, nE), K::T, smem, st>>>(g, a, b, E, act);
-    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
-}
-
-template <int LN, int LE, int LR>
-int a32_col(const PcgGeo& g, const void* a, void* b, const int* act, double2* part, int pstride, int nE,
-            cudaStream_t st) {
-    using K = Cfg1D<float, LN, LE, LR>;
-    const size_t smem = sizeof(float2) * 2 * TWA32 * K::N + 64;
-    auto k = a_col_kernel<float, LN, LE, LR, TWA32>;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) return SOFT_ERR_CUDA;
-    const int nb = g.nx / TWA32;
-    if (nE > 0) k<<<dim3(nb, nE), TWA32 * K::T, smem, st>>>(g, a, b, act, part, pstride > nb ? pstride : nb);
-    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+template <typename R, int LN, int LE, int LR, int TW, int MB>
+int pc_col(const PcgGeo& g, void* t, const double* E, const int* act, int nE, cudaStream_t st) {
+    using K = Cfg1D<R, LN, LE, LR>;
+    using C = typename K::C;
+    const size_t smem = sizeof(C) * 2 * TW * ColPitch<C, K::N>::value + 64;
+    auto k = pc_col_kernel<R, LN, LE, LR, TW, MB>;
+    if (!set_smem(k, smem)) return SOFT_ERR_CUDA;
+    if (nE > 0) k<<<dim3(g.nx / TW, nE), TW * K::T, smem, st>>>(g, t, E, act);
+    return done();
 }
 
 }  // namespace
 
-int pcg_a32_row(int logn, const PcgGeo& g, const void* p, void* w, const double* E, const int* act,
-                int nE, cudaStream_t st) {
-    switch (logn) {
-    case 8: return a32_row<8, 3, 3>(g, p, w, E, act, nE, st);
-    case 9: return a32_row<9, 3, 3>(g, p, w, E, act, nE, st);
-    case 10: return a32_row<10, 3, 3>(g, p, w, E, act, nE, st);
-    case 11: return a32_row<11, 3, 3>(g, p, w, E, act, nE, st);
-    }
+// every pass runs with LOGE = LOGRM = 3 (radix 8, eight elements per thread)
+#define PCG_SIZES(CALL)                                  \
+    switch (logn) {                                      \
+    case 8: return CALL(8);                              \
+    case 9: return CALL(9);                              \
+    case 10: return CALL(10);                            \
+    case 11: return CALL(11);                            \
+    }                                                    \
     return SOFT_ERR_UNSUPPORTED;
-}
-
-int pcg_a32_col(int logn, const PcgGeo& g, const void* p, void* w, const int* act, double2* part,
-                int pstride, int nE, cudaStream_t st) {
-    switch (logn) {
-    case 8: return a32_col<8, 3, 3>(g, p, w, act, part, pstride, nE, st);
-    case 9: return a32_col<9, 3, 3>(g, p, w, act, part, pstride, nE, st);
-    case 10: return a32_col<10, 3, 3>(g, p, w, act, part, pstride, nE, st);
-    case 11: return a32_col<11, 3, 3>(g, p, w, act, part, pstride, nE, st);
-    }
-    return SOFT_ERR_UNSUPPORTED;
-}
-
-int pcg_a32_col_blocks(int nx) { return nx / TWA32; }
-
-int pcg_pc32_row(int logn, int which, const PcgGeo& g, const void* a, void* b, const void* c,
-                 const int* act, double2* part, int nE, cudaStream_t st) {
-    switch (logn) {
-    case 8: return pc32_row<8, 3, 3>(which, g, a, b, c, act, part, nE, st);
-    case 9: return pc32_row<9, 3, 3>(which, g, a, b, c, act, part, nE, st);
-    case 10: return pc32_row<10, 3, 3>(which, g, a, b, c, act, part, nE, st);
-    case 11: return pc32_row<11, 3, 3>(which, g, a, b, c, act, part, nE, st);
-    }
-    return SOFT_ERR_UNSUPPORTED;
-}
-
-int pcg_pc32_col(int logn, const PcgGeo& g, void* b, const double* E, const int* act, int nE,
-                 cudaStream_t st) {
-    switch (logn) {
-    case 8: return pc32_col<8, 3, 3>(g, b, E, act, nE, st);
-    case 9: return pc32_col<9, 3, 3>(g, b, E, act, nE, st);
-    case 10: return pc32_col<10, 3, 3>(g, b, E, act, nE, st);
-    case 11: return pc32_col<11, 3, 3>(g, b, E, act, nE, st);
-    }
-    return SOFT_ERR_UNSUPPORTED;
-}
 
 int pcg_row(int logn, int which, const PcgGeo& g, const void* a, void* b, const void* c,
             const double* E, const int* act, double2* part, int nE, cudaStream_t st) {
-    switch (logn) {
-    case 8: return row_kernels<8, 3, 3>(which, g, a, b, c, E, act, part, nE, st);
-    case 9: return row_kernels<9, 3, 3>(which, g, a, b, c, E, act, part, nE, st);
-    case 10: return row_kernels<10, 3, 3>(which, g, a, b, c, E, act, part, nE, st);
-    case 11: return row_kernels<11, 3, 3>(which, g, a, b, c, E, act, part, nE, st);
-    }
-    return SOFT_ERR_UNSUPPORTED;
+#define CALL(L) (which == 0 ? a_row<double, double2, L, 3, 3>(g, a, b, E, act, nE, st) \
+                            : pc_row<double, double2, L, 3, 3>(which, g, a, b, c, nullptr, act, part, nullptr, nE, st))
+    PCG_SIZES(CALL)
+#undef CALL
 }
 
 int pcg_col(int logn, int which, const PcgGeo& g, const void* a, void* b, const double* E,
             const int* act, double2* part, int nE, cudaStream_t st) {
-    switch (logn) {
-    case 8: return col_kernels<8, 3, 3>(which, g, a, b, E, act, part, nE, st);
-    case 9: return col_kernels<9, 3, 3>(which, g, a, b, E, act, part, nE, st);
-    case 10: return col_kernels<10, 3, 3>(which, g, a, b, E, act, part, nE, st);
-    case 11: return col_kernels<11, 3, 3>(which, g, a, b, E, act, part, nE, st);
-    }
-    return SOFT_ERR_UNSUPPORTED;
+#define CALL(L) (which == 0 ? a_col<double, double2, L, 3, 3, TWP, 1>(g, a, b, act, part, 0, nE, st) \
+                            : pc_col<double, L, 3, 3, TWP, 1>(g, b, E, act, nE, st))
+    PCG_SIZES(CALL)
+#undef CALL
 }
 
 int pcg_col_blocks(int nx) { return nx / TWP; }
+
+int pcg_pc32_row(int logn, int which, const PcgGeo& g, const void* a, void* b, const void* c,
+                 const int* act, double2* part, int nE, cudaStream_t st) {
+#define CALL(L) pc_row<float, double2, L, 3, 3>(which, g, a, b, c, nullptr, act, part, nullptr, nE, st)
+    PCG_SIZES(CALL)
+#undef CALL
+}
+
+int pcg_pc32_col(int logn, const PcgGeo& g, void* b, const double* E, const int* act, int nE,
+                 cudaStream_t st) {
+#define CALL(L) pc_col<float, L, 3, 3, TW32, MinB32<TW32 * Cfg1D<float, L, 3, 3>::T>::value>(g, b, E, act, nE, st)
+    PCG_SIZES(CALL)
+#undef CALL
+}
+
+int pcg_pc32f_row(int logn, int which, const PcgGeo& g, const void* a, void* b, const void* r, const void* w,
+                  const int* act, double2* part, double2* part2, int nE, cudaStream_t st) {
+#define CALL(L) pc_row<float, float2, L, 3, 3>(which, g, a, b, r, w, act, part, part2, nE, st)
+    PCG_SIZES(CALL)
+#undef CALL
+}
+
+int pcg_a32_row(int logn, const PcgGeo& g, const void* p, void* w, const double* E, const int* act,
+                int nE, cudaStream_t st) {
+#define CALL(L) a_row<float, float2, L, 3, 3>(g, p, w, E, act, nE, st)
+    PCG_SIZES(CALL)
+#undef CALL
+}
+
+int pcg_a32_col(int logn, const PcgGeo& g, const void* p, void* w, const int* act, double2* part,
+                int pstride, int nE, cudaStream_t st) {
+#define CALL(L) a_col<float, float2, L, 3, 3, TW32, MinB32<TW32 * Cfg1D<float, L, 3, 3>::T>::value>( \
+    g, p, w, act, part, pstride, nE, st)
+    PCG_SIZES(CALL)
+#undef CALL
+}
+
+int pcg_a64f_row(int logn, const PcgGeo& g, const void* p, void* w, const double* E, const int* act,
+                 int nE, cudaStream_t st) {
+#define CALL(L) a_row<double, float2, L, 3, 3>(g, p, w, E, act, nE, st)
+    PCG_SIZES(CALL)
+#undef CALL
+}
+
+int pcg_a64f_col(int logn, const PcgGeo& g, const void* p, void* w, const int* act, double2* part,
+                 int pstride, int nE, cudaStream_t st) {
+#define CALL(L) a_col<double, float2, L, 3, 3, TWP, 1>(g, p, w, act, part, pstride, nE, st)
+    PCG_SIZES(CALL)
+#undef CALL
+}
+#undef PCG_SIZES
+
 
 // ------------------------------------------------------------ vector kernels
 __device__ __forceinline__ double2 sum_warp(double2 v) {
@@ -236,26 +221,6 @@ __global__ void vec_xr_kernel(double2* __restrict__ x, double2* __restrict__ r,
     }
     const double2 t = block_sum2(acc, red);
     if (threadIdx.x == 0) part[(int64_t)e * gridDim.x + blockIdx.x] = t;
-}
-
-// r = f - t (t = A x in FP64) for the energies with upd set; partial ||r||^2
-__global__ void vec_res_kernel(const double2* __restrict__ f, const double2* __restrict__ t,
-                               double2* __restrict__ r, const int* __restrict__ upd, int64_t N,
-                               double2* __restrict__ part) {
-    const int e = blockIdx.y;
-    if (!upd[e]) return;
-    __shared__ double2 red[32];
-    const int64_t o = (int64_t)e * N;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const double2 fv = f[i], tv = t[o + i];
-        const double2 rv = make_double2(fv.x - tv.x, fv.y - tv.y);
-        r[o + i] = rv;
-        acc.x += rv.x * rv.x + rv.y * rv.y;
-    }
-    const double2 s = block_sum2(acc, red);
-    if (threadIdx.x == 0) part[(int64_t)e * gridDim.x + blockIdx.x] = s;
 }
 
 // p = z + beta p (beta = 0 with copy = 1: p = z)
@@ -379,12 +344,6 @@ int vec_xr(void* x, void* r, const void* p, const void* w, const double2* alpha,
                                                      (const double2*)w, alpha, act, N, part);
     return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
 }
-int vec_res(const void* f, const void* t, void* r, const int* upd, int64_t N, int nE, double2* part,
-            int nparts, cudaStream_t st) {
-    vec_res_kernel<<<dim3(nparts, nE), 256, 0, st>>>((const double2*)f, (const double2*)t, (double2*)r, upd,
-                                                      N, part);
-    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
-}
 int vec_p(void* p, const void* z, const double2* beta, const int* act, int64_t N, int nE, int copy,
           cudaStream_t st) {
     vec_p_kernel<<<dim3(256, nE), 256, 0, st>>>((double2*)p, (const double2*)z, beta, act, N, copy);
@@ -415,6 +374,169 @@ int vec_dot2(const void* r, const void* z, const void* w, const int* act, int64_
              double2* part1, double2* part2, int nparts, cudaStream_t st) {
     vec_dot2_kernel<<<dim3(nparts, nE), 256, 0, st>>>((const double2*)r, (const double2*)z,
                                                        (const double2*)w, act, N, part1, part2);
+    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+}
+
+// -------------------------------------- mixed iteration (complex64 vectors)
+// r, p, z, w are complex64; the solution increment since the last true-
+// residual update is a double-float pair (xh + xl, about 48 significant
+// bits), folded into the complex128 x at each update.  Double-float sums use
+// Knuth's TwoSum and Dekker's Fast2Sum, products the FMA-based TwoProduct.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {   // |a| >= |b|
+    s = a + b;
+    e = b - (s - a);
+}
+// (xh, xl) += (yh, yl)
+__device__ __forceinline__ void df_add(float& xh, float& xl, float yh, float yl) {
+    float s, e;
+    two_sum(xh, yh, s, e);
+    e += xl + yl;
+    fast_two_sum(s, e, xh, xl);
+}
+// (ah + al) b as an unnormalised pair (ph, pl)
+__device__ __forceinline__ void df_mul(float ah, float al, float b, float& ph, float& pl) {
+    ph = ah * b;
+    pl = fmaf(ah, b, -ph);
+    pl = fmaf(al, b, pl);
+}
+__device__ __forceinline__ void df_split(double a, float& h, float& l) {
+    h = (float)a;
+    l = (float)(a - (double)h);
+}
+
+// x = 0, r = f (rounded), increment = 0
+__global__ void vec_init32_kernel(const double2* __restrict__ f, double2* __restrict__ x, float2* __restrict__ r,
+                                  float2* __restrict__ xh, float2* __restrict__ xl, int64_t N, int nE) {
+    const int64_t tot = N * nE;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 fv = f[i % N];
+        x[i] = make_double2(0.0, 0.0);
+        r[i] = make_float2((float)fv.x, (float)fv.y);
+        xh[i] = make_float2(0.f, 0.f);
+        xl[i] = make_float2(0.f, 0.f);
+    }
+}
+
+// increment += alpha p (double-float), r -= alpha w (FP32); partial ||r||^2
+// (each thread sums its terms in FP32, the block sum is FP64)
+__global__ void vec_xr32_kernel(float2* __restrict__ xh, float2* __restrict__ xl, float2* __restrict__ r,
+                                const float2* __restrict__ p, const float2* __restrict__ w,
+                                const double2* __restrict__ alpha, const int* __restrict__ active,
+                                int64_t N, double2* __restrict__ part) {
+    const int e = blockIdx.y;
+    if (!active[e]) return;
+    __shared__ double2 red[32];
+    const double2 a = alpha[e];
+    float axh, axl, ayh, ayl;
+    df_split(a.x, axh, axl);
+    df_split(a.y, ayh, ayl);
+    const int64_t o = (int64_t)e * N;
+    float acc = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 pv = p[o + i], wv = w[o + i];
+        float2 hv = xh[o + i], lv = xl[o + i], rv = r[o + i];
+        float ph, pl;
+        df_mul(axh, axl, pv.x, ph, pl); df_add(hv.x, lv.x, ph, pl);      // re += ax px - ay py
+        df_mul(ayh, ayl, pv.y, ph, pl); df_add(hv.x, lv.x, -ph, -pl);
+        df_mul(axh, axl, pv.y, ph, pl); df_add(hv.y, lv.y, ph, pl);      // im += ax py + ay px
+        df_mul(ayh, ayl, pv.x, ph, pl); df_add(hv.y, lv.y, ph, pl);
+        rv.x -= axh * wv.x - ayh * wv.y;
+        rv.y -= axh * wv.y + ayh * wv.x;
+        xh[o + i] = hv;
+        xl[o + i] = lv;
+        r[o + i] = rv;
+        acc += rv.x * rv.x + rv.y * rv.y;
+    }
+    const double2 t = block_sum2(make_double2((double)acc, 0.0), red);
+    if (threadIdx.x == 0) part[(int64_t)e * gridDim.x + blockIdx.x] = t;
+}
+
+// p = z + beta p (beta = 0 with copy = 1: p = z), FP32
+__global__ void vec_p32_kernel(float2* __restrict__ p, const float2* __restrict__ z,
+                               const double2* __restrict__ beta, const int* __restrict__ active,
+                               int64_t N, int copy) {
+    const int e = blockIdx.y;
+    if (!active[e]) return;
+    const float2 b = copy ? make_float2(0.f, 0.f) : make_float2((float)beta[e].x, (float)beta[e].y);
+    const int64_t o = (int64_t)e * N;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 zv = z[o + i];
+        const float2 pv = copy ? make_float2(0.f, 0.f) : p[o + i];
+        p[o + i] = make_float2(zv.x + b.x * pv.x - b.y * pv.y, zv.y + b.x * pv.y + b.y * pv.x);
+    }
+}
+
+// x += xh + xl, increment = 0, for the energies with mask set (all if null)
+__global__ void vec_fold_kernel(double2* __restrict__ x, float2* __restrict__ xh, float2* __restrict__ xl,
+                                const int* __restrict__ mask, int64_t N) {
+    const int e = blockIdx.y;
+    if (mask && !mask[e]) return;
+    const int64_t o = (int64_t)e * N;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 hv = xh[o + i], lv = xl[o + i];
+        double2 xv = x[o + i];
+        xv.x += (double)hv.x + (double)lv.x;
+        xv.y += (double)hv.y + (double)lv.y;
+        x[o + i] = xv;
+        xh[o + i] = make_float2(0.f, 0.f);
+        xl[o + i] = make_float2(0.f, 0.f);
+    }
+}
+
+// r = f - t (FP64, t = A x), stored rounded to complex64, for the energies
+// with upd set; partial ||f - t||^2 in FP64
+__global__ void vec_res32_kernel(const double2* __restrict__ f, const double2* __restrict__ t,
+                                 float2* __restrict__ r, const int* __restrict__ upd, int64_t N,
+                                 double2* __restrict__ part) {
+    const int e = blockIdx.y;
+    if (!upd[e]) return;
+    __shared__ double2 red[32];
+    const int64_t o = (int64_t)e * N;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 fv = f[i], tv = t[o + i];
+        const double2 rv = make_double2(fv.x - tv.x, fv.y - tv.y);
+        r[o + i] = make_float2((float)rv.x, (float)rv.y);
+        acc.x += rv.x * rv.x + rv.y * rv.y;
+    }
+    const double2 s = block_sum2(acc, red);
+    if (threadIdx.x == 0) part[(int64_t)e * gridDim.x + blockIdx.x] = s;
+}
+
+int vec_init32(const void* f, void* x, void* r, void* xh, void* xl, int64_t N, int nE, cudaStream_t st) {
+    vec_init32_kernel<<<1024, 256, 0, st>>>((const double2*)f, (double2*)x, (float2*)r, (float2*)xh,
+                                            (float2*)xl, N, nE);
+    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+}
+int vec_xr32(void* xh, void* xl, void* r, const void* p, const void* w, const double2* alpha, const int* act,
+             int64_t N, int nE, double2* part, int nparts, cudaStream_t st) {
+    vec_xr32_kernel<<<dim3(nparts, nE), 256, 0, st>>>((float2*)xh, (float2*)xl, (float2*)r, (const float2*)p,
+                                                       (const float2*)w, alpha, act, N, part);
+    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+}
+int vec_p32(void* p, const void* z, const double2* beta, const int* act, int64_t N, int nE, int copy,
+            cudaStream_t st) {
+    vec_p32_kernel<<<dim3(256, nE), 256, 0, st>>>((float2*)p, (const float2*)z, beta, act, N, copy);
+    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+}
+int vec_fold(void* x, void* xh, void* xl, const int* mask, int64_t N, int nE, cudaStream_t st) {
+    vec_fold_kernel<<<dim3(256, nE), 256, 0, st>>>((double2*)x, (float2*)xh, (float2*)xl, mask, N);
+    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+}
+int vec_res32(const void* f, const void* t, void* r, const int* upd, int64_t N, int nE, double2* part,
+              int nparts, cudaStream_t st) {
+    vec_res32_kernel<<<dim3(nparts, nE), 256, 0, st>>>((const double2*)f, (const double2*)t, (float2*)r, upd,
+                                                        N, part);
     return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
 }
 

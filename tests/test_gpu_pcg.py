@@ -52,9 +52,12 @@ def test_apply_A_and_preconditioners_match_oracle():
         for E in (0.3, 1.7):
             S.sse_apply_A(plan, E, dx, dy)
             assert relerr(host(dy), st.apply_A(x, E)) < 1e-12
-            # A computing in FP32: 2^-24 per operation over the two FFT pairs
-            S.sse_apply_A32(plan, E, dx, dy)
-            assert relerr(host(dy), st.apply_A(x, E)) < 5e-6
+            # A computing in FP32 on complex64: 2^-24 per operation over the
+            # two FFT pairs (compared with A of the rounded input)
+            x32 = x.astype(np.complex64)
+            y32 = torch.zeros((256, 256), dtype=torch.complex64, device="cuda")
+            S.sse_apply_A32(plan, E, torch.from_numpy(x32).cuda(), y32)
+            assert relerr(host(y32).astype(np.complex128), st.apply_A(x32.astype(np.complex128), E)) < 5e-6
             S.sse_apply_precond(plan, E, 0, dx, dy)
             assert relerr(host(dy), st.precond_simple(x, E)) < 1e-11
             S.sse_apply_precond(plan, E, 1, dx, dy)
@@ -95,10 +98,11 @@ def test_pcg_fp32_preconditioner():
 
 
 def test_pcg_mixed_precision_reliable_updates():
-    """precond 5: A and the banded preconditioner computing in FP32, the
-    residual replaced by the true FP64 one each time it has dropped tenfold.
-    Every energy must reach the tolerance on the oracle's A (so the reported
-    residual is the true one), in about the iterations of the FP64 solve."""
+    """precond 5: A and the banded preconditioner computing in FP32 on
+    complex64 vectors, the residual replaced by the true FP64 one each time
+    it has dropped tenfold.  Every energy must reach the tolerance on the
+    oracle's A (so the reported residual is the true one), in about the
+    iterations of the FP64 solve."""
     plan, p2, st = setup()
     try:
         n = 256
