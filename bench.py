@@ -291,6 +291,8 @@ def bench_pcg(S, torch, dev, args):
                          soft_a2=w["a2"])
     f = torch.tensor(w["f"], dtype=torch.complex128, device=dev)
     E = [float(e) for e in w["E"]]
+    if args.pcg_energies > 0:
+        E = E[:args.pcg_energies]
     out = torch.zeros((len(E), n, n), dtype=torch.complex128, device=dev)
     st = torch.cuda.current_stream(dev)
     S.sse_pcg_solve(plan, E[:2], f, out, tol=w["tol"], maxit=4, precond=1, stream=st)   # warm-up
@@ -466,6 +468,8 @@ def main():
                     help="run one of the extra measurements alone (for profiling captures; not a bench line)")
     ap.add_argument("--pcg-precond", default="1,4,5",
                     help="stationary-solver modes to time (sse_pcg_solve precond values)")
+    ap.add_argument("--pcg-energies", type=int, default=0,
+                    help="solve only the first K energies of the stationary workload (profiling captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

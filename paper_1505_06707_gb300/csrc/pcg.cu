@@ -103,9 +103,17 @@ static int build_pc(Plan2D* Q, int type, PcgTables& T, int prec = SOFT_C128) {
     g.posy = ub(inv_perm(Q->ly, Q->lry));
     g.bsx = ub(bx.start); g.bsy = ub(by.start);
     g.bwx = ub(bx.width); g.bwy = ub(by.width);
-    g.box = ub(bx.off); g.boy = ub(by.off);
-    g.xfx = uc(bx.xf); g.xfy = uc(by.xf);
-    g.xbx = uc(bx.xb); g.xby = uc(by.xb);
+    // band rows u-major (entry u of row nu at u * n + nu), zero past each width
+    auto umajor = [](const BandAxis& B, const std::vector<cd>& tab) {
+        int wmax = 0;
+        for (int wd : B.width) wmax = std::max(wmax, wd);
+        std::vector<cd> t((size_t)wmax * B.n, cd(0.0, 0.0));
+        for (int nu = 0; nu < B.n; ++nu)
+            for (int u = 0; u < B.width[nu]; ++u) t[(size_t)u * B.n + nu] = tab[(size_t)B.off[nu] + u];
+        return t;
+    };
+    g.xfx = uc(umajor(bx, bx.xf)); g.xfy = uc(umajor(by, by.xf));
+    g.xbx = uc(umajor(bx, bx.xb)); g.xby = uc(umajor(by, by.xb));
     g.lamx = uc(bx.lam); g.lamy = uc(by.lam);
     if (prec == SOFT_C64) {      // FFT twiddles of the FP32 passes
         auto ut = [&](const std::vector<cd>& v) -> const void* {

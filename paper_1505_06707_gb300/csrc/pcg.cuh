@@ -31,7 +31,8 @@ struct PcgGeo {
     const int* posx; const int* posy;      // FFT output position of natural index
     const int* bsx; const int* bsy;        // band start
     const int* bwx; const int* bwy;        // band width
-    const int* box; const int* boy;        // row offset in xf/xb
+    // band rows, u-major: entry u of row nu at [u * n + nu], zero past the
+    // row's width, so that one u of consecutive rows is one contiguous load
     const void* xfx; const void* xfy;      // forward band rows (complex)
     const void* xbx; const void* xby;      // backward band rows (complex)
     const void* lamx; const void* lamy;    // eigenvalues (complex)
@@ -185,13 +186,13 @@ a_col_kernel(PcgGeo g, const void* __restrict__ p_v, void* __restrict__ w_v,
 }
 
 // --------------------------------------------------------- preconditioner
-// band mat-vec: out[nu] = sum_{u < width} tab[off[nu] + u] * in(start[nu] + u)
+// band mat-vec: out[nu] = sum_{u < width} tab[u * n + nu] * in(start[nu] + u)
 template <typename C, class In>
-__device__ __forceinline__ C band_row(int nu, const int* __restrict__ bs, const int* __restrict__ bw,
-                                      const int* __restrict__ bo, const C* __restrict__ tab, In in) {
-    const int s0 = __ldg(&bs[nu]), wd = __ldg(&bw[nu]), o = __ldg(&bo[nu]);
+__device__ __forceinline__ C band_row(int nu, int n, const int* __restrict__ bs, const int* __restrict__ bw,
+                                      const C* __restrict__ tab, In in) {
+    const int s0 = __ldg(&bs[nu]), wd = __ldg(&bw[nu]);
     C acc; acc.x = 0; acc.y = 0;
-    for (int u = 0; u < wd; ++u) acc = cfma(__ldg(&tab[o + u]), in(s0 + u), acc);
+    for (int u = 0; u < wd; ++u) acc = cfma(__ldg(&tab[u * n + nu]), in(s0 + u), acc);
     return acc;
 }
 
@@ -222,7 +223,7 @@ pc_row1_kernel(PcgGeo g, const void* __restrict__ r_v, void* __restrict__ t_v,
     const C* xf = reinterpret_cast<const C*>(g.xfx);
     for (int j = 0; j < E_; ++j) {
         const int nu = tid + j * T;
-        t[nu] = band_row<C>(nu, g.bsx, g.bwx, g.box, xf,
+        t[nu] = band_row<C>(nu, N, g.bsx, g.bwx, xf,
                             [&](int m) { return cconj(S[swz<C>(__ldg(&g.posx[m]))]); });
     }
 }
@@ -263,7 +264,7 @@ pc_col_kernel(PcgGeo g, void* __restrict__ t_v, const double* __restrict__ E,
     const C* ly = reinterpret_cast<const C*>(g.lamy);
     for (int j = 0; j < E_; ++j) {                 // X_y, then the eigenvalue denominator
         const int mu = tid + j * T;
-        C c = band_row<C>(mu, g.bsy, g.bwy, g.boy, xf,
+        C c = band_row<C>(mu, N, g.bsy, g.bwy, xf,
                           [&](int m) { return cconj(Sc[swz<C>(__ldg(&g.posy[m]))]); });
         const C lm = __ldg(&ly[mu]);
         const C den = cmk<C>(lx.x + lm.x - En, lx.y + lm.y);
@@ -273,7 +274,7 @@ pc_col_kernel(PcgGeo g, void* __restrict__ t_v, const double* __restrict__ E,
     __syncthreads();
     for (int j = 0; j < E_; ++j) {                 // X_y^T into FFT positions (conjugated)
         const int m = tid + j * T;
-        const C d = band_row<C>(m, g.bsy, g.bwy, g.boy, xb, [&](int nu2) { return S2c[nu2]; });
+        const C d = band_row<C>(m, N, g.bsy, g.bwy, xb, [&](int nu2) { return S2c[nu2]; });
         Sc[swz<C>(__ldg(&g.posy[m]))] = cconj(d);
     }
     __syncthreads();
@@ -317,7 +318,7 @@ pc_row2_kernel(PcgGeo g, const void* __restrict__ t_v, void* __restrict__ z_v,
     const C* xb = reinterpret_cast<const C*>(g.xbx);
     for (int j = 0; j < E_; ++j) {
         const int m = tid + j * T;
-        const C d = band_row<C>(m, g.bsx, g.bwx, g.box, xb, [&](int nu) { return Tn[nu]; });
+        const C d = band_row<C>(m, N, g.bsx, g.bwx, xb, [&](int nu) { return Tn[nu]; });
         S[swz<C>(__ldg(&g.posx[m]))] = cconj(d);
     }
     __syncthreads();

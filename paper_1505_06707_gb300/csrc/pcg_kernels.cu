@@ -247,23 +247,32 @@ __device__ __forceinline__ void retire(const PcgState& s, int e, int st) {
     atomicSub(s.nactive, 1);
 }
 
-// per-energy scalar updates of the iteration (one thread per energy; the
+// sum of n partials by one warp: lane l adds l, l + 32, ... in order, then a
+// fixed butterfly; every lane returns the total (same order on every call)
+__device__ __forceinline__ double2 warp_sum_parts(const double2* __restrict__ p, int n) {
+    double2 t = make_double2(0.0, 0.0);
+    for (int i = threadIdx.x; i < n; i += 32) { t.x += p[i].x; t.y += p[i].y; }
+    return sum_warp(t);
+}
+
+// per-energy scalar updates of the iteration (one warp per energy; the
 // partial sums are added in a fixed order, so results are reproducible)
 __global__ void pcg_scalar_kernel(int stage, int nE, const double2* __restrict__ part, int nparts,
                                   PcgState s, const double2* __restrict__ part2) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = blockIdx.x;
     if (stage == STAGE_FNORM) {
         if (e == 0) {
-            double t = 0;
-            for (int i = 0; i < nparts; ++i) t += part[i].x;
-            *s.fnorm2 = t;
+            const double2 t = warp_sum_parts(part, nparts);
+            if (threadIdx.x == 0) *s.fnorm2 = t.x;
         }
         return;
     }
     if (e >= nE || !s.active[e]) return;
     if (stage == STAGE_TRUE && !s.upd[e]) return;
-    double2 t = make_double2(0.0, 0.0);
-    for (int i = 0; i < nparts; ++i) { t.x += part[(int64_t)e * nparts + i].x; t.y += part[(int64_t)e * nparts + i].y; }
+    const double2 t = warp_sum_parts(part + (int64_t)e * nparts, nparts);
+    const double2 u = stage == STAGE_BETA_FLEX ? warp_sum_parts(part2 + (int64_t)e * nparts, nparts)
+                                               : make_double2(0.0, 0.0);
+    if (threadIdx.x != 0) return;
     if (stage == STAGE_RHO) {
         s.rho[e] = t;
         if (!(fabs(t.x) + fabs(t.y) > 1e-300)) { retire(s, e, SOFT_ERR_BREAKDOWN); }
@@ -307,8 +316,6 @@ __global__ void pcg_scalar_kernel(int stage, int nE, const double2* __restrict__
         s.rref[e] = rel;
     } else if (stage == STAGE_BETA_FLEX) {
         // flexible (Polak-Ribiere) beta = z'^T (r' - r) / rho = -alpha z'^T w / rho
-        double2 u = make_double2(0.0, 0.0);
-        for (int i = 0; i < nparts; ++i) { u.x += part2[(int64_t)e * nparts + i].x; u.y += part2[(int64_t)e * nparts + i].y; }
         const double2 rho = s.rho[e], al = s.alpha[e];
         const double d = rho.x * rho.x + rho.y * rho.y;
         if (!(d > 0.0)) { retire(s, e, SOFT_ERR_BREAKDOWN); return; }
@@ -651,7 +658,7 @@ int gcr_step(int phase, void* Pb, void* Q, int64_t slot_stride, int mu, int ld, 
 
 int pcg_scalars(int stage, int nE, const double2* part, int nparts, const PcgState& s,
                 cudaStream_t st, const double2* part2) {
-    pcg_scalar_kernel<<<(nE + 63) / 64, 64, 0, st>>>(stage, nE, part, nparts, s, part2);
+    pcg_scalar_kernel<<<stage == STAGE_FNORM ? 1 : nE, 32, 0, st>>>(stage, nE, part, nparts, s, part2);
     return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
 }
 
