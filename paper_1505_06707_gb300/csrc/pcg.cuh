@@ -186,15 +186,28 @@ a_col_kernel(PcgGeo g, const void* __restrict__ p_v, void* __restrict__ w_v,
 }
 
 // --------------------------------------------------------- preconditioner
-// band mat-vec: out[nu] = sum_{u < width} tab[u * n + nu] * in(start[nu] + u)
-template <typename C, class In>
-__device__ __forceinline__ C band_row(int nu, int n, const int* __restrict__ bs, const int* __restrict__ bw,
-                                      const C* __restrict__ tab, In in) {
-    const int s0 = __ldg(&bs[nu]), wd = __ldg(&bw[nu]);
-    C acc; acc.x = 0; acc.y = 0;
-    for (int u = 0; u < wd; ++u) acc = cfma(__ldg(&tab[u * n + nu]), in(s0 + u), acc);
-    return acc;
+// band mat-vec for NJ rows nu_j = nu0 + j step at once (independent chains):
+// out[j] = sum_{u < width} tab[u * n + nu_j] * in(start[nu_j] + u).  The
+// tables are zero past each row's width, so every row runs to the widest of
+// the NJ with its input index clamped to n - 1.
+template <typename C, int NJ, class In>
+__device__ __forceinline__ void band_rows(int nu0, int step, int n, const int* __restrict__ bs,
+                                          const int* __restrict__ bw, const C* __restrict__ tab, In in,
+                                          C (&out)[NJ]) {
+    int s0[NJ], wm = 0;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        s0[j] = __ldg(&bs[nu0 + j * step]);
+        wm = max(wm, __ldg(&bw[nu0 + j * step]));
+        out[j].x = 0; out[j].y = 0;
+    }
+    for (int u = 0; u < wm; ++u) {
+#pragma unroll
+        for (int j = 0; j < NJ; ++j)
+            out[j] = cfma(__ldg(&tab[u * n + nu0 + j * step]), in(min(s0[j] + u, n - 1)), out[j]);
+    }
 }
+constexpr int BAND_NJ = 4;     // band rows per thread at once
 
 // row pass 1: t = X_x F_x r (F with e^{+ikx}), natural nu order
 // (r is IO; the pass computes in R: t and the tables are in R)
@@ -206,10 +219,12 @@ pc_row1_kernel(PcgGeo g, const void* __restrict__ r_v, void* __restrict__ t_v,
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
     using C = typename K::C;
     constexpr int N = K::N, T = K::T, E_ = K::E;
+    static_assert(E_ % BAND_NJ == 0, "band rows per thread");
     const int y = blockIdx.x, e = blockIdx.y;
     if (active && !active[e]) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* S = reinterpret_cast<C*>(smem_raw);
+    C* Fn = S + N;                               // F_x r in natural index order
     const int tid = threadIdx.x;
     const int64_t base = (int64_t)e * g.N + (int64_t)y * N;
     const IO* __restrict__ r = reinterpret_cast<const IO*>(r_v) + base;
@@ -220,11 +235,17 @@ pc_row1_kernel(PcgGeo g, const void* __restrict__ r_v, void* __restrict__ t_v,
     }
     __syncthreads();
     fwd_fft<R, LOGN, LOGE, LOGRM, 0>(S, reinterpret_cast<const C*>(g.Wx), tid);
-    const C* xf = reinterpret_cast<const C*>(g.xfx);
     for (int j = 0; j < E_; ++j) {
-        const int nu = tid + j * T;
-        t[nu] = band_row<C>(nu, N, g.bsx, g.bwx, xf,
-                            [&](int m) { return cconj(S[swz<C>(__ldg(&g.posx[m]))]); });
+        const int m = tid + j * T;
+        Fn[m] = cconj(S[swz<C>(__ldg(&g.posx[m]))]);
+    }
+    __syncthreads();
+    const C* xf = reinterpret_cast<const C*>(g.xfx);
+    for (int j0 = 0; j0 < E_; j0 += BAND_NJ) {
+        C o[BAND_NJ];
+        band_rows<C, BAND_NJ>(tid + j0 * T, T, N, g.bsx, g.bwx, xf, [&](int m) { return Fn[m]; }, o);
+#pragma unroll
+        for (int j = 0; j < BAND_NJ; ++j) t[tid + (j0 + j) * T] = o[j];
     }
 }
 
@@ -237,6 +258,7 @@ pc_col_kernel(PcgGeo g, void* __restrict__ t_v, const double* __restrict__ E,
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
     using C = typename K::C;
     constexpr int N = K::N, T = K::T, E_ = K::E, PITCH = ColPitch<C, N>::value;
+    static_assert(E_ % BAND_NJ == 0, "band rows per thread");
     const int e = blockIdx.y;
     if (active && !active[e]) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -256,34 +278,43 @@ pc_col_kernel(PcgGeo g, void* __restrict__ t_v, const double* __restrict__ E,
     C* S2c = S2 + col * PITCH;
     const C* W = reinterpret_cast<const C*>(g.Wy);
     fwd_fft<R, LOGN, LOGE, LOGRM, 0>(Sc, W, tid);
+    for (int j = 0; j < E_; ++j) {                 // F_y t in natural index order
+        const int m = tid + j * T;
+        S2c[m] = cconj(Sc[swz<C>(__ldg(&g.posy[m]))]);
+    }
+    __syncthreads();
     const int nu = c0 + col;
     const C lx = reinterpret_cast<const C*>(g.lamx)[nu];
     const R En = (R)E[e];
     const C* xf = reinterpret_cast<const C*>(g.xfy);
     const C* xb = reinterpret_cast<const C*>(g.xby);
     const C* ly = reinterpret_cast<const C*>(g.lamy);
-    for (int j = 0; j < E_; ++j) {                 // X_y, then the eigenvalue denominator
-        const int mu = tid + j * T;
-        C c = band_row<C>(mu, N, g.bsy, g.bwy, xf,
-                          [&](int m) { return cconj(Sc[swz<C>(__ldg(&g.posy[m]))]); });
-        const C lm = __ldg(&ly[mu]);
-        const C den = cmk<C>(lx.x + lm.x - En, lx.y + lm.y);
-        const R dn = den.x * den.x + den.y * den.y;
-        S2c[mu] = cscale(cmulc(c, den), (R)1 / dn);   // c / den
+    for (int j0 = 0; j0 < E_; j0 += BAND_NJ) {    // X_y, then the eigenvalue denominator
+        C o[BAND_NJ];
+        band_rows<C, BAND_NJ>(tid + j0 * T, T, N, g.bsy, g.bwy, xf, [&](int m) { return S2c[m]; }, o);
+#pragma unroll
+        for (int j = 0; j < BAND_NJ; ++j) {
+            const int mu = tid + (j0 + j) * T;
+            const C lm = __ldg(&ly[mu]);
+            const C den = cmk<C>(lx.x + lm.x - En, lx.y + lm.y);
+            const R dn = den.x * den.x + den.y * den.y;
+            Sc[mu] = cscale(cmulc(o[j], den), (R)1 / dn);    // c / den, natural order
+        }
     }
     __syncthreads();
-    for (int j = 0; j < E_; ++j) {                 // X_y^T into FFT positions (conjugated)
-        const int m = tid + j * T;
-        const C d = band_row<C>(m, N, g.bsy, g.bwy, xb, [&](int nu2) { return S2c[nu2]; });
-        Sc[swz<C>(__ldg(&g.posy[m]))] = cconj(d);
+    for (int j0 = 0; j0 < E_; j0 += BAND_NJ) {    // X_y^T into FFT positions (conjugated)
+        C o[BAND_NJ];
+        band_rows<C, BAND_NJ>(tid + j0 * T, T, N, g.bsy, g.bwy, xb, [&](int nu2) { return Sc[nu2]; }, o);
+#pragma unroll
+        for (int j = 0; j < BAND_NJ; ++j) S2c[swz<C>(__ldg(&g.posy[tid + (j0 + j) * T]))] = cconj(o[j]);
     }
     __syncthreads();
-    inv_fft<R, LOGN, LOGE, LOGRM, K::NPASS - 1>(Sc, W, tid);
+    inv_fft<R, LOGN, LOGE, LOGRM, K::NPASS - 1>(S2c, W, tid);
 #pragma unroll
     for (int it = 0; it < E_; ++it) {
         const int idx = threadIdx.x + it * TW * T;
         const int yy = idx / TW, j = idx % TW;
-        t[(int64_t)yy * nx + c0 + j] = cconj(S[j * PITCH + swz<C>(yy)]);
+        t[(int64_t)yy * nx + c0 + j] = cconj(S2[j * PITCH + swz<C>(yy)]);
     }
 }
 
@@ -300,6 +331,7 @@ pc_row2_kernel(PcgGeo g, const void* __restrict__ t_v, void* __restrict__ z_v,
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
     using C = typename K::C;
     constexpr int N = K::N, T = K::T, E_ = K::E;
+    static_assert(E_ % BAND_NJ == 0, "band rows per thread");
     const int y = blockIdx.x, e = blockIdx.y;
     if (active && !active[e]) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -316,10 +348,11 @@ pc_row2_kernel(PcgGeo g, const void* __restrict__ t_v, void* __restrict__ z_v,
     }
     __syncthreads();
     const C* xb = reinterpret_cast<const C*>(g.xbx);
-    for (int j = 0; j < E_; ++j) {
-        const int m = tid + j * T;
-        const C d = band_row<C>(m, N, g.bsx, g.bwx, xb, [&](int nu) { return Tn[nu]; });
-        S[swz<C>(__ldg(&g.posx[m]))] = cconj(d);
+    for (int j0 = 0; j0 < E_; j0 += BAND_NJ) {
+        C o[BAND_NJ];
+        band_rows<C, BAND_NJ>(tid + j0 * T, T, N, g.bsx, g.bwx, xb, [&](int nu) { return Tn[nu]; }, o);
+#pragma unroll
+        for (int j = 0; j < BAND_NJ; ++j) S[swz<C>(__ldg(&g.posx[tid + (j0 + j) * T]))] = cconj(o[j]);
     }
     __syncthreads();
     inv_fft<R, LOGN, LOGE, LOGRM, K::NPASS - 1>(S, reinterpret_cast<const C*>(g.Wx), tid);
