@@ -172,6 +172,21 @@ int soft_step_batch(soft_plan* plan, void* psi, int64_t nsteps, double* t_inout,
 int soft_observe(const soft_plan* plan, const void* psi, double* norm_in, double* flux,
                  void* stream);
 
+/* soft_set_potential -- replace the static potential of a single 1D plan or
+ * a 2D plan.  It enters the step as e^{-iU tau/2} (Sec. II, the scheme
+ * after Eq. C_FD) and A as U - E (Sec. III, Eq. linsys); the default is the
+ * soft-Coulomb potential of soft_options.
+ *   U_re_im  host double[2n], interleaved complex: U at the complex-scaled
+ *            grid points z(x_i) (2D: [ny][nx], x fastest).  The plan's
+ *            comparison-absorber potential (CAP / TFAP contours) is added.
+ *   n        grid points (N, or nx * ny).
+ * The plan's potential tables (and the stationary solver's, once built) are
+ * rewritten in place after a device synchronisation, so call it between
+ * steps; captured graphs stay valid.  SOFT_ERR_UNSUPPORTED for batch plans,
+ * SOFT_ERR_INVALID_ARG for a size mismatch, SOFT_ERR_NONFINITE for a
+ * non-finite value. */
+int soft_set_potential(soft_plan* plan, const double* U_re_im, int64_t n);
+
 /* sse_pcg_solve -- solve A psi_e = f for nE energies E[e] by complex-symmetric
  * CG (Sec. III: the unconjugated form r^T z replaces the inner product),
  * x0 = 0, stopping when ||r||_2 / ||f||_2 < tol (Hermitian norms, FP64).

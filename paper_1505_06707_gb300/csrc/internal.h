@@ -42,6 +42,7 @@ struct Tables1D {
     double R0 = 0, theta = 0;
     Axis1D ax;                    // host FP64 grid, contour, C
     std::vector<cd> U0;           // potential at z(x_j)
+    std::vector<cd> Uabs;         // its comparison-absorber part (zero for the ECS contours)
     void* TK = nullptr;           // device buffers in the plan's precision
     void* TKh = nullptr;
     void* TV = nullptr;

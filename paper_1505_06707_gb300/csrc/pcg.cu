@@ -358,6 +358,14 @@ static int ensure_gcr(Pcg* S, int nE) {
     return SOFT_OK;
 }
 
+int pcg_refill_potential(Plan2D* Q) {
+    Pcg* S = Q->pcg;
+    if (!S || !S->tables) return SOFT_OK;
+    int rc;
+    if ((rc = refill_c(S->U, Q->U, SOFT_C128))) return rc;
+    return refill_c(S->U32, Q->U, SOFT_C64);
+}
+
 void Plan2D::free_pcg() {
     delete pcg;
     pcg = nullptr;

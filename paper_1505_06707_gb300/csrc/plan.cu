@@ -97,6 +97,46 @@ int upload_tw(void** dst, const std::vector<cd>& v, int prec) {
     return upload(dst, buf.data(), buf.size() * sizeof(float));
 }
 
+// the upload_* conversions into a temporary device buffer, then one copy
+// into dst
+static int refill_with(int (*up)(void**, const std::vector<cd>&, int), void* dst,
+                       const std::vector<cd>& v, int prec) {
+    if (v.empty()) return SOFT_OK;
+    const size_t bytes = v.size() * (prec == SOFT_C128 ? 16 : 8);
+    void* tmp = nullptr;
+    int rc = up(&tmp, v, prec);
+    if (rc == SOFT_OK) rc = cuda_status(cudaMemcpy(dst, tmp, bytes, cudaMemcpyDeviceToDevice));
+    cudaFree(tmp);
+    return rc;
+}
+int refill_c(void* dst, const std::vector<cd>& v, int prec) { return refill_with(upload_c, dst, v, prec); }
+int refill_vtab(void* dst, const std::vector<cd>& v, int prec) { return refill_with(upload_vtab, dst, v, prec); }
+
+// Potential factors of one step from U0 (Sec. II, the scheme after Eq. C_FD):
+// tv[j] = e^{-iU0 tau} off the strip block (both half factors merged),
+// e^{-iU0 tau/2} on it (the strip CN sits between the halves); tvs holds
+// the block rows' factors in the chunk layout of the strip CN (thread t of
+// the n >> loge threads owns rows t*ch .. t*ch + ch - 1, entry c*T + t).
+static void potential_tables_1d(const Tables1D& T, int n, double tau, std::vector<cd>& tv,
+                                std::vector<cd>& tvs) {
+    tv.resize(n);
+    for (int j = 0; j < n; ++j) {
+        const bool inblk = ((j - T.blk0 + n) % n) < T.nb;
+        tv[j] = std::exp(cd(0.0, -1.0) * T.U0[j] * tau * (inblk ? 0.5 : 1.0));
+    }
+    tvs.clear();
+    if (T.nb > 0) {
+        const int thr = n >> T.loge, nb = T.nb;
+        const int ch = (nb + thr - 1) / thr;
+        tvs.assign((size_t)ch * thr, 1.0);
+        for (int t = 0; t < thr; ++t)
+            for (int c = 0; c < ch; ++c) {
+                const int i = t * ch + c;
+                if (i < nb) tvs[(size_t)c * thr + t] = tv[(T.blk0 + i) % n];
+            }
+    }
+}
+
 static int ilog2(int64_t n) {
     int l = 0;
     while ((int64_t(1) << l) < n) ++l;
@@ -125,10 +165,14 @@ int make_tables_1d(Tables1D* T, int n, double a, double b, double R0, double the
         if (A.x[j] < R0) T->iR = j + 1;
     }
     T->U0.resize(n);
-    for (int j = 0; j < n; ++j) T->U0[j] = soft_coulomb(&A.z[j], 1, o.soft_a2, o.charge) + cf.absorber(A.x[j]);
+    T->Uabs.resize(n);
+    for (int j = 0; j < n; ++j) {
+        T->Uabs[j] = cf.absorber(A.x[j]);
+        T->U0[j] = soft_coulomb(&A.z[j], 1, o.soft_a2, o.charge) + T->Uabs[j];
+    }
     // kinetic tables in the forward FFT's output order, 1/N folded in
     const std::vector<int> perm = dif_output_order(logn, logrm);
-    std::vector<cd> tk(n), tkh(n), tv(n);
+    std::vector<cd> tk(n), tkh(n), tv, tvs;
     const std::vector<cd> w = pass_twiddles(logn, logrm);
     // The step kernel reads them in its last forward pass, whose butterflies
     // hold R consecutive positions b*R + m (R its radix): entry (b, m) is
@@ -141,17 +185,13 @@ int make_tables_1d(Tables1D* T, int n, double a, double b, double R0, double the
         tk[q] = std::polar(1.0 / n, -0.5 * k * k * tau);
         tkh[q] = std::polar(1.0 / n, -0.25 * k * k * tau);
     }
-    // potential factor: full step off the block, half step on it
-    for (int j = 0; j < n; ++j) {
-        const bool inblk = ((j - T->blk0 + n) % n) < T->nb;
-        tv[j] = std::exp(cd(0.0, -1.0) * T->U0[j] * tau * (inblk ? 0.5 : 1.0));
-    }
+    potential_tables_1d(*T, n, tau, tv, tvs);
     // Strip CN coefficients for the kernel's chunked solve: thread t of the
     // T = n >> loge threads owns rows t*ch .. t*ch + ch - 1 (ch = ceil(nb/T)).
     // M is complex symmetric, so mb_i = mf_{i+1}: the kernel reads mf of rows
     // t*ch + c, c <= ch, at c*T + t (0 past the block), then g of row t*ch + c
-    // at (ch+1)*T + c*T + t, and TV of the row at c*T + t of tvs.
-    std::vector<cd> mf, mb, g, cnv, tvs;
+    // at (ch+1)*T + c*T + t (tvs holds the rows' potential factors).
+    std::vector<cd> mf, mb, g, cnv;
     if (T->nb > 0) {
         double err = 0;
         rc = strip_factor(A, T->blk0, T->nb, mf, mb, g, &err);
@@ -161,15 +201,11 @@ int make_tables_1d(Tables1D* T, int n, double a, double b, double R0, double the
             if (std::abs(mb[i] - mf[i + 1]) > 1e-12 * (std::abs(mb[i]) + 1e-300)) return SOFT_ERR_SETUP;
         const int ch = (nb + thr - 1) / thr, P1 = (ch + 1) * thr;
         cnv.assign((size_t)P1 + (size_t)ch * thr, 0.0);
-        tvs.assign((size_t)ch * thr, 1.0);
         for (int t = 0; t < thr; ++t)
             for (int c = 0; c <= ch; ++c) {
                 const int i = t * ch + c;
                 if (i < nb) cnv[(size_t)c * thr + t] = mf[i];
-                if (c < ch && i < nb) {
-                    cnv[P1 + (size_t)c * thr + t] = g[i];
-                    tvs[(size_t)c * thr + t] = tv[(T->blk0 + i) % n];
-                }
+                if (c < ch && i < nb) cnv[P1 + (size_t)c * thr + t] = g[i];
             }
     }
     if ((rc = upload_tab(&T->TK, tk, o.prec))) return rc;
@@ -434,6 +470,27 @@ int soft_observe(const soft_plan* P, const void* psi, double* norm_in, double* f
                               (cudaStream_t)stream);
     const_cast<soft_plan*>(P)->last_launches = 1;
     return rc;
+}
+
+int soft_set_potential(soft_plan* P, const double* U, int64_t n) {
+    if (!P || !U || n <= 0) return SOFT_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < 2 * n; ++i)
+        if (!std::isfinite(U[i])) return SOFT_ERR_NONFINITE;
+    if (P->kind == 2) {
+        if (n != (int64_t)P->p2->nx * P->p2->ny) return SOFT_ERR_INVALID_ARG;
+        return P->p2->set_potential(U);
+    }
+    if (P->kind != 1 || !P->single || P->tabs.size() != 1) return SOFT_ERR_UNSUPPORTED;
+    Tables1D* T = P->tabs[0].get();
+    const int nn = 1 << T->logn;
+    if (n != nn) return SOFT_ERR_INVALID_ARG;
+    int rc = cuda_status(cudaDeviceSynchronize());      // no step may still read the tables
+    if (rc) return rc;
+    for (int j = 0; j < nn; ++j) T->U0[j] = cd(U[2 * j], U[2 * j + 1]) + T->Uabs[j];
+    std::vector<cd> tv, tvs;
+    potential_tables_1d(*T, nn, P->dt, tv, tvs);
+    if ((rc = refill_vtab(T->TV, tv, T->prec))) return rc;
+    return refill_vtab(T->TVs, tvs, T->prec);
 }
 
 void soft_destroy(soft_plan* P) { delete P; }

@@ -24,6 +24,21 @@ static int ilog2_2d(int64_t n) {
     return (int64_t(1) << l) == n ? l : -1;
 }
 
+// replace the potential (host complex [ny][nx], plus the plan's absorber
+// part) and rewrite e^{-iU tau/2} and the solver's U tables in place
+int Plan2D::set_potential(const double* Uin) {
+    int rc = cuda_status(cudaDeviceSynchronize());      // no step may still read the tables
+    if (rc) return rc;
+    const size_t n = (size_t)nx * ny;
+    std::vector<cd> tvh(n);
+    for (size_t i = 0; i < n; ++i) {
+        U[i] = cd(Uin[2 * i], Uin[2 * i + 1]) + Uabs[i];
+        tvh[i] = std::exp(cd(0.0, -0.5 * tau) * U[i]);
+    }
+    if ((rc = refill_vtab(TVh, tvh, prec))) return rc;
+    return pcg_refill_potential(this);
+}
+
 Plan2D::~Plan2D() {
     void* bufs[] = {Wx, Wy, TKx, TKhx, TKy, TKhy, TVh, cnx, cny};
     for (void* b : bufs) cudaFree(b);
@@ -106,12 +121,14 @@ int create_2d(const soft_grid* grid, const double* box, double R0, double theta,
     if ((o.prec == SOFT_C64 ? 8 : 16) * (size_t)nby * 12 > 227 * 1024) return SOFT_ERR_UNSUPPORTED;
     // potential at (z(x), z(y)) and e^{-iU tau/2}
     Q->U.resize((size_t)nx * ny);
+    Q->Uabs.resize((size_t)nx * ny);
     std::vector<cd> tvh((size_t)nx * ny);
     for (int64_t yy = 0; yy < ny; ++yy)
         for (int64_t xx = 0; xx < nx; ++xx) {
             const cd z[2] = {Q->ax.z[xx], Q->ay.z[yy]};
-            const cd u = soft_coulomb(z, 2, o.soft_a2, o.charge) + cx.absorber(Q->ax.x[xx]) +
-                         cy.absorber(Q->ay.x[yy]);
+            const cd ua = cx.absorber(Q->ax.x[xx]) + cy.absorber(Q->ay.x[yy]);
+            const cd u = soft_coulomb(z, 2, o.soft_a2, o.charge) + ua;
+            Q->Uabs[yy * nx + xx] = ua;
             Q->U[yy * nx + xx] = u;
             tvh[yy * nx + xx] = std::exp(cd(0.0, -0.5 * dt) * u);
         }

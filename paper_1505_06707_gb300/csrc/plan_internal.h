@@ -12,6 +12,12 @@ int upload_c(void** dst, const std::vector<cd>& v, int prec);
 int upload_tab(void** dst, const std::vector<cd>& v, int prec);
 int upload_vtab(void** dst, const std::vector<cd>& v, int prec);
 int upload_tw(void** dst, const std::vector<cd>& v, int prec);
+// rewrite an existing device buffer in place (same size and format as the
+// matching upload_*), so that pointers held by kernels and graphs stay valid
+int refill_c(void* dst, const std::vector<cd>& v, int prec);
+int refill_vtab(void* dst, const std::vector<cd>& v, int prec);
+struct Plan2D;
+int pcg_refill_potential(Plan2D* Q);     // the stationary solver's U tables, if built
 int make_tables_1d(Tables1D* T, int n, double a, double b, double R0, double theta, double tau,
                    const soft_options& o, int loge, int logrm);
 
@@ -31,6 +37,7 @@ struct Plan2D {
     double R0 = 0, theta = 0, tau = 0;
     Axis1D ax, ay;                 // host FP64 axes (grid, k, q, z, C)
     std::vector<cd> U;             // U(z(x), z(y)), [ny][nx]
+    std::vector<cd> Uabs;          // its comparison-absorber part, [ny][nx]
     void *Wx = nullptr, *Wy = nullptr, *TKx = nullptr, *TKhx = nullptr, *TKy = nullptr,
          *TKhy = nullptr, *TVh = nullptr, *cnx = nullptr, *cny = nullptr;
     Geo2D geo{};
@@ -45,6 +52,7 @@ struct Plan2D {
     int ypass(void* psi, cudaStream_t st);
     int enqueue_step(void* psi, bool last, cudaStream_t st);
     void free_pcg();
+    int set_potential(const double* U_re_im);   // host complex [ny][nx]
     ~Plan2D();
 };
 }  // namespace soft

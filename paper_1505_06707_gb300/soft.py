@@ -14,7 +14,8 @@ __all__ = [
     "SoftError", "SOFT_C64", "SOFT_C128", "CONTOUR_SHARP", "CONTOUR_SECS", "CONTOUR_TFECS",
     "ABSORB_CAP", "ABSORB_TFAP",
     "load", "lib_path", "exported_symbols", "Options", "Field", "soft_create", "soft_create_batch",
-    "soft_batch_layout", "soft_step", "soft_step_batch", "soft_step_noalloc", "soft_observe", "sse_pcg_solve",
+    "soft_batch_layout", "soft_step", "soft_step_batch", "soft_step_noalloc", "soft_observe",
+    "soft_set_potential", "sse_pcg_solve",
     "sse_apply_A", "sse_apply_A32", "sse_apply_precond", "soft_destroy", "sse_nn_set_weights", "sse_nn_get_weights",
     "sse_nn_forward", "sse_nn_grad", "sse_nn_train", "NN_PARAMS", "soft_plan_points", "soft_plan_count",
     "soft_last_launches", "Plan",
@@ -32,7 +33,7 @@ _lib = None
 # every symbol include/soft.h declares
 exported_symbols = [
     "soft_default_options", "soft_create", "soft_create_batch", "soft_batch_layout", "soft_step",
-    "soft_step_batch", "soft_observe", "sse_pcg_solve", "sse_apply_A", "sse_apply_A32",
+    "soft_step_batch", "soft_observe", "soft_set_potential", "sse_pcg_solve", "sse_apply_A", "sse_apply_A32",
     "sse_apply_precond", "soft_destroy", "soft_strerror", "soft_plan_count", "soft_plan_points", "soft_plan_prec",
     "soft_last_launches", "soft_step_noalloc", "sse_nn_set_weights", "sse_nn_get_weights",
     "sse_nn_forward", "sse_nn_grad", "sse_nn_train",
@@ -87,6 +88,7 @@ def load():
     L.soft_step_batch.argtypes = [P, P, i64, C.POINTER(dbl), P]
     L.soft_step_noalloc.argtypes = [P, P, i64, C.POINTER(Field), C.POINTER(dbl), P]
     L.soft_observe.argtypes = [P, P, P, P, P]
+    L.soft_set_potential.argtypes = [P, P, i64]
     L.sse_pcg_solve.argtypes = [P, C.POINTER(dbl), C.c_int, P, P, dbl, C.c_int, C.c_int,
                                 C.POINTER(C.c_int), C.POINTER(dbl), P]
     L.sse_apply_A.argtypes = [P, dbl, P, P, P]
@@ -230,6 +232,14 @@ def soft_step_batch(plan, psi, nsteps, t, stream=None):
 def soft_observe(plan, psi, norm_in, flux, stream=None):
     _check(load().soft_observe(plan, _ptr(psi), _ptr(norm_in), _ptr(flux), _stream(stream)),
            "soft_observe")
+
+
+def soft_set_potential(plan, U):
+    """U: complex array of the plan's grid shape (host), the potential at
+    the complex-scaled grid points."""
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(U, dtype=np.complex128).ravel())
+    _check(load().soft_set_potential(plan, a.ctypes.data, a.size), "soft_set_potential")
 
 
 def sse_pcg_solve(plan, E, rhs, psi_out, tol=1e-8, maxit=1000, precond=1, stream=None):

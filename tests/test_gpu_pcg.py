@@ -70,6 +70,29 @@ def test_apply_A_and_preconditioners_match_oracle():
         S.soft_destroy(plan)
 
 
+def test_set_potential_reaches_the_solver():
+    """soft_set_potential after the solver's tables exist: A (FP64 and FP32)
+    must use the new U (oracle A with the same U)."""
+    plan, p2, st = setup()
+    try:
+        rng = np.random.default_rng(12)
+        x = rng.standard_normal((256, 256)) + 1j * rng.standard_normal((256, 256))
+        dx, dy = dev(x), dev(np.zeros_like(x))
+        S.sse_apply_A(plan, 0.6, dx, dy)                      # builds the tables
+        zx = T.z_contour(p2.x, T.SHARP, 30.0, 40.0, 0.4, 0.5)
+        U = -2.0 * np.exp(-(zx[None, :] ** 2 + zx[:, None] ** 2) / 9.0) + 0.1j * np.cos(zx[:, None])
+        S.soft_set_potential(plan, U)
+        p2.U = np.ascontiguousarray(U, dtype=np.complex128)
+        S.sse_apply_A(plan, 0.6, dx, dy)
+        assert relerr(host(dy), st.apply_A(x, 0.6)) < 1e-12
+        x32 = x.astype(np.complex64)
+        y32 = torch.zeros((256, 256), dtype=torch.complex64, device="cuda")
+        S.sse_apply_A32(plan, 0.6, torch.from_numpy(x32).cuda(), y32)
+        assert relerr(host(y32).astype(np.complex128), st.apply_A(x32.astype(np.complex128), 0.6)) < 5e-6
+    finally:
+        S.soft_destroy(plan)
+
+
 def test_pcg_fp32_preconditioner():
     """COCG (flexible beta) with the banded preconditioner computing in FP32
     (A, the residual and the dots stay FP64): every energy reaches the

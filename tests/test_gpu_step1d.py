@@ -193,6 +193,45 @@ def test_nsteps_zero_is_noop_and_theta0_has_no_strip():
 
 
 @pytest.mark.parametrize("prec", [S.SOFT_C128, S.SOFT_C64])
+def test_set_potential(prec):
+    """soft_set_potential: a user potential (a complex-scaled Gaussian well
+    plus a weak harmonic term, evaluated at z(x_i)) replaces the soft-Coulomb
+    one; the oracle steps with the same U.  Also with a laser field, and
+    setting the default back restores the default run."""
+    n, hw, R0, th, dt, nst = 1024, 40.0, 30.0, 0.5, 0.02, 150
+    ref = P.Problem1D(n, -hw, hw, R0, theta=th, a2=2.0, dt=dt)
+    U_default = ref.U0.copy()
+    U = -1.5 * np.exp(-ref.z ** 2 / 4.0) + 0.002 * ref.z ** 2
+    x = ref.x
+    psi0 = np.exp(-(x - 3.0) ** 2 / 4.0 + 0.8j * x)
+    field = (0.04, 0.3, 2.0)
+    plan = S.soft_create(n, (-hw, hw), R0, th, dt, prec=prec, soft_a2=2.0)
+    try:
+        S.soft_set_potential(plan, U)
+        ref.U0 = U.copy()
+        for fld in (None, field):
+            d = torch.tensor(psi0, dtype=CT[prec], device="cuda")
+            S.soft_step(plan, d, nst, 0.0, field=fld)
+            torch.cuda.synchronize()
+            want = ref.step(psi0, nst, 0.0, field=fld)
+            assert relerr(d.cpu().numpy().astype(np.complex128), want) < tol(prec, nst, n)
+        S.soft_set_potential(plan, U_default)
+        d = torch.tensor(psi0, dtype=CT[prec], device="cuda")
+        S.soft_step(plan, d, nst, 0.0)
+        torch.cuda.synchronize()
+        ref.U0 = U_default
+        assert relerr(d.cpu().numpy().astype(np.complex128), ref.step(psi0, nst)) < tol(prec, nst, n)
+        with pytest.raises(S.SoftError):
+            S.soft_set_potential(plan, U[: n // 2])
+        bad = U.copy()
+        bad[7] = np.nan
+        with pytest.raises(S.SoftError):
+            S.soft_set_potential(plan, bad)
+    finally:
+        S.soft_destroy(plan)
+
+
+@pytest.mark.parametrize("prec", [S.SOFT_C128, S.SOFT_C64])
 def test_batch_mixed_sizes_with_fields(prec):
     """A batch of instances of the laser workload (mixed N, own E0 each)
     advanced in one call; each compared with its own oracle run."""

@@ -14,6 +14,7 @@ torch = pytest.importorskip("torch")
 import paper_1505_06707_gb300 as S  # noqa: E402
 import workloads as W  # noqa: E402
 from oracle import propagate as P  # noqa: E402
+from oracle import tables as T  # noqa: E402
 
 CT = {S.SOFT_C64: torch.complex64, S.SOFT_C128: torch.complex128}
 
@@ -61,6 +62,33 @@ def packet2d(nx, ny, box, seed):
 def _cuda():
     assert torch.cuda.is_available(), "GPU tests need CUDA"
     S.load()
+
+
+@pytest.mark.parametrize("prec", [S.SOFT_C128, S.SOFT_C64])
+def test_set_potential_2d(prec):
+    """soft_set_potential on a 2D plan: an anisotropic well at (z(x), z(y))
+    replaces the soft-Coulomb potential after a first call has captured the
+    step graph; the replayed graph must use the rewritten tables (oracle with
+    the same U, 24 steps)."""
+    n, box, R0, th = 256, (-40.0, 40.0, -40.0, 40.0), 30.0, 0.4
+    ref = P.Problem2D(n, n, box, R0, theta=th, a2=1.0, dt=0.02)
+    zx = T.z_contour(ref.x, T.SHARP, R0, box[1], th, 0.5)
+    zy = T.z_contour(ref.y, T.SHARP, R0, box[3], th, 0.5)
+    U = -2.0 * np.exp(-(zx[None, :] ** 2 + 0.5 * zy[:, None] ** 2) / 9.0)
+    psi0 = packet2d(n, n, box, 99)
+    plan = S.soft_create((n, n), box, R0, th, 0.02, prec=prec, soft_a2=1.0)
+    try:
+        d = torch.tensor(psi0, dtype=CT[prec], device="cuda")
+        S.soft_step(plan, d, 24, 0.0)
+        S.soft_set_potential(plan, U)
+        d.copy_(torch.tensor(psi0, dtype=CT[prec]))
+        S.soft_step(plan, d, 24, 0.0)
+        torch.cuda.synchronize()
+        ref.U = np.ascontiguousarray(U, dtype=np.complex128)
+        want = ref.step(psi0, 24)
+        assert relerr(d.cpu().numpy().astype(np.complex128), want) < tol(prec, 24, n)
+    finally:
+        S.soft_destroy(plan)
 
 
 @pytest.mark.parametrize("prec", [S.SOFT_C128, S.SOFT_C64])
