@@ -280,6 +280,45 @@ def bench_2d(S, torch, dev, args):
     return res
 
 
+def oracle_2d_sample(steps=3):
+    """The FP64 C oracle's literal 2D step (four FFTs, full cyclic CN) on the
+    2048^2 workload, timed for a few steps on the host cores."""
+    import workloads as W
+    from oracle import propagate as P
+    w = W.w3()
+    p = P.Problem2D(w["nx"], w["ny"], w["box"], w["R0"], theta=w["theta"], a2=w["a2"], dt=w["dt"])
+    t0 = time.perf_counter()
+    p.step(w["psi0"], steps)
+    sec = time.perf_counter() - t0
+    return {"value": w["nx"] * w["ny"] * steps / sec, "unit": "grid-point-steps/s", "seconds_per_step": sec / steps,
+            "cores": P.num_threads(), "kind": "oracle",
+            "sample": "%d steps of the 2048^2 workload, FP64 C oracle, OpenMP over rows/columns" % steps}
+
+
+def oracle_pcg_sample(mean_iterations, iters=6):
+    """The oracle's COCG (numpy FP64, banded preconditioner) on one energy of
+    the 1024^2 workload: a few iterations timed, scaled to a solve at the
+    given mean iteration count."""
+    import workloads as W
+    from oracle import propagate as P
+    from oracle import stationary as ST
+    from oracle import tables as T
+    w = W.w4()
+    n = w["nx"]
+    p2 = P.Problem2D(n, n, w["box"], w["R0"], theta=w["theta"], a2=w["a2"], dt=0.02)
+    st = ST.Stationary2D(p2, nbw=10, kind=T.SHARP, R0=w["R0"], theta=w["theta"])
+    E = float(w["E"][0])
+    t0 = time.perf_counter()
+    ST.cocg(lambda v: st.apply_A(v, E), lambda r: st.precond_band(r, E), w["f"], tol=1e-30, maxit=iters)
+    per_it = (time.perf_counter() - t0) / iters
+    per_solve = per_it * mean_iterations
+    return {"value": 1.0 / per_solve, "unit": "solves/s", "seconds_per_iteration": per_it,
+            "seconds_per_solve": per_solve, "cores": 1, "kind": "oracle",
+            "sample": "%d COCG iterations (banded preconditioner) on one 1024^2 energy, numpy FP64 on one "
+                      "core, scaled to %.0f iterations per solve (the GPU FP64 COCG's mean)"
+                      % (iters, mean_iterations)}
+
+
 def bench_pcg(S, torch, dev, args):
     """The stationary workload: 64 energies solved as one batch on 1024^2 with
     the banded ECS preconditioner to relative residual 1e-8."""
@@ -310,6 +349,14 @@ def bench_pcg(S, torch, dev, args):
         res[name] = {"solves_per_s": len(E) / sec, "seconds": sec, "status": rc,
                      "iterations_mean": float(np.mean(its)), "iterations_max": int(np.max(its)),
                      "max_relres": float(np.max(rr))}
+        if pc == 5:
+            # minimum HBM traffic of one mixed iteration, per grid point (complex64
+            # vectors, double-float increment): A row 16 + column 24, P row 16 +
+            # column 16 + row 32 (t, z, r, w), x/r update 64, p update 24
+            bpp = 192.0
+            gbs = float(np.sum(its)) * n * n * bpp / sec / 1e9
+            res[name]["hbm_alg"] = {"GBps": gbs, "frac": gbs / _hbm_peak(_peaks()[0]),
+                                    "bytes_per_point_iteration": bpp}
     S.soft_destroy(plan)
     del out
     best = max(res.values(), key=lambda r: r["solves_per_s"] if r["status"] == 0 else 0)
@@ -652,6 +699,11 @@ def main():
         out["w5_learned"] = bench_learned(S, torch, dev, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_sample()
+        if not args.no_extra:
+            out["w3_2d"]["cpu_baseline"] = oracle_2d_sample()
+            pc = out["w4_pcg"]
+            its = (pc.get("band_fp64") or pc.get("mixed_fp32_reliable") or {}).get("iterations_mean", 378.0)
+            out["w4_pcg"]["cpu_baseline"] = oracle_pcg_sample(its)
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
