@@ -231,6 +231,31 @@ def test_paper_setup_absorption_ordering():
     assert e_tf < e_se < e_sh
 
 
+@pytest.mark.slow
+def test_tfecs_parasitic_reflection_is_second_order_in_h():
+    """Sec. IV, the grid-convergence study (Fig. h_convergence(b)): with
+    TFECS, the error left in the unscaled region is the parasitic reflection
+    caused by the three-point approximation of C, and it falls quadratically
+    with h.  The paper's test (b = -a = 51.2, r_s = 40, v0 = 2) at N = 512,
+    1024, 2048 with one common tau (so only h changes), measured at t = 30
+    once the reflection has come back inside: each halving of h divides the
+    L2 distance to the free packet by about 4 (a first-order C would give
+    2, a fourth-order one 16)."""
+    g = json.load(open(os.path.join(GOLD, "paper_test_setup.json")))
+    rmax, rs, v0, tt = g["rmax"], g["r_s"], g["v0"], 30.0
+    errs = []
+    for n in (512, 1024, 2048):
+        p = P.Problem1D(n, -rmax, rmax, R0=rs, theta=math.pi / 4, kind=T.TFECS,
+                        alpha=g["tfecs_alpha"], dt=0.0025, potential=False)
+        psi0 = math.pi ** -0.25 * np.exp(-p.x ** 2 / 2 + 1j * v0 * p.x)   # Eq. psi0
+        psi = p.step(psi0, int(round(tt / p.dt)))
+        ex = free_packet(p.x, tt, 1.0, 0.0, v0, 0.0, 1e9, images=0)
+        m = np.abs(p.x) < rs
+        errs.append(math.sqrt(p.h) * np.linalg.norm((psi - ex)[m]))
+    for coarse, fine in zip(errs, errs[1:]):
+        assert 3.0 < coarse / fine < 6.0, errs
+
+
 def test_tfecs_contour_log_divergence():
     """Sec. IV after Eq. qTFECS: z(x_N) grows like sqrt(alpha i) dx_CS
     ln(2 dx_CS / h) as h -> 0.  The remainder z(x_N) - r_s - that term must
