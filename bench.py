@@ -334,7 +334,8 @@ def bench_pcg(S, torch, dev, args):
         E = E[:args.pcg_energies]
     out = torch.zeros((len(E), n, n), dtype=torch.complex128, device=dev)
     st = torch.cuda.current_stream(dev)
-    S.sse_pcg_solve(plan, E[:2], f, out, tol=w["tol"], maxit=4, precond=1, stream=st)   # warm-up
+    # warm-up: builds the tables and the workspace for all energies
+    S.sse_pcg_solve(plan, E, f, out, tol=w["tol"], maxit=2, precond=1, stream=st)
     torch.cuda.synchronize()
     res = {}
     names = {1: "band_fp64", 4: "band_fp32", 5: "mixed_fp32_reliable"}
