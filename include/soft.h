@@ -218,8 +218,10 @@ int soft_set_potential(soft_plan* plan, const double* U_re_im, int64_t n);
  *               only that true residual decides convergence, so the
  *               stopping test means the same as for 0-4.  An energy whose
  *               true residual has not halved between two updates
- *               continues with the FP64 A, after a restart.  iters_out
- *               counts the iterations.
+ *               continues with the FP64 A, after a restart; if it stalls
+ *               again, it is finished by the all-FP64 COCG of precond 1
+ *               started from its current psi (up to maxit more
+ *               iterations).  iters_out counts all iterations.
  *   iters_out, relres_out: host int[nE], double[nE]; may be NULL.
  * Returns SOFT_ERR_NOT_CONVERGED if any energy stopped at maxit (its last
  * iterate is written), SOFT_ERR_BREAKDOWN on a vanishing CG denominator.

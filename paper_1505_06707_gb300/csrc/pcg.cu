@@ -255,6 +255,60 @@ static int apply_A(Plan2D* Q, const void* p, void* w, const double* dE, const in
     return pcg_col(Q->ly, 0, g, p, w, dE, act, part, nE, st);
 }
 
+// COCG (Sec. III) with preconditioner type precond (0, 1 or 4) over the
+// energies in s.active, from x = 0 or (warm) from the x already in psi_out
+static int solve_cocg(Plan2D* Q, const PcgState& s, const void* rhs, void* psi_out, int maxit, int nE,
+                      int precond, bool warm, cudaStream_t st) {
+    Pcg* S = Q->pcg;
+    const int64_t N = S->N;
+    const int np_row = Q->ny, np_vec = 256, np_col = pcg_col_blocks(Q->nx);
+    int rc;
+    if (warm) {                              // r = f - A x for the active energies
+        if ((rc = apply_A(Q, psi_out, S->w, S->dE, S->active, S->part2, nE, st))) return rc;
+        if ((rc = vec_sub(rhs, S->w, S->r, S->active, N, nE, st))) return rc;
+        Q->launches += 1;
+    } else if ((rc = vec_init(rhs, psi_out, S->r, N, nE, st))) {     // x = 0, r = f
+        return rc;
+    }
+    // ||f||^2, z = P^-1 r, rho = r^T z, p = z
+    if ((rc = vec_norm2(rhs, N, S->part, np_vec, st))) return rc;
+    if ((rc = pcg_scalars(STAGE_FNORM, nE, S->part, np_vec, s, st))) return rc;
+    // COCG (Sec. III): z = P^-1 r, rho = r^T z, p = z
+    if ((rc = apply_pc(Q, precond, S->r, S->z, S->dE, S->active, S->part, nE, st))) return rc;
+    if ((rc = pcg_scalars(STAGE_RHO, nE, S->part, np_row, s, st))) return rc;
+    if ((rc = vec_p(S->p, S->z, S->beta, S->active, N, nE, 1, st))) return rc;
+    Q->launches += 5;
+    const int CHECK = 4;
+    for (int it = 1; it <= maxit; ++it) {
+        if ((rc = apply_A(Q, S->p, S->w, S->dE, S->active, S->part, nE, st))) return rc;
+        if ((rc = pcg_scalars(STAGE_ALPHA, nE, S->part, np_col, s, st))) return rc;
+        if ((rc = vec_xr(psi_out, S->r, S->p, S->w, S->alpha, S->active, N, nE, S->part, np_vec, st))) return rc;
+        if ((rc = pcg_scalars(STAGE_RNORM, nE, S->part, np_vec, s, st))) return rc;
+        Q->launches += 3;
+        if (it % CHECK == 0 || it == maxit) {
+            int na = 0;
+            if ((rc = cuda_status(cudaMemcpyAsync(&na, S->nactive, sizeof(int), cudaMemcpyDeviceToHost, st)))) return rc;
+            if ((rc = cuda_status(cudaStreamSynchronize(st)))) return rc;
+            if (na <= 0) break;
+        }
+        if (it == maxit) break;
+        if (precond == 4) {
+            // FP32 preconditioner: not exactly symmetric, so the flexible
+            // beta = z'^T (r' - r) / rho = -alpha z'^T w / rho
+            if ((rc = apply_pc(Q, precond, S->r, S->z, S->dE, S->active, nullptr, nE, st))) return rc;
+            if ((rc = vec_dot2(S->r, S->z, S->w, S->active, N, nE, S->part, S->part2, np_vec, st))) return rc;
+            if ((rc = pcg_scalars(STAGE_BETA_FLEX, nE, S->part, np_vec, s, st, S->part2))) return rc;
+            Q->launches += 1;
+        } else {
+            if ((rc = apply_pc(Q, precond, S->r, S->z, S->dE, S->active, S->part, nE, st))) return rc;
+            if ((rc = pcg_scalars(STAGE_BETA, nE, S->part, np_row, s, st))) return rc;
+        }
+        if ((rc = vec_p(S->p, S->z, S->beta, S->active, N, nE, 0, st))) return rc;
+        Q->launches += 5;
+    }
+    return SOFT_OK;
+}
+
 // w = A p on complex64 vectors (mixed iteration): A computing in FP32 for
 // the energies in act32 (all if null), in FP64 for those in act64 (none if
 // null); partials of p^T w at the stride of the FP64 column pass
@@ -293,7 +347,8 @@ static int apply_pc_mixed(Plan2D* Q, const void* r, void* z, const void* w, cons
 // the complex128 x and the residual replaced by f - A x with A in FP64; only
 // that true residual decides convergence.  An energy whose true residual has
 // not halved since its previous update switches to the FP64 A (on the same
-// complex64 vectors) after a restart.
+// complex64 vectors) after a restart; if it stalls again it leaves with mode
+// bit 2 set, and the caller restarts it in FP64 (solve_cocg, warm).
 static int solve_mixed(Plan2D* Q, const PcgState& s, const void* rhs, void* psi_out, int maxit, int nE,
                        cudaStream_t st) {
     Pcg* S = Q->pcg;
@@ -469,76 +524,57 @@ int sse_pcg_solve(soft_plan* P, const double* E, int nE, const void* rhs, void* 
     PcgState s{S->rho, S->alpha, S->beta, S->relres, S->fnorm2, S->active, S->iters, S->status,
                S->nactive, tol, S->rref, S->upd, RU_DELTA, RU_MAXGAP, S->lastu,
                mixed ? S->mode : nullptr, mixed ? S->act32 : nullptr, mixed ? S->act64 : nullptr};
-    const int np_row = Q->ny, np_vec = 256, np_col = pcg_col_blocks(Q->nx);
+    const int np_vec = 256;
     if (mixed) {
         if ((rc = solve_mixed(Q, s, rhs, psi_out, maxit, nE, st))) return rc;
+        if ((rc = cuda_status(cudaStreamSynchronize(st)))) return rc;
+        // energies whose mixed iteration stalled even with the FP64 A (mode
+        // bit 2): COCG in FP64 with the banded preconditioner, from their x
+        std::vector<int> mode_h(nE), redo(nE, 0);
+        if ((rc = cuda_status(cudaMemcpy(mode_h.data(), S->mode, sizeof(int) * nE, cudaMemcpyDeviceToHost)))) return rc;
+        int nredo = 0;
+        for (int e = 0; e < nE; ++e)
+            if (mode_h[e] & 4) { redo[e] = 1; ++nredo; }
+        if (nredo > 0) {
+            if ((rc = cuda_status(cudaMemcpy(S->active, redo.data(), sizeof(int) * nE, cudaMemcpyHostToDevice)))) return rc;
+            if ((rc = cuda_status(cudaMemcpy(S->nactive, &nredo, sizeof(int), cudaMemcpyHostToDevice)))) return rc;
+            PcgState s2 = s;
+            s2.mode = nullptr; s2.act32 = nullptr; s2.act64 = nullptr;
+            if ((rc = solve_cocg(Q, s2, rhs, psi_out, maxit, nE, 1, true, st))) return rc;
+        }
+    } else if (!flexible) {
+        if ((rc = solve_cocg(Q, s, rhs, psi_out, maxit, nE, precond, false, st))) return rc;
     } else {
-        // x = 0, r = f, ||f||^2, z = P^-1 r, rho = r^T z, p = z
+        // x = 0, r = f, ||f||^2
         if ((rc = vec_init(rhs, psi_out, S->r, N, nE, st))) return rc;
         if ((rc = vec_norm2(rhs, N, S->part, np_vec, st))) return rc;
         if ((rc = pcg_scalars(STAGE_FNORM, nE, S->part, np_vec, s, st))) return rc;
-        if (!flexible) {
-            // COCG (Sec. III): z = P^-1 r, rho = r^T z, p = z
-            if ((rc = apply_pc(Q, precond, S->r, S->z, S->dE, S->active, S->part, nE, st))) return rc;
-            if ((rc = pcg_scalars(STAGE_RHO, nE, S->part, np_row, s, st))) return rc;
-            if ((rc = vec_p(S->p, S->z, S->beta, S->active, N, nE, 1, st))) return rc;
-            Q->launches += 5;
-            const int CHECK = 4;
-            for (int it = 1; it <= maxit; ++it) {
-                if ((rc = apply_A(Q, S->p, S->w, S->dE, S->active, S->part, nE, st))) return rc;
-                if ((rc = pcg_scalars(STAGE_ALPHA, nE, S->part, np_col, s, st))) return rc;
-                if ((rc = vec_xr(psi_out, S->r, S->p, S->w, S->alpha, S->active, N, nE, S->part, np_vec, st))) return rc;
-                if ((rc = pcg_scalars(STAGE_RNORM, nE, S->part, np_vec, s, st))) return rc;
-                Q->launches += 3;
-                if (it % CHECK == 0 || it == maxit) {
-                    int na = 0;
-                    if ((rc = cuda_status(cudaMemcpyAsync(&na, S->nactive, sizeof(int), cudaMemcpyDeviceToHost, st)))) return rc;
-                    if ((rc = cuda_status(cudaStreamSynchronize(st)))) return rc;
-                    if (na <= 0) break;
-                }
-                if (it == maxit) break;
-                if (precond == 4) {
-                    // FP32 preconditioner: not exactly symmetric, so the flexible
-                    // beta = z'^T (r' - r) / rho = -alpha z'^T w / rho
-                    if ((rc = apply_pc(Q, precond, S->r, S->z, S->dE, S->active, nullptr, nE, st))) return rc;
-                    if ((rc = vec_dot2(S->r, S->z, S->w, S->active, N, nE, S->part, S->part2, np_vec, st))) return rc;
-                    if ((rc = pcg_scalars(STAGE_BETA_FLEX, nE, S->part, np_vec, s, st, S->part2))) return rc;
-                    Q->launches += 1;
-                } else {
-                    if ((rc = apply_pc(Q, precond, S->r, S->z, S->dE, S->active, S->part, nE, st))) return rc;
-                    if ((rc = pcg_scalars(STAGE_BETA, nE, S->part, np_row, s, st))) return rc;
-                }
-                if ((rc = vec_p(S->p, S->z, S->beta, S->active, N, nE, 0, st))) return rc;
-                Q->launches += 5;
-            }
-        } else {
-            // flexible GCR with the last GCR_M direction pairs (minimal residual,
-            // valid for a preconditioner that changes from one iteration to the
-            // next, e.g. the learned correction)
-            if ((rc = ensure_gcr(S, nE))) return rc;
-            const int M = Pcg::GCR_M;
-            const int64_t ss = N * nE;
-            double2* gPb = (double2*)S->gP;
-            double2* gQb = (double2*)S->gQ;
-            const int CHECK = 4;
-            for (int it = 1; it <= maxit; ++it) {
-                const int slot = (it - 1) % M, mu = std::min(it, M);
-                double2* Ps = gPb + slot * ss;
-                double2* Qs = gQb + slot * ss;
-                if ((rc = apply_pc(Q, precond, S->r, Ps, S->dE, S->active, nullptr, nE, st))) return rc;
-                if (learned && (rc = P->nn->correct_c128(Ps, nE, Q->ny, Q->nx, S->active, st))) return rc;
-                if ((rc = apply_A(Q, Ps, Qs, S->dE, S->active, S->part, nE, st))) return rc;
-                if ((rc = gcr_step(0, gPb, gQb, ss, mu, M, slot, S->gbeta, S->gqn, S->r, S->active, N, nE,
-                                   S->gpart, S->part, S->part2, np_vec, s, st))) return rc;
-                if ((rc = vec_xr(psi_out, S->r, Ps, Qs, S->alpha, S->active, N, nE, S->part, np_vec, st))) return rc;
-                if ((rc = pcg_scalars(STAGE_RNORM, nE, S->part, np_vec, s, st))) return rc;
-                Q->launches += (learned ? 4 : 0) + 3 + 2 + 4 + 2;
-                if (it % CHECK == 0 || it == maxit) {
-                    int na = 0;
-                    if ((rc = cuda_status(cudaMemcpyAsync(&na, S->nactive, sizeof(int), cudaMemcpyDeviceToHost, st)))) return rc;
-                    if ((rc = cuda_status(cudaStreamSynchronize(st)))) return rc;
-                    if (na <= 0) break;
-                }
+        // flexible GCR with the last GCR_M direction pairs (minimal residual,
+        // valid for a preconditioner that changes from one iteration to the
+        // next, e.g. the learned correction)
+        if ((rc = ensure_gcr(S, nE))) return rc;
+        const int M = Pcg::GCR_M;
+        const int64_t ss = N * nE;
+        double2* gPb = (double2*)S->gP;
+        double2* gQb = (double2*)S->gQ;
+        const int CHECK = 4;
+        for (int it = 1; it <= maxit; ++it) {
+            const int slot = (it - 1) % M, mu = std::min(it, M);
+            double2* Ps = gPb + slot * ss;
+            double2* Qs = gQb + slot * ss;
+            if ((rc = apply_pc(Q, precond, S->r, Ps, S->dE, S->active, nullptr, nE, st))) return rc;
+            if (learned && (rc = P->nn->correct_c128(Ps, nE, Q->ny, Q->nx, S->active, st))) return rc;
+            if ((rc = apply_A(Q, Ps, Qs, S->dE, S->active, S->part, nE, st))) return rc;
+            if ((rc = gcr_step(0, gPb, gQb, ss, mu, M, slot, S->gbeta, S->gqn, S->r, S->active, N, nE,
+                               S->gpart, S->part, S->part2, np_vec, s, st))) return rc;
+            if ((rc = vec_xr(psi_out, S->r, Ps, Qs, S->alpha, S->active, N, nE, S->part, np_vec, st))) return rc;
+            if ((rc = pcg_scalars(STAGE_RNORM, nE, S->part, np_vec, s, st))) return rc;
+            Q->launches += (learned ? 4 : 0) + 3 + 2 + 4 + 2;
+            if (it % CHECK == 0 || it == maxit) {
+                int na = 0;
+                if ((rc = cuda_status(cudaMemcpyAsync(&na, S->nactive, sizeof(int), cudaMemcpyDeviceToHost, st)))) return rc;
+                if ((rc = cuda_status(cudaStreamSynchronize(st)))) return rc;
+                if (na <= 0) break;
             }
         }
     }

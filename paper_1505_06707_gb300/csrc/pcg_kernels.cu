@@ -223,6 +223,19 @@ __global__ void vec_xr_kernel(double2* __restrict__ x, double2* __restrict__ r,
     if (threadIdx.x == 0) part[(int64_t)e * gridDim.x + blockIdx.x] = t;
 }
 
+// r = f - t for the energies with active set
+__global__ void vec_sub_kernel(const double2* __restrict__ f, const double2* __restrict__ t,
+                               double2* __restrict__ r, const int* __restrict__ active, int64_t N) {
+    const int e = blockIdx.y;
+    if (!active[e]) return;
+    const int64_t o = (int64_t)e * N;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 fv = f[i], tv = t[o + i];
+        r[o + i] = make_double2(fv.x - tv.x, fv.y - tv.y);
+    }
+}
+
 // p = z + beta p (beta = 0 with copy = 1: p = z)
 __global__ void vec_p_kernel(double2* __restrict__ p, const double2* __restrict__ z,
                              const double2* __restrict__ beta, const int* __restrict__ active,
@@ -308,7 +321,12 @@ __global__ void pcg_scalar_kernel(int stage, int nE, const double2* __restrict__
         s.lastu[e] = s.iters[e];
         if (!isfinite(rel)) { retire(s, e, SOFT_ERR_NONFINITE); return; }
         if (rel < s.tol) { retire(s, e, SOFT_OK); return; }
-        if (!(rel < 0.5 * s.rref[e]) && !(s.mode[e] & 1)) {
+        if (!(rel < 0.5 * s.rref[e])) {
+            if (s.mode[e] & 1) {                           // stalled on the FP64 A too: leave the
+                s.mode[e] |= 4;                            // mixed iteration for an FP64 restart
+                retire(s, e, SOFT_ERR_NOT_CONVERGED);
+                return;
+            }
             s.mode[e] = 3;
             s.act32[e] = 0;
             s.act64[e] = 1;
@@ -349,6 +367,10 @@ int vec_xr(void* x, void* r, const void* p, const void* w, const double2* alpha,
            int64_t N, int nE, double2* part, int nparts, cudaStream_t st) {
     vec_xr_kernel<<<dim3(nparts, nE), 256, 0, st>>>((double2*)x, (double2*)r, (const double2*)p,
                                                      (const double2*)w, alpha, act, N, part);
+    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+}
+int vec_sub(const void* f, const void* t, void* r, const int* act, int64_t N, int nE, cudaStream_t st) {
+    vec_sub_kernel<<<dim3(256, nE), 256, 0, st>>>((const double2*)f, (const double2*)t, (double2*)r, act, N);
     return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
 }
 int vec_p(void* p, const void* z, const double2* beta, const int* act, int64_t N, int nE, int copy,

@@ -79,6 +79,8 @@ int vec_xr(void* x, void* r, const void* p, const void* w, const double2* alpha,
            int64_t N, int nE, double2* part, int nparts, cudaStream_t st);
 int vec_p(void* p, const void* z, const double2* beta, const int* act, int64_t N, int nE, int copy,
           cudaStream_t st);
+// r = f - t (complex128) for the active energies
+int vec_sub(const void* f, const void* t, void* r, const int* act, int64_t N, int nE, cudaStream_t st);
 int pcg_scalars(int stage, int nE, const double2* part, int nparts, const PcgState& s,
                 cudaStream_t st, const double2* part2 = nullptr);
 // one flexible-GCR orthogonalisation of slot `slot` against the other mu-1

@@ -149,6 +149,37 @@ def test_pcg_mixed_precision_reliable_updates():
         S.soft_destroy(plan)
 
 
+@pytest.mark.parametrize("contour", [S.CONTOUR_SECS, S.CONTOUR_TFECS, S.ABSORB_CAP, S.ABSORB_TFAP])
+def test_pcg_contours_and_absorbers(contour):
+    """The stationary solver on the smooth contours (Eqs. qSECS, qTFECS) and
+    with the comparison absorbers (Sec. IV), banded preconditioner in FP64
+    and the mixed mode: every residual recomputed by the oracle's A built
+    with the same contour."""
+    n, box, R0, th = 256, (-40.0, 40.0, -40.0, 40.0), 30.0, 0.4
+    okind = {S.CONTOUR_SECS: T.SECS, S.CONTOUR_TFECS: T.TFECS, S.ABSORB_CAP: T.CAP,
+             S.ABSORB_TFAP: T.TFAP}[contour]
+    plan = S.soft_create((n, n), box, R0, th, 0.02, prec=S.SOFT_C128, soft_a2=1.0, contour=contour,
+                         cap_energy=2.0, tfap_kmin=0.25)
+    try:
+        p2 = P.Problem2D(n, n, box, R0, theta=th, kind=okind, alpha=0.5, a2=1.0, dt=0.02, e_cap=2.0,
+                         kmin=0.25)
+        st = ST.Stationary2D(p2, nbw=10, kind=okind, R0=R0, theta=th)
+        xg = -40.0 + 80.0 / n * (np.arange(n) + 0.5)
+        f = -np.exp(-(xg[None, :] ** 2 + (xg[:, None] - 3.0) ** 2) / 32.0).astype(np.complex128)
+        Es = [0.4, 1.3]
+        out = torch.zeros((len(Es), n, n), dtype=torch.complex128, device="cuda")
+        for pc in (1, 5):
+            rc, its, rr = S.sse_pcg_solve(plan, Es, dev(f), out, tol=1e-8, maxit=3000, precond=pc)
+            assert rc == 0, (pc, rc, its, rr)
+            xs = host(out)
+            for e, E in enumerate(Es):
+                res = np.linalg.norm(st.apply_A(xs[e], E) - f) / np.linalg.norm(f)
+                assert res < 2e-8, (pc, E, res, its[e])
+            print("contour", contour, "precond", pc, "iterations", its)
+    finally:
+        S.soft_destroy(plan)
+
+
 @pytest.mark.parametrize("precond", [0, 1])
 def test_pcg_solves_batch_small(precond):
     """Four energies at once; each residual recomputed with the oracle's A

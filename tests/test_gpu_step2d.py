@@ -125,6 +125,21 @@ def test_comparison_absorbers_2d(kind, prec):
     assert relerr(got, ref) < tol(prec, 40, n)
 
 
+@pytest.mark.parametrize("prec", [S.SOFT_C128, S.SOFT_C64])
+@pytest.mark.parametrize("contour", [S.CONTOUR_SECS, S.CONTOUR_TFECS])
+def test_smooth_contours_2d(contour, prec):
+    """SECS and TFECS (Eqs. qSECS, qTFECS) on both axes: 256^2, 40 steps
+    against the oracle with the same contour."""
+    n = 256
+    box = (-40.0, 40.0, -40.0, 40.0)
+    R0, th = 30.0, 0.4
+    psi0 = packet2d(n, n, box, 41 + contour)
+    okind = T.SECS if contour == S.CONTOUR_SECS else T.TFECS
+    ref = P.Problem2D(n, n, box, R0, theta=th, kind=okind, alpha=0.5, a2=1.0, dt=0.02).step(psi0, 40)
+    got, _ = run2d(n, n, box, R0, th, 0.02, psi0, 40, prec, soft_a2=1.0, contour=contour)
+    assert relerr(got, ref) < tol(prec, 40, n)
+
+
 def test_free_gaussian_closed_form_2d():
     """theta = 0, U = 0: the 2D step must reproduce the separable closed-form
     free Gaussian (summed over periodic images)."""
