@@ -16,7 +16,13 @@ namespace soft {
 namespace {
 
 constexpr int TWP = 2;    // columns per CTA of the FP64 column passes
-constexpr int TW32 = 4;   // columns per CTA of the FP32 column passes
+// columns per CTA of the FP32 column passes: 8 (64-byte row runs of
+// complex64), fewer where that would exceed 1024 threads
+template <int LN>
+struct Tw32 {
+    static constexpr int T = Cfg1D<float, LN, 3, 3>::T;
+    static constexpr int value = 1024 / T < 8 ? 1024 / T : 8;
+};
 
 // CTAs per SM: 1024 threads per SM, <= 64 registers (FP32 column passes)
 template <int THREADS>
@@ -122,7 +128,7 @@ int pcg_pc32_row(int logn, int which, const PcgGeo& g, const void* a, void* b, c
 
 int pcg_pc32_col(int logn, const PcgGeo& g, void* b, const double* E, const int* act, int nE,
                  cudaStream_t st) {
-#define CALL(L) pc_col<float, L, 3, 3, TW32, MinB32<TW32 * Cfg1D<float, L, 3, 3>::T>::value>(g, b, E, act, nE, st)
+#define CALL(L) pc_col<float, L, 3, 3, Tw32<L>::value, MinB32<Tw32<L>::value * Tw32<L>::T>::value>(g, b, E, act, nE, st)
     PCG_SIZES(CALL)
 #undef CALL
 }
@@ -143,7 +149,7 @@ int pcg_a32_row(int logn, const PcgGeo& g, const void* p, void* w, const double*
 
 int pcg_a32_col(int logn, const PcgGeo& g, const void* p, void* w, const int* act, double2* part,
                 int pstride, int nE, cudaStream_t st) {
-#define CALL(L) a_col<float, float2, L, 3, 3, TW32, MinB32<TW32 * Cfg1D<float, L, 3, 3>::T>::value>( \
+#define CALL(L) a_col<float, float2, L, 3, 3, Tw32<L>::value, MinB32<Tw32<L>::value * Tw32<L>::T>::value>( \
     g, p, w, act, part, pstride, nE, st)
     PCG_SIZES(CALL)
 #undef CALL
