@@ -53,10 +53,9 @@ def _hbm_peak(d):
 
 
 # DRAM bytes (read + write) of one launch of the dominant kernel, from an
-# ncu capture of that launch (dram__bytes_read.sum + dram__bytes_write.sum;
-# summary and command in profiles/soft1d_kernel_laser_batch_c64.md), valid
-# only while the kernel sources hash to the same value and the launch has the
-# same instances and steps.
+# ncu capture of that launch (dram__bytes_read.sum + dram__bytes_write.sum),
+# valid only while the kernel sources hash to the same value and the launch
+# has the same instances and steps.
 TRAFFIC_MEASURED = {
     "c64": {"src_sha1": "017cc908ca484d84bee6e1e40864622eadd99c5a", "n": 16384, "instances": 988,
             "steps": 256, "bytes": 133621504 + 78311936},
@@ -81,12 +80,41 @@ def _traffic(prec, n, instances, steps):
     return float(t["bytes"])
 
 
-# FP32 SIMT peak derived from the unit counts and the maximum clock:
-# 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# FP64: measured on this machine by an FMA-throughput probe (independent DFMA
-# chains, 152 x 8 CTAs of 256 threads): 1.198 TFLOP/s
-FP64_PEAK_TFLOPS = 1.198
+# FMA lanes per SM and clock: 128 FP32 lanes; FP64 2 DFMA per clock per SM
+# (NVIDIA's dense FP64 figure for GB300, 1.25 TFLOP/s at 152 SMs and
+# 2.07 GHz, which the FMA probe of this package reproduces within a few %)
+FP32_FMA_PER_SM_CLK = 128
+FP64_FMA_PER_SM_CLK = 2
+
+
+def alu_peaks(torch=None, dev=0):
+    """ALU peaks derived from unit counts and the maximum SM clock: SM count
+    of the device x FMA lanes x 2 flop x clock (TFLOP/s)."""
+    nsm = None
+    if torch is not None and torch.cuda.is_available():
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks, _ = _peaks()
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    nsm = nsm or 152
+    return {"fp32_tflops": nsm * FP32_FMA_PER_SM_CLK * 2 * mhz * 1e6 / 1e12,
+            "fp64_tflops": nsm * FP64_FMA_PER_SM_CLK * 2 * mhz * 1e6 / 1e12,
+            "sms": nsm, "sm_max_mhz": mhz,
+            "how": "SMs x FMA lanes per SM (FP32 128, FP64 2) x 2 flop x max SM clock"}
+
+
+def alu_probe(iters=4096):
+    """The FMA throughput probe (paper_1505_06707_gb300/probe/alu_peak.cu):
+    measured FP32 and FP64 rates, TFLOP/s."""
+    import ctypes as C
+    lib = C.CDLL(os.path.join(ROOT, "paper_1505_06707_gb300", "_lib", "libaluprobe.so"))
+    lib.alu_fma_rate.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    out = {}
+    for name, f64, it in (("fp32", 0, iters), ("fp64", 1, iters // 32)):
+        fl, ms = C.c_double(), C.c_double()
+        rc = lib.alu_fma_rate(f64, it, C.byref(fl), C.byref(ms))
+        out[name + "_tflops"] = fl.value / 1e12 if rc == 0 else None
+        out[name + "_ms_per_launch"] = ms.value if rc == 0 else None
+    return out
 
 
 def flops_per_call(ns, nbs, steps, field=True):
@@ -512,7 +540,7 @@ def main():
     ap.add_argument("--steps-per-call", type=int, default=STEPS_PER_CALL)
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the 2D step and stationary-solver measurements")
-    ap.add_argument("--only", choices=["2d", "pcg", "learned", "conv", "accuracy"], default=None,
+    ap.add_argument("--only", choices=["2d", "pcg", "learned", "conv", "accuracy", "peaks"], default=None,
                     help="run one of the extra measurements alone (for profiling captures; not a bench line)")
     ap.add_argument("--pcg-precond", default="1,4,5",
                     help="stationary-solver modes to time (sse_pcg_solve precond values)")
@@ -528,6 +556,8 @@ def main():
         torch.cuda.set_device(dev)
         if args.only == "accuracy":
             r = bench_accuracy(S, torch, dev, args, sizes=(2048, 4096, 8192, 16384))
+        elif args.only == "peaks":
+            r = {"derived": alu_peaks(torch, 0), "probe": alu_probe()}
         else:
             fn = {"2d": bench_2d, "pcg": bench_pcg, "learned": bench_learned, "conv": bench_conv}[args.only]
             r = fn(S, torch, dev, args)
@@ -675,15 +705,17 @@ def main():
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": args.prec.replace("c64", "c64 (f32)")
            .replace("c128", "c128 (f64)"), "data": "synthetic", "config": config(args.prec, args.instances, spc)}
-    peak = FP32_PEAK_TFLOPS if prec == S.SOFT_C64 else FP64_PEAK_TFLOPS
+    ap_ = alu_peaks(torch, local)
+    peak = ap_["fp32_tflops"] if prec == S.SOFT_C64 else ap_["fp64_tflops"]
     out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                        "frac": achieved / peak,
                        "traffic": _traffic(args.prec, sizes[0], len(groups[sizes[0]]), spc),
                        "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
                        "kernel": "soft1d_kernel, N = %d group (%d instances, %d steps per launch), "
                                  "%.3f ms per launch, timed alone" % (sizes[0], len(groups[sizes[0]]), spc, kms),
-                       "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
-                       if prec == S.SOFT_C64 else "measured DFMA probe"}
+                       "peak_source": "derived: %d SMs x %d %s FMA per clock x 2 x %.0f MHz" % (
+                           ap_["sms"], FP32_FMA_PER_SM_CLK if prec == S.SOFT_C64 else FP64_FMA_PER_SM_CLK,
+                           "FP32" if prec == S.SOFT_C64 else "FP64", ap_["sm_max_mhz"])}
     # the same throughput against HBM, counting one read + one write of the state per time step
     bytes_pt = 16 if prec == S.SOFT_C64 else 32
     out["hbm_effective"] = {"GBps": value / world * bytes_pt / 1e9, "peak": hbm,

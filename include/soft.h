@@ -90,7 +90,7 @@ typedef struct {
     int prec;            /* soft_prec [SOFT_C128]                            */
     int contour;         /* soft_contour [SOFT_CONTOUR_SHARP]                */
     double tfecs_alpha;  /* alpha of Eq. qTFECS [0.5]                        */
-    double soft_a2;      /* a^2 of U = -Z/sqrt(|z|^2 + a^2) [2.0]            */
+    double soft_a2;      /* a^2 of U = -Z/sqrt(z^2 + a^2), z complex [2.0]   */
     double charge;       /* Z [1.0]; 0 gives U = 0                           */
     int band_width;      /* N_BW of the banded preconditioner [10]           */
     int autotune;        /* 1: time the built kernel variants of every 1D size
@@ -171,6 +171,15 @@ int soft_step_batch(soft_plan* plan, void* psi, int64_t nsteps, double* t_inout,
  * FP64 accumulation. */
 int soft_observe(const soft_plan* plan, const void* psi, double* norm_in, double* flux,
                  void* stream);
+
+/* soft_step_status -- wait for the work queued on `stream` and report whether
+ * a step of this 1D plan (single or batch) has left a non-finite value in a
+ * state since the last query: each step kernel tests its instance's first
+ * element after its last step, where a NaN or Inf anywhere in the state has
+ * arrived through the FFT.  Returns SOFT_ERR_NONFINITE and clears the flag if
+ * so, SOFT_OK otherwise; SOFT_ERR_UNSUPPORTED for 2D plans.  The step calls
+ * themselves never wait for the device, so they cannot report it. */
+int soft_step_status(soft_plan* plan, void* stream);
 
 /* soft_set_potential -- replace the static potential of a single 1D plan or
  * a 2D plan.  It enters the step as e^{-iU tau/2} (Sec. II, the scheme

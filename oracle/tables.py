@@ -112,8 +112,11 @@ def z_contour(x, kind: int, R0: float, rmax: float, theta: float = 0.0,
     if kind == SHARP:
         z[out] = sg[out] * (R0 + np.exp(1j * theta) * d)
     elif kind == SECS:
-        c = 1j * theta / (rmax - R0)
-        z[out] = sg[out] * (R0 + (np.exp(c * d) - 1.0) / c)
+        if theta == 0.0:                    # q = 1: no scaling
+            z[out] = x[out]
+        else:
+            c = 1j * theta / (rmax - R0)
+            z[out] = sg[out] * (R0 + (np.exp(c * d) - 1.0) / c)
     elif kind == TFECS:
         from scipy.integrate import quad
         vals = []

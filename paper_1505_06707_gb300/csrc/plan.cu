@@ -97,6 +97,14 @@ int upload_tw(void** dst, const std::vector<cd>& v, int prec) {
     return upload(dst, buf.data(), buf.size() * sizeof(float));
 }
 
+// Twiddle bases of the 1D step kernel: complex128 as is; complex64 as
+// compensated float4 (hi.re, hi.im, lo.re, lo.im), hi + lo = the FP64 value
+// to ~2^-48 (the kernel applies them by compensated multiplies, see
+// soft1d.cuh)
+int upload_tw_comp(void** dst, const std::vector<cd>& v, int prec) {
+    return upload_tab(dst, v, prec);
+}
+
 // the upload_* conversions into a temporary device buffer, then one copy
 // into dst
 static int refill_with(int (*up)(void**, const std::vector<cd>&, int), void* dst,
@@ -211,7 +219,7 @@ int make_tables_1d(Tables1D* T, int n, double a, double b, double R0, double the
     if ((rc = upload_tab(&T->TK, tk, o.prec))) return rc;
     if ((rc = upload_tab(&T->TKh, tkh, o.prec))) return rc;
     if ((rc = upload_vtab(&T->TV, tv, o.prec))) return rc;
-    if ((rc = upload_tw(&T->W, w, o.prec))) return rc;
+    if ((rc = upload_tw_comp(&T->W, w, o.prec))) return rc;
     if ((rc = upload_c(&T->cn, cnv, o.prec))) return rc;
     if ((rc = upload_vtab(&T->TVs, tvs, o.prec))) return rc;
     return SOFT_OK;
@@ -275,14 +283,18 @@ static int check_axis(int64_t n, double a, double b, double R0) {
 }
 
 // Time every built kernel variant of one 1D size on a sample of instances
-// (up to four waves of 152 SMs) and return the fastest configuration.
+// (up to four waves of the device's SMs) and return the fastest configuration.
 static int autotune_size(const soft_options& o, int n, double a, double b, double R0, double theta,
                          double dt, int count, int* best_e, int* best_r) {
     int le[16], lr[16];
     const int logn = ilog2(n);
     const int nv = soft1d_variants(o.prec, logn, le, lr, 16);
     if (nv <= 1) return SOFT_OK;
-    const int ns = std::min(count, 4 * 152);
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+        return SOFT_ERR_CUDA;
+    const int ns = std::min(count, 4 * nsm);
     const size_t eb = o.prec == SOFT_C64 ? 8 : 16;
     void* psi = nullptr;
     int rc = cuda_status(cudaMalloc(&psi, eb * (size_t)ns * n));
@@ -453,7 +465,7 @@ int soft_step(soft_plan* P, void* psi, int64_t nsteps, const soft_field* field, 
     if (P->kind == 2) return P->step_2d(psi, nsteps, t_inout, (cudaStream_t)stream);
     if (P->kind != 1) return SOFT_ERR_INVALID_ARG;
     if (P->single) {
-        int rc = P->set_single_field(field);
+        int rc = P->set_single_field(field, (cudaStream_t)stream);
         if (rc) return rc;
     }
     return P->step_1d(psi, nsteps, t_inout, (cudaStream_t)stream);
@@ -470,6 +482,18 @@ int soft_observe(const soft_plan* P, const void* psi, double* norm_in, double* f
                               (cudaStream_t)stream);
     const_cast<soft_plan*>(P)->last_launches = 1;
     return rc;
+}
+
+int soft_step_status(soft_plan* P, void* stream) {
+    if (!P || P->kind != 1) return P ? SOFT_ERR_UNSUPPORTED : SOFT_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int h = 0;
+    int rc = cuda_status(cudaMemcpyAsync(&h, P->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (rc == SOFT_OK) rc = cuda_status(cudaStreamSynchronize(st));
+    if (rc) return rc;
+    if (h == 0) return SOFT_OK;
+    rc = cuda_status(cudaMemsetAsync(P->d_status, 0, sizeof(int), st));
+    return rc ? rc : SOFT_ERR_NONFINITE;
 }
 
 int soft_set_potential(soft_plan* P, const double* U, int64_t n) {
@@ -583,8 +607,12 @@ int soft_plan::build_1d_device() {
     return SOFT_OK;
 }
 
-// soft_step on a single-instance plan: the call's field replaces the plan's
-int soft_plan::set_single_field(const soft_field* f) {
+// soft_step on a single-instance plan: the call's field replaces the plan's.
+// The descriptor and pulse-class copies are queued on the call's stream, so
+// they take effect after every step already queued there (a step still
+// waiting on a non-blocking stream keeps the field it was called with);
+// pageable sources are staged before cudaMemcpyAsync returns.
+int soft_plan::set_single_field(const soft_field* f, cudaStream_t st) {
     InstHost& ih = inst[0];
     int has = 0, fc = 0;
     double E0 = 0;
@@ -595,8 +623,8 @@ int soft_plan::set_single_field(const soft_field* f) {
         if (call_cls[0] != f->omega || call_cls[1] != Tp) {
             call_cls[0] = f->omega;
             call_cls[1] = Tp;
-            int rc = cuda_status(cudaMemcpy(d_cls + 2 * ncls, call_cls, 2 * sizeof(double),
-                                            cudaMemcpyHostToDevice));
+            int rc = cuda_status(cudaMemcpyAsync(d_cls + 2 * ncls, call_cls, 2 * sizeof(double),
+                                                 cudaMemcpyHostToDevice, st));
             if (rc) return rc;
         }
         has = 1; fc = ncls; E0 = f->E0;
@@ -605,11 +633,11 @@ int soft_plan::set_single_field(const soft_field* f) {
         ih.has_field = has; ih.fcls = fc; ih.E0 = E0;
         Inst1D d = descriptor(0);
         for (auto& g : groups) {
-            int rc = cuda_status(cudaMemcpy(g.d_inst, &d, sizeof(d), cudaMemcpyHostToDevice));
+            int rc = cuda_status(cudaMemcpyAsync(g.d_inst, &d, sizeof(d), cudaMemcpyHostToDevice, st));
             if (rc) return rc;
         }
         h_obs[0] = d;
-        int rc = cuda_status(cudaMemcpy(d_inst_obs, &d, sizeof(d), cudaMemcpyHostToDevice));
+        int rc = cuda_status(cudaMemcpyAsync(d_inst_obs, &d, sizeof(d), cudaMemcpyHostToDevice, st));
         if (rc) return rc;
     }
     return SOFT_OK;

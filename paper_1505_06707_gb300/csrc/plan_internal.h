@@ -12,6 +12,7 @@ int upload_c(void** dst, const std::vector<cd>& v, int prec);
 int upload_tab(void** dst, const std::vector<cd>& v, int prec);
 int upload_vtab(void** dst, const std::vector<cd>& v, int prec);
 int upload_tw(void** dst, const std::vector<cd>& v, int prec);
+int upload_tw_comp(void** dst, const std::vector<cd>& v, int prec);
 // rewrite an existing device buffer in place (same size and format as the
 // matching upload_*), so that pointers held by kernels and graphs stay valid
 int refill_c(void* dst, const std::vector<cd>& v, int prec);
@@ -101,7 +102,7 @@ struct soft_plan {
 
     soft::Inst1D descriptor(int i) const;
     int build_1d_device();
-    int set_single_field(const soft_field* f);
+    int set_single_field(const soft_field* f, cudaStream_t st);
     int enqueue_chunk(void* psi, int64_t chunk, cudaStream_t st);
     int step_1d(void* psi, int64_t nsteps, double* t_inout, cudaStream_t st);
 

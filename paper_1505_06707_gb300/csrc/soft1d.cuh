@@ -47,6 +47,27 @@ __device__ __forceinline__ float2 vmul(float2 x, float2 d) {
 }
 __device__ __forceinline__ double2 vmul(double2 x, double2 t) { return cmul(x, t); }
 
+// x * conj(hi + lo) for a compensated FP32 value t = (hi.re, hi.im, lo.re, lo.im)
+__device__ __forceinline__ float2 tmulc(float2 x, float4 t) {
+    const float a = x.x, b = x.y;
+    const float re = fmaf(a, t.x, fmaf(b, t.y, fmaf(a, t.z, b * t.w)));
+    const float im = fmaf(b, t.x, fmaf(-a, t.y, fmaf(b, t.z, -a * t.w)));
+    return make_float2(re, im);
+}
+
+// Pass twiddle tables.  Complex128 plans store the four bases W^{2^k off}
+// of each offset as double2.  Complex64 plans of the 1D step store each base
+// as a compensated float4 (hi + lo = the FP64 value) and apply W^{M off} as
+// one compensated multiply per set bit of M: forming the product of rounded
+// bases (or rounding any stored twiddle) leaves |w| != 1 by up to ~1e-7,
+// and since the forward and the inverse FFT apply the same twiddle to the
+// same position, that modulus error returns unchanged in every step and the
+// state drifts linearly in time.  With compensated factors the modulus is
+// exact to ~2^-48 and only the data's own roundings remain.
+template <typename R> struct TwT;
+template <> struct TwT<float> { using T = float4; };
+template <> struct TwT<double> { using T = double2; };
+
 template <typename R, int LOGN, int LOGE, int LOGRM>
 struct Cfg1D {
     using C = typename CT<R>::C;
@@ -95,25 +116,49 @@ __device__ __forceinline__ C tw_pow(const C* b) {
     }
 }
 
-// The element M of a butterfly lives at base + M s; the callers pass
-// sb = swz(base) and the offset of element M is the constant swz(M s).
-template <typename C, int RR, int SS, int M>
-struct StoreFwd {   // y_M = v[bitrev(M)] * W^{M off}, stored at base + M s
-    __device__ __forceinline__ static void run(C* S, const C* v, const C* b, int sb, bool tw) {
-        constexpr int LOGR = (RR == 16) ? 4 : (RR == 8) ? 3 : (RR == 4) ? 2 : (RR == 2) ? 1 : 0;
-        C y = v[bitrev_c(M, LOGR)];
-        if constexpr (M > 0) { if (tw) y = cmul(y, tw_pow<C, M>(b)); }
-        S[sb ^ swz<C>(M * SS)] = y;
-        if constexpr (M + 1 < RR) StoreFwd<C, RR, SS, M + 1>::run(S, v, b, sb, tw);
+// y * W^{M off} (fwd) and y * conj(W^{M off}) (inv) from the bases b[k] =
+// W^{2^k off}: plain bases (TW = C) through one product twiddle, compensated
+// FP32 bases (TW = float4) by one compensated multiply per set bit of M
+template <typename C, typename TW, int M> struct TwMul {
+    __device__ __forceinline__ static C fwd(C y, const C* b) { return cmul(y, tw_pow<C, M>(b)); }
+    __device__ __forceinline__ static C inv(C y, const C* b) { return cmulc(y, tw_pow<C, M>(b)); }
+};
+template <int M> struct TwMul<float2, float4, M> {
+    __device__ __forceinline__ static float2 fwd(float2 y, const float4* b) {
+        if constexpr ((M & 1) != 0) y = tmul(y, b[0]);
+        if constexpr ((M & 2) != 0) y = tmul(y, b[1]);
+        if constexpr ((M & 4) != 0) y = tmul(y, b[2]);
+        if constexpr ((M & 8) != 0) y = tmul(y, b[3]);
+        return y;
+    }
+    __device__ __forceinline__ static float2 inv(float2 y, const float4* b) {
+        if constexpr ((M & 1) != 0) y = tmulc(y, b[0]);
+        if constexpr ((M & 2) != 0) y = tmulc(y, b[1]);
+        if constexpr ((M & 4) != 0) y = tmulc(y, b[2]);
+        if constexpr ((M & 8) != 0) y = tmulc(y, b[3]);
+        return y;
     }
 };
-template <typename C, int RR, int SS, int M>
+
+// The element M of a butterfly lives at base + M s; the callers pass
+// sb = swz(base) and the offset of element M is the constant swz(M s).
+template <typename C, typename TW, int RR, int SS, int M>
+struct StoreFwd {   // y_M = v[bitrev(M)] * W^{M off}, stored at base + M s
+    __device__ __forceinline__ static void run(C* S, const C* v, const TW* b, int sb, bool tw) {
+        constexpr int LOGR = (RR == 16) ? 4 : (RR == 8) ? 3 : (RR == 4) ? 2 : (RR == 2) ? 1 : 0;
+        C y = v[bitrev_c(M, LOGR)];
+        if constexpr (M > 0) { if (tw) y = TwMul<C, TW, M>::fwd(y, b); }
+        S[sb ^ swz<C>(M * SS)] = y;
+        if constexpr (M + 1 < RR) StoreFwd<C, TW, RR, SS, M + 1>::run(S, v, b, sb, tw);
+    }
+};
+template <typename C, typename TW, int RR, int SS, int M>
 struct LoadInv {    // v_M = S[base + M s] * conj(W^{M off})
-    __device__ __forceinline__ static void run(const C* S, C* v, const C* b, int sb, bool tw) {
+    __device__ __forceinline__ static void run(const C* S, C* v, const TW* b, int sb, bool tw) {
         C y = S[sb ^ swz<C>(M * SS)];
-        if constexpr (M > 0) { if (tw) y = cmulc(y, tw_pow<C, M>(b)); }
+        if constexpr (M > 0) { if (tw) y = TwMul<C, TW, M>::inv(y, b); }
         v[M] = y;
-        if constexpr (M + 1 < RR) LoadInv<C, RR, SS, M + 1>::run(S, v, b, sb, tw);
+        if constexpr (M + 1 < RR) LoadInv<C, TW, RR, SS, M + 1>::run(S, v, b, sb, tw);
     }
 };
 template <typename C, int RR, int SS, int M>
@@ -141,9 +186,8 @@ struct TwCount {
 };
 
 // forward DIF pass P (radix 2^LOGR on sub-transforms of length 2^LOGL)
-template <typename R, int LOGN, int LOGE, int LOGRM, int P, bool SH = false>
-__device__ __forceinline__ void fwd_pass(typename CT<R>::C* S, const typename CT<R>::C* __restrict__ W,
-                                         int tid) {
+template <typename R, int LOGN, int LOGE, int LOGRM, int P, bool SH = false, typename TW = typename CT<R>::C>
+__device__ __forceinline__ void fwd_pass(typename CT<R>::C* S, const TW* __restrict__ W, int tid) {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
     using C = typename K::C;
     using G = PassGeom<LOGN, LOGRM, P>;
@@ -160,16 +204,15 @@ __device__ __forceinline__ void fwd_pass(typename CT<R>::C* S, const typename CT
 #pragma unroll
         for (int j = 0; j < RR; ++j) v[j] = S[sb ^ swz<C>(j * s)];
         dft_reg<C, RR, -1>(v);
-        C tb[4];
-        if constexpr (s > 1) load_tw<C, NB, s, SH>(tb, W + G::TOFF + off);
-        StoreFwd<C, RR, s, 0>::run(S, v, tb, sb, s > 1);
+        TW tb[4];
+        if constexpr (s > 1) load_tw<TW, NB, s, SH>(tb, W + G::TOFF + off);
+        StoreFwd<C, TW, RR, s, 0>::run(S, v, tb, sb, s > 1);
     }
 }
 
 // inverse DIT pass P (undoes fwd_pass P up to the factor 2^LOGR)
-template <typename R, int LOGN, int LOGE, int LOGRM, int P, bool SH = false>
-__device__ __forceinline__ void inv_pass(typename CT<R>::C* S, const typename CT<R>::C* __restrict__ W,
-                                         int tid) {
+template <typename R, int LOGN, int LOGE, int LOGRM, int P, bool SH = false, typename TW = typename CT<R>::C>
+__device__ __forceinline__ void inv_pass(typename CT<R>::C* S, const TW* __restrict__ W, int tid) {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
     using C = typename K::C;
     using G = PassGeom<LOGN, LOGRM, P>;
@@ -183,9 +226,9 @@ __device__ __forceinline__ void inv_pass(typename CT<R>::C* S, const typename CT
         const int blk = b / s, off = b & (s - 1);
         const int sb = swz<C>(blk * L + off);
         C v[RR];
-        C tb[4];
-        if constexpr (s > 1) load_tw<C, NB, s, SH>(tb, W + G::TOFF + off);
-        LoadInv<C, RR, s, 0>::run(S, v, tb, sb, s > 1);
+        TW tb[4];
+        if constexpr (s > 1) load_tw<TW, NB, s, SH>(tb, W + G::TOFF + off);
+        LoadInv<C, TW, RR, s, 0>::run(S, v, tb, sb, s > 1);
         dft_reg<C, RR, +1>(v);
         StoreNat<C, RR, s, 0>::run(S, v, sb);
     }
@@ -378,20 +421,20 @@ struct Step1D {
 template <typename R, int LOGN, int LOGE, int LOGRM>
 __host__ __device__ constexpr size_t soft1d_smem() {
     return sizeof(typename CT<R>::C) *
-               ((Cfg1D<R, LOGN, LOGE, LOGRM>::GM ? 0 : (size_t(1) << LOGN)) + TwCount<LOGN, LOGRM>::value + 64 +
-                (size_t(1) << LOGE) + 36) + 64;
+               ((Cfg1D<R, LOGN, LOGE, LOGRM>::GM ? 0 : (size_t(1) << LOGN)) + 64 + (size_t(1) << LOGE) + 36) +
+           sizeof(typename TwT<R>::T) * TwCount<LOGN, LOGRM>::value + 64;
 }
 
-template <typename R, int LOGN, int LOGE, int LOGRM, int P, int PEND>
-__device__ __forceinline__ void fwd_passes(typename CT<R>::C* S, const typename CT<R>::C* Ws, int tid) {
+template <typename R, int LOGN, int LOGE, int LOGRM, int P, int PEND, typename TW>
+__device__ __forceinline__ void fwd_passes(typename CT<R>::C* S, const TW* Ws, int tid) {
     if constexpr (P < PEND) {
         fwd_pass<R, LOGN, LOGE, LOGRM, P, true>(S, Ws, tid);
         __syncthreads();
         fwd_passes<R, LOGN, LOGE, LOGRM, P + 1, PEND>(S, Ws, tid);
     }
 }
-template <typename R, int LOGN, int LOGE, int LOGRM, int P, int PSTOP>
-__device__ __forceinline__ void inv_passes(typename CT<R>::C* S, const typename CT<R>::C* Ws, int tid) {
+template <typename R, int LOGN, int LOGE, int LOGRM, int P, int PSTOP, typename TW>
+__device__ __forceinline__ void inv_passes(typename CT<R>::C* S, const TW* Ws, int tid) {
     if constexpr (P >= PSTOP) {
         inv_pass<R, LOGN, LOGE, LOGRM, P, true>(S, Ws, tid);
         __syncthreads();
@@ -487,8 +530,8 @@ __device__ __forceinline__ void field_setup(typename CT<R>::C* fr, R al, const I
 // Inverse pass 0; with V set, followed by the potential factor of the next
 // step on every output: the full e^{-iU tau} off the strip block, the half
 // factor on it (U = U0(z) + E(t + tau/2) x, Sec. II under Eq. SSFFT).
-template <typename R, int LOGN, int LOGE, int LOGRM>
-__device__ __forceinline__ void inv_pass0_v(typename CT<R>::C* S, const typename CT<R>::C* __restrict__ Ws,
+template <typename R, int LOGN, int LOGE, int LOGRM, typename TW>
+__device__ __forceinline__ void inv_pass0_v(typename CT<R>::C* S, const TW* __restrict__ Ws,
                                             const typename VabT<R>::T* __restrict__ TV,
                                             const typename CT<R>::C* fr, R al, const Inst1D& I, int tid,
                                             bool V) {
@@ -514,9 +557,9 @@ __device__ __forceinline__ void inv_pass0_v(typename CT<R>::C* S, const typename
         const int off = tid + u * K::T;        // L = N: a single block
         const int sb = swz<C>(off);
         C v[RR];
-        C tb[4];
-        if constexpr (s > 1) load_tw<C, NB, s, true>(tb, Ws + G::TOFF + off);
-        LoadInv<C, RR, s, 0>::run(S, v, tb, sb, s > 1);
+        TW tb[4];
+        if constexpr (s > 1) load_tw<TW, NB, s, true>(tb, Ws + G::TOFF + off);
+        LoadInv<C, TW, RR, s, 0>::run(S, v, tb, sb, s > 1);
         dft_reg<C, RR, +1>(v);
         if (!V) {
             StoreNat<C, RR, s, 0>::run(S, v, sb);
@@ -573,15 +616,16 @@ soft1d_kernel(const Inst1D* __restrict__ insts, void* __restrict__ psi_base, int
     static_assert(Q::R0 <= 16, "pass radix <= 16");
     static_assert(soft1d_smem<R, LOGN, LOGE, LOGRM>() <= 227 * 1024, "shared memory");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* Ws = reinterpret_cast<C*>(smem_raw) + (K::GM ? 0 : N);   // twiddles, TWN complex
-    C* scan = Ws + Q::TWN;           // 2*32 complex
+    using TWT = typename TwT<R>::T;
+    TWT* Ws = reinterpret_cast<TWT*>(reinterpret_cast<C*>(smem_raw) + (K::GM ? 0 : N));   // twiddles, TWN bases
+    C* scan = reinterpret_cast<C*>(Ws + Q::TWN);           // 2*32 complex
     C* fr = scan + 64;               // E + 36 complex: field phases (field_setup)
 
     const Inst1D I = insts[blockIdx.x];
     C* __restrict__ g_psi = reinterpret_cast<C*>(psi_base) + I.off;
     // the state: shared memory, or (GM) the instance's buffer itself
     C* S = K::GM ? g_psi : reinterpret_cast<C*>(smem_raw);
-    const C* __restrict__ W = reinterpret_cast<const C*>(I.W);
+    const TWT* __restrict__ W = reinterpret_cast<const TWT*>(I.W);
     using TT = typename K::TT;
     const TT* __restrict__ TK = reinterpret_cast<const TT*>(I.TK);
     const TT* __restrict__ TKh = reinterpret_cast<const TT*>(I.TKh);

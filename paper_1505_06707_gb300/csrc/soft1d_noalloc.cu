@@ -60,6 +60,18 @@ int scratch_address(NoallocScratch** out) {
     return SOFT_OK;
 }
 
+// Writes this call's descriptor and pulse class into the scratch and clears
+// its status word.  The values travel as kernel arguments, so no host buffer
+// has to outlive the call.
+__global__ void noalloc_setup_kernel(NoallocScratch* sc, soft::Inst1D desc, double omega, double Tp) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        sc->desc = desc;
+        sc->cls[0] = omega;
+        sc->cls[1] = Tp;
+        sc->status = 0;
+    }
+}
+
 }  // namespace
 
 extern "C" int soft_step_noalloc(const soft_plan* P, void* psi, int64_t nsteps,
@@ -85,12 +97,8 @@ extern "C" int soft_step_noalloc(const soft_plan* P, void* psi, int64_t nsteps,
         d.has_field = 1;
         d.E0 = field->E0;
     }
-    // pageable source: the copy is staged before cudaMemcpyAsync returns
-    if ((rc = soft::cuda_status(cudaMemcpyAsync(&sc->desc, &d, sizeof(d), cudaMemcpyHostToDevice, st))))
-        return rc;
-    if ((rc = soft::cuda_status(cudaMemcpyAsync(sc->cls, cls, sizeof(cls), cudaMemcpyHostToDevice, st))))
-        return rc;
-    if ((rc = soft::cuda_status(cudaMemsetAsync(&sc->status, 0, sizeof(int), st)))) return rc;
+    noalloc_setup_kernel<<<1, 32, 0, st>>>(sc, d, cls[0], cls[1]);
+    if ((rc = soft::cuda_status(cudaGetLastError()))) return rc;
     if (d.has_field) {
         rc = soft::launch_field_table(sc->cls, 1, *t_inout, P->dt, nsteps, sc->pulse,
                                       NOALLOC_MAX_STEPS, st);

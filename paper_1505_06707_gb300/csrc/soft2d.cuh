@@ -41,7 +41,7 @@ __device__ __forceinline__ void inv_pass0_post(typename CT<R>::C* S, const typen
         C v[RR];
         C tb[4];
         if constexpr (s > 1) load_tw<C, NB, s, false>(tb, W + G::TOFF + off);
-        LoadInv<C, RR, s, 0>::run(S, v, tb, sb, s > 1);
+        LoadInv<C, C, RR, s, 0>::run(S, v, tb, sb, s > 1);
         dft_reg<C, RR, +1>(v);
 #pragma unroll
         for (int m = 0; m < RR; ++m) S[sb ^ swz<C>(m * s)] = post(off + m * s, v[bitrev_c(m, LOGR)]);

@@ -75,8 +75,12 @@ cd ContourFn::z(double x) const {
     switch (kind) {
     case SOFT_CONTOUR_SHARP: return sg * (R0 + std::polar(1.0, theta) * d);
     case SOFT_CONTOUR_SECS: {
-        const cd c(0.0, theta / (rmax - R0));
-        return sg * (R0 + (std::exp(c * d) - 1.0) / c);
+        // (W/(i theta)) (e^{i phi} - 1) with phi = theta d/W, written as
+        // d sinc(phi/2) e^{i phi/2}: no cancellation for small theta, and
+        // theta = 0 gives the unscaled z = x
+        const double ph = theta * d / (rmax - R0);
+        const double sinc = ph == 0.0 ? 1.0 : std::sin(0.5 * ph) / (0.5 * ph);
+        return sg * (R0 + d * sinc * std::polar(1.0, 0.5 * ph));
     }
     case SOFT_CONTOUR_TFECS: {
         // q grows like 1/(1-s) towards s = 1; with s = 1 - e^{-u} the

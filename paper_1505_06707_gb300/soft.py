@@ -14,7 +14,8 @@ __all__ = [
     "SoftError", "SOFT_C64", "SOFT_C128", "CONTOUR_SHARP", "CONTOUR_SECS", "CONTOUR_TFECS",
     "ABSORB_CAP", "ABSORB_TFAP",
     "load", "lib_path", "exported_symbols", "Options", "Field", "soft_create", "soft_create_batch",
-    "soft_batch_layout", "soft_step", "soft_step_batch", "soft_step_noalloc", "soft_observe",
+    "soft_batch_layout", "soft_step", "soft_step_batch", "soft_step_noalloc", "soft_step_status",
+    "soft_observe",
     "soft_set_potential", "sse_pcg_solve",
     "sse_apply_A", "sse_apply_A32", "sse_apply_precond", "soft_destroy", "sse_nn_set_weights", "sse_nn_get_weights",
     "sse_nn_forward", "sse_nn_grad", "sse_nn_train", "NN_PARAMS", "soft_plan_points", "soft_plan_count",
@@ -35,7 +36,7 @@ exported_symbols = [
     "soft_default_options", "soft_create", "soft_create_batch", "soft_batch_layout", "soft_step",
     "soft_step_batch", "soft_observe", "soft_set_potential", "sse_pcg_solve", "sse_apply_A", "sse_apply_A32",
     "sse_apply_precond", "soft_destroy", "soft_strerror", "soft_plan_count", "soft_plan_points", "soft_plan_prec",
-    "soft_last_launches", "soft_step_noalloc", "sse_nn_set_weights", "sse_nn_get_weights",
+    "soft_last_launches", "soft_step_noalloc", "soft_step_status", "sse_nn_set_weights", "sse_nn_get_weights",
     "sse_nn_forward", "sse_nn_grad", "sse_nn_train",
 ]
 
@@ -87,6 +88,7 @@ def load():
     L.soft_step.argtypes = [P, P, i64, C.POINTER(Field), C.POINTER(dbl), P]
     L.soft_step_batch.argtypes = [P, P, i64, C.POINTER(dbl), P]
     L.soft_step_noalloc.argtypes = [P, P, i64, C.POINTER(Field), C.POINTER(dbl), P]
+    L.soft_step_status.argtypes = [P, P]
     L.soft_observe.argtypes = [P, P, P, P, P]
     L.soft_set_potential.argtypes = [P, P, i64]
     L.sse_pcg_solve.argtypes = [P, C.POINTER(dbl), C.c_int, P, P, dbl, C.c_int, C.c_int,
@@ -227,6 +229,12 @@ def soft_step_batch(plan, psi, nsteps, t, stream=None):
     _check(load().soft_step_batch(plan, _ptr(psi), int(nsteps), C.byref(tt), _stream(stream)),
            "soft_step_batch")
     return tt.value
+
+
+def soft_step_status(plan, stream=None):
+    """Wait for the stream; raise SoftError(NONFINITE) if a step of this 1D
+    plan has produced a non-finite state since the last query."""
+    _check(load().soft_step_status(plan, _stream(stream)), "soft_step_status")
 
 
 def soft_observe(plan, psi, norm_in, flux, stream=None):

@@ -353,3 +353,68 @@ def test_w2_full_batch_sampled(prec):
                         fields=[(w["E0"], w["omega"], w["ncyc"]) for w in sw])
     for i, w, r in zip(sample, sw, refs):
         assert relerr(got[i], r) < tol(prec, nst, w["n"]), (i, w["n"])
+
+
+def test_nonfinite_state_reported_by_status_query():
+    """A NaN in the input state reaches the instance's first element through
+    the FFT; soft_step_status reports it once (then the flag is clear), and a
+    finite run reports nothing."""
+    n, a, b, R0 = 1024, -50.0, 50.0, 40.0
+    x = a + (b - a) / n * (np.arange(n) + 0.5)
+    psi0 = np.exp(-x ** 2 / 8.0 + 0.5j * x)
+    for prec in (S.SOFT_C128, S.SOFT_C64):
+        plan = S.soft_create(n, (a, b), R0, 0.5, 0.05, prec=prec)
+        try:
+            d = torch.tensor(psi0, dtype=CT[prec], device="cuda")
+            S.soft_step(plan, d, 5, 0.0)
+            S.soft_step_status(plan)                 # finite: no error
+            bad = psi0.copy()
+            bad[700] = np.nan
+            d = torch.tensor(bad, dtype=CT[prec], device="cuda")
+            S.soft_step(plan, d, 3, 0.0)
+            with pytest.raises(S.SoftError) as e:
+                S.soft_step_status(plan)
+            assert e.value.status == -8
+            S.soft_step_status(plan)                 # cleared by the query
+        finally:
+            S.soft_destroy(plan)
+
+
+def test_field_change_between_calls_on_a_side_stream():
+    """Two calls on a non-blocking stream, queued back to back with different
+    fields and no synchronisation between them: each call must run with its
+    own field (the descriptor update is ordered on the stream)."""
+    w = W.w2_instance(3)
+    n = w["n"]
+    f1 = (w["E0"], w["omega"], w["ncyc"])
+    f2 = (0.5 * w["E0"], 1.5 * w["omega"], 2.0)
+    prob = P.Problem1D(n, w["a"], w["b"], w["R0"], theta=w["theta"], kind=w["contour"],
+                       a2=w["a2"], dt=w["dt"])
+    ref = prob.step(w["psi0"], 200, t0=5.0, field=f1)
+    ref = prob.step(ref, 40, t0=5.0 + 200 * w["dt"], field=f2)
+    plan = S.soft_create(n, (w["a"], w["b"]), w["R0"], w["theta"], w["dt"], prec=S.SOFT_C128,
+                         contour=w["contour"], soft_a2=w["a2"])
+    try:
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            d = torch.tensor(w["psi0"], dtype=torch.complex128, device="cuda")
+        t = S.soft_step(plan, d, 200, 5.0, field=f1, stream=st)
+        t = S.soft_step(plan, d, 40, t, field=f2, stream=st)
+        st.synchronize()
+        got = d.cpu().numpy()
+    finally:
+        S.soft_destroy(plan)
+    assert relerr(got, ref) < 1e-11
+
+
+@pytest.mark.parametrize("prec", [S.SOFT_C128, S.SOFT_C64])
+def test_secs_zero_angle_reduces_to_the_unscaled_step(prec):
+    """The SECS contour at theta = 0 is q = 1 (no strip): the GPU step must
+    match the oracle's unscaled step (the plan tables take the theta -> 0
+    limit of the SECS z(x))."""
+    n, a, b, R0 = 1024, -50.0, 50.0, 40.0
+    x = a + (b - a) / n * (np.arange(n) + 0.5)
+    psi0 = np.exp(-(x + 5.0) ** 2 / 6.0 + 0.9j * x)
+    ref = P.Problem1D(n, a, b, R0, theta=0.0, kind=T.SHARP, a2=2.0, dt=0.02).step(psi0, 100)
+    got = gpu_run(n, (a, b), R0, 0.0, 0.02, psi0, 100, prec=prec, contour=S.CONTOUR_SECS)
+    assert relerr(got, ref) < (1e-12 if prec == S.SOFT_C128 else 2e-6)
