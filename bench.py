@@ -1,14 +1,18 @@
 """Benchmark: the batched 1D laser workload of the ECS split-operator method.
 
 Workload: 4096 independent 1D instances, N drawn from {2048, 4096, 8192,
-16384}, box [-8N/1024, 8N/1024] (h = 1/64), sharp ECS at 75% of the
-half-width (theta = 0.5), soft-Coulomb a^2 = 2, laser pulse E0 sin^2 sin with
-omega = 0.057, 4 cycles, E0 ~ U[0.01, 0.1]; dt = 0.02.  One benchmark step
-advances every instance by STEPS_PER_CALL time steps in one library call.
+16384}, box [-8N/1024, 8N/1024] (h = 1/64), smooth (SECS) ECS from 75% of
+the half-width to theta = 0.5 at the edge, soft-Coulomb a^2 = 2, laser pulse
+E0 sin^2 sin with omega = 0.057, 4 cycles, E0 ~ U[0.01, 0.1]; dt = 0.02.
+One benchmark step advances every instance by STEPS_PER_CALL time steps in
+one library call (one persistent kernel over all instances).
+
+The headline line is complex128 (FP64 arithmetic, the oracle's precision);
+complex64 is reported beside it with its error after the whole pulse.
 
 Metric: grid-point-steps per second = sum_j N_j * time steps / seconds.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec c64|c128]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec c128|c64]
   python bench.py --impl reference      # the FP64 CPU oracle on a sample
 
 One JSON line is printed by rank 0."""
@@ -30,6 +34,7 @@ METRIC = "ECS SO-FFT grid-point-steps/s"
 UNIT = "grid-point-steps/s"
 N_INST = 4096
 STEPS_PER_CALL = 256
+W2_DT = 0.02
 L2_BYTES = 129 * 1024 * 1024
 
 
@@ -179,7 +184,7 @@ def workload(count=N_INST):
     return [W.w2_instance(j) for j in range(count)]
 
 
-def config(prec, instances=N_INST, spc=STEPS_PER_CALL):
+def config(prec="c128", instances=N_INST, spc=STEPS_PER_CALL):
     return {"workload": "1D ECS SO-FFT laser batch: %d instances, N in {2048..16384}, h=1/64, "
                         "smooth (SECS) ECS from R0=0.75 half-width to theta=0.5 at the edge, soft-Coulomb a2=2, "
                         "pulse omega=0.057 4 cycles, dt=0.02" % instances,
@@ -527,21 +532,158 @@ def bench_learned(S, torch, dev, args):
     return res
 
 
+def bench_pcg1d(S, torch, dev, args):
+    """The paper's own stationary test (Sec. IV, closing remarks) on the GPU:
+    N = 1024, b = -a = 51.2, r_s = 40, tau = h^2; the packet propagated to
+    t_max = 20 by the GPU step is the right-hand side of 30 solves,
+    E = k^2/2 for k = 0.2 .. 6, by COCG with the banded preconditioner
+    (N_l = 10) to 1e-12, for the three absorbers of that test."""
+    import numpy as np
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_test_setup.json")))
+    n, rmax, rs, v0 = g["N"], g["rmax"], g["r_s"], g["v0"]
+    Es = [0.5 * (0.2 * k) ** 2 for k in range(1, 31)]
+    h = 2 * rmax / n
+    tau = h * h
+    x = -rmax + h * (np.arange(n) + 0.5)
+    psi0 = math.pi ** -0.25 * np.exp(-x ** 2 / 2 + 1j * v0 * x)
+    st = torch.cuda.current_stream(dev)
+    res = {}
+    for name, kind in (("secs", S.CONTOUR_SECS), ("tfecs", S.CONTOUR_TFECS), ("tfap", S.ABSORB_TFAP)):
+        plan = S.soft_create(n, (-rmax, rmax), rs, math.pi / 4, tau, prec=S.SOFT_C128, contour=kind,
+                             charge=0.0, tfecs_alpha=g["tfecs_alpha"], cap_energy=g["cap_energy"],
+                             tfap_kmin=g["tfap_kmin"])
+        d = torch.tensor(psi0, dtype=torch.complex128, device=dev)
+        S.soft_step(plan, d, int(round(g["t_max"] / tau)), 0.0, stream=st)
+        out = torch.zeros((len(Es), n), dtype=torch.complex128, device=dev)
+        S.sse_pcg_solve(plan, Es, d, out, tol=g["pcg_tolerance"], maxit=2000, precond=1, stream=st)   # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        rc, its, rr = S.sse_pcg_solve(plan, Es, d, out, tol=g["pcg_tolerance"], maxit=2000, precond=1, stream=st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        res[name] = {"status": rc, "iterations_mean": float(np.mean(its)), "iterations_max": int(max(its)),
+                     "seconds": sec, "solves_per_s": len(Es) / sec, "max_relres": float(max(rr)),
+                     "paper_iterations": g["claims"]["pcg_iterations_" + name]}
+        S.soft_destroy(plan)
+    res["setup"] = ("N = 1024, [-51.2, 51.2], r_s = 40, 30 energies k = 0.2 .. 6, banded preconditioner "
+                    "N_l = 10, tolerance 1e-12, one launch for all energies (one CTA per energy)")
+    return res
+
+
+def measure_w2(S, torch, dev, args, prec_name, steps, warmup, world=1, with_e2e=True, persistent=1):
+    """The laser batch through one batch plan: the persistent kernel over all
+    4096 instances (one graph per call: pulse table, queue reset, the
+    kernel, time advance).  Device-timed region of `steps` calls, the graph
+    call timed alone for the roofline, and the end-to-end rate with host
+    copies of the whole packed state every call."""
+    import numpy as np
+    prec = S.SOFT_C64 if prec_name == "c64" else S.SOFT_C128
+    cdt_np = np.complex64 if prec == S.SOFT_C64 else np.complex128
+    spc = args.steps_per_call
+    ws = workload(args.instances)
+    plan = S.soft_create_batch([w["n"] for w in ws], [(w["a"], w["b"]) for w in ws],
+                               [w["R0"] for w in ws], [w["theta"] for w in ws],
+                               [(w["E0"], w["omega"], w["ncyc"]) for w in ws], W2_DT,
+                               prec=prec, contour=ws[0]["contour"], persistent=persistent, autotune=1)
+    offs, total = S.soft_batch_layout(plan)
+    h0 = np.concatenate([w["psi0"] for w in ws]).astype(cdt_np)
+    state = torch.from_numpy(h0).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    ns = [w["n"] for w in ws]
+    pts_call = float(sum(ns)) * spc
+    nbs = [n // 4 + 2 for n in ns]           # strip block: 2 x N/8 strip rows + 2 coupled neighbours
+    flops_call = flops_per_call(ns, nbs, spc)
+    t = 0.0
+    for _ in range(warmup):
+        t = S.soft_step_batch(plan, state, spc, t, stream=stream)
+    torch.cuda.synchronize()
+    launches = S.soft_last_launches(plan)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(dev.index or 0)
+    clk.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(steps):
+        ev[k][0].record(stream)
+        t = S.soft_step_batch(plan, state, spc, t, stream=stream)
+        ev[k][1].record(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    kms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    out = {"value": whole_job_value(pts_call, steps, world, ms), "ms_per_step": ms / steps,
+           "call_ms": kms, "flops_per_call": flops_call, "gpu_launches": int(launches * steps),
+           "clocks": clocks, "points": int(total), "instances": len(ws)}
+    if with_e2e:
+        hb = torch.from_numpy(h0).pin_memory()
+        ob = torch.empty_like(hb).pin_memory()
+
+        def e2e_call(tt):
+            state.copy_(hb, non_blocking=True)
+            tt = S.soft_step_batch(plan, state, spc, tt, stream=stream)
+            ob.copy_(state, non_blocking=True)
+            return tt
+        t = e2e_call(t)
+        torch.cuda.synchronize()
+        ke = max(3, steps // 2)
+        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_.record(stream)
+        for _ in range(ke):
+            t = e2e_call(t)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        out["e2e"] = {"value": pts_call * ke * world / (a_.elapsed_time(b_) / 1e3), "unit": UNIT,
+                      "h2d_bytes_per_step": int(h0.nbytes), "d2h_bytes_per_step": int(h0.nbytes)}
+    S.soft_destroy(plan)
+    del state
+    return out
+
+
+def roofline_w2(torch, dev, m, prec_name):
+    """The persistent kernel (one launch per call) against the ALU peak of
+    its precision: algorithmic FLOPs of the call over the call's duration."""
+    ap_ = alu_peaks(torch, dev.index or 0)
+    c64 = prec_name == "c64"
+    peak = ap_["fp32_tflops"] if c64 else ap_["fp64_tflops"]
+    achieved = m["flops_per_call"] / (m["call_ms"] / 1e3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None,
+            "kernel": "soft1d_persist_kernel, all %d instances, %d steps per launch, %.3f ms per call "
+                      "(graph: pulse table, queue reset, the kernel, time advance)"
+                      % (m["instances"], STEPS_PER_CALL, m["call_ms"]),
+            "peak_source": "derived: %d SMs x %d %s FMA per clock x 2 x %.0f MHz" % (
+                ap_["sms"], FP32_FMA_PER_SM_CLK if c64 else FP64_FMA_PER_SM_CLK, "FP32" if c64 else "FP64",
+                ap_["sm_max_mhz"]),
+            "flop_count": "per time step and instance 10 N log2 N (two FFTs) + 12 N (phase products) + "
+                          "6 N (field) + 32 per strip row"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--prec", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--prec", default="c128", choices=["c64", "c128"],
+                    help="precision of the headline line (the other is reported beside it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--instances", type=int, default=N_INST,
                     help="fewer instances for profiling captures (not a bench line)")
     ap.add_argument("--steps-per-call", type=int, default=STEPS_PER_CALL)
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the 2D step and stationary-solver measurements")
-    ap.add_argument("--only", choices=["2d", "pcg", "learned", "conv", "accuracy", "peaks"], default=None,
-                    help="run one of the extra measurements alone (for profiling captures; not a bench line)")
+                    help="skip the other precision, the 2D step and the stationary-solver measurements")
+    ap.add_argument("--only", choices=["2d", "pcg", "learned", "conv", "accuracy", "peaks", "w2", "pcg1d"],
+                    default=None,
+                    help="run one measurement alone (for profiling captures; not a bench line)")
+    ap.add_argument("--persistent", type=int, default=1, choices=[0, 1],
+                    help="0: one kernel per size group instead of the persistent kernel (comparison)")
     ap.add_argument("--pcg-precond", default="1,4,5",
                     help="stationary-solver modes to time (sse_pcg_solve precond values)")
     ap.add_argument("--pcg-energies", type=int, default=0,
@@ -558,13 +700,17 @@ def main():
             r = bench_accuracy(S, torch, dev, args, sizes=(2048, 4096, 8192, 16384))
         elif args.only == "peaks":
             r = {"derived": alu_peaks(torch, 0), "probe": alu_probe()}
+        elif args.only == "w2":
+            r = measure_w2(S, torch, dev, args, args.prec, args.steps, args.warmup, with_e2e=False,
+                           persistent=args.persistent)
+            r["roofline"] = roofline_w2(torch, dev, r, args.prec)
         else:
-            fn = {"2d": bench_2d, "pcg": bench_pcg, "learned": bench_learned, "conv": bench_conv}[args.only]
+            fn = {"2d": bench_2d, "pcg": bench_pcg, "learned": bench_learned, "conv": bench_conv,
+                  "pcg1d": bench_pcg1d}[args.only]
             r = fn(S, torch, dev, args)
         print(json.dumps({"only": args.only, "result": r}))
         return
 
-    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -577,156 +723,37 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    prec = S.SOFT_C64 if args.prec == "c64" else S.SOFT_C128
-    cdt = torch.complex64 if prec == S.SOFT_C64 else torch.complex128
 
-    # weak scaling: every rank runs its own 4096-instance batch (independent problems).
-    # One plan per size group, so that the dominant kernel (N = 16384) is timed
-    # on its own with CUDA events inside the timed region.
-    spc = args.steps_per_call
-    ws = workload(args.instances)
-    groups = {}
-    for w in ws:
-        groups.setdefault(w["n"], []).append(w)
-    sizes = sorted(groups, reverse=True)
-    plans, states, hosts, flops_g, nbs_all = [], [], [], [], []
-    cdt_np = np.complex64 if prec == S.SOFT_C64 else np.complex128
-    for n in sizes:
-        g = groups[n]
-        plans.append(S.soft_create_batch([w["n"] for w in g], [(w["a"], w["b"]) for w in g],
-                                         [w["R0"] for w in g], [w["theta"] for w in g],
-                                         [(w["E0"], w["omega"], w["ncyc"]) for w in g], 0.02,
-                                         prec=prec, contour=g[0]["contour"], autotune=1))
-        h0 = np.concatenate([w["psi0"] for w in g]).astype(cdt_np)
-        hosts.append(h0)
-        states.append(torch.from_numpy(h0).to(dev))
-        nb = [n // 4 + 2] * len(g)       # strip block: 2 x N/8 strip rows + 2 coupled neighbours
-        flops_g.append(flops_per_call([n] * len(g), nb, spc))
-    ns = [w["n"] for w in ws]
-    pts_call = float(sum(ns)) * spc
-    stream = torch.cuda.current_stream(dev)
-
-    # the size groups run on parallel streams (independent problems); the
-    # dominant group's kernel is bracketed by events on its own stream
-    side = [torch.cuda.Stream(dev) for _ in plans]
-
-    def one_call(t, evs=None):
-        t2 = t
-        fork = torch.cuda.Event()
-        fork.record(stream)
-        joins = []
-        for i, (pl, st_, ss) in enumerate(zip(plans, states, side)):
-            ss.wait_event(fork)
-            if evs is not None and i == 0:
-                evs[0].record(ss)
-            t2 = S.soft_step_batch(pl, st_, spc, t, stream=ss)
-            if evs is not None and i == 0:
-                evs[1].record(ss)
-            j = torch.cuda.Event()
-            j.record(ss)
-            joins.append(j)
-        for j in joins:
-            stream.wait_event(j)
-        return t2
-
-    t = 0.0
-    for _ in range(args.warmup):
-        t = one_call(t)
-    torch.cuda.synchronize()
-    launches_per_call = sum(S.soft_last_launches(pl) for pl in plans)
-
-    # device-timed region: states resident in HBM (252 MB c64 > L2)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clk = ClockSampler(local)
-    clk.start()
-    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for k in range(args.steps):
-        t = one_call(t, kev[k])
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    clocks = clk.stop()
-    ms = ev0.elapsed_time(ev1)
-    kms = sum(a.elapsed_time(b) for a, b in kev) / args.steps
-    ms = max_over_ranks(ms, world, dev)
-    if world > 1:
-        dist.barrier()
-    sec = ms / 1e3
-    value = whole_job_value(pts_call, args.steps, world, ms)
-    # roofline of the dominant kernel: its size group alone on one stream,
-    # timed with events around each launch (the shared timed region above
-    # overlaps the groups, which would inflate its duration)
-    dk = []
-    t1 = 0.0
-    for k in range(args.steps):
-        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a_.record(stream)
-        t1 = S.soft_step_batch(plans[0], states[0], spc, t1, stream=stream)
-        b_.record(stream)
-        dk.append((a_, b_))
-    torch.cuda.synchronize()
-    kms = sum(a_.elapsed_time(b_) for a_, b_ in dk) / args.steps
-    achieved = flops_g[0] / (kms / 1e3) / 1e12
-
-    # end to end through the public calls with host buffers: H2D of every
-    # state, the calls, D2H of every state, each step
-    hb = [torch.from_numpy(h).pin_memory() for h in hosts]
-    ob = [torch.empty_like(h) .pin_memory() for h in hb]
-
-    def e2e_call():
-        for h, st_ in zip(hb, states):
-            st_.copy_(h, non_blocking=True)
-        one_call(0.0)
-        for o, st_ in zip(ob, states):
-            o.copy_(st_, non_blocking=True)
-    for _ in range(2):
-        e2e_call()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ke = max(3, args.steps // 2)
-    e0.record(stream)
-    for _ in range(ke):
-        e2e_call()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e = pts_call * ke * world / (e0.elapsed_time(e1) / 1e3)
-    nbytes = sum(h.nbytes for h in hosts)
-    for pl in plans:
-        S.soft_destroy(pl)
-    del states
-
+    # weak scaling: every rank runs its own 4096-instance batch (independent problems)
+    m = measure_w2(S, torch, dev, args, args.prec, args.steps, args.warmup, world, persistent=args.persistent)
     peaks, src = _peaks()
     hbm = _hbm_peak(peaks)
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": args.prec.replace("c64", "c64 (f32)")
-           .replace("c128", "c128 (f64)"), "data": "synthetic", "config": config(args.prec, args.instances, spc)}
-    ap_ = alu_peaks(torch, local)
-    peak = ap_["fp32_tflops"] if prec == S.SOFT_C64 else ap_["fp64_tflops"]
-    out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                       "frac": achieved / peak,
-                       "traffic": _traffic(args.prec, sizes[0], len(groups[sizes[0]]), spc),
-                       "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
-                       "kernel": "soft1d_kernel, N = %d group (%d instances, %d steps per launch), "
-                                 "%.3f ms per launch, timed alone" % (sizes[0], len(groups[sizes[0]]), spc, kms),
-                       "peak_source": "derived: %d SMs x %d %s FMA per clock x 2 x %.0f MHz" % (
-                           ap_["sms"], FP32_FMA_PER_SM_CLK if prec == S.SOFT_C64 else FP64_FMA_PER_SM_CLK,
-                           "FP32" if prec == S.SOFT_C64 else "FP64", ap_["sm_max_mhz"])}
-    # the same throughput against HBM, counting one read + one write of the state per time step
-    bytes_pt = 16 if prec == S.SOFT_C64 else 32
-    out["hbm_effective"] = {"GBps": value / world * bytes_pt / 1e9, "peak": hbm,
-                            "frac": value / world * bytes_pt / 1e9 / hbm,
+    dname = {"c64": "c64 (f32)", "c128": "c128 (f64)"}
+    out = {"metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": dname[args.prec], "data": "synthetic",
+           "config": config(args.prec, args.instances, args.steps_per_call)}
+    out["roofline"] = roofline_w2(torch, dev, m, args.prec)
+    bytes_pt = 16 if args.prec == "c64" else 32
+    out["hbm_effective"] = {"GBps": m["value"] / world * bytes_pt / 1e9, "peak": hbm,
+                            "frac": m["value"] / world * bytes_pt / 1e9 / hbm,
                             "peak_source": src, "note": "state stays in shared memory for a whole "
                             "call; this is the rate a one-pass-per-step design would need"}
-    out["e2e"] = {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
-    out["gpu_launches"] = int(launches_per_call * args.steps)
-    out["clocks"] = clocks
+    out["e2e"] = m["e2e"]
+    out["gpu_launches"] = m["gpu_launches"]
+    out["clocks"] = m["clocks"]
     if not args.no_extra:
-        out["fp32_accuracy"] = bench_accuracy(S, torch, dev, args)
+        other = "c64" if args.prec == "c128" else "c128"
+        o_steps = args.steps if other == "c64" else min(args.steps, 5)
+        mo = measure_w2(S, torch, dev, args, other, o_steps, min(args.warmup, 3), world)
+        mo["roofline"] = roofline_w2(torch, dev, mo, other)
+        mo["dtype"] = dname[other]
+        if other == "c64":
+            g = measure_w2(S, torch, dev, args, "c64", o_steps, 2, world, with_e2e=False, persistent=0)
+            mo["group_kernels_ms_per_step"] = g["ms_per_step"]
+        out[other] = mo
+        out["fp32_accuracy"] = bench_accuracy(S, torch, dev, args, sizes=(2048, 4096, 8192, 16384))
+        out["pcg1d_paper_test"] = bench_pcg1d(S, torch, dev, args)
         out["w3_2d"] = bench_2d(S, torch, dev, args)
         out["w4_pcg"] = bench_pcg(S, torch, dev, args)
         out["w5_learned"] = bench_learned(S, torch, dev, args)

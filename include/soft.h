@@ -97,6 +97,12 @@ typedef struct {
                             at plan creation and keep the fastest [0]       */
     double cap_energy;   /* E_CAP of the linear CAP [2.0]                    */
     double tfap_kmin;    /* k_min of TFAP [0.25]                             */
+    int persistent;      /* batch plans: 1 advances the instances with
+                            N = 2048 .. 16384 by one persistent kernel that
+                            takes packs of same-size instances from a queue,
+                            largest N first; 0 launches one kernel per size
+                            group.  With autotune the plan times both on one
+                            16-step chunk and keeps the faster [1]           */
 } soft_options;
 
 /* Laser pulse (length gauge, x-polarised), E(t) = E0 sin^2(pi t/T) sin(omega t)
@@ -154,9 +160,11 @@ int soft_step(soft_plan* plan, void* psi, int64_t nsteps, const soft_field* fiel
 
 /* soft_step_batch -- soft_step for a batch plan; psi is the packed state.
  * Calls are replayed from a CUDA graph (captured on the first call with a
- * given state pointer, stream and step count): the pulse-shape table and one
- * kernel per size group, the groups on parallel branches so that their CTAs
- * share the GPU. */
+ * given state pointer, stream and step count): the pulse-shape table, the
+ * persistent kernel over the instances with N = 2048 .. 16384 (one CTA per
+ * SM; 1, 2, 2, 4 instances of N = 16384, 8192, 4096, 2048 per work item
+ * for complex64, 1, 1, 2, 2 for complex128) and one kernel per remaining
+ * size group, on parallel branches so that their CTAs share the GPU. */
 int soft_step_batch(soft_plan* plan, void* psi, int64_t nsteps, double* t_inout,
                     void* stream);
 
@@ -199,6 +207,9 @@ int soft_set_potential(soft_plan* plan, const double* U_re_im, int64_t n);
 /* sse_pcg_solve -- solve A psi_e = f for nE energies E[e] by complex-symmetric
  * CG (Sec. III: the unconjugated form r^T z replaces the inner product),
  * x0 = 0, stopping when ||r||_2 / ||f||_2 < tol (Hermitian norms, FP64).
+ * 1D plans (single instance, N = 256 .. 2048, complex128) take precond 0
+ * and 1: one CTA per energy runs the whole iteration with its vectors in
+ * shared memory (one launch for all energies); 2D plans take every mode.
  *   E        host double[nE].
  *   rhs      device, one right-hand side f shared by all energies.
  *   psi_out  device, nE consecutive solutions.
@@ -242,7 +253,8 @@ int sse_pcg_solve(soft_plan* plan, const double* E, int nE, const void* rhs, voi
 
 /* sse_apply_A / sse_apply_A32 / sse_apply_precond -- one application of A
  * (Sec. III under Eq. linsys) or of the chosen preconditioner, for one
- * energy, device in and out (x and y must not alias).  sse_apply_A32
+ * energy, device in and out (x and y must not alias); 1D plans take
+ * sse_apply_A and precond 0 and 1 (SOFT_ERR_UNSUPPORTED otherwise).  sse_apply_A32
  * computes A in FP32 on complex64 x and y, as precond 5 does inside its
  * iteration; the others take complex128.  Exposed for testing and for
  * callers that run their own Krylov method; precond 0, 1 or 4 (as in

@@ -174,10 +174,12 @@ int orc_step1d(int n, long nsteps, cplx *psi, const double *k, const cplx *U0,
     cplx *work = (cplx *)malloc(sizeof(cplx) * 16 * n);
     cplx *vh = (cplx *)malloc(sizeof(cplx) * n);
     if (!work || !vh) { free(work); free(vh); return -2; }
-    double t = t0;
     int rc = 0;
     for (long s = 0; s < nsteps && rc == 0; ++s) {
-        double Ef = has_field ? pulse(t + 0.5 * tau, E0, omega, ncyc) : 0.0;
+        /* step s starts at t0 + s tau; its potential is taken at the midpoint
+         * (computed directly: a running sum t += tau would drift by ~1e-10
+         * over 1e4 steps) */
+        double Ef = has_field ? pulse(t0 + ((double)s + 0.5) * tau, E0, omega, ncyc) : 0.0;
         for (int i = 0; i < n; ++i) {
             cplx U = U0[i] + Ef * xc[i];
             vh[i] = cexp(-I * U * tau * 0.5);
@@ -187,7 +189,6 @@ int orc_step1d(int n, long nsteps, cplx *psi, const double *k, const cplx *U0,
         rc = cn_apply(n, Cs, Cd, Cu, tau, psi, work);
         for (int i = 0; i < n; ++i) psi[i] *= vh[i];
         kinetic_half(psi, n, k, tau);
-        t += tau;
     }
     free(work); free(vh);
     return rc;

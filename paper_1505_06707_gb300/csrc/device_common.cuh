@@ -7,6 +7,19 @@
 
 namespace soft {
 
+// Barrier of the threads that own one transform: the whole CTA
+// (__syncthreads), or one warp-aligned group of a CTA that runs several
+// transforms side by side (named barrier `id`, `n` threads).
+struct BarCTA {
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+struct BarGroup {
+    int id, n;
+    __device__ __forceinline__ void sync() const {
+        asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+    }
+};
+
 template <typename R> struct CT;
 template <> struct CT<float> { using C = float2; };
 template <> struct CT<double> { using C = double2; };
@@ -143,9 +156,12 @@ __device__ __forceinline__ void dft_reg(C* v) {
 // order (REV = false: thread 0 first; REV = true: thread T-1 first).  Returns,
 // for each thread, the value produced by all preceding maps applied to 0, i.e.
 // the carry that enters this thread's chunk.  scratch: 2 * (T/32) complex.
-template <typename C, int T, bool REV>
-__device__ __forceinline__ C affine_carry(C M, C Y, C* scratch) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// tid is the thread's index in the group of T threads (warp-aligned) that
+// runs the scan, bar that group's barrier.
+template <typename C, int T, bool REV, class B = BarCTA>
+__device__ __forceinline__ C affine_carry(C M, C Y, C* scratch, int tid = -1, B bar = B()) {
+    if (tid < 0) tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
     constexpr int NW = T / 32;
     // inclusive warp scan
 #pragma unroll
@@ -184,7 +200,7 @@ __device__ __forceinline__ C affine_carry(C M, C Y, C* scratch) {
     } else {
         const int tail = REV ? 0 : 31;
         if (lane == tail) { scratch[2 * warp] = M; scratch[2 * warp + 1] = Y; }
-        __syncthreads();
+        bar.sync();
         // carry entering each warp: warp 0 scans the warp totals (lane l holds
         // the l-th warp in composition order) and leaves warp w's carry in
         // scratch[2 w]
@@ -206,9 +222,9 @@ __device__ __forceinline__ C affine_carry(C M, C Y, C* scratch) {
             __syncwarp();
             if (lane < NW) scratch[2 * w] = cw;
         }
-        __syncthreads();
+        bar.sync();
         const C carry = scratch[2 * warp];
-        __syncthreads();
+        bar.sync();
         return cfma(Mex, carry, Yex);
     }
 }

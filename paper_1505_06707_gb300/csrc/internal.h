@@ -51,8 +51,17 @@ struct Tables1D {
     void* TVs = nullptr;
 };
 
+// Work item of the persistent batch kernel: up to G instances of one size.
+struct Pack1D {
+    int var;      // variant index in the kernel's list
+    int first;    // first descriptor of the pack (descriptors in pack order)
+    int count;    // instances in the pack (<= the variant's group count)
+    int pad_;
+};
+
 struct Group1D {                  // instances sharing one kernel configuration
     int logn = 0, loge = 0, logrm = 0;
+    bool in_persist = false;      // also in the persistent kernel's packs
     std::vector<int> members;     // instance indices
     Inst1D* d_inst = nullptr;     // device descriptors
 };
@@ -67,6 +76,12 @@ int launch_field_table(const double* d_cls /*omega, Tp pairs*/, int ncls, double
 int launch_field_table_dev(const double* d_cls, int ncls, const double* d_t0, double tau,
                            int64_t nsteps, double* out, int64_t stride, cudaStream_t st);
 int soft1d_variants(int prec, int logn, int* loge, int* logrm, int maxv);
+// the persistent mixed-size kernel (soft1d_persist_*.cu); packs point to
+// Pack1D records, counter to the queue position (zero before the launch)
+int launch_persist(int prec, const void* packs, int npacks, int* counter, const Inst1D* insts, void* psi,
+                   int64_t nsteps, const double* ftab, int64_t fstride, int* status, cudaStream_t st,
+                   int* ctas_out);
+int persist_config(int prec, int logn, int* loge, int* logrm, int* groups);
 int launch_advance_time(double* d_t, double dt, cudaStream_t st);
 bool soft1d_supported(int prec, int logn, int loge, int logrm);
 void soft1d_default_cfg(int prec, int logn, int* loge, int* logrm);

@@ -431,6 +431,7 @@ void Plan2D::free_pcg() {
 extern "C" {
 
 int sse_apply_A(soft_plan* P, double E, const void* x, void* y, void* stream) {
+    if (P && P->kind == 1 && x && y && std::isfinite(E)) return sse1d_apply(P, E, 0, 0, x, y, (cudaStream_t)stream);
     if (!P || !x || !y || P->kind != 2 || !std::isfinite(E)) return SOFT_ERR_INVALID_ARG;
     if (P->prec != SOFT_C128) return SOFT_ERR_UNSUPPORTED;
     Plan2D* Q = P->p2;
@@ -446,6 +447,7 @@ int sse_apply_A(soft_plan* P, double E, const void* x, void* y, void* stream) {
 }
 
 int sse_apply_A32(soft_plan* P, double E, const void* x, void* y, void* stream) {
+    if (P && P->kind == 1) return SOFT_ERR_UNSUPPORTED;
     if (!P || !x || !y || P->kind != 2 || !std::isfinite(E)) return SOFT_ERR_INVALID_ARG;
     if (P->prec != SOFT_C128) return SOFT_ERR_UNSUPPORTED;
     Plan2D* Q = P->p2;
@@ -461,6 +463,10 @@ int sse_apply_A32(soft_plan* P, double E, const void* x, void* y, void* stream) 
 }
 
 int sse_apply_precond(soft_plan* P, double E, int precond, const void* x, void* y, void* stream) {
+    if (P && P->kind == 1 && x && y && std::isfinite(E)) {
+        if (precond != 0 && precond != 1 && precond != 4) return SOFT_ERR_INVALID_ARG;
+        return sse1d_apply(P, E, 1, precond, x, y, (cudaStream_t)stream);
+    }
     if (!P || !x || !y || P->kind != 2 || !std::isfinite(E)) return SOFT_ERR_INVALID_ARG;
     if (precond != 0 && precond != 1 && precond != 4) return SOFT_ERR_INVALID_ARG;
     if (P->prec != SOFT_C128) return SOFT_ERR_UNSUPPORTED;
@@ -480,6 +486,12 @@ int sse_pcg_solve(soft_plan* P, const double* E, int nE, const void* rhs, void* 
                   int maxit, int precond, int* iters_out, double* relres_out, void* stream) {
     if (!P || !E || nE <= 0 || !rhs || !psi_out || !(tol > 0) || maxit <= 0) return SOFT_ERR_INVALID_ARG;
     if (precond < 0 || precond > 5) return SOFT_ERR_INVALID_ARG;
+    if (P->kind == 1) {                  // 1D plans: the resident solver of sse1d.cu
+        for (int e = 0; e < nE; ++e)
+            if (!std::isfinite(E[e])) return SOFT_ERR_INVALID_ARG;
+        return sse1d_solve(P, E, nE, rhs, psi_out, tol, maxit, precond, iters_out, relres_out,
+                           (cudaStream_t)stream);
+    }
     const bool flexible = precond == 2 || precond == 3;
     // precond 5: the mixed iteration (solve_mixed); reliable updates after a
     // tenfold drop of the recursive residual, or after 200 iterations

@@ -241,6 +241,7 @@ void soft_default_options(soft_options* opt) {
     opt->autotune = 0;
     opt->cap_energy = 2.0;
     opt->tfap_kmin = 0.25;
+    opt->persistent = 1;
 }
 
 const char* soft_strerror(int s) {
@@ -271,6 +272,7 @@ static int check_opts(const soft_options* opt, soft_options* o) {
         return SOFT_ERR_INVALID_ARG;
     if (!(o->soft_a2 > 0) && o->charge != 0) return SOFT_ERR_INVALID_ARG;
     if (o->band_width < 1) return SOFT_ERR_INVALID_ARG;
+    if (o->persistent != 0 && o->persistent != 1) return SOFT_ERR_INVALID_ARG;
     return SOFT_OK;
 }
 
@@ -365,14 +367,17 @@ static int create_1d(int count, const soft_grid* grids, const double* boxes, con
         int rc = check_axis(n, a, b, R0[i]);
         if (rc) return rc;
         const int logn = ilog2(n);
-        int loge, logrm;
+        int loge, logrm, pgroups;
         soft1d_default_cfg(o.prec, logn, &loge, &logrm);
-        if (!soft1d_supported(o.prec, logn, loge, logrm)) return SOFT_ERR_UNSUPPORTED;
+        // sizes of the persistent kernel keep its (elements per thread, radix)
+        const bool persist = !single && o.persistent &&
+                             persist_config(o.prec, logn, &loge, &logrm, &pgroups) >= 0;
+        if (!persist && !soft1d_supported(o.prec, logn, loge, logrm)) return SOFT_ERR_UNSUPPORTED;
         auto key = std::make_tuple(n, a, b, R0[i], theta[i]);
         int tab;
         auto it = seen.find(key);
         if (it == seen.end()) {
-            if (o.autotune) {
+            if (o.autotune && !persist) {
                 int cnt = 0;
                 for (int j = i; j < count; ++j)
                     if (grids[j].n[0] == n) ++cnt;
@@ -422,6 +427,7 @@ static int create_1d(int count, const soft_grid* grids, const double* boxes, con
     P->total = off;
     int rc = P->build_1d_device();
     if (rc) return rc;
+    if (!single && o.persistent && o.autotune && P->npacks > 0 && (rc = P->time_schedules())) return rc;
     *out = P.release();
     return SOFT_OK;
 }
@@ -514,7 +520,8 @@ int soft_set_potential(soft_plan* P, const double* U, int64_t n) {
     std::vector<cd> tv, tvs;
     potential_tables_1d(*T, nn, P->dt, tv, tvs);
     if ((rc = refill_vtab(T->TV, tv, T->prec))) return rc;
-    return refill_vtab(T->TVs, tvs, T->prec);
+    if ((rc = refill_vtab(T->TVs, tvs, T->prec))) return rc;
+    return sse1d_refill_potential(P);
 }
 
 void soft_destroy(soft_plan* P) { delete P; }
@@ -537,12 +544,16 @@ int64_t soft_last_launches(const soft_plan* P) { return P ? P->last_launches : 0
 soft_plan::~soft_plan() {
     for (auto& t : tabs) free_tables(t.get());
     for (auto& g : groups) cudaFree(g.d_inst);
+    cudaFree(d_pinst);
+    cudaFree(d_packs);
+    cudaFree(d_pcount);
     cudaFree(d_inst_obs);
     cudaFree(d_cls);
     cudaFree(d_ftab);
     cudaFree(d_status);
     cudaFree(d_t0);
     delete nn;
+    sse1d_free(s1);
     if (gexec) cudaGraphExecDestroy(gexec);
     if (side_ready) {
         for (size_t g = 0; g < groups.size() && g < MAX_SIDE; ++g) {
@@ -586,6 +597,39 @@ int soft_plan::build_1d_device() {
     }
     std::sort(groups.begin(), groups.end(), [](const Group1D& a, const Group1D& b) { return a.logn > b.logn; });
     int rc;
+    // the persistent kernel's sizes leave the group list: their instances
+    // form packs of up to G same-size instances, largest N first
+    if (!single && opt.persistent) {
+        std::vector<Pack1D> packs;
+        std::vector<Inst1D> pd;
+        for (auto& g : groups) {
+            int le, lr, G;
+            const int v = persist_config(prec, g.logn, &le, &lr, &G);
+            if (v < 0 || le != g.loge || lr != g.logrm) continue;
+            g.in_persist = true;
+            for (size_t k = 0; k < g.members.size(); k += G) {
+                Pack1D pk;
+                pk.var = v;
+                pk.first = (int)pd.size();
+                pk.count = (int)std::min<size_t>(G, g.members.size() - k);
+                pk.pad_ = 0;
+                for (int j = 0; j < pk.count; ++j) pd.push_back(descriptor(g.members[k + j]));
+                packs.push_back(pk);
+            }
+        }
+        std::stable_sort(packs.begin(), packs.end(), [](const Pack1D& a, const Pack1D& b) { return a.var < b.var; });
+        npacks = (int)packs.size();
+        use_persist = npacks > 0;
+        if (npacks > 0) {
+            if ((rc = upload((void**)&d_pinst, pd.data(), pd.size() * sizeof(Inst1D)))) return rc;
+            if ((rc = upload(&d_packs, packs.data(), packs.size() * sizeof(Pack1D)))) return rc;
+            if ((rc = cuda_status(cudaMalloc((void**)&d_pcount, sizeof(int))))) return rc;
+            // sets the kernel's shared-memory attribute outside any capture
+            if ((rc = launch_persist(prec, nullptr, 0, nullptr, nullptr, nullptr, 0, nullptr, 0, nullptr, 0,
+                                     nullptr)))
+                return rc;
+        }
+    }
     for (auto& g : groups) {
         std::vector<Inst1D> d;
         for (int i : g.members) d.push_back(descriptor(i));
@@ -644,7 +688,8 @@ int soft_plan::set_single_field(const soft_field* f, cudaStream_t st) {
 }
 
 // one chunk of steps on the given stream: pulse table from the device start
-// time, the size groups on parallel branches, then the start time advanced
+// time, the persistent kernel (if used) and the size groups on parallel
+// branches, then the start time advanced
 int soft_plan::enqueue_chunk(void* psi, int64_t chunk, cudaStream_t st) {
     const int nc = ncls + (single ? 1 : 0);
     int rc;
@@ -652,9 +697,21 @@ int soft_plan::enqueue_chunk(void* psi, int64_t chunk, cudaStream_t st) {
         if ((rc = launch_field_table_dev(d_cls, nc, d_t0, dt, chunk, d_ftab, ftab_cap, st))) return rc;
         ++last_launches;
     }
-    const bool fork = groups.size() > 1;
+    const bool persist = use_persist && npacks > 0;
+    int nlaunch = persist ? 1 : 0;
+    for (const auto& G : groups)
+        if (!(persist && G.in_persist)) ++nlaunch;
+    const bool fork = nlaunch > 1;
     if (fork && (rc = cuda_status(cudaEventRecord(ev_fork, st)))) return rc;
+    if (persist) {           // the persistent kernel on the call's stream, the groups beside it
+        if ((rc = cuda_status(cudaMemsetAsync(d_pcount, 0, sizeof(int), st)))) return rc;
+        if ((rc = launch_persist(prec, d_packs, npacks, d_pcount, d_pinst, psi, chunk, d_ftab, ftab_cap, d_status,
+                                 st, nullptr)))
+            return rc;
+        last_launches += 1;
+    }
     for (size_t g = 0; g < groups.size(); ++g) {
+        if (persist && groups[g].in_persist) continue;
         cudaStream_t gs = fork ? side[g] : st;
         if (fork && (rc = cuda_status(cudaStreamWaitEvent(gs, ev_fork, 0)))) return rc;
         const Group1D& G = groups[g];
@@ -672,9 +729,7 @@ int soft_plan::enqueue_chunk(void* psi, int64_t chunk, cudaStream_t st) {
     return SOFT_OK;
 }
 
-int soft_plan::step_1d(void* psi, int64_t nsteps, double* t_inout, cudaStream_t st) {
-    last_launches = 0;
-    if (nsteps == 0) return SOFT_OK;
+int soft_plan::ensure_side() {
     int rc;
     if (!side_ready) {
         for (size_t g = 0; g < groups.size() && g < MAX_SIDE; ++g) {
@@ -684,7 +739,51 @@ int soft_plan::step_1d(void* psi, int64_t nsteps, double* t_inout, cudaStream_t 
         if ((rc = cuda_status(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming)))) return rc;
         side_ready = true;
     }
-    if (groups.size() > MAX_SIDE) return SOFT_ERR_UNSUPPORTED;
+    return groups.size() > MAX_SIDE ? SOFT_ERR_UNSUPPORTED : SOFT_OK;
+}
+
+// The schedule autotuner of a batch plan: one chunk of 16 steps on a zero
+// state with the persistent kernel and with one kernel per size group
+// (each timed after a warm-up run); the faster is kept.
+int soft_plan::time_schedules() {
+    int rc = ensure_side();
+    if (rc) return rc;
+    const size_t eb = prec == SOFT_C64 ? 8 : 16;
+    void* tmp = nullptr;
+    if ((rc = cuda_status(cudaMalloc(&tmp, eb * (size_t)total)))) return rc;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float ms[2] = {0, 0};
+    rc = cuda_status(cudaMemset(tmp, 0, eb * (size_t)total));
+    if (!rc) rc = cuda_status(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    if (!rc) rc = cuda_status(cudaEventCreate(&e0));
+    if (!rc) rc = cuda_status(cudaEventCreate(&e1));
+    for (int mode = 0; mode < 2 && !rc; ++mode) {
+        use_persist = mode == 0;
+        const double zero = 0.0;
+        rc = cuda_status(cudaMemcpyAsync(d_t0, &zero, sizeof(double), cudaMemcpyHostToDevice, st));
+        for (int rep = 0; rep < 2 && !rc; ++rep) {
+            if (rep == 1) rc = cuda_status(cudaEventRecord(e0, st));
+            if (!rc) rc = enqueue_chunk(tmp, 16, st);
+            if (!rc && rep == 1) rc = cuda_status(cudaEventRecord(e1, st));
+        }
+        if (!rc) rc = cuda_status(cudaEventSynchronize(e1));
+        if (!rc) rc = cuda_status(cudaEventElapsedTime(&ms[mode], e0, e1));
+    }
+    use_persist = rc == SOFT_OK && ms[0] <= ms[1];
+    last_launches = 0;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    cudaFree(tmp);
+    return rc;
+}
+
+int soft_plan::step_1d(void* psi, int64_t nsteps, double* t_inout, cudaStream_t st) {
+    last_launches = 0;
+    if (nsteps == 0) return SOFT_OK;
+    int rc;
+    if ((rc = ensure_side())) return rc;
     // start time: a pageable copy is consumed before the call returns
     const double t0 = *t_inout;
     if ((rc = cuda_status(cudaMemcpyAsync(d_t0, &t0, sizeof(double), cudaMemcpyHostToDevice, st)))) return rc;

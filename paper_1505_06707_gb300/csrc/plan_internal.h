@@ -24,6 +24,12 @@ int make_tables_1d(Tables1D* T, int n, double a, double b, double R0, double the
 
 struct Geo2D;
 struct NNState;
+struct Sse1D;
+void sse1d_free(Sse1D* s);
+int sse1d_refill_potential(soft_plan* P);
+int sse1d_solve(soft_plan* P, const double* E, int nE, const void* rhs, void* psi_out, double tol, int maxit,
+                int precond, int* iters_out, double* relres_out, cudaStream_t st);
+int sse1d_apply(soft_plan* P, double E, int what, int precond, const void* x, void* y, cudaStream_t st);
 }  // namespace soft
 
 #include "soft2d_geo.h"
@@ -77,6 +83,12 @@ struct soft_plan {
     std::vector<std::unique_ptr<soft::Tables1D>> tabs;
     std::vector<InstHost> inst;
     std::vector<soft::Group1D> groups;
+    // instances of the persistent kernel: descriptors in pack order, packs
+    int npacks = 0;
+    bool use_persist = false;      // launch the packs' sizes through the persistent kernel
+    soft::Inst1D* d_pinst = nullptr;
+    void* d_packs = nullptr;
+    int* d_pcount = nullptr;
     std::vector<soft::Inst1D> h_obs;
     soft::Inst1D* d_inst_obs = nullptr;
     std::vector<double> h_cls;     // (omega, Tp) per pulse class
@@ -104,7 +116,10 @@ struct soft_plan {
     int build_1d_device();
     int set_single_field(const soft_field* f, cudaStream_t st);
     int enqueue_chunk(void* psi, int64_t chunk, cudaStream_t st);
+    int ensure_side();
+    int time_schedules();
     int step_1d(void* psi, int64_t nsteps, double* t_inout, cudaStream_t st);
+    soft::Sse1D* s1 = nullptr;     // stationary solver of a single 1D plan (sse1d.cu)
 
     // ---- 2D (plan2d.cu), learned correction (nn.cu)
     soft::Plan2D* p2 = nullptr;

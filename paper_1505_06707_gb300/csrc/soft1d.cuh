@@ -342,9 +342,9 @@ __device__ __forceinline__ void strip_cn(C* S, const C* __restrict__ cn, int nb,
 // tvs[c*T + t] = TV at row i0 + c.  Every coefficient is read once, before
 // the sweep that uses it; the in-chunk products of the carry corrections are
 // formed from registers.  post(n, tv, v) gets the row's grid index and potential.
-template <typename C, typename VT, int T, int CMAX, int N, class Post>
+template <typename C, typename VT, int T, int CMAX, int N, class Post, class B = BarCTA>
 __device__ __forceinline__ void strip_cn_1d(C* S, const C* __restrict__ cn, const VT* __restrict__ tvs,
-                                            int nb, int blk0, int tid, C* scan, Post post) {
+                                            int nb, int blk0, int tid, C* scan, Post post, B bar = B()) {
     const int ch = (nb + T - 1) / T;             // host guarantees ch <= CMAX
     const int P1 = (ch + 1) * T;
     const int i0 = tid * ch;
@@ -364,7 +364,7 @@ __device__ __forceinline__ void strip_cn_1d(C* S, const C* __restrict__ cn, cons
             y[c] = yl;
         }
     }
-    C carry = affine_carry<C, T, false>(Mp, yl, scan);
+    C carry = affine_carry<C, T, false>(Mp, yl, scan, tid, bar);
     {
         C pr; pr.x = 1; pr.y = 0;
 #pragma unroll
@@ -385,7 +385,7 @@ __device__ __forceinline__ void strip_cn_1d(C* S, const C* __restrict__ cn, cons
             y[c] = xl;
         }
     }
-    carry = affine_carry<C, T, true>(Mp, xl, scan);
+    carry = affine_carry<C, T, true>(Mp, xl, scan, tid, bar);
     C pr; pr.x = 1; pr.y = 0;
 #pragma unroll
     for (int c = CMAX - 1; c >= 0; --c) {
@@ -425,20 +425,20 @@ __host__ __device__ constexpr size_t soft1d_smem() {
            sizeof(typename TwT<R>::T) * TwCount<LOGN, LOGRM>::value + 64;
 }
 
-template <typename R, int LOGN, int LOGE, int LOGRM, int P, int PEND, typename TW>
-__device__ __forceinline__ void fwd_passes(typename CT<R>::C* S, const TW* Ws, int tid) {
+template <typename R, int LOGN, int LOGE, int LOGRM, int P, int PEND, typename TW, class B = BarCTA>
+__device__ __forceinline__ void fwd_passes(typename CT<R>::C* S, const TW* Ws, int tid, B bar = B()) {
     if constexpr (P < PEND) {
         fwd_pass<R, LOGN, LOGE, LOGRM, P, true>(S, Ws, tid);
-        __syncthreads();
-        fwd_passes<R, LOGN, LOGE, LOGRM, P + 1, PEND>(S, Ws, tid);
+        bar.sync();
+        fwd_passes<R, LOGN, LOGE, LOGRM, P + 1, PEND>(S, Ws, tid, bar);
     }
 }
-template <typename R, int LOGN, int LOGE, int LOGRM, int P, int PSTOP, typename TW>
-__device__ __forceinline__ void inv_passes(typename CT<R>::C* S, const TW* Ws, int tid) {
+template <typename R, int LOGN, int LOGE, int LOGRM, int P, int PSTOP, typename TW, class B = BarCTA>
+__device__ __forceinline__ void inv_passes(typename CT<R>::C* S, const TW* Ws, int tid, B bar = B()) {
     if constexpr (P >= PSTOP) {
         inv_pass<R, LOGN, LOGE, LOGRM, P, true>(S, Ws, tid);
-        __syncthreads();
-        inv_passes<R, LOGN, LOGE, LOGRM, P - 1, PSTOP>(S, Ws, tid);
+        bar.sync();
+        inv_passes<R, LOGN, LOGE, LOGRM, P - 1, PSTOP>(S, Ws, tid, bar);
     }
 }
 
@@ -603,29 +603,36 @@ __device__ __forceinline__ C strip_field(const C* fr, R al, const Inst1D& I, int
     return field_direct<R, C>(al, I.x0, I.h, n);
 }
 
+// shared-memory bytes of one instance's private part: the state (unless
+// GM), 64 complex of scan scratch and E + 36 field phases
 template <typename R, int LOGN, int LOGE, int LOGRM>
-__global__ void __launch_bounds__(Cfg1D<R, LOGN, LOGE, LOGRM>::T, Cfg1D<R, LOGN, LOGE, LOGRM>::MINB)
-soft1d_kernel(const Inst1D* __restrict__ insts, void* __restrict__ psi_base, int64_t nsteps,
-              const double* __restrict__ ftab_base, int64_t ftab_stride, int* __restrict__ status)
+__host__ __device__ constexpr size_t soft1d_inst_smem() {
+    return sizeof(typename CT<R>::C) *
+           ((Cfg1D<R, LOGN, LOGE, LOGRM>::GM ? 0 : (size_t(1) << LOGN)) + 64 + (size_t(1) << LOGE) + 36);
+}
+
+// All nsteps steps of one instance, run by the T threads of a group (tid =
+// index in the group, bar = its barrier).  Ss: the state in shared memory
+// (unused with GM); scan: 64 complex of scan scratch followed by E + 36
+// field phases; Ws: the twiddle bases, already in shared memory and visible
+// to the group by its first barrier.
+template <typename R, int LOGN, int LOGE, int LOGRM, class B>
+__device__ __forceinline__ void soft1d_run(const Inst1D& I, void* __restrict__ psi_base, int64_t nsteps,
+                                           const double* __restrict__ ftab_base, int64_t ftab_stride,
+                                           int* __restrict__ status, typename CT<R>::C* Ss,
+                                           typename CT<R>::C* scan, const typename TwT<R>::T* Ws, int tid,
+                                           B bar)
 {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
-    using Q = Step1D<R, LOGN, LOGRM>;
     using C = typename K::C;
     constexpr int N = K::N, T = K::T, E = K::E;
     static_assert(K::NPASS >= 2, "at least two FFT passes");
-    static_assert(Q::R0 <= 16, "pass radix <= 16");
-    static_assert(soft1d_smem<R, LOGN, LOGE, LOGRM>() <= 227 * 1024, "shared memory");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    using TWT = typename TwT<R>::T;
-    TWT* Ws = reinterpret_cast<TWT*>(reinterpret_cast<C*>(smem_raw) + (K::GM ? 0 : N));   // twiddles, TWN bases
-    C* scan = reinterpret_cast<C*>(Ws + Q::TWN);           // 2*32 complex
+    static_assert(Step1D<R, LOGN, LOGRM>::R0 <= 16, "pass radix <= 16");
     C* fr = scan + 64;               // E + 36 complex: field phases (field_setup)
 
-    const Inst1D I = insts[blockIdx.x];
     C* __restrict__ g_psi = reinterpret_cast<C*>(psi_base) + I.off;
     // the state: shared memory, or (GM) the instance's buffer itself
-    C* S = K::GM ? g_psi : reinterpret_cast<C*>(smem_raw);
-    const TWT* __restrict__ W = reinterpret_cast<const TWT*>(I.W);
+    C* S = K::GM ? g_psi : Ss;
     using TT = typename K::TT;
     const TT* __restrict__ TK = reinterpret_cast<const TT*>(I.TK);
     const TT* __restrict__ TKh = reinterpret_cast<const TT*>(I.TKh);
@@ -633,12 +640,11 @@ soft1d_kernel(const Inst1D* __restrict__ insts, void* __restrict__ psi_base, int
     const VT* __restrict__ TV = reinterpret_cast<const VT*>(I.TV);
     const C* __restrict__ cn = reinterpret_cast<const C*>(I.cn);
     const VT* __restrict__ TVs = reinterpret_cast<const VT*>(I.TVs);
-    const int tid = threadIdx.x;
     const int nb = I.nb, blk0 = I.blk0;
     if (nsteps <= 0) return;
 
     // load the state (GM: permute the buffer into the swizzled order in place;
-    // swz is an involution, so it is a product of disjoint swaps) and the twiddles
+    // swz is an involution, so it is a product of disjoint swaps)
     if constexpr (K::GM) {
         for (int j = 0; j < E; ++j) {
             const int n = tid + j * T, p = swz<C>(n);
@@ -651,8 +657,7 @@ soft1d_kernel(const Inst1D* __restrict__ insts, void* __restrict__ psi_base, int
             S[swz<C>(n)] = g_psi[n];
         }
     }
-    for (int i = tid; i < Q::TWN; i += T) Ws[i] = __ldg(&W[i]);
-    __syncthreads();
+    bar.sync();
 
     const double* __restrict__ ftab = I.has_field ? ftab_base + (int64_t)I.fcls * ftab_stride : nullptr;
     // field amplitude of step s: alpha = tau E(t + tau/2) / 2
@@ -669,22 +674,22 @@ soft1d_kernel(const Inst1D* __restrict__ insts, void* __restrict__ psi_base, int
                 v = vmul(v, tv);
                 if (I.has_field) v = cmul(v, strip_field<R, C, E>(fr, al, I, n));
                 return v;
-            });
-            __syncthreads();
+            }, bar);
+            bar.sync();
         }
         // ---- kinetic: forward FFT, e^{-iK tau} (e^{-iK tau/2} in the first
         //      and last pass of the call), inverse FFT, potential of the next step
         const bool more = step + 1 < nsteps;
-        fwd_passes<R, LOGN, LOGE, LOGRM, 0, K::NPASS - 1>(S, Ws, tid);
+        fwd_passes<R, LOGN, LOGE, LOGRM, 0, K::NPASS - 1>(S, Ws, tid, bar);
         kcenter<R, LOGN, LOGE, LOGRM>(S, (step >= 0 && more) ? TK : TKh, tid);
         if (more && I.has_field) {
             al = alpha(step + 1);
             field_setup<R, LOGN, LOGE, LOGRM>(fr, al, I, tid);
         }
-        __syncthreads();
-        inv_passes<R, LOGN, LOGE, LOGRM, K::NPASS - 2, 1>(S, Ws, tid);
+        bar.sync();
+        inv_passes<R, LOGN, LOGE, LOGRM, K::NPASS - 2, 1>(S, Ws, tid, bar);
         inv_pass0_v<R, LOGN, LOGE, LOGRM>(S, Ws, TV, fr, al, I, tid, more);
-        __syncthreads();
+        bar.sync();
     }
 
     // store
@@ -704,6 +709,30 @@ soft1d_kernel(const Inst1D* __restrict__ insts, void* __restrict__ psi_base, int
         const C v = S[0];
         if (!(isfinite((double)v.x) && isfinite((double)v.y))) atomicOr(status, 1);
     }
+}
+
+// One CTA per instance: blockIdx.x indexes insts.
+template <typename R, int LOGN, int LOGE, int LOGRM>
+__global__ void __launch_bounds__(Cfg1D<R, LOGN, LOGE, LOGRM>::T, Cfg1D<R, LOGN, LOGE, LOGRM>::MINB)
+soft1d_kernel(const Inst1D* __restrict__ insts, void* __restrict__ psi_base, int64_t nsteps,
+              const double* __restrict__ ftab_base, int64_t ftab_stride, int* __restrict__ status)
+{
+    using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
+    using Q = Step1D<R, LOGN, LOGRM>;
+    using C = typename K::C;
+    static_assert(soft1d_smem<R, LOGN, LOGE, LOGRM>() <= 227 * 1024, "shared memory");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using TWT = typename TwT<R>::T;
+    // layout: [state (unless GM)] [twiddles] [scan] [field phases]
+    C* Ss = reinterpret_cast<C*>(smem_raw);
+    TWT* Ws = reinterpret_cast<TWT*>(Ss + (K::GM ? 0 : K::N));
+    const Inst1D I = insts[blockIdx.x];
+    const TWT* __restrict__ W = reinterpret_cast<const TWT*>(I.W);
+    if (nsteps <= 0) return;
+    for (int i = threadIdx.x; i < Q::TWN; i += K::T) Ws[i] = __ldg(&W[i]);
+    // the run's first barrier (after its state load) also covers the twiddles
+    soft1d_run<R, LOGN, LOGE, LOGRM>(I, psi_base, nsteps, ftab_base, ftab_stride, status, Ss,
+                                     reinterpret_cast<C*>(Ws + Q::TWN), Ws, (int)threadIdx.x, BarCTA());
 }
 
 template <typename R, int LOGN, int LOGE, int LOGRM>

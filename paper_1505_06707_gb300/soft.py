@@ -55,7 +55,8 @@ class Grid(C.Structure):
 class Options(C.Structure):
     _fields_ = [("prec", C.c_int), ("contour", C.c_int), ("tfecs_alpha", C.c_double),
                 ("soft_a2", C.c_double), ("charge", C.c_double), ("band_width", C.c_int),
-                ("autotune", C.c_int), ("cap_energy", C.c_double), ("tfap_kmin", C.c_double)]
+                ("autotune", C.c_int), ("cap_energy", C.c_double), ("tfap_kmin", C.c_double),
+                ("persistent", C.c_int)]
 
 
 class Field(C.Structure):
@@ -145,12 +146,13 @@ def _check(rc, where):
 
 
 def _options(prec=SOFT_C128, contour=CONTOUR_SHARP, tfecs_alpha=0.5, soft_a2=2.0, charge=1.0,
-             band_width=10, autotune=0, cap_energy=2.0, tfap_kmin=0.25):
+             band_width=10, autotune=0, cap_energy=2.0, tfap_kmin=0.25, persistent=1):
     o = Options()
     load().soft_default_options(C.byref(o))
     o.prec, o.contour, o.tfecs_alpha = prec, contour, tfecs_alpha
     o.soft_a2, o.charge, o.band_width = soft_a2, charge, band_width
     o.autotune = autotune
+    o.persistent = persistent
     o.cap_energy, o.tfap_kmin = cap_energy, tfap_kmin
     return o
 

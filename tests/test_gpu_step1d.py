@@ -2,14 +2,12 @@
 through the C ABI.
 
 Bars.  complex128: rel-L2 <= 1e-11 after the full propagation.  complex64:
-the target is 1e-5, but an FP32 FFT drifts coherently: its rounded twiddles
-give every Fourier mode a fixed gain/phase error of order 1e-7 per
-forward/inverse pair, which adds up linearly with the number of steps (an
-FP32 emulation reproduces this; a compensated kinetic table alone removes
-the table part of the drift but not the FFT part).  The drift grows with the
-FFT depth: measured 1.05e-7 per step at N = 1024 and 2.1e-7 at N = 16384.
-The complex64 bound is therefore max(2e-6, C64_DRIFT * log2(N) * steps),
-about twice the measured rate; runs of up to ~30 steps meet the 1e-5 target."""
+1e-5, the FP32 target, for every run here (up to the 2000 steps of the 1D
+workload, measured 5e-6 there).  The FP32 FFT applies its constant
+rotations and pass twiddles as compensated hi+lo products: a rounded
+(cos, sin) pair has |w| != 1 and, applied at the same positions in every
+step, gave a coherent drift of ~1e-7 per step before.  The whole 22046-step
+pulse of the laser workload is covered by test_gpu_full_propagation."""
 import math
 
 import numpy as np
@@ -26,13 +24,10 @@ from oracle import propagate as P  # noqa: E402
 from oracle import tables as T  # noqa: E402
 
 CT = {S.SOFT_C64: torch.complex64, S.SOFT_C128: torch.complex128}
-C64_DRIFT = 2.5e-8        # rel-L2 per step and FFT level, see the module docstring
 
 
-def tol(prec, nsteps, n=16384):
-    if prec == S.SOFT_C128:
-        return 1e-11
-    return max(2e-6, C64_DRIFT * math.log2(n) * nsteps)
+def tol(prec, nsteps=None, n=None):
+    return 1e-11 if prec == S.SOFT_C128 else 1e-5
 
 
 def relerr(a, b):
@@ -318,34 +313,28 @@ def test_autotuned_batch_matches_default(prec):
 
 @pytest.mark.parametrize("prec", [S.SOFT_C64, S.SOFT_C128])
 def test_w2_full_batch_sampled(prec):
-    """The whole laser batch (4096 instances, N = 2048 .. 16384) advanced by
-    one call of 256 steps, as the benchmark launches it (one plan per size,
-    autotuned kernels); 8 sampled instances, two per size, compared with
-    their own oracle runs."""
+    """The whole laser batch (4096 instances, N = 2048 .. 16384) in one mixed
+    batch plan advanced by one call of 256 steps, as the benchmark launches
+    it (autotuned: persistent kernel or per-size kernels, whichever is
+    faster); 8 sampled instances, two per size, compared with their own
+    oracle runs."""
     ws = [W.w2_instance(j) for j in range(4096)]
     nst, t0 = 256, 0.0
     sample = []
     for n in W.W2_SIZES:
         sample += [i for i, w in enumerate(ws) if w["n"] == n][:2]
-    got = {}
-    for n in W.W2_SIZES:
-        members = [i for i, w in enumerate(ws) if w["n"] == n]
-        g = [ws[i] for i in members]
-        plan = S.soft_create_batch([w["n"] for w in g], [(w["a"], w["b"]) for w in g],
-                                   [w["R0"] for w in g], [w["theta"] for w in g],
-                                   [(w["E0"], w["omega"], w["ncyc"]) for w in g], W.W2_DT,
-                                   prec=prec, contour=W.W2_CONTOUR, autotune=1)
-        try:
-            offs, tot = S.soft_batch_layout(plan)
-            d = torch.tensor(np.concatenate([w["psi0"] for w in g]), dtype=CT[prec], device="cuda")
-            S.soft_step_batch(plan, d, nst, t0)
-            torch.cuda.synchronize()
-            h = d.cpu().numpy().astype(np.complex128)
-        finally:
-            S.soft_destroy(plan)
-        for k, i in enumerate(members):
-            if i in sample:
-                got[i] = h[offs[k]:offs[k] + n]
+    plan = S.soft_create_batch([w["n"] for w in ws], [(w["a"], w["b"]) for w in ws],
+                               [w["R0"] for w in ws], [w["theta"] for w in ws],
+                               [(w["E0"], w["omega"], w["ncyc"]) for w in ws], W.W2_DT,
+                               prec=prec, contour=W.W2_CONTOUR, autotune=1)
+    try:
+        offs, tot = S.soft_batch_layout(plan)
+        d = torch.tensor(np.concatenate([w["psi0"] for w in ws]), dtype=CT[prec], device="cuda")
+        S.soft_step_batch(plan, d, nst, t0)
+        torch.cuda.synchronize()
+        got = {i: d[offs[i]:offs[i] + ws[i]["n"]].cpu().numpy().astype(np.complex128) for i in sample}
+    finally:
+        S.soft_destroy(plan)
     sw = [ws[i] for i in sample]
     probs = [P.Problem1D(w["n"], w["a"], w["b"], w["R0"], theta=w["theta"], kind=w["contour"],
                          a2=w["a2"], dt=w["dt"]) for w in sw]
@@ -418,3 +407,48 @@ def test_secs_zero_angle_reduces_to_the_unscaled_step(prec):
     ref = P.Problem1D(n, a, b, R0, theta=0.0, kind=T.SHARP, a2=2.0, dt=0.02).step(psi0, 100)
     got = gpu_run(n, (a, b), R0, 0.0, 0.02, psi0, 100, prec=prec, contour=S.CONTOUR_SECS)
     assert relerr(got, ref) < (1e-12 if prec == S.SOFT_C128 else 2e-6)
+
+
+@pytest.mark.parametrize("prec", [S.SOFT_C64, S.SOFT_C128])
+def test_persistent_batch_matches_group_kernels(prec):
+    """A batch plan runs its instances of N = 2048 .. 16384 through the
+    persistent kernel (packs of same-size instances from a queue, several
+    instances per CTA on named barriers) and the rest through one kernel per
+    size group, beside it.  Both must give exactly what one kernel per size
+    group gives (the same arithmetic per instance), including part-filled
+    packs and sizes outside the persistent kernel, and match the oracle."""
+    ws = [W.w2_instance(j) for j in range(37)]
+    extra = []
+    for n in (512, 1024):                   # sizes outside the persistent kernel
+        hw = 8.0 * n / 1024
+        x = -hw + 2 * hw / n * (np.arange(n) + 0.5)
+        extra.append(dict(n=n, a=-hw, b=hw, R0=0.75 * hw, theta=0.5, contour=W.W2_CONTOUR, a2=2.0,
+                          dt=W.W2_DT, E0=0.05, omega=W.W2_OMEGA, ncyc=W.W2_NCYC,
+                          psi0=np.exp(-x ** 2 / 3.0 + 0.3j)))
+    ws = ws[:20] + extra + ws[20:]
+    args = ([w["n"] for w in ws], [(w["a"], w["b"]) for w in ws], [w["R0"] for w in ws],
+            [w["theta"] for w in ws], [(w["E0"], w["omega"], w["ncyc"]) for w in ws], W.W2_DT)
+    packed = np.concatenate([w["psi0"] for w in ws])
+    outs = []
+    for pers in (1, 0):
+        plan = S.soft_create_batch(*args, prec=prec, contour=W.W2_CONTOUR, persistent=pers)
+        try:
+            d = torch.tensor(packed, dtype=CT[prec], device="cuda")
+            t = 3.0
+            for _ in range(2):
+                t = S.soft_step_batch(plan, d, 12, t)
+            torch.cuda.synchronize()
+            outs.append(d.cpu().numpy())
+            if pers:
+                assert S.soft_last_launches(plan) == 5   # table, persistent, 2 groups, time
+        finally:
+            S.soft_destroy(plan)
+    assert np.array_equal(outs[0], outs[1])
+    sample = [0, 5, 20, 21, 30, len(ws) - 1]
+    probs = [P.Problem1D(ws[i]["n"], ws[i]["a"], ws[i]["b"], ws[i]["R0"], theta=ws[i]["theta"],
+                         kind=ws[i]["contour"], a2=ws[i]["a2"], dt=ws[i]["dt"]) for i in sample]
+    refs = P.step_batch(probs, [ws[i]["psi0"] for i in sample], 24, t0s=[3.0] * len(sample),
+                        fields=[(ws[i]["E0"], ws[i]["omega"], ws[i]["ncyc"]) for i in sample])
+    offs = np.concatenate([[0], np.cumsum([w["n"] for w in ws])[:-1]])
+    for i, r in zip(sample, refs):
+        assert relerr(outs[0][offs[i]:offs[i] + ws[i]["n"]].astype(np.complex128), r) < tol(prec)

@@ -1,7 +1,6 @@
 """GPU parity of the 2D ECS split-operator step (Sec. II with separable K and
 C = C_x (x) I + I (x) C_y) against the oracle's literal 4-FFT 2D step.
-complex128: rel-L2 <= 1e-11.  complex64: the FP32 drift bound of the 1D
-tests, with log2 of the larger axis."""
+complex128: rel-L2 <= 1e-11.  complex64: 1e-5, the FP32 target."""
 import math
 
 import numpy as np
@@ -19,10 +18,8 @@ from oracle import tables as T  # noqa: E402
 CT = {S.SOFT_C64: torch.complex64, S.SOFT_C128: torch.complex128}
 
 
-def tol(prec, nsteps, n):
-    if prec == S.SOFT_C128:
-        return 1e-11
-    return max(3e-6, 2.5e-8 * math.log2(n) * nsteps * 1.5)
+def tol(prec, nsteps=None, n=None):
+    return 1e-11 if prec == S.SOFT_C128 else 1e-5
 
 
 def relerr(a, b):
