@@ -572,7 +572,7 @@ def bench_pcg1d(S, torch, dev, args):
     return res
 
 
-def measure_w2(S, torch, dev, args, prec_name, steps, warmup, world=1, with_e2e=True, persistent=1):
+def measure_w2(S, torch, dev, args, prec_name, steps, warmup, world=1, with_e2e=True, persistent=1, autotune=1):
     """The laser batch through one batch plan: the persistent kernel over all
     4096 instances (one graph per call: pulse table, queue reset, the
     kernel, time advance).  Device-timed region of `steps` calls, the graph
@@ -586,7 +586,7 @@ def measure_w2(S, torch, dev, args, prec_name, steps, warmup, world=1, with_e2e=
     plan = S.soft_create_batch([w["n"] for w in ws], [(w["a"], w["b"]) for w in ws],
                                [w["R0"] for w in ws], [w["theta"] for w in ws],
                                [(w["E0"], w["omega"], w["ncyc"]) for w in ws], W2_DT,
-                               prec=prec, contour=ws[0]["contour"], persistent=persistent, autotune=1)
+                               prec=prec, contour=ws[0]["contour"], persistent=persistent, autotune=autotune)
     offs, total = S.soft_batch_layout(plan)
     h0 = np.concatenate([w["psi0"] for w in ws]).astype(cdt_np)
     state = torch.from_numpy(h0).to(dev)
@@ -618,9 +618,16 @@ def measure_w2(S, torch, dev, args, prec_name, steps, warmup, world=1, with_e2e=
     clocks = clk.stop()
     ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     kms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    # the plan's schedule (the autotuner keeps the faster): 3 launches per
+    # call with the persistent kernel (pulse table, kernel, time advance),
+    # 2 + one per size group otherwise
+    nsizes = len(set(ns))
+    sched = ("soft1d_persist_kernel" if launches == 3 and nsizes > 1 else
+             "soft1d_kernel x %d size groups" % nsizes)
     out = {"value": whole_job_value(pts_call, steps, world, ms), "ms_per_step": ms / steps,
            "call_ms": kms, "flops_per_call": flops_call, "gpu_launches": int(launches * steps),
-           "clocks": clocks, "points": int(total), "instances": len(ws)}
+           "clocks": clocks, "points": int(total), "instances": len(ws), "schedule": sched,
+           "steps_per_call": spc}
     if with_e2e:
         hb = torch.from_numpy(h0).pin_memory()
         ob = torch.empty_like(hb).pin_memory()
@@ -655,9 +662,10 @@ def roofline_w2(torch, dev, m, prec_name):
     achieved = m["flops_per_call"] / (m["call_ms"] / 1e3) / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": None,
-            "kernel": "soft1d_persist_kernel, all %d instances, %d steps per launch, %.3f ms per call "
-                      "(graph: pulse table, queue reset, the kernel, time advance)"
-                      % (m["instances"], STEPS_PER_CALL, m["call_ms"]),
+            "kernel": "%s, all %d instances, %d steps per call, %.3f ms per call (graph: pulse table, %s, "
+                      "time advance)" % (m["schedule"], m["instances"], m["steps_per_call"], m["call_ms"],
+                                         "queue reset, the persistent kernel" if m["schedule"].startswith("soft1d_persist")
+                                         else "one soft1d_kernel per size group on parallel branches"),
             "peak_source": "derived: %d SMs x %d %s FMA per clock x 2 x %.0f MHz" % (
                 ap_["sms"], FP32_FMA_PER_SM_CLK if c64 else FP64_FMA_PER_SM_CLK, "FP32" if c64 else "FP64",
                 ap_["sm_max_mhz"]),
@@ -684,6 +692,8 @@ def main():
                     help="run one measurement alone (for profiling captures; not a bench line)")
     ap.add_argument("--persistent", type=int, default=1, choices=[0, 1],
                     help="0: one kernel per size group instead of the persistent kernel (comparison)")
+    ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
+                    help="0: no timing runs at plan creation (profiling captures)")
     ap.add_argument("--pcg-precond", default="1,4,5",
                     help="stationary-solver modes to time (sse_pcg_solve precond values)")
     ap.add_argument("--pcg-energies", type=int, default=0,
@@ -702,7 +712,7 @@ def main():
             r = {"derived": alu_peaks(torch, 0), "probe": alu_probe()}
         elif args.only == "w2":
             r = measure_w2(S, torch, dev, args, args.prec, args.steps, args.warmup, with_e2e=False,
-                           persistent=args.persistent)
+                           persistent=args.persistent, autotune=args.autotune)
             r["roofline"] = roofline_w2(torch, dev, r, args.prec)
         else:
             fn = {"2d": bench_2d, "pcg": bench_pcg, "learned": bench_learned, "conv": bench_conv,
