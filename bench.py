@@ -566,6 +566,27 @@ def bench_pcg1d(S, torch, dev, args):
         res[name] = {"status": rc, "iterations_mean": float(np.mean(its)), "iterations_max": int(max(its)),
                      "seconds": sec, "solves_per_s": len(Es) / sec, "max_relres": float(max(rr)),
                      "paper_iterations": g["claims"]["pcg_iterations_" + name]}
+        if name != "tfap":
+            # the whole t&E-SURFF extraction: sampled propagation to t_max,
+            # the 30 solves, the amplitudes (Filon-Simpson); error against
+            # Eq. Ateor for 1 <= |k| <= 6
+            nst = int(round(g["t_max"] / tau))
+            samp = torch.zeros((nst + 1, 4), dtype=torch.complex128, device=dev)
+            d2 = torch.tensor(psi0, dtype=torch.complex128, device=dev)
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(st)
+            S.soft_step_surface(plan, d2, nst, 0.0, samp, stream=st)
+            S.sse_pcg_solve(plan, Es, d2, out, tol=g["pcg_tolerance"], maxit=2000, precond=1, stream=st)
+            amp = S.sse_surff(plan, Es, out, samp, t0=0.0, rule=1, stream=st)
+            b_.record(st)
+            torch.cuda.synchronize()
+            ks = np.array([math.sqrt(2 * E) for E in Es])
+            a_np = amp.cpu().numpy()
+            sel = ks >= 1.0 - 1e-9
+            ate = lambda k: math.pi ** -0.25 * np.exp(-(k - v0) ** 2 / 2)
+            err = max(np.abs(a_np[sel, 0] - ate(ks[sel])).max(), np.abs(a_np[sel, 1] - ate(-ks[sel])).max())
+            res[name]["tE_SURFF"] = {"seconds": a_.elapsed_time(b_) / 1e3, "steps": nst, "amplitudes": 2 * len(Es),
+                                     "max_error_vs_Ateor_1_le_absk_le_6": float(err)}
         S.soft_destroy(plan)
     res["setup"] = ("N = 1024, [-51.2, 51.2], r_s = 40, 30 energies k = 0.2 .. 6, banded preconditioner "
                     "N_l = 10, tolerance 1e-12, one launch for all energies (one CTA per energy)")

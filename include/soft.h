@@ -189,6 +189,41 @@ int soft_observe(const soft_plan* plan, const void* psi, double* norm_in, double
  * themselves never wait for the device, so they cannot report it. */
 int soft_step_status(soft_plan* plan, void* stream);
 
+/* soft_step_surface -- soft_step on a single 1D complex128 plan (N = 256 ..
+ * 8192) that also samples the wave function at the two boundaries
+ * x = +R0 and x = -R0 of the unscaled region after every step: the
+ * quantities the amplitude extraction of the paper's test draws from the
+ * propagation (t-SURFF part of t&E-SURFF, Sec. I and Sec. IV).  psi and
+ * dpsi/dx there are those of the trigonometric interpolant of the grid
+ * function (the FFT representation of Sec. II), taken from the spectrum
+ * inside the step kernel.
+ *   samples  device complex128 [nsteps + 1][4]: psi(R0), psi'(R0), psi(-R0),
+ *            psi'(-R0) at t_inout + s dt, s = 0 .. nsteps.
+ * Other arguments as soft_step.  SOFT_ERR_UNSUPPORTED for other plans. */
+int soft_step_surface(soft_plan* plan, void* psi, int64_t nsteps, const soft_field* field,
+                      double* t_inout, void* samples, void* stream);
+
+/* sse_surff -- momentum amplitudes by t&E-SURFF (Sec. I, Sec. IV) for a
+ * packet that is free beyond R0, for nE energies at once: with
+ * k = sqrt(2 E) and T = t0 + (nsamples - 1) dt,
+ *   A(+-k) = -+ (i/2) (2 pi)^-1/2 e^{-+ik R0} [ int_t0^T e^{iEt} g(t) dt
+ *            + i e^{iET} (phi' +- ik phi)(+-R0) ],   g = psi' +- ik psi at +-R0,
+ * where (E - H) phi = psi(T): the flux through the boundary up to T
+ * (t-SURFF) plus the rest of the packet through the stationary equation
+ * with right-hand side psi(T) (E-SURFF, the SSE of Sec. III).
+ *   E        host double[nE], E > 0.
+ *   phi      device complex128 [nE][N]: the solutions of A phi_A = psi(T)
+ *            that sse_pcg_solve returns (A = H - E, so phi = -phi_A).
+ *   samples  device, from soft_step_surface: nsamples rows, nsamples - 1
+ *            even; the first at time t0.
+ *   rule     0: Simpson's rule; 1: Filon-Simpson (e^{iEt} times the
+ *            quadratic interpolant of g on each pair of steps, exact in
+ *            the exponential; Sec. IV recommends it for large |k|).
+ *   amp      device complex128 [nE][2]: A(+k), A(-k).
+ * Single 1D complex128 plans (N = 256 .. 8192). */
+int sse_surff(soft_plan* plan, int nE, const double* E, const void* phi, const void* samples,
+              int64_t nsamples, double t0, int rule, void* amp, void* stream);
+
 /* soft_set_potential -- replace the static potential of a single 1D plan or
  * a 2D plan.  It enters the step as e^{-iU tau/2} (Sec. II, the scheme
  * after Eq. C_FD) and A as U - E (Sec. III, Eq. linsys); the default is the

@@ -554,6 +554,7 @@ soft_plan::~soft_plan() {
     cudaFree(d_t0);
     delete nn;
     sse1d_free(s1);
+    surf1d_free(sf);
     if (gexec) cudaGraphExecDestroy(gexec);
     if (side_ready) {
         for (size_t g = 0; g < groups.size() && g < MAX_SIDE; ++g) {

@@ -26,6 +26,8 @@ struct Geo2D;
 struct NNState;
 struct Sse1D;
 void sse1d_free(Sse1D* s);
+struct Surf1D;
+void surf1d_free(Surf1D* s);
 int sse1d_refill_potential(soft_plan* P);
 int sse1d_solve(soft_plan* P, const double* E, int nE, const void* rhs, void* psi_out, double tol, int maxit,
                 int precond, int* iters_out, double* relres_out, cudaStream_t st);
@@ -120,6 +122,7 @@ struct soft_plan {
     int time_schedules();
     int step_1d(void* psi, int64_t nsteps, double* t_inout, cudaStream_t st);
     soft::Sse1D* s1 = nullptr;     // stationary solver of a single 1D plan (sse1d.cu)
+    soft::Surf1D* sf = nullptr;    // surface-sampling tables (soft1d_surf.cu)
 
     // ---- 2D (plan2d.cu), learned correction (nn.cu)
     soft::Plan2D* p2 = nullptr;

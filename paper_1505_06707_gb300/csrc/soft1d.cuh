@@ -445,9 +445,14 @@ __device__ __forceinline__ void inv_passes(typename CT<R>::C* S, const TW* Ws, i
 // last forward pass (stride 1, no twiddles), the k-space table, the first
 // inverse pass: butterfly b owns the R consecutive points b*R + m of the
 // digit-reversed spectrum, whose factors the table holds at m*(N/R) + b
-template <typename R, int LOGN, int LOGE, int LOGRM>
+//
+// With SURF, the spectrum entering the k-space factor is also contracted with
+// four weight rows sw[r * N + q] (same transposed index q as the table) into
+// acc[r] (surface sampling, soft1d_surf_kernel).
+template <typename R, int LOGN, int LOGE, int LOGRM, bool SURF = false>
 __device__ __forceinline__ void kcenter(typename CT<R>::C* S, const typename TabT<R>::T* __restrict__ tab,
-                                        int tid) {
+                                        int tid, const typename CT<R>::C* __restrict__ sw = nullptr,
+                                        typename CT<R>::C* acc = nullptr) {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
     using C = typename K::C;
     using G = PassGeom<LOGN, LOGRM, K::NPASS - 1>;
@@ -484,6 +489,14 @@ __device__ __forceinline__ void kcenter(typename CT<R>::C* S, const typename Tab
 #pragma unroll
         for (int j = 0; j < RR; ++j) v[j] = S[sb ^ swz<C>(j)];
         dft_reg<C, RR, -1>(v);
+        if constexpr (SURF) {
+#pragma unroll
+            for (int m = 0; m < RR; ++m) {
+                const int q = m * (K::N / RR) + tid + u * K::T;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) acc[r] = cfma(v[bitrev_c(m, LOGR)], __ldg(&sw[r * K::N + q]), acc[r]);
+            }
+        }
         C w[RR];
 #pragma unroll
         for (int m = 0; m < RR; ++m) w[m] = tmul(v[bitrev_c(m, LOGR)], tc[m]);
@@ -603,6 +616,32 @@ __device__ __forceinline__ C strip_field(const C* fr, R al, const Inst1D& I, int
     return field_direct<R, C>(al, I.x0, I.h, n);
 }
 
+// Sum of four complex values over the group; thread 0 writes them to out.
+// scratch: 4 * (T/32) complex (the scan scratch, free at this point).
+template <typename C, int T, class B>
+__device__ __forceinline__ void surf_reduce(C (&acc)[4], C* scratch, int tid, B bar, C* __restrict__ out) {
+    static_assert(T / 32 <= 16, "scratch of 64 complex");
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc[r].x += __shfl_xor_sync(0xffffffffu, acc[r].x, o);
+            acc[r].y += __shfl_xor_sync(0xffffffffu, acc[r].y, o);
+        }
+    if ((tid & 31) == 0)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) scratch[4 * (tid >> 5) + r] = acc[r];
+    bar.sync();
+    if (tid == 0) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            C t = cmk<C>(0, 0);
+            for (int w = 0; w < (T + 31) / 32; ++w) t = cadd(t, scratch[4 * w + r]);
+            out[r] = t;
+        }
+    }
+}
+
 // shared-memory bytes of one instance's private part: the state (unless
 // GM), 64 complex of scan scratch and E + 36 field phases
 template <typename R, int LOGN, int LOGE, int LOGRM>
@@ -616,12 +655,18 @@ __host__ __device__ constexpr size_t soft1d_inst_smem() {
 // (unused with GM); scan: 64 complex of scan scratch followed by E + 36
 // field phases; Ws: the twiddle bases, already in shared memory and visible
 // to the group by its first barrier.
-template <typename R, int LOGN, int LOGE, int LOGRM, class B>
+//
+// SURF: sample psi and psi' at the two surfaces into samples[0 ..
+// nsteps][4] (soft1d_surf_kernel; sw holds two sets of four weight rows:
+// for the state at the call's start and, with the half kinetic factor
+// e^{-iK tau/2} folded in, for the state after each step).
+template <typename R, int LOGN, int LOGE, int LOGRM, class B, bool SURF = false>
 __device__ __forceinline__ void soft1d_run(const Inst1D& I, void* __restrict__ psi_base, int64_t nsteps,
                                            const double* __restrict__ ftab_base, int64_t ftab_stride,
                                            int* __restrict__ status, typename CT<R>::C* Ss,
                                            typename CT<R>::C* scan, const typename TwT<R>::T* Ws, int tid,
-                                           B bar)
+                                           B bar, const typename CT<R>::C* __restrict__ sw = nullptr,
+                                           typename CT<R>::C* __restrict__ samples = nullptr)
 {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
     using C = typename K::C;
@@ -681,7 +726,16 @@ __device__ __forceinline__ void soft1d_run(const Inst1D& I, void* __restrict__ p
         //      and last pass of the call), inverse FFT, potential of the next step
         const bool more = step + 1 < nsteps;
         fwd_passes<R, LOGN, LOGE, LOGRM, 0, K::NPASS - 1>(S, Ws, tid, bar);
-        kcenter<R, LOGN, LOGE, LOGRM>(S, (step >= 0 && more) ? TK : TKh, tid);
+        if constexpr (SURF) {
+            C acc[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[r] = cmk<C>(0, 0);
+            kcenter<R, LOGN, LOGE, LOGRM, true>(S, (step >= 0 && more) ? TK : TKh, tid,
+                                                sw + (step >= 0 ? 4 * N : 0), acc);
+            surf_reduce<C, T>(acc, scan, tid, bar, samples + 4 * (step + 1));
+        } else {
+            kcenter<R, LOGN, LOGE, LOGRM>(S, (step >= 0 && more) ? TK : TKh, tid);
+        }
         if (more && I.has_field) {
             al = alpha(step + 1);
             field_setup<R, LOGN, LOGE, LOGRM>(fr, al, I, tid);
@@ -733,6 +787,46 @@ soft1d_kernel(const Inst1D* __restrict__ insts, void* __restrict__ psi_base, int
     // the run's first barrier (after its state load) also covers the twiddles
     soft1d_run<R, LOGN, LOGE, LOGRM>(I, psi_base, nsteps, ftab_base, ftab_stride, status, Ss,
                                      reinterpret_cast<C*>(Ws + Q::TWN), Ws, (int)threadIdx.x, BarCTA());
+}
+
+// One instance (blockIdx.x 0) with surface sampling: samples[s][r] for the
+// state at the call's start plus s steps, rows psi(R), psi'(R), psi(-R),
+// psi'(-R) (sw: the eight weight rows, see soft1d_run).
+template <typename R, int LOGN, int LOGE, int LOGRM>
+__global__ void __launch_bounds__(Cfg1D<R, LOGN, LOGE, LOGRM>::T, Cfg1D<R, LOGN, LOGE, LOGRM>::MINB)
+soft1d_surf_kernel(const Inst1D* __restrict__ insts, void* __restrict__ psi_base, int64_t nsteps,
+                   const double* __restrict__ ftab_base, int64_t ftab_stride, int* __restrict__ status,
+                   const void* __restrict__ sw, void* __restrict__ samples)
+{
+    using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
+    using Q = Step1D<R, LOGN, LOGRM>;
+    using C = typename K::C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using TWT = typename TwT<R>::T;
+    C* Ss = reinterpret_cast<C*>(smem_raw);
+    TWT* Ws = reinterpret_cast<TWT*>(Ss + (K::GM ? 0 : K::N));
+    const Inst1D I = insts[0];
+    const TWT* __restrict__ W = reinterpret_cast<const TWT*>(I.W);
+    if (nsteps <= 0) return;
+    for (int i = threadIdx.x; i < Q::TWN; i += K::T) Ws[i] = __ldg(&W[i]);
+    soft1d_run<R, LOGN, LOGE, LOGRM, BarCTA, true>(I, psi_base, nsteps, ftab_base, ftab_stride, status, Ss,
+                                                   reinterpret_cast<C*>(Ws + Q::TWN), Ws, (int)threadIdx.x,
+                                                   BarCTA(), reinterpret_cast<const C*>(sw),
+                                                   reinterpret_cast<C*>(samples));
+}
+
+template <typename R, int LOGN, int LOGE, int LOGRM>
+int launch_soft1d_surf_t(const Inst1D* d_inst, void* psi, int64_t nsteps, const double* ftab, int64_t ftab_stride,
+                         int* d_status, const void* sw, void* samples, cudaStream_t st)
+{
+    using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
+    auto kern = soft1d_surf_kernel<R, LOGN, LOGE, LOGRM>;
+    const size_t smem = soft1d_smem<R, LOGN, LOGE, LOGRM>();
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return SOFT_ERR_CUDA;
+    kern<<<1, K::T, smem, st>>>(d_inst, psi, nsteps, ftab, ftab_stride, d_status, sw, samples);
+    return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
 }
 
 template <typename R, int LOGN, int LOGE, int LOGRM>

@@ -15,7 +15,7 @@ __all__ = [
     "ABSORB_CAP", "ABSORB_TFAP",
     "load", "lib_path", "exported_symbols", "Options", "Field", "soft_create", "soft_create_batch",
     "soft_batch_layout", "soft_step", "soft_step_batch", "soft_step_noalloc", "soft_step_status",
-    "soft_observe",
+    "soft_step_surface", "sse_surff", "soft_observe",
     "soft_set_potential", "sse_pcg_solve",
     "sse_apply_A", "sse_apply_A32", "sse_apply_precond", "soft_destroy", "sse_nn_set_weights", "sse_nn_get_weights",
     "sse_nn_forward", "sse_nn_grad", "sse_nn_train", "NN_PARAMS", "soft_plan_points", "soft_plan_count",
@@ -36,7 +36,8 @@ exported_symbols = [
     "soft_default_options", "soft_create", "soft_create_batch", "soft_batch_layout", "soft_step",
     "soft_step_batch", "soft_observe", "soft_set_potential", "sse_pcg_solve", "sse_apply_A", "sse_apply_A32",
     "sse_apply_precond", "soft_destroy", "soft_strerror", "soft_plan_count", "soft_plan_points", "soft_plan_prec",
-    "soft_last_launches", "soft_step_noalloc", "soft_step_status", "sse_nn_set_weights", "sse_nn_get_weights",
+    "soft_last_launches", "soft_step_noalloc", "soft_step_status", "soft_step_surface", "sse_surff",
+    "sse_nn_set_weights", "sse_nn_get_weights",
     "sse_nn_forward", "sse_nn_grad", "sse_nn_train",
 ]
 
@@ -90,6 +91,8 @@ def load():
     L.soft_step_batch.argtypes = [P, P, i64, C.POINTER(dbl), P]
     L.soft_step_noalloc.argtypes = [P, P, i64, C.POINTER(Field), C.POINTER(dbl), P]
     L.soft_step_status.argtypes = [P, P]
+    L.soft_step_surface.argtypes = [P, P, i64, C.POINTER(Field), C.POINTER(dbl), P, P]
+    L.sse_surff.argtypes = [P, C.c_int, C.POINTER(dbl), P, P, i64, dbl, C.c_int, P, P]
     L.soft_observe.argtypes = [P, P, P, P, P]
     L.soft_set_potential.argtypes = [P, P, i64]
     L.sse_pcg_solve.argtypes = [P, C.POINTER(dbl), C.c_int, P, P, dbl, C.c_int, C.c_int,
@@ -237,6 +240,30 @@ def soft_step_status(plan, stream=None):
     """Wait for the stream; raise SoftError(NONFINITE) if a step of this 1D
     plan has produced a non-finite state since the last query."""
     _check(load().soft_step_status(plan, _stream(stream)), "soft_step_status")
+
+
+def soft_step_surface(plan, psi, nsteps, t, samples, field=None, stream=None):
+    """soft_step that also writes psi, dpsi/dx at +R0 and -R0 after every step
+    into samples (device complex128 [nsteps + 1][4]).  Returns the time."""
+    tt = C.c_double(t)
+    F = Field(*field) if field is not None else None
+    _check(load().soft_step_surface(plan, _ptr(psi), int(nsteps), C.byref(F) if F is not None else None,
+                                    C.byref(tt), _ptr(samples), _stream(stream)), "soft_step_surface")
+    return tt.value
+
+
+def sse_surff(plan, E, phi, samples, t0=0.0, rule=1, amp=None, stream=None):
+    """t&E-SURFF amplitudes A(+k), A(-k) for k = sqrt(2E); phi: device
+    complex128 [nE][N] from sse_pcg_solve with right-hand side psi(T);
+    samples from soft_step_surface.  Returns the device array amp [nE][2]."""
+    import torch
+    nE = len(E)
+    if amp is None:
+        amp = torch.zeros((nE, 2), dtype=torch.complex128, device=phi.device)
+    Ea = (C.c_double * nE)(*E)
+    _check(load().sse_surff(plan, nE, Ea, _ptr(phi), _ptr(samples), int(samples.shape[0]), float(t0),
+                            int(rule), _ptr(amp), _stream(stream)), "sse_surff")
+    return amp
 
 
 def soft_observe(plan, psi, norm_in, flux, stream=None):
