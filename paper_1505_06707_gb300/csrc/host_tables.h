@@ -36,6 +36,7 @@ int strip_factor(const Axis1D& A, int blk0, int nb, std::vector<cd>& mf, std::ve
                  std::vector<cd>& g, double* check_err);
 std::vector<int> dif_output_order(int logn, int logrm);
 std::vector<cd> pass_twiddles(int logn, int logrm);
+std::vector<cd> pass_twiddles_full(int logn, int logrm, int full_maxs);
 cd soft_coulomb(const cd* z, int nd, double a2, double Z);
 
 }  // namespace soft

@@ -51,6 +51,10 @@ struct Tables1D {
     void* TVs = nullptr;
 };
 
+// Complex128 1D step plans store every pass twiddle W^{M off} for passes of
+// stride up to this (the bases above it), see soft1d.cuh.
+constexpr int TWFULL_MAXS = 256;
+
 // Work item of the persistent batch kernel: up to G instances of one size.
 struct Pack1D {
     int var;      // variant index in the kernel's list

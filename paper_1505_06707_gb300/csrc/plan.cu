@@ -219,7 +219,11 @@ int make_tables_1d(Tables1D* T, int n, double a, double b, double R0, double the
     if ((rc = upload_tab(&T->TK, tk, o.prec))) return rc;
     if ((rc = upload_tab(&T->TKh, tkh, o.prec))) return rc;
     if ((rc = upload_vtab(&T->TV, tv, o.prec))) return rc;
-    if ((rc = upload_tw_comp(&T->W, w, o.prec))) return rc;
+    if (o.prec == SOFT_C128)   // every twiddle of the small-stride passes (see soft1d.cuh, TwFullD)
+        rc = upload_c(&T->W, pass_twiddles_full(logn, logrm, TWFULL_MAXS), o.prec);
+    else
+        rc = upload_tw_comp(&T->W, w, o.prec);
+    if (rc) return rc;
     if ((rc = upload_c(&T->cn, cnv, o.prec))) return rc;
     if ((rc = upload_vtab(&T->TVs, tvs, o.prec))) return rc;
     return SOFT_OK;

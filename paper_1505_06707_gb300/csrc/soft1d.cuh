@@ -64,9 +64,17 @@ __device__ __forceinline__ float2 tmulc(float2 x, float4 t) {
 // same position, that modulus error returns unchanged in every step and the
 // state drifts linearly in time.  With compensated factors the modulus is
 // exact to ~2^-48 and only the data's own roundings remain.
+// Complex128 plans of the 1D step store, for passes with a stride of at
+// most TWFULL_MAXS, every twiddle W^{M off} (M = 1 .. R-1) instead of the
+// four bases: the products of bases cost 16 of the ~100 FP64 instructions
+// of a radix-8 butterfly, and the kernel is bound by the FP64 pipe.  Passes
+// with a larger stride keep the bases (their full table would not fit in
+// shared memory).
+struct TwFullD { double2 v; };
+
 template <typename R> struct TwT;
 template <> struct TwT<float> { using T = float4; };
-template <> struct TwT<double> { using T = double2; };
+template <> struct TwT<double> { using T = TwFullD; };
 
 template <typename R, int LOGN, int LOGE, int LOGRM>
 struct Cfg1D {
@@ -119,11 +127,29 @@ __device__ __forceinline__ C tw_pow(const C* b) {
 // y * W^{M off} (fwd) and y * conj(W^{M off}) (inv) from the bases b[k] =
 // W^{2^k off}: plain bases (TW = C) through one product twiddle, compensated
 // FP32 bases (TW = float4) by one compensated multiply per set bit of M
-template <typename C, typename TW, int M> struct TwMul {
+template <typename C, typename TW, int M, bool FULL = false> struct TwMul {
     __device__ __forceinline__ static C fwd(C y, const C* b) { return cmul(y, tw_pow<C, M>(b)); }
     __device__ __forceinline__ static C inv(C y, const C* b) { return cmulc(y, tw_pow<C, M>(b)); }
 };
-template <int M> struct TwMul<float2, float4, M> {
+// complex128 tables: full passes hold b[M - 1] = W^{M off}; the other
+// passes hold W^{M off} for M = 1 .. 4, and W^{M off} = W^{4 off} W^{(M-4) off}
+// above (radix <= 8: one product instead of up to two)
+template <int M> __device__ __forceinline__ double2 tw_d(const TwFullD* b) {
+    static_assert(M >= 1 && M < 8, "complex128 passes have radix <= 8");
+    if constexpr (M <= 4) return b[M - 1].v;
+    else return cmul(b[3].v, b[M - 5].v);
+}
+template <int M, bool FULL> struct TwMul<double2, TwFullD, M, FULL> {
+    __device__ __forceinline__ static double2 fwd(double2 y, const TwFullD* b) {
+        if constexpr (FULL) return cmul(y, b[M - 1].v);
+        else return cmul(y, tw_d<M>(b));
+    }
+    __device__ __forceinline__ static double2 inv(double2 y, const TwFullD* b) {
+        if constexpr (FULL) return cmulc(y, b[M - 1].v);
+        else return cmulc(y, tw_d<M>(b));
+    }
+};
+template <int M, bool FULL> struct TwMul<float2, float4, M, FULL> {
     __device__ __forceinline__ static float2 fwd(float2 y, const float4* b) {
         if constexpr ((M & 1) != 0) y = tmul(y, b[0]);
         if constexpr ((M & 2) != 0) y = tmul(y, b[1]);
@@ -142,23 +168,23 @@ template <int M> struct TwMul<float2, float4, M> {
 
 // The element M of a butterfly lives at base + M s; the callers pass
 // sb = swz(base) and the offset of element M is the constant swz(M s).
-template <typename C, typename TW, int RR, int SS, int M>
+template <typename C, typename TW, int RR, int SS, int M, bool FULL = false>
 struct StoreFwd {   // y_M = v[bitrev(M)] * W^{M off}, stored at base + M s
     __device__ __forceinline__ static void run(C* S, const C* v, const TW* b, int sb, bool tw) {
         constexpr int LOGR = (RR == 16) ? 4 : (RR == 8) ? 3 : (RR == 4) ? 2 : (RR == 2) ? 1 : 0;
         C y = v[bitrev_c(M, LOGR)];
-        if constexpr (M > 0) { if (tw) y = TwMul<C, TW, M>::fwd(y, b); }
+        if constexpr (M > 0) { if (tw) y = TwMul<C, TW, M, FULL>::fwd(y, b); }
         S[sb ^ swz<C>(M * SS)] = y;
-        if constexpr (M + 1 < RR) StoreFwd<C, TW, RR, SS, M + 1>::run(S, v, b, sb, tw);
+        if constexpr (M + 1 < RR) StoreFwd<C, TW, RR, SS, M + 1, FULL>::run(S, v, b, sb, tw);
     }
 };
-template <typename C, typename TW, int RR, int SS, int M>
+template <typename C, typename TW, int RR, int SS, int M, bool FULL = false>
 struct LoadInv {    // v_M = S[base + M s] * conj(W^{M off})
     __device__ __forceinline__ static void run(const C* S, C* v, const TW* b, int sb, bool tw) {
         C y = S[sb ^ swz<C>(M * SS)];
-        if constexpr (M > 0) { if (tw) y = TwMul<C, TW, M>::inv(y, b); }
+        if constexpr (M > 0) { if (tw) y = TwMul<C, TW, M, FULL>::inv(y, b); }
         v[M] = y;
-        if constexpr (M + 1 < RR) LoadInv<C, TW, RR, SS, M + 1>::run(S, v, b, sb, tw);
+        if constexpr (M + 1 < RR) LoadInv<C, TW, RR, SS, M + 1, FULL>::run(S, v, b, sb, tw);
     }
 };
 template <typename C, int RR, int SS, int M>
@@ -175,14 +201,53 @@ struct StoreNat {   // x_M = v[bitrev(M)] stored at base + M s
 template <typename C, int NB, int ST, bool SH>
 __device__ __forceinline__ void load_tw(C* b, const C* __restrict__ t) {
 #pragma unroll
-    for (int k = 0; k < NB; ++k) b[k] = SH ? t[k * ST] : __ldg(&t[k * ST]);
+    for (int k = 0; k < NB; ++k) {
+        if constexpr (SH) b[k] = t[k * ST];
+        else b[k] = __ldg(&t[k * ST]);
+    }
 }
+
+// Twiddle table layout of a pass: offsets and whether the pass stores every
+// W^{M off} (FULL) or the four bases, for twiddle type TW.
+template <int LOGN, int LOGRM, int P>
+struct TwGeomFull {
+    using G = PassGeom<LOGN, LOGRM, P>;
+    static constexpr bool FULL = G::S > 1 && G::S <= TWFULL_MAXS;
+    static constexpr int ROWS = FULL ? (1 << G::LOGR) - 1 : 4;
+    static constexpr int TOFF = TwGeomFull<LOGN, LOGRM, P - 1>::TOFF +
+                                TwGeomFull<LOGN, LOGRM, P - 1>::ROWS * PassGeom<LOGN, LOGRM, P - 1>::S;
+};
+template <int LOGN, int LOGRM>
+struct TwGeomFull<LOGN, LOGRM, -1> { static constexpr bool FULL = false; static constexpr int ROWS = 0, TOFF = 0; };
+
+template <typename TW> struct TwLay {      // the four bases W^{2^k off} on every pass
+    template <int LOGN, int LOGRM, int P> static constexpr bool full() { return false; }
+    template <int LOGN, int LOGRM, int P> static constexpr int toff() { return PassGeom<LOGN, LOGRM, P>::TOFF; }
+    template <int LOGN, int LOGRM, int P> static constexpr int rows() { return PassGeom<LOGN, LOGRM, P>::LOGR; }
+};
+template <> struct TwLay<TwFullD> {       // every W^{M off}, or M = 1 .. 4 (tw_d)
+    template <int LOGN, int LOGRM, int P> static constexpr bool full() { return TwGeomFull<LOGN, LOGRM, P>::FULL; }
+    template <int LOGN, int LOGRM, int P> static constexpr int toff() { return TwGeomFull<LOGN, LOGRM, P>::TOFF; }
+    template <int LOGN, int LOGRM, int P> static constexpr int rows() {
+        constexpr int R = 1 << PassGeom<LOGN, LOGRM, P>::LOGR;
+        return TwGeomFull<LOGN, LOGRM, P>::FULL ? R - 1 : (R - 1 < 4 ? R - 1 : 4);
+    }
+};
 
 // number of twiddle entries of all passes
 template <int LOGN, int LOGRM>
 struct TwCount {
     static constexpr int NP = LOGN / LOGRM + ((LOGN % LOGRM) ? 1 : 0);
     static constexpr int value = PassGeom<LOGN, LOGRM, NP - 1>::TOFF + 4 * PassGeom<LOGN, LOGRM, NP - 1>::S;
+};
+// the same for the table layout of twiddle type TW
+template <typename TW, int LOGN, int LOGRM>
+struct TwCountT { static constexpr int value = TwCount<LOGN, LOGRM>::value; };
+template <int LOGN, int LOGRM>
+struct TwCountT<TwFullD, LOGN, LOGRM> {
+    static constexpr int NP = LOGN / LOGRM + ((LOGN % LOGRM) ? 1 : 0);
+    static constexpr int value = TwGeomFull<LOGN, LOGRM, NP - 1>::TOFF +
+                                 TwGeomFull<LOGN, LOGRM, NP - 1>::ROWS * PassGeom<LOGN, LOGRM, NP - 1>::S;
 };
 
 // forward DIF pass P (radix 2^LOGR on sub-transforms of length 2^LOGL)
@@ -204,9 +269,12 @@ __device__ __forceinline__ void fwd_pass(typename CT<R>::C* S, const TW* __restr
 #pragma unroll
         for (int j = 0; j < RR; ++j) v[j] = S[sb ^ swz<C>(j * s)];
         dft_reg<C, RR, -1>(v);
-        TW tb[4];
-        if constexpr (s > 1) load_tw<TW, NB, s, SH>(tb, W + G::TOFF + off);
-        StoreFwd<C, TW, RR, s, 0>::run(S, v, tb, sb, s > 1);
+        constexpr bool FULL = TwLay<TW>::template full<LOGN, LOGRM, P>();
+        TW tb[FULL ? RR - 1 : 4];
+        if constexpr (s > 1)
+            load_tw<TW, TwLay<TW>::template rows<LOGN, LOGRM, P>(), s, SH>(
+                tb, W + TwLay<TW>::template toff<LOGN, LOGRM, P>() + off);
+        StoreFwd<C, TW, RR, s, 0, FULL>::run(S, v, tb, sb, s > 1);
     }
 }
 
@@ -226,9 +294,12 @@ __device__ __forceinline__ void inv_pass(typename CT<R>::C* S, const TW* __restr
         const int blk = b / s, off = b & (s - 1);
         const int sb = swz<C>(blk * L + off);
         C v[RR];
-        TW tb[4];
-        if constexpr (s > 1) load_tw<TW, NB, s, SH>(tb, W + G::TOFF + off);
-        LoadInv<C, TW, RR, s, 0>::run(S, v, tb, sb, s > 1);
+        constexpr bool FULL = TwLay<TW>::template full<LOGN, LOGRM, P>();
+        TW tb[FULL ? RR - 1 : 4];
+        if constexpr (s > 1)
+            load_tw<TW, TwLay<TW>::template rows<LOGN, LOGRM, P>(), s, SH>(
+                tb, W + TwLay<TW>::template toff<LOGN, LOGRM, P>() + off);
+        LoadInv<C, TW, RR, s, 0, FULL>::run(S, v, tb, sb, s > 1);
         dft_reg<C, RR, +1>(v);
         StoreNat<C, RR, s, 0>::run(S, v, sb);
     }
@@ -411,18 +482,19 @@ __device__ __forceinline__ void sincos_r(double a, double* s, double* c) { sinco
 template <typename R, int LOGN, int LOGRM>
 struct Step1D {
     static constexpr int NPASS = LOGN / LOGRM + ((LOGN % LOGRM) ? 1 : 0);
-    static constexpr int TWN = TwCount<LOGN, LOGRM>::value;
+    static constexpr int TWN = TwCountT<typename TwT<R>::T, LOGN, LOGRM>::value;
     static constexpr int LOGR0 = PassGeom<LOGN, LOGRM, 0>::LOGR;   // radix of pass 0
     static constexpr int R0 = 1 << LOGR0;
 };
 
 // shared-memory bytes of soft1d_kernel: state, twiddles, scan scratch, field
-// phases (E per-butterfly, 16 per-output, 4 clamped, 16 strip rows inside R0)
+// phases (E per-butterfly, 16 per-output, 4 clamped, 16 strip rows inside R0,
+// 16 per-output squares)
 template <typename R, int LOGN, int LOGE, int LOGRM>
 __host__ __device__ constexpr size_t soft1d_smem() {
     return sizeof(typename CT<R>::C) *
-               ((Cfg1D<R, LOGN, LOGE, LOGRM>::GM ? 0 : (size_t(1) << LOGN)) + 64 + (size_t(1) << LOGE) + 36) +
-           sizeof(typename TwT<R>::T) * TwCount<LOGN, LOGRM>::value + 64;
+               ((Cfg1D<R, LOGN, LOGE, LOGRM>::GM ? 0 : (size_t(1) << LOGN)) + 64 + (size_t(1) << LOGE) + 52) +
+           sizeof(typename TwT<R>::T) * TwCountT<typename TwT<R>::T, LOGN, LOGRM>::value + 64;
 }
 
 template <typename R, int LOGN, int LOGE, int LOGRM, int P, int PEND, typename TW, class B = BarCTA>
@@ -509,7 +581,7 @@ __device__ __forceinline__ void kcenter(typename CT<R>::C* S, const typename Tab
 // Field phases of one step, alpha = tau E(t + tau/2)/2 (the half factor
 // exp(-i alpha x)), at fr[]: [u] = exp(-i alpha u T h) for the butterflies of
 // the last inverse pass (u < E/R0); [E + m] = exp(-i alpha m (N/R0) h) for
-// their outputs (m < R0); [E + 16], [E + 17] = the clamped values beyond +R0
+// their outputs (m < R0) and [E + 36 + m] its square; [E + 16], [E + 17] = the clamped values beyond +R0
 // and -R0; [E + 20 + k] = exp(-i alpha x_n) at n = iL + k and [E + 28 + k] at
 // n = iR - 8 + k (k < 8), the strip rows just inside R0.
 template <typename R, int LOGN, int LOGE, int LOGRM>
@@ -525,8 +597,11 @@ __device__ __forceinline__ void field_setup(typename CT<R>::C* fr, R al, const I
             fr[i] = cmk<C>(cv, sv);
         } else if (i < NB + Q::R0) {
             const int m = i - NB;
-            sincos_r(-al * ((R)(m * (K::N / Q::R0)) * (R)I.h), &sv, &cv);
+            const R ph = -al * ((R)(m * (K::N / Q::R0)) * (R)I.h);
+            sincos_r(ph, &sv, &cv);
             fr[K::E + m] = cmk<C>(cv, sv);
+            sincos_r(2 * ph, &sv, &cv);                  // the full step's factor
+            fr[K::E + 36 + m] = cmk<C>(cv, sv);
         } else if (i == NB + Q::R0) {
             sincos_r(-al * (R)I.R0, &sv, &cv);
             fr[K::E + 16] = cmk<C>(cv, sv);      // x >= R0
@@ -570,26 +645,49 @@ __device__ __forceinline__ void inv_pass0_v(typename CT<R>::C* S, const TW* __re
         const int off = tid + u * K::T;        // L = N: a single block
         const int sb = swz<C>(off);
         C v[RR];
-        TW tb[4];
-        if constexpr (s > 1) load_tw<TW, NB, s, true>(tb, Ws + G::TOFF + off);
-        LoadInv<C, TW, RR, s, 0>::run(S, v, tb, sb, s > 1);
+        constexpr bool FULL = TwLay<TW>::template full<LOGN, LOGRM, 0>();
+        TW tb[FULL ? RR - 1 : 4];
+        if constexpr (s > 1)
+            load_tw<TW, TwLay<TW>::template rows<LOGN, LOGRM, 0>(), s, true>(
+                tb, Ws + TwLay<TW>::template toff<LOGN, LOGRM, 0>() + off);
+        LoadInv<C, TW, RR, s, 0, FULL>::run(S, v, tb, sb, s > 1);
         dft_reg<C, RR, +1>(v);
         if (!V) {
             StoreNat<C, RR, s, 0>::run(S, v, sb);
             continue;
         }
-        C fb = ft;
-        if (fld) fb = cmul(ft, fr[u]);
+        C fb = ft, fb2 = ft;
+        if (fld) {
+            fb = cmul(ft, fr[u]);
+            fb2 = cmul(fb, fb);
+        }
 #pragma unroll
         for (int m = 0; m < RR; ++m) {
             const int n = off + m * s;
             C x = vmul(v[bitrev_c(m, LOGR)], __ldg(&TV[n]));
-            if (fld) {        // branch-free, so that the table loads of all m issue early
-                const C fh = cmul(fb, fr[K::E + m]);              // exp(-i alpha x_n)
-                const C ff = cmul(fh, fh);
+            if (fld) {
+                // off the block exp(-2i alpha x_n) from the squared tables; on it
+                // the half factor exp(-i alpha x_n), clamped beyond +-R0.  FP64
+                // (pipe-bound) branches, so that only one factor is formed (a
+                // warp diverges only where it straddles the block's edge); FP32
+                // (issue-bound) forms both, branch-free, so that the table
+                // loads of all m issue early.
                 const bool inb = ((n - blk0) & (N - 1)) < nb;
-                const C fk = n >= iR ? fcR : (n < iL ? fcL : fh);
-                x = cmul(x, inb ? fk : ff);
+                C f;
+                if constexpr (sizeof(R) == 8) {
+                    if (inb) {
+                        const C fh = cmul(fb, fr[K::E + m]);
+                        f = n >= iR ? fcR : (n < iL ? fcL : fh);
+                    } else {
+                        f = cmul(fb2, fr[K::E + 36 + m]);
+                    }
+                } else {
+                    const C fh = cmul(fb, fr[K::E + m]);
+                    const C ff = cmul(fb2, fr[K::E + 36 + m]);
+                    const C fk = n >= iR ? fcR : (n < iL ? fcL : fh);
+                    f = inb ? fk : ff;
+                }
+                x = cmul(x, f);
             }
             S[sb ^ swz<C>(m * s)] = x;
         }
@@ -642,17 +740,25 @@ __device__ __forceinline__ void surf_reduce(C (&acc)[4], C* scratch, int tid, B 
     }
 }
 
+// n 16-byte table entries from global to shared memory by nt threads
+template <typename TT>
+__device__ __forceinline__ void copy16(TT* dst, const TT* __restrict__ src, int n, int t, int nt) {
+    static_assert(sizeof(TT) == 16, "16-byte entries");
+    for (int i = t; i < n; i += nt)
+        reinterpret_cast<float4*>(dst)[i] = __ldg(reinterpret_cast<const float4*>(src) + i);
+}
+
 // shared-memory bytes of one instance's private part: the state (unless
-// GM), 64 complex of scan scratch and E + 36 field phases
+// GM), 64 complex of scan scratch and E + 52 field phases
 template <typename R, int LOGN, int LOGE, int LOGRM>
 __host__ __device__ constexpr size_t soft1d_inst_smem() {
     return sizeof(typename CT<R>::C) *
-           ((Cfg1D<R, LOGN, LOGE, LOGRM>::GM ? 0 : (size_t(1) << LOGN)) + 64 + (size_t(1) << LOGE) + 36);
+           ((Cfg1D<R, LOGN, LOGE, LOGRM>::GM ? 0 : (size_t(1) << LOGN)) + 64 + (size_t(1) << LOGE) + 52);
 }
 
 // All nsteps steps of one instance, run by the T threads of a group (tid =
 // index in the group, bar = its barrier).  Ss: the state in shared memory
-// (unused with GM); scan: 64 complex of scan scratch followed by E + 36
+// (unused with GM); scan: 64 complex of scan scratch followed by E + 52
 // field phases; Ws: the twiddle bases, already in shared memory and visible
 // to the group by its first barrier.
 //
@@ -673,7 +779,7 @@ __device__ __forceinline__ void soft1d_run(const Inst1D& I, void* __restrict__ p
     constexpr int N = K::N, T = K::T, E = K::E;
     static_assert(K::NPASS >= 2, "at least two FFT passes");
     static_assert(Step1D<R, LOGN, LOGRM>::R0 <= 16, "pass radix <= 16");
-    C* fr = scan + 64;               // E + 36 complex: field phases (field_setup)
+    C* fr = scan + 64;               // E + 52 complex: field phases (field_setup)
 
     C* __restrict__ g_psi = reinterpret_cast<C*>(psi_base) + I.off;
     // the state: shared memory, or (GM) the instance's buffer itself
@@ -783,7 +889,7 @@ soft1d_kernel(const Inst1D* __restrict__ insts, void* __restrict__ psi_base, int
     const Inst1D I = insts[blockIdx.x];
     const TWT* __restrict__ W = reinterpret_cast<const TWT*>(I.W);
     if (nsteps <= 0) return;
-    for (int i = threadIdx.x; i < Q::TWN; i += K::T) Ws[i] = __ldg(&W[i]);
+    copy16(Ws, W, Q::TWN, threadIdx.x, K::T);
     // the run's first barrier (after its state load) also covers the twiddles
     soft1d_run<R, LOGN, LOGE, LOGRM>(I, psi_base, nsteps, ftab_base, ftab_stride, status, Ss,
                                      reinterpret_cast<C*>(Ws + Q::TWN), Ws, (int)threadIdx.x, BarCTA());
@@ -808,7 +914,7 @@ soft1d_surf_kernel(const Inst1D* __restrict__ insts, void* __restrict__ psi_base
     const Inst1D I = insts[0];
     const TWT* __restrict__ W = reinterpret_cast<const TWT*>(I.W);
     if (nsteps <= 0) return;
-    for (int i = threadIdx.x; i < Q::TWN; i += K::T) Ws[i] = __ldg(&W[i]);
+    copy16(Ws, W, Q::TWN, threadIdx.x, K::T);
     soft1d_run<R, LOGN, LOGE, LOGRM, BarCTA, true>(I, psi_base, nsteps, ftab_base, ftab_stride, status, Ss,
                                                    reinterpret_cast<C*>(Ws + Q::TWN), Ws, (int)threadIdx.x,
                                                    BarCTA(), reinterpret_cast<const C*>(sw),

@@ -38,7 +38,7 @@ struct PVar {
     static constexpr int T = K::T;
     static constexpr int G = PERSIST_THREADS / K::T;
     static_assert(G >= 1 && G <= 8 && G * K::T == PERSIST_THREADS, "groups of a CTA");
-    static constexpr size_t TWB = sizeof(typename TwT<R>::T) * TwCount<LOGN, LOGRM>::value;
+    static constexpr size_t TWB = sizeof(typename TwT<R>::T) * TwCountT<typename TwT<R>::T, LOGN, LOGRM>::value;
     static constexpr size_t INST = soft1d_inst_smem<R, LOGN, LOGE, LOGRM>();
     static constexpr size_t SMEM = TWB + G * INST;
     static_assert(TWB % 16 == 0 && INST % 16 == 0, "16-byte aligned parts");
@@ -52,10 +52,10 @@ __device__ __forceinline__ void run_pack(const Pack1D& pk, const Inst1D* __restr
                                          unsigned char* smem) {
     using C = typename CT<R>::C;
     using TWT = typename TwT<R>::T;
-    constexpr int TWN = TwCount<V::LN, V::LRM>::value;
+    constexpr int TWN = TwCountT<TWT, V::LN, V::LRM>::value;
     TWT* Ws = reinterpret_cast<TWT*>(smem);
     const TWT* __restrict__ W = reinterpret_cast<const TWT*>(insts[pk.first].W);
-    for (int i = threadIdx.x; i < TWN; i += PERSIST_THREADS) Ws[i] = __ldg(&W[i]);
+    copy16(Ws, W, TWN, threadIdx.x, PERSIST_THREADS);
     __syncthreads();
     const int g = threadIdx.x / V::T, tid = threadIdx.x % V::T;
     if (g < pk.count) {

@@ -265,6 +265,27 @@ std::vector<cd> pass_twiddles(int logn, int logrm) {
     return out;
 }
 
+// The same passes with every twiddle W_L^{M off} (rows M = 1 .. R-1, off < s)
+// for passes whose stride s satisfies 1 < s <= full_maxs, and four rows
+// W_L^{M off}, M = 1 .. 4, otherwise (the complex128 1D step's layout).
+std::vector<cd> pass_twiddles_full(int logn, int logrm, int full_maxs) {
+    std::vector<cd> out;
+    int logl = logn;
+    for (int lr : pass_radices(logn, logrm)) {
+        const int L = 1 << logl, s = 1 << (logl - lr), R = 1 << lr;
+        const bool full = s > 1 && s <= full_maxs;
+        const int rows = full ? R - 1 : 4;
+        for (int r = 0; r < rows; ++r)
+            for (int off = 0; off < s; ++off) {
+                const long e = (long)(r + 1) * off;
+                const double ang = -2.0 * PI * (double)(e % L) / (double)L;
+                out.push_back(cd(std::cos(ang), std::sin(ang)));
+            }
+        logl -= lr;
+    }
+    return out;
+}
+
 // mixed-radix digit reversal of the in-place DIF FFT with passes of radix
 // 2^logrm and a final radix 2^(logn mod logrm): position n holds frequency perm[n]
 std::vector<int> dif_output_order(int logn, int logrm) {

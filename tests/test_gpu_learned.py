@@ -149,11 +149,15 @@ def harvest(plan, st, f, energies, ks, xstar):
 def test_learned_flexible_gcr_gain():
     """Train on errors of plain CG runs at 8 energies, evaluate on 4 held-out
     energies.  The learned correction needs an outer iteration that accepts a
-    preconditioner changing between iterations (flexible GCR); what the
-    network gains is measured against the same flexible GCR without it
-    (precond 3), and COCG with the plain banded preconditioner (the paper's
-    method) is printed for context.  Every learned solution must meet the
-    tolerance with its residual recomputed by the oracle's A."""
+    preconditioner changing between iterations (flexible GCR).  Measured
+    against the method without the network -- COCG with the banded
+    preconditioner (precond 1, the paper's method) -- and against the same
+    flexible GCR without the network (precond 3); iterations and GPU times
+    of all three are printed.  Asserted: every learned solution meets the
+    tolerance with its residual recomputed by the oracle's A, and the
+    network improves on flexible GCR alone.  It does not beat COCG with the
+    banded preconditioner (measured 1.2-1.6x its iterations here, and at
+    1024^2 it stalls), which is reported, not asserted."""
     n, box, R0, th = 256, (-40.0, 40.0, -40.0, 40.0), 30.0, 0.4
     plan = small_plan()
     try:
@@ -171,12 +175,24 @@ def test_learned_flexible_gcr_gain():
                                 steps=400, batch=8, lr=2e-3, seed=7)
         assert np.isfinite(losses).all() and losses[-20:].mean() < losses[:5].mean()
         out = torch.zeros((len(test_E), n, n), dtype=torch.complex128, device="cuda")
-        rc0, it0, _ = S.sse_pcg_solve(plan, test_E, df, out, tol=1e-8, maxit=1000, precond=1)
-        rc3, it3, _ = S.sse_pcg_solve(plan, test_E, df, out, tol=1e-8, maxit=1000, precond=3)
-        rc2, it2, rr2 = S.sse_pcg_solve(plan, test_E, df, out, tol=1e-8, maxit=1000, precond=2)
+        times = {}
+
+        def timed(pc):
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record()
+            r = S.sse_pcg_solve(plan, test_E, df, out, tol=1e-8, maxit=1000, precond=pc)
+            b_.record()
+            torch.cuda.synchronize()
+            times[pc] = a_.elapsed_time(b_)
+            return r
+        rc0, it0, _ = timed(1)
+        rc3, it3, _ = timed(3)
+        rc2, it2, rr2 = timed(2)
         xl = out.cpu().numpy()
-        print("loss %.3e -> %.3e; iterations COCG+band %s, FGCR+band %s, FGCR+band+learned %s" %
-              (losses[:10].mean(), losses[-10:].mean(), it0, it3, it2))
+        print("loss %.3e -> %.3e; iterations (ms): COCG+band %s (%.1f), FGCR+band %s (%.1f), "
+              "FGCR+band+learned %s (%.1f); learned / COCG+band iterations %.2f" %
+              (losses[:10].mean(), losses[-10:].mean(), it0, times[1], it3, times[3], it2, times[2],
+               sum(it2) / sum(it0)))
         assert rc2 == 0
         for e, E in enumerate(test_E):
             res = np.linalg.norm(st.apply_A(xl[e], E) - f) / np.linalg.norm(f)
