@@ -31,6 +31,9 @@ def lib():
         _lib.orc_step2d.argtypes = [C.c_int, C.c_int, C.c_long, P, P, P, P, P, P, P,
                                     P, P, P, C.c_double]
         _lib.orc_step2d.restype = C.c_int
+        _lib.orc_step3d.argtypes = [C.c_int, C.c_int, C.c_int, C.c_long, P, P, P, P, P,
+                                    P, P, P, C.c_double]
+        _lib.orc_step3d.restype = C.c_int
         _lib.orc_num_threads.restype = C.c_int
     return _lib
 
@@ -160,6 +163,45 @@ class Problem2D:
                               _p(cy[0]), _p(cy[1]), _p(cy[2]), float(self.dt))
         if rc:
             raise FloatingPointError("oracle 2D step failed")
+        return psi
+
+
+class Problem3D:
+    """3D instance on box = (ax, bx, ay, by, az, bz), psi stored [nz][ny][nx]
+    (x fastest).  Same contour kind on the three axes;
+    U = -Z/sqrt(z_x^2 + z_y^2 + z_z^2 + a2) plus the axes' absorber terms."""
+
+    def __init__(self, n, box, R0, theta=0.4, kind=T.SHARP, alpha=0.5, a2=1.0,
+                 charge=1.0, dt=0.02, potential=True, e_cap=2.0, kmin=0.25):
+        self.n, self.box, self.dt = tuple(n), tuple(box), dt
+        self.x, self.k, z, ua, self.C = [], [], [], [], []
+        for d in range(3):
+            a, b = box[2 * d], box[2 * d + 1]
+            xd, _ = T.grid(n[d], a, b)
+            self.x.append(xd)
+            self.k.append(T.kgrid(n[d], a, b))
+            z.append(T.z_contour(xd, kind, R0, b, theta, alpha))
+            ua.append(T.absorbing_potential(xd, kind, R0, b, theta, e_cap, kmin))
+            self.C.append(T.c_tridiag(n[d], a, b, kind, R0, theta, alpha))
+        zx, zy, zz = z[0][None, None, :], z[1][None, :, None], z[2][:, None, None]
+        if potential:
+            U = T.soft_coulomb([zx, zy, zz], a2, charge)
+        else:
+            U = np.zeros((n[2], n[1], n[0]), dtype=np.complex128)
+        U = U + ua[0][None, None, :] + ua[1][None, :, None] + ua[2][:, None, None]
+        self.U = np.ascontiguousarray(np.broadcast_to(U, (n[2], n[1], n[0])), dtype=np.complex128)
+
+    def step(self, psi, nsteps):
+        psi = np.ascontiguousarray(psi, dtype=np.complex128).copy()
+        cs, cd, cu = (np.ascontiguousarray(np.concatenate([c[i] for c in self.C]))
+                      for i in range(3))
+        k = [np.ascontiguousarray(kk) for kk in self.k]
+        U = np.ascontiguousarray(self.U)
+        rc = lib().orc_step3d(self.n[0], self.n[1], self.n[2], int(nsteps), _p(psi),
+                              _p(k[0]), _p(k[1]), _p(k[2]), _p(U), _p(cs), _p(cd), _p(cu),
+                              float(self.dt))
+        if rc:
+            raise FloatingPointError("oracle 3D step failed")
         return psi
 
 

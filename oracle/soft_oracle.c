@@ -1,6 +1,6 @@
 /*
  * Oracle: plain FP64 CPU statement of the ECS split-operator FFT time step
- * (Serov & Sergeeva, arXiv:1505.06707, Sec. II) for 1D and 2D grids.
+ * (Serov & Sergeeva, arXiv:1505.06707, Sec. II) for 1D, 2D and 3D grids.
  *
  * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
  * CPU-baseline leg of the benchmark load this library; the GPU library never
@@ -279,6 +279,111 @@ int orc_step2d(int nx, int ny, long nsteps, cplx *psi, const double *kx, const d
         }
         for (long i = 0; i < np; ++i) psi[i] *= vh[i];
         kinetic_half2(psi, nx, ny, kx, ky, tau);
+    }
+    free(vh);
+    return bad ? -1 : 0;
+}
+
+/* --------------------------------------------------------------- 3D --- */
+/* psi is [nz][ny][nx], x fastest.  A line of the grid along axis d starts
+ * at `base` and has stride st[d]. */
+static void line_get(const cplx *psi, long base, long stride, int n, cplx *line)
+{
+    for (int i = 0; i < n; ++i) line[i] = psi[base + (long)i * stride];
+}
+
+static void line_put(cplx *psi, long base, long stride, int n, const cplx *line)
+{
+    for (int i = 0; i < n; ++i) psi[base + (long)i * stride] = line[i];
+}
+
+/* the start of line j of the lines along axis d (j runs over the other two
+ * indices, the faster one first) */
+static long line_base(int d, long j, int nx, int ny)
+{
+    if (d == 0) return j * nx;                              /* j = z ny + y */
+    if (d == 1) return (j / nx) * (long)nx * ny + j % nx;   /* j = z nx + x */
+    return j;                                               /* j = y nx + x */
+}
+
+static void fft3(cplx *psi, const int *n, int sign)
+{
+    const long st[3] = {1, n[0], (long)n[0] * n[1]};
+    const long np = (long)n[0] * n[1] * n[2];
+    for (int d = 0; d < 3; ++d) {
+        const long nl = np / n[d];
+        #pragma omp parallel
+        {
+            cplx *line = (cplx *)malloc(sizeof(cplx) * n[d]);
+            #pragma omp for schedule(static)
+            for (long j = 0; j < nl; ++j) {
+                const long b = line_base(d, j, n[0], n[1]);
+                line_get(psi, b, st[d], n[d], line);
+                orc_fft(line, n[d], sign);
+                line_put(psi, b, st[d], n[d], line);
+            }
+            free(line);
+        }
+    }
+}
+
+static void kinetic_half3(cplx *psi, const int *n, const double *kx, const double *ky,
+                          const double *kz, double tau)
+{
+    fft3(psi, n, -1);
+    const double inv = 1.0 / ((double)n[0] * (double)n[1] * (double)n[2]);
+    #pragma omp parallel for schedule(static)
+    for (int z = 0; z < n[2]; ++z)
+        for (int y = 0; y < n[1]; ++y)
+            for (int x = 0; x < n[0]; ++x) {
+                double ph = -0.5 * (kx[x] * kx[x] + ky[y] * ky[y] + kz[z] * kz[z]) * tau * 0.5;
+                psi[((long)z * n[1] + y) * n[0] + x] *= (cos(ph) + I * sin(ph)) * inv;
+            }
+    fft3(psi, n, +1);
+}
+
+/* 3D form of the scheme (the multidimensional case the paper names at the
+ * end of Sec. V): K = (kx^2 + ky^2 + kz^2)/2, C = C_x + C_y + C_z as
+ * Kronecker sums, e^{-iC tau} = e^{-iC_x tau} e^{-iC_y tau} e^{-iC_z tau}
+ * (the three act on different indices and commute), each by CN on every
+ * full-length line along its axis.  Cs, Cd, Cu hold the three axes' C
+ * (sub, diag, super) one after another: x (nx each), then y, then z. */
+int orc_step3d(int nx, int ny, int nz, long nsteps, cplx *psi, const double *kx,
+               const double *ky, const double *kz, const cplx *U, const cplx *Cs,
+               const cplx *Cd, const cplx *Cu, double tau)
+{
+    const int n[3] = {nx, ny, nz};
+    const long st[3] = {1, nx, (long)nx * ny};
+    const long np = (long)nx * ny * nz;
+    const long coff[3] = {0, nx, (long)nx + ny};
+    cplx *vh = (cplx *)malloc(sizeof(cplx) * np);
+    if (!vh) return -2;
+    for (long i = 0; i < np; ++i) vh[i] = cexp(-I * U[i] * tau * 0.5);
+    int m = nx > ny ? nx : ny;
+    if (nz > m) m = nz;
+    int bad = 0;
+    for (long s = 0; s < nsteps && !bad; ++s) {
+        kinetic_half3(psi, n, kx, ky, kz, tau);
+        for (long i = 0; i < np; ++i) psi[i] *= vh[i];
+        for (int d = 0; d < 3; ++d) {
+            const long nl = np / n[d];
+            #pragma omp parallel reduction(|:bad)
+            {
+                cplx *work = (cplx *)malloc(sizeof(cplx) * 16 * m);
+                cplx *line = (cplx *)malloc(sizeof(cplx) * m);
+                #pragma omp for schedule(static)
+                for (long j = 0; j < nl; ++j) {
+                    const long b = line_base(d, j, nx, ny);
+                    line_get(psi, b, st[d], n[d], line);
+                    if (cn_apply(n[d], Cs + coff[d], Cd + coff[d], Cu + coff[d], tau, line, work))
+                        bad = 1;
+                    line_put(psi, b, st[d], n[d], line);
+                }
+                free(work); free(line);
+            }
+        }
+        for (long i = 0; i < np; ++i) psi[i] *= vh[i];
+        kinetic_half3(psi, n, kx, ky, kz, tau);
     }
     free(vh);
     return bad ? -1 : 0;
