@@ -313,6 +313,76 @@ def bench_2d(S, torch, dev, args):
     return res
 
 
+def bench_3d(S, torch, dev, args):
+    """The 3D workload (256^3, sharp theta = 0.4) in both precisions, and
+    512^3 in complex64: throughput of the step and its HBM rate counting the
+    minimum traffic of the pass structure, 6 state passes per step (rows, y
+    lines, z lines, each read and written once) plus the potential table
+    once; the strip rows' extra round trips are not counted."""
+    import workloads as W
+    w = W.w6()
+    peaks, src = _peaks()
+    hbm = _hbm_peak(peaks)
+    res = {}
+    for prec, name, n, nst, reps in ((S.SOFT_C64, "c64", 256, 24, 3), (S.SOFT_C128, "c128", 256, 8, 2),
+                                     (S.SOFT_C64, "c64_512", 512, 8, 2)):
+        box = (-w["box"][1] * n / 256, w["box"][1] * n / 256) * 3   # h fixed at 0.3125
+        R0 = w["R0"] * n / 256
+        t0 = time.perf_counter()
+        plan = S.soft_create((n, n, n), box, R0, w["theta"], w["dt"], prec=prec, soft_a2=w["a2"],
+                             contour=w["kind"])
+        setup = time.perf_counter() - t0
+        psi0 = W.w6_state((n, n, n), box, seed=0)
+        d = torch.tensor(psi0, dtype=torch.complex64 if prec == S.SOFT_C64 else torch.complex128,
+                         device=dev)
+        del psi0
+        st = torch.cuda.current_stream(dev)
+        S.soft_step(plan, d, nst, 0.0, stream=st)        # warm-up (captures the graph)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            S.soft_step(plan, d, nst, 0.0, stream=st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        steps = nst * reps
+        Sb = 8 if prec == S.SOFT_C64 else 16
+        tab = 8 if prec == S.SOFT_C64 else 16             # e^{-iU tau/2} per point (c64: minus 1, float2)
+        bytes_pt = 6 * Sb + tab
+        pts = n ** 3
+        gps = pts * steps / sec
+        res[name] = {"n": n, "grid_point_steps_per_s": gps, "ms_per_step": 1e3 * sec / steps,
+                     "hbm_GBps_alg": gps * bytes_pt / 1e9, "hbm_frac_alg": gps * bytes_pt / 1e9 / hbm,
+                     "bytes_per_point_step": bytes_pt, "launches_per_call": S.soft_last_launches(plan),
+                     "plan_setup_s": setup, "state_MB": pts * Sb / 1e6}
+        S.soft_destroy(plan)
+        del d
+        torch.cuda.empty_cache()
+    res["workload"] = ("256^3 on [-40,40]^3 (h = 0.3125; 512^3 on [-80,80]^3), sharp ECS R0 = 0.75 of the "
+                       "half-width, theta=0.4, U=-1/sqrt(r^2+1), dt=0.02")
+    res["hbm_peak_GBps"] = hbm
+    res["hbm_peak_source"] = src
+    return res
+
+
+def oracle_3d_sample(steps=1):
+    """The FP64 C oracle's literal 3D step (four 3D FFTs, full cyclic CN on
+    every line) on the 256^3 workload, timed on the host cores."""
+    import workloads as W
+    from oracle import propagate as P
+    w = W.w6()
+    p = P.Problem3D(w["n"], w["box"], w["R0"], theta=w["theta"], kind=w["kind"], a2=w["a2"], dt=w["dt"])
+    psi0 = W.w6_state(w["n"], w["box"], seed=0)
+    t0 = time.perf_counter()
+    p.step(psi0, steps)
+    sec = time.perf_counter() - t0
+    pts = w["n"][0] * w["n"][1] * w["n"][2]
+    return {"value": pts * steps / sec, "unit": "grid-point-steps/s", "seconds_per_step": sec / steps,
+            "cores": P.num_threads(), "kind": "oracle",
+            "sample": "%d step of the 256^3 workload, FP64 C oracle, OpenMP over lines" % steps}
+
+
 def oracle_2d_sample(steps=3):
     """The FP64 C oracle's literal 2D step (four FFTs, full cyclic CN) on the
     2048^2 workload, timed for a few steps on the host cores."""
@@ -700,10 +770,12 @@ def measure_w2(S, torch, dev, args, prec_name, steps, warmup, world=1, with_e2e=
 
 
 # DRAM bytes (read + write) per launch of the complex128 N = 16384 group
-# kernel, from an ncu capture of 69 instances x 16 steps (25.72 MB) scaled by
+# kernel, from an ncu capture of 69 instances x 16 steps (28.12 MB) scaled by
 # the instance count: each instance's 256 KB state is read and written back
 # once per launch and stays in L2 between steps (the tables are shared).
-TRAFFIC_C128_PER_INSTANCE = (23.392512e6 + 2.327040e6) / 69
+# Valid while the kernel sources hash to src_sha1.
+TRAFFIC_C128 = {"src_sha1": "bf925e9ff4b11786c5c09d63ed73735e47513476",
+                "per_instance": (25.101824e6 + 3.019520e6) / 69}
 
 
 def roofline_w2(torch, dev, m, prec_name):
@@ -718,7 +790,9 @@ def roofline_w2(torch, dev, m, prec_name):
     if dom:
         achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e12
         kern = "%s, %.3f ms per launch" % (dom["kernel"], dom["ms"])
-        traffic = (TRAFFIC_C128_PER_INSTANCE * dom["instances"]) if (not c64 and dom["n"] == 16384) else None
+        traffic = None
+        if not c64 and dom["n"] == 16384 and TRAFFIC_C128["src_sha1"] == _kernel_src_sha1():
+            traffic = TRAFFIC_C128["per_instance"] * dom["instances"]
     else:
         achieved = m["flops_per_call"] / (m["call_ms"] / 1e3) / 1e12
         kern = ("%s, all %d instances, %d steps per call, %.3f ms per call (graph: pulse table, queue reset, "
@@ -753,7 +827,8 @@ def main():
     ap.add_argument("--steps-per-call", type=int, default=STEPS_PER_CALL)
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the other precision, the 2D step and the stationary-solver measurements")
-    ap.add_argument("--only", choices=["2d", "pcg", "learned", "conv", "accuracy", "peaks", "w2", "pcg1d"],
+    ap.add_argument("--only", choices=["2d", "3d", "pcg", "learned", "conv", "accuracy", "peaks", "w2",
+                                       "pcg1d"],
                     default=None,
                     help="run one measurement alone (for profiling captures; not a bench line)")
     ap.add_argument("--persistent", type=int, default=1, choices=[0, 1],
@@ -781,8 +856,8 @@ def main():
                            persistent=args.persistent, autotune=args.autotune)
             r["roofline"] = roofline_w2(torch, dev, r, args.prec)
         else:
-            fn = {"2d": bench_2d, "pcg": bench_pcg, "learned": bench_learned, "conv": bench_conv,
-                  "pcg1d": bench_pcg1d}[args.only]
+            fn = {"2d": bench_2d, "3d": bench_3d, "pcg": bench_pcg, "learned": bench_learned,
+                  "conv": bench_conv, "pcg1d": bench_pcg1d}[args.only]
             r = fn(S, torch, dev, args)
         print(json.dumps({"only": args.only, "result": r}))
         return
@@ -831,12 +906,14 @@ def main():
         out["fp32_accuracy"] = bench_accuracy(S, torch, dev, args, sizes=(2048, 4096, 8192, 16384))
         out["pcg1d_paper_test"] = bench_pcg1d(S, torch, dev, args)
         out["w3_2d"] = bench_2d(S, torch, dev, args)
+        out["w6_3d"] = bench_3d(S, torch, dev, args)
         out["w4_pcg"] = bench_pcg(S, torch, dev, args)
         out["w5_learned"] = bench_learned(S, torch, dev, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_sample()
         if not args.no_extra:
             out["w3_2d"]["cpu_baseline"] = oracle_2d_sample()
+            out["w6_3d"]["cpu_baseline"] = oracle_3d_sample()
             pc = out["w4_pcg"]
             its = (pc.get("band_fp64") or pc.get("mixed_fp32_reliable") or {}).get("iterations_mean", 378.0)
             out["w4_pcg"]["cpu_baseline"] = oracle_pcg_sample(its)

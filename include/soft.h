@@ -81,8 +81,9 @@ typedef enum {
 } soft_contour;
 
 typedef struct {
-    int ndim;        /* 1 or 2                                             */
-    int64_t n[2];    /* points per axis, powers of two; n[1] unused in 1D  */
+    int ndim;        /* 1, 2 or 3                                          */
+    int64_t n[3];    /* points per axis (x, y, z), powers of two; unused
+                        entries ignored                                    */
 } soft_grid;
 
 /* Optional settings; NULL means the defaults given in brackets. */
@@ -119,8 +120,10 @@ typedef struct soft_plan soft_plan;   /* opaque, library-owned */
 void soft_default_options(soft_options* opt);
 
 /* soft_create -- build the tables of one problem (Sec. II, Sec. III).
- *   grid   host; 1D or 2D sizes.
- *   box    host; a0, b0 [, a1, b1] with a = -b on each axis.
+ *   grid   host; 1D, 2D or 3D sizes.  2D grids are stored [ny][nx], 3D
+ *          grids [nz][ny][nx] (x fastest).  2D axes take 256 .. 2048
+ *          points, 3D axes 64 .. 2048.
+ *   box    host; a0, b0 [, a1, b1 [, a2, b2]] with a = -b on each axis.
  *   R0     onset |x| of the scaling, 0 < R0 < b on each axis.
  *   theta  rotation angle of the sharp contour, final angle of SECS (pi/4 is
  *          the paper's SECS); ignored by TFECS.
@@ -154,7 +157,12 @@ int soft_batch_layout(const soft_plan* plan, int64_t* offsets, int64_t* total);
  * plans use their own per-instance fields and ignore it).  t_inout: host,
  * the time at entry, advanced by nsteps*dt on return.  The half-kinetic
  * factors of consecutive steps inside one call are merged (the scheme is
- * unchanged up to rounding).  nsteps = 0 is a no-op. */
+ * unchanged up to rounding).  nsteps = 0 is a no-op.  2D and 3D plans take
+ * no field (it is ignored) and run their steps as passes over the grid's
+ * lines (rows, then columns), with C = C_x + C_y (+ C_z) as Kronecker sums
+ * so that e^{-iC tau} factors into one CN per axis; the middle steps are
+ * replayed from a CUDA graph captured on the first call with a given state
+ * pointer and stream. */
 int soft_step(soft_plan* plan, void* psi, int64_t nsteps, const soft_field* field,
               double* t_inout, void* stream);
 

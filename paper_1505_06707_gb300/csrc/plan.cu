@@ -446,6 +446,7 @@ int soft_create(const soft_grid* grid, const double* box, double R0, double thet
     if (rc) return rc;
     if (grid->ndim == 1) return create_1d(1, grid, box, &R0, &theta, nullptr, dt, o, true, out);
     if (grid->ndim == 2) return create_2d(grid, box, R0, theta, dt, o, out);
+    if (grid->ndim == 3) return create_3d(grid, box, R0, theta, dt, o, out);
     return SOFT_ERR_INVALID_ARG;
 }
 
@@ -473,6 +474,7 @@ int soft_step(soft_plan* P, void* psi, int64_t nsteps, const soft_field* field, 
               void* stream) {
     if (!P || !psi || !t_inout || nsteps < 0) return SOFT_ERR_INVALID_ARG;
     if (P->kind == 2) return P->step_2d(psi, nsteps, t_inout, (cudaStream_t)stream);
+    if (P->kind == 3) return P->step_3d(psi, nsteps, t_inout, (cudaStream_t)stream);
     if (P->kind != 1) return SOFT_ERR_INVALID_ARG;
     if (P->single) {
         int rc = P->set_single_field(field, (cudaStream_t)stream);
@@ -514,6 +516,10 @@ int soft_set_potential(soft_plan* P, const double* U, int64_t n) {
         if (n != (int64_t)P->p2->nx * P->p2->ny) return SOFT_ERR_INVALID_ARG;
         return P->p2->set_potential(U);
     }
+    if (P->kind == 3) {
+        if (n != P->points_3d()) return SOFT_ERR_INVALID_ARG;
+        return P->p3->set_potential(U);
+    }
     if (P->kind != 1 || !P->single || P->tabs.size() != 1) return SOFT_ERR_UNSUPPORTED;
     Tables1D* T = P->tabs[0].get();
     const int nn = 1 << T->logn;
@@ -537,7 +543,7 @@ int soft_plan_count(const soft_plan* P) {
 int64_t soft_plan_points(const soft_plan* P, int i) {
     if (!P) return 0;
     if (P->kind == 1) return (i >= 0 && i < (int)P->inst.size()) ? P->inst[i].n : 0;
-    return P->points_2d();
+    return P->kind == 3 ? P->points_3d() : P->points_2d();
 }
 int soft_plan_prec(const soft_plan* P) { return P ? P->prec : 0; }
 int64_t soft_last_launches(const soft_plan* P) { return P ? P->last_launches : 0; }
@@ -568,6 +574,7 @@ soft_plan::~soft_plan() {
         cudaEventDestroy(ev_fork);
     }
     free_2d();
+    free_3d();
 }
 
 Inst1D soft_plan::descriptor(int i) const {

@@ -11,13 +11,6 @@ using namespace soft;
 
 namespace soft {
 
-int soft2d_row_c64(int, int, int, int, const Geo2D&, void*, int, int, const void*, cudaStream_t);
-int soft2d_row_c128(int, int, int, int, const Geo2D&, void*, int, int, const void*, cudaStream_t);
-int soft2d_col_c64(int, int, int, const Geo2D&, void*, const void*, cudaStream_t);
-int soft2d_col_c128(int, int, int, const Geo2D&, void*, const void*, cudaStream_t);
-int soft2d_cny_c64(const Geo2D&, void*, cudaStream_t);
-int soft2d_cny_c128(const Geo2D&, void*, cudaStream_t);
-
 static int ilog2_2d(int64_t n) {
     int l = 0;
     while ((int64_t(1) << l) < n) ++l;
@@ -48,18 +41,20 @@ Plan2D::~Plan2D() {
 
 int Plan2D::row(int mode, void* psi, int row0, int nrows, const void* tkx, cudaStream_t st) {
     ++launches;
-    if (prec == SOFT_C64) return soft2d_row_c64(lx, lex, lrx, mode, geo, psi, row0, nrows, tkx, st);
-    return soft2d_row_c128(lx, lex, lrx, mode, geo, psi, row0, nrows, tkx, st);
+    if (prec == SOFT_C64) return soft2d_row_c64(lx, lex, lrx, mode, geo, psi, row0, nrows, tkx, nullptr, st);
+    return soft2d_row_c128(lx, lex, lrx, mode, geo, psi, row0, nrows, tkx, nullptr, st);
 }
 int Plan2D::col(void* psi, const void* tky, cudaStream_t st) {
     ++launches;
-    if (prec == SOFT_C64) return soft2d_col_c64(ly, ley, lry, geo, psi, tky, st);
-    return soft2d_col_c128(ly, ley, lry, geo, psi, tky, st);
+    const LineGeo lg{geo.Wy, geo.nx, 0};
+    if (prec == SOFT_C64) return soft2d_col_c64(ly, ley, lry, lg, 1, psi, tky, st);
+    return soft2d_col_c128(ly, ley, lry, lg, 1, psi, tky, st);
 }
 int Plan2D::ypass(void* psi, cudaStream_t st) {
     ++launches;
-    if (prec == SOFT_C64) return soft2d_cny_c64(geo, psi, st);
-    return soft2d_cny_c128(geo, psi, st);
+    const CnGeo cg{geo.cny, geo.nby, geo.blk0y, geo.ny, geo.nx, 0};
+    if (prec == SOFT_C64) return soft2d_cny_c64(cg, 1, psi, st);
+    return soft2d_cny_c128(cg, 1, psi, st);
 }
 
 // one full step in (k_x, y) representation; last = use the half kinetic tables

@@ -37,6 +37,14 @@ int sse1d_apply(soft_plan* P, double E, int what, int precond, const void* x, vo
 #include "soft2d_geo.h"
 
 namespace soft {
+// pass kernels of the 2D and 3D steps (soft2d_c64.cu, soft2d_c128.cu)
+int soft2d_row_c64(int, int, int, int, const Geo2D&, void*, int, int, const void*, const int*, cudaStream_t);
+int soft2d_row_c128(int, int, int, int, const Geo2D&, void*, int, int, const void*, const int*, cudaStream_t);
+int soft2d_col_c64(int, int, int, const LineGeo&, int, void*, const void*, cudaStream_t);
+int soft2d_col_c128(int, int, int, const LineGeo&, int, void*, const void*, cudaStream_t);
+int soft2d_cny_c64(const CnGeo&, int, void*, cudaStream_t);
+int soft2d_cny_c128(const CnGeo&, int, void*, cudaStream_t);
+
 // 2D plan state (plan2d.cu) and the stationary solver workspace (pcg.cu)
 struct Plan2D {
     static constexpr int64_t GRAPH_STEPS = 16;
@@ -64,10 +72,37 @@ struct Plan2D {
     int set_potential(const double* U_re_im);   // host complex [ny][nx]
     ~Plan2D();
 };
+
+// 3D plan state (plan3d.cu): a [nz][ny][nx] grid stepped by the 2D pass
+// kernels (rows; lines along y and z; strip CN along y and z)
+struct Plan3D {
+    static constexpr int64_t GRAPH_STEPS = 8;
+    int prec = SOFT_C128;
+    int n[3] = {}, l[3] = {}, le[3] = {}, lr[3] = {};
+    int nb[3] = {}, blk0[3] = {};  // strip block of each axis
+    double tau = 0, a2 = 2.0, charge = 1.0;
+    Axis1D ax[3];
+    std::vector<cd> ua[3];         // comparison-absorber potential of each axis
+    void *W[3] = {}, *TK[3] = {}, *TKh[3] = {}, *TVh = nullptr, *cn[3] = {};
+    int *rows_full = nullptr, *rows_strip = nullptr;
+    int nfull = 0, nstrip = 0;
+    Geo2D geo{};
+    int64_t launches = 0, graph_launches = 0;
+    cudaGraphExec_t graph_exec = nullptr;
+    void* graph_psi = nullptr;
+    cudaStream_t graph_stream = nullptr;
+
+    int row(int mode, void* psi, int row0, int nrows, const int* rows, const void* tkx, cudaStream_t st);
+    int line(int d, void* psi, const void* tk, cudaStream_t st);
+    int cnpass(int d, void* psi, cudaStream_t st);
+    int enqueue_step(void* psi, bool last, cudaStream_t st);
+    int set_potential(const double* U_re_im);   // host complex [nz][ny][nx]
+    ~Plan3D();
+};
 }  // namespace soft
 
 struct soft_plan {
-    int kind = 0;              // 1: 1D (single or batch), 2: 2D
+    int kind = 0;              // 1: 1D (single or batch), 2: 2D, 3: 3D
     bool single = false;
     int prec = SOFT_C128;
     soft_options opt{};
@@ -131,8 +166,16 @@ struct soft_plan {
     int64_t points_2d() const;
     void free_2d();
 
+    // ---- 3D (plan3d.cu)
+    soft::Plan3D* p3 = nullptr;
+    int step_3d(void* psi, int64_t nsteps, double* t_inout, cudaStream_t st);
+    int64_t points_3d() const;
+    void free_3d();
+
     ~soft_plan();
 };
 
 int create_2d(const soft_grid* grid, const double* box, double R0, double theta, double dt,
+              const soft_options& o, soft_plan** out);
+int create_3d(const soft_grid* grid, const double* box, double R0, double theta, double dt,
               const soft_options& o, soft_plan** out);

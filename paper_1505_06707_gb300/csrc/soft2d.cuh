@@ -48,12 +48,13 @@ __device__ __forceinline__ void inv_pass0_post(typename CT<R>::C* S, const typen
     }
 }
 
-// One CTA per row.  rows are (row0 + blockIdx.x) mod ny.  The potential
-// factor is applied as the last inverse pass stores, the x kinetic factor as
-// the row is written back.
+// One CTA per row.  Rows are rows[row0 + blockIdx.x] with a row list, else
+// (row0 + blockIdx.x) mod ny.  The potential factor is applied as the last
+// inverse pass stores, the x kinetic factor as the row is written back.
 template <typename R, int LOGN, int LOGE, int LOGRM, int MODE>
 __global__ void __launch_bounds__(Cfg1D<R, LOGN, LOGE, LOGRM>::T, Cfg1D<R, LOGN, LOGE, LOGRM>::MINB)
-row_pass_kernel(Geo2D g, void* __restrict__ psi_v, int row0, const void* __restrict__ tkx_v)
+row_pass_kernel(Geo2D g, void* __restrict__ psi_v, int row0, const void* __restrict__ tkx_v,
+                const int* __restrict__ rows)
 {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
     using C = typename K::C;
@@ -64,7 +65,7 @@ row_pass_kernel(Geo2D g, void* __restrict__ psi_v, int row0, const void* __restr
     C* S = reinterpret_cast<C*>(smem_raw);
     C* scan = S + N;
     const int tid = threadIdx.x;
-    const int y = (row0 + (int)blockIdx.x) % g.ny;
+    const int y = rows ? __ldg(&rows[row0 + (int)blockIdx.x]) : (row0 + (int)blockIdx.x) % g.ny;
     C* __restrict__ row = reinterpret_cast<C*>(psi_v) + (int64_t)y * N;
     const C* __restrict__ W = reinterpret_cast<const C*>(g.Wx);
     const VT* __restrict__ tv = reinterpret_cast<const VT*>(g.TVh) + (int64_t)y * N;
@@ -134,7 +135,7 @@ struct ColCfg {
 
 template <typename R, int LOGN, int LOGE, int LOGRM, int TW>
 __global__ void __launch_bounds__(ColCfg<R, LOGN, LOGE, LOGRM, TW>::THREADS, ColCfg<R, LOGN, LOGE, LOGRM, TW>::MINB)
-col_pass_kernel(Geo2D g, void* __restrict__ psi_v, const void* __restrict__ tky_v)
+col_pass_kernel(LineGeo lg, void* __restrict__ psi_v, const void* __restrict__ tky_v)
 {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
     using C = typename K::C;
@@ -146,10 +147,11 @@ col_pass_kernel(Geo2D g, void* __restrict__ psi_v, const void* __restrict__ tky_
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* S = reinterpret_cast<C*>(smem_raw);
     C* Ws = S + TW * PITCH;
-    C* __restrict__ psi = reinterpret_cast<C*>(psi_v);
-    const C* __restrict__ W = reinterpret_cast<const C*>(g.Wy);
-    const int c0 = blockIdx.x * TW;
-    const int nx = g.nx;
+    const int64_t nx = lg.ld;
+    const int64_t gpp = nx / TW;                    // CTAs per plane
+    C* __restrict__ psi = reinterpret_cast<C*>(psi_v) + (int64_t)(blockIdx.x / gpp) * lg.plane;
+    const C* __restrict__ W = reinterpret_cast<const C*>(lg.W);
+    const int64_t c0 = (int64_t)(blockIdx.x % gpp) * TW;
 #pragma unroll 8
     for (int it = 0; it < NIT; ++it) {              // row by row: the TW columns of a row are adjacent
         const int idx = threadIdx.x + it * TW * T;
@@ -179,15 +181,17 @@ col_pass_kernel(Geo2D g, void* __restrict__ psi_v, const void* __restrict__ tky_
 // sweeps.
 template <typename C, int CH, int TWC>
 __global__ void __launch_bounds__(32 * TWC, 512 / (32 * TWC))
-cny_kernel(Geo2D g, void* __restrict__ psi_v)
+cny_kernel(CnGeo g, void* __restrict__ psi_v)
 {
     constexpr int PITCH = TWC + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* S = reinterpret_cast<C*>(smem_raw);
-    C* __restrict__ psi = reinterpret_cast<C*>(psi_v);
-    const C* __restrict__ cn = reinterpret_cast<const C*>(g.cny);
-    const int c0 = blockIdx.x * TWC;
-    const int nb = g.nby, nx = g.nx, ny = g.ny;
+    const int64_t nx = g.ld;
+    const int64_t gpp = nx / TWC;                   // CTAs per plane
+    C* __restrict__ psi = reinterpret_cast<C*>(psi_v) + (int64_t)(blockIdx.x / gpp) * g.plane;
+    const C* __restrict__ cn = reinterpret_cast<const C*>(g.cn);
+    const int64_t c0 = (int64_t)(blockIdx.x % gpp) * TWC;
+    const int nb = g.nb, ny = g.n;
     // the LU coefficients (mf, mb, g) are the same for every column: one
     // copy in shared memory, read by each lane at its own row (a warp's
     // rows are a chunk apart, which in global memory touched one cache
@@ -197,7 +201,7 @@ cny_kernel(Geo2D g, void* __restrict__ psi_v)
 #pragma unroll 8
     for (int idx = threadIdx.x; idx < nb * TWC; idx += blockDim.x) {   // several rows in flight
         const int r = idx / TWC, j = idx % TWC;
-        const int yy = (g.blk0y + r) % ny;
+        const int yy = (g.blk0 + r) % ny;
         S[r * PITCH + j] = psi[(int64_t)yy * nx + c0 + j];
     }
     __syncthreads();
@@ -260,7 +264,7 @@ cny_kernel(Geo2D g, void* __restrict__ psi_v)
 #pragma unroll 8
     for (int idx = threadIdx.x; idx < nb * TWC; idx += blockDim.x) {
         const int r = idx / TWC, j = idx % TWC;
-        const int yy = (g.blk0y + r) % ny;
+        const int yy = (g.blk0 + r) % ny;
         psi[(int64_t)yy * nx + c0 + j] = S[r * PITCH + j];
     }
 }
@@ -268,10 +272,10 @@ cny_kernel(Geo2D g, void* __restrict__ psi_v)
 // ---------------------------------------------------------------- launchers
 template <typename R, int LOGN, int LOGE, int LOGRM>
 int launch_row_t(int mode, const Geo2D& g, void* psi, int row0, int nrows, const void* tkx,
-                 cudaStream_t st) {
+                 const int* rows, cudaStream_t st) {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
     const size_t smem = Cfg2DRow<R, LOGN, LOGE, LOGRM>::SMEM2;
-    void (*k)(Geo2D, void*, int, const void*) = nullptr;
+    void (*k)(Geo2D, void*, int, const void*, const int*) = nullptr;
     switch (mode) {
     case ROW_FWD: k = row_pass_kernel<R, LOGN, LOGE, LOGRM, ROW_FWD>; break;
     case ROW_FULL: k = row_pass_kernel<R, LOGN, LOGE, LOGRM, ROW_FULL>; break;
@@ -284,12 +288,13 @@ int launch_row_t(int mode, const Geo2D& g, void* psi, int row0, int nrows, const
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return SOFT_ERR_CUDA;
     if (nrows <= 0 || !psi) return SOFT_OK;
-    k<<<nrows, K::T, smem, st>>>(g, psi, row0, tkx);
+    k<<<nrows, K::T, smem, st>>>(g, psi, row0, tkx, rows);
     return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
 }
 
+// lines of planes planes (LineGeo); ld must be a multiple of TW
 template <typename R, int LOGN, int LOGE, int LOGRM, int TW>
-int launch_col_t(const Geo2D& g, void* psi, const void* tky, cudaStream_t st) {
+int launch_col_t(const LineGeo& g, int planes, void* psi, const void* tky, cudaStream_t st) {
     using CC = ColCfg<R, LOGN, LOGE, LOGRM, TW>;
     const size_t smem = CC::SMEM;
     auto k = col_pass_kernel<R, LOGN, LOGE, LOGRM, TW>;
@@ -297,20 +302,26 @@ int launch_col_t(const Geo2D& g, void* psi, const void* tky, cudaStream_t st) {
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return SOFT_ERR_CUDA;
     if (!psi) return SOFT_OK;             // attribute set only
-    k<<<g.nx / TW, CC::THREADS, smem, st>>>(g, psi, tky);
+    if (g.ld % TW || planes < 1) return SOFT_ERR_INVALID_ARG;
+    const int64_t grid = g.ld / TW * planes;
+    if (grid > 0x7fffffff) return SOFT_ERR_TOO_LARGE;
+    k<<<(unsigned)grid, CC::THREADS, smem, st>>>(g, psi, tky);
     return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
 }
 
 template <typename C, int CH>
-int launch_cny_t(const Geo2D& g, void* psi, cudaStream_t st) {
+int launch_cny_t(const CnGeo& g, int planes, void* psi, cudaStream_t st) {
     constexpr int TWC = 8;
-    const size_t smem = sizeof(C) * (size_t)g.nby * (TWC + 1 + 3);   // tile + LU coefficients
+    const size_t smem = sizeof(C) * (size_t)g.nb * (TWC + 1 + 3);   // tile + LU coefficients
     auto k = cny_kernel<C, CH, TWC>;
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return SOFT_ERR_CUDA;
-    if (g.nby <= 0 || !psi) return SOFT_OK;
-    k<<<g.nx / TWC, 32 * TWC, smem, st>>>(g, psi);
+    if (g.nb <= 0 || !psi) return SOFT_OK;
+    if (g.ld % TWC || planes < 1 || (g.nb + 31) / 32 > CH) return SOFT_ERR_INVALID_ARG;
+    const int64_t grid = g.ld / TWC * planes;
+    if (grid > 0x7fffffff) return SOFT_ERR_TOO_LARGE;
+    k<<<(unsigned)grid, 32 * TWC, smem, st>>>(g, psi);
     return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
 }
 

@@ -1,5 +1,7 @@
-// Geometry and table pointers of a 2D plan, passed by value to the 2D kernels.
+// Geometry and table pointers of a 2D or 3D plan, passed by value to the
+// pass kernels.
 #pragma once
+#include <cstdint>
 
 namespace soft {
 
@@ -9,9 +11,25 @@ struct Geo2D {              // passed by value to every 2D kernel
     const void* TVh;        // e^{-iU tau/2}, [ny][nx] (minus 1, float2, for complex64)
     const void* cnx;        // x-strip LU (mf, mb, g) for the row pass
     const void* cny;        // y-strip LU (mf, mb, g) for the y-block pass
-    int nx, ny;
+    int nx, ny;             // row length; number of rows (3D: ny nz)
     int nbx, blk0x;         // x-strip block (same for every row)
     int nby, blk0y;         // y-strip block (same for every column)
+};
+
+// Lines along a strided axis: element i of line c of plane p sits at
+// p plane + i ld + c, c < ld (2D columns: ld = nx, one plane; 3D y lines:
+// ld = nx, plane = nx ny, nz planes; 3D z lines: ld = nx ny, one plane).
+struct LineGeo {
+    const void* W;          // pass twiddles of the line FFT
+    int64_t ld, plane;
+};
+
+// The strip CN along a strided axis: the cyclic block blk0 .. blk0 + nb - 1
+// (mod n) of every line, lines laid out as in LineGeo.
+struct CnGeo {
+    const void* cn;         // LU (mf, mb, g) of the block
+    int nb, blk0, n;
+    int64_t ld, plane;
 };
 
 }  // namespace soft

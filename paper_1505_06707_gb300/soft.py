@@ -50,7 +50,7 @@ class SoftError(RuntimeError):
 
 
 class Grid(C.Structure):
-    _fields_ = [("ndim", C.c_int), ("n", C.c_int64 * 2)]
+    _fields_ = [("ndim", C.c_int), ("n", C.c_int64 * 3)]
 
 
 class Options(C.Structure):
@@ -161,13 +161,16 @@ def _options(prec=SOFT_C128, contour=CONTOUR_SHARP, tfecs_alpha=0.5, soft_a2=2.0
 
 
 def soft_create(n, box, R0, theta, dt, **opts):
-    """n: int (1D) or (nx, ny); box: (a, b) or (ax, bx, ay, by)."""
+    """n: int (1D), (nx, ny) or (nx, ny, nz); box: (a, b), (ax, bx, ay, by) or
+    (ax, bx, ay, by, az, bz)."""
     L = load()
     g = Grid()
-    if isinstance(n, (tuple, list)):
-        g.ndim, g.n[0], g.n[1] = 2, n[0], n[1]
-    else:
-        g.ndim, g.n[0], g.n[1] = 1, n, 0
+    dims = list(n) if isinstance(n, (tuple, list)) else [n]
+    if not 1 <= len(dims) <= 3 or len(box) != 2 * len(dims):
+        raise ValueError("soft_create: n and box disagree")
+    g.ndim = len(dims)
+    for d, v in enumerate(dims):
+        g.n[d] = v
     bx = (C.c_double * len(box))(*box)
     o = _options(**opts)
     out = C.c_void_p()
@@ -180,7 +183,7 @@ def soft_create_batch(ns, boxes, R0s, thetas, fields, dt, **opts):
     cnt = len(ns)
     G = (Grid * cnt)()
     for i, n in enumerate(ns):
-        G[i].ndim, G[i].n[0], G[i].n[1] = 1, n, 0
+        G[i].ndim, G[i].n[0] = 1, n
     bx = (C.c_double * (2 * cnt))(*[v for b in boxes for v in b])
     r0 = (C.c_double * cnt)(*R0s)
     th = (C.c_double * cnt)(*thetas)

@@ -24,6 +24,10 @@ Workloads (all lengths in atomic units):
       Gaussian (sigma 4, seeded centre in [-10,10]^2, seeded phase); 64
       energies ~ U[0.05, 2.0] sorted; tolerance 1e-8.  The linear system is
       A psi = f with f = -chi (A = H - E).
+  W6  3D single instance: 256^3 on [-40,40]^3 (h = 0.3125),
+      U=-1/sqrt(x^2+y^2+z^2+1), sharp ECS on every axis R0=30 theta=0.4;
+      sum of 4 seeded Gaussians (centres within a quarter of the half-width,
+      sigma ~ U[0.08, 0.15] of the half-width, |k| <= 1.5, phases); dt=0.02.
 """
 from __future__ import annotations
 
@@ -126,3 +130,32 @@ def w4(n=1024, box=(-200.0, 200.0, -200.0, 200.0), n_energies=64):
     chi = gaussian(y, cy, 4.0, 0.0, 0.0)[:, None] * gaussian(x, cx, 4.0, 0.0, ph)[None, :]
     return dict(nx=n, ny=n, box=box, R0=150.0, theta=0.4, a2=1.0, E=E, tol=1e-8,
                 chi=chi, f=-chi)
+
+
+# ---------------------------------------------------------------- W6 ------
+def w6_state(n, box, seed=0, ngauss=4, noise=0.0):
+    """Sum of ngauss seeded 3D Gaussians on the [nz][ny][nx] grid of box
+    (ax, bx, ay, by, az, bz), normalised; `noise` adds that fraction of
+    seeded complex white noise (it reaches every mode, the strips included)."""
+    g = rng(6, seed)
+    ax = [half_shifted_grid(n[d], box[2 * d], box[2 * d + 1]) for d in range(3)]
+    half = min(box[2 * d + 1] for d in range(3))
+    psi = np.zeros((n[2], n[1], n[0]), dtype=np.complex128)
+    for _ in range(ngauss):
+        c = [g.uniform(-0.25, 0.25) * box[2 * d + 1] for d in range(3)]
+        sg = g.uniform(0.08, 0.15) * half
+        k = g.uniform(-1.0, 1.0, size=3)
+        k *= 1.5 * math.sqrt(g.uniform(0, 1)) / max(1e-12, float(np.linalg.norm(k)))
+        ph = g.uniform(0, 2 * math.pi)
+        f = [gaussian(ax[d][0], c[d], sg, k[d], ph if d == 0 else 0.0) for d in range(3)]
+        psi += f[2][:, None, None] * f[1][None, :, None] * f[0][None, None, :]
+    if noise:
+        psi += noise * float(np.abs(psi).max()) * (g.standard_normal(psi.shape)
+                                                  + 1j * g.standard_normal(psi.shape))
+    return normalise(psi, ax[0][1] * ax[1][1] * ax[2][1])
+
+
+def w6(n=256, half=40.0):
+    """The 3D benchmark workload (parameters; the state from w6_state)."""
+    return dict(n=(n, n, n), box=(-half, half) * 3, R0=30.0, theta=0.4, kind=0, a2=1.0,
+                dt=0.02)
