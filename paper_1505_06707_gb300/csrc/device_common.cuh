@@ -20,6 +20,24 @@ struct BarGroup {
     }
 };
 
+// Asynchronous global -> shared copies of 8 or 16 bytes (cp.async): the
+// copies of a thread are in flight together with no register staging;
+// cp_async_wait<0>() waits for the thread's own copies (a barrier after it
+// publishes them to the other threads).  Both addresses must be aligned to
+// the copy size.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+    static_assert(BYTES == 8 || BYTES == 16, "8- or 16-byte copies");
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 template <typename R> struct CT;
 template <> struct CT<float> { using C = float2; };
 template <> struct CT<double> { using C = double2; };

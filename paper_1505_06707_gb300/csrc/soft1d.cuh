@@ -521,7 +521,9 @@ __device__ __forceinline__ void inv_passes(typename CT<R>::C* S, const TW* Ws, i
 // With SURF, the spectrum entering the k-space factor is also contracted with
 // four weight rows sw[r * N + q] (same transposed index q as the table) into
 // acc[r] (surface sampling, soft1d_surf_kernel).
-template <typename R, int LOGN, int LOGE, int LOGRM, bool SURF = false>
+//
+// TSH: the table has been copied to shared memory (plain loads).
+template <typename R, int LOGN, int LOGE, int LOGRM, bool SURF = false, bool TSH = false>
 __device__ __forceinline__ void kcenter(typename CT<R>::C* S, const typename TabT<R>::T* __restrict__ tab,
                                         int tid, const typename CT<R>::C* __restrict__ sw = nullptr,
                                         typename CT<R>::C* acc = nullptr) {
@@ -536,10 +538,14 @@ __device__ __forceinline__ void kcenter(typename CT<R>::C* S, const typename Tab
     // is computed (radix <= 4: the loads of one butterfly alone would leave
     // the L2 latency exposed)
     constexpr bool PF = RR <= 4 && NU > 1;
+    auto ld = [&](int i) -> TT {
+        if constexpr (TSH) return tab[i];
+        else return __ldg(&tab[i]);
+    };
     TT tn[PF ? RR : 1];
     if constexpr (PF) {
 #pragma unroll
-        for (int m = 0; m < RR; ++m) tn[m] = __ldg(&tab[m * (K::N / RR) + tid]);
+        for (int m = 0; m < RR; ++m) tn[m] = ld(m * (K::N / RR) + tid);
     }
 #pragma unroll 1
     for (int u = 0; u < NU; ++u) {
@@ -550,11 +556,11 @@ __device__ __forceinline__ void kcenter(typename CT<R>::C* S, const typename Tab
             for (int m = 0; m < RR; ++m) tc[m] = tn[m];
             if (u + 1 < NU) {
 #pragma unroll
-                for (int m = 0; m < RR; ++m) tn[m] = __ldg(&tab[m * (K::N / RR) + tid + (u + 1) * K::T]);
+                for (int m = 0; m < RR; ++m) tn[m] = ld(m * (K::N / RR) + tid + (u + 1) * K::T);
             }
         } else {
 #pragma unroll
-            for (int m = 0; m < RR; ++m) tc[m] = __ldg(&tab[m * (K::N / RR) + tid + u * K::T]);
+            for (int m = 0; m < RR; ++m) tc[m] = ld(m * (K::N / RR) + tid + u * K::T);
         }
         const int sb = swz<C>(base);
         C v[RR];

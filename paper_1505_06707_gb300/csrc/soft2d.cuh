@@ -19,13 +19,26 @@ namespace soft {
 
 enum RowMode { ROW_FWD = 0, ROW_FULL = 1, ROW_A = 2, ROW_B = 3, ROW_INV = 4 };
 
+// Shared memory of the row pass: the row (swizzled) and the scan scratch of
+// the strip CN; one table buffer that holds the row's e^{-iU tau/2} while
+// the potential is applied and the kinetic table afterwards; the twiddles.
 template <typename R, int LOGN, int LOGE, int LOGRM>
 struct Cfg2DRow : Cfg1D<R, LOGN, LOGE, LOGRM> {
-    static constexpr size_t SMEM2 = sizeof(typename CT<R>::C) * ((1 << LOGN) + 64) + 64;
+    using C = typename CT<R>::C;
+    using VT = typename VabT<R>::T;
+    using TT = typename TabT<R>::T;
+    static constexpr int N = 1 << LOGN;
+    static constexpr int TWN = TwCount<LOGN, LOGRM>::value;
+    static constexpr size_t OFF_B = sizeof(C) * (N + 64);
+    static constexpr size_t BYTES_B = (sizeof(VT) > sizeof(TT) ? sizeof(VT) : sizeof(TT)) * N;
+    static constexpr size_t OFF_W = OFF_B + BYTES_B;
+    static constexpr size_t SMEM2 = OFF_W + sizeof(C) * TWN;
+    static_assert(OFF_B % 16 == 0 && OFF_W % 16 == 0, "16-byte aligned parts");
 };
 
-// Inverse pass 0 with post(n, v) applied to every output as it is stored.
-template <typename R, int LOGN, int LOGE, int LOGRM, class Post>
+// Inverse pass 0 with post(n, v) applied to every output as it is stored
+// (SH: twiddles in shared memory).
+template <typename R, int LOGN, int LOGE, int LOGRM, bool SH, class Post>
 __device__ __forceinline__ void inv_pass0_post(typename CT<R>::C* S, const typename CT<R>::C* __restrict__ W,
                                                int tid, Post post) {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
@@ -40,7 +53,7 @@ __device__ __forceinline__ void inv_pass0_post(typename CT<R>::C* S, const typen
         const int sb = swz<C>(off);
         C v[RR];
         C tb[4];
-        if constexpr (s > 1) load_tw<C, NB, s, false>(tb, W + G::TOFF + off);
+        if constexpr (s > 1) load_tw<C, NB, s, SH>(tb, W + G::TOFF + off);
         LoadInv<C, C, RR, s, 0>::run(S, v, tb, sb, s > 1);
         dft_reg<C, RR, +1>(v);
 #pragma unroll
@@ -49,7 +62,10 @@ __device__ __forceinline__ void inv_pass0_post(typename CT<R>::C* S, const typen
 }
 
 // One CTA per row.  Rows are rows[row0 + blockIdx.x] with a row list, else
-// (row0 + blockIdx.x) mod ny.  The potential factor is applied as the last
+// (row0 + blockIdx.x) mod ny.  The row, its potential factors and the
+// twiddles are staged in shared memory by asynchronous copies issued
+// together at the start; the kinetic table is fetched the same way while
+// the forward FFT runs.  The potential factor is applied as the last
 // inverse pass stores, the x kinetic factor as the row is written back.
 template <typename R, int LOGN, int LOGE, int LOGRM, int MODE>
 __global__ void __launch_bounds__(Cfg1D<R, LOGN, LOGE, LOGRM>::T, Cfg1D<R, LOGN, LOGE, LOGRM>::MINB)
@@ -57,13 +73,19 @@ row_pass_kernel(Geo2D g, void* __restrict__ psi_v, int row0, const void* __restr
                 const int* __restrict__ rows)
 {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
+    using RC = Cfg2DRow<R, LOGN, LOGE, LOGRM>;
     using C = typename K::C;
     using TT = typename K::TT;
     using VT = typename VabT<R>::T;
     constexpr int N = K::N, T = K::T, E = K::E;
+    constexpr bool POT = MODE == ROW_FULL || MODE == ROW_A || MODE == ROW_B;
+    constexpr bool KIN = MODE == ROW_FULL || MODE == ROW_B || MODE == ROW_FWD;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* S = reinterpret_cast<C*>(smem_raw);
     C* scan = S + N;
+    VT* Tv = reinterpret_cast<VT*>(smem_raw + RC::OFF_B);
+    TT* Tk = reinterpret_cast<TT*>(smem_raw + RC::OFF_B);
+    C* Ws = reinterpret_cast<C*>(smem_raw + RC::OFF_W);
     const int tid = threadIdx.x;
     const int y = rows ? __ldg(&rows[row0 + (int)blockIdx.x]) : (row0 + (int)blockIdx.x) % g.ny;
     C* __restrict__ row = reinterpret_cast<C*>(psi_v) + (int64_t)y * N;
@@ -74,19 +96,28 @@ row_pass_kernel(Geo2D g, void* __restrict__ psi_v, int row0, const void* __restr
 #pragma unroll
     for (int j = 0; j < E; ++j) {
         const int n = tid + j * T;
-        C v = row[n];
-        if (MODE == ROW_B) v = vmul(v, __ldg(&tv[n]));
-        S[swz<C>(n)] = v;
+        cp_async<sizeof(C)>(&S[swz<C>(n)], &row[n]);
+        if constexpr (POT) cp_async<sizeof(VT)>(&Tv[n], &tv[n]);
+    }
+    for (int i = tid; i < RC::TWN; i += T) cp_async<sizeof(C)>(&Ws[i], &W[i]);
+    cp_async_commit();
+    cp_async_wait<0>();
+    if constexpr (MODE == ROW_B) {
+#pragma unroll
+        for (int j = 0; j < E; ++j) {         // the thread's own copies
+            const int n = tid + j * T;
+            S[swz<C>(n)] = vmul(S[swz<C>(n)], Tv[n]);
+        }
     }
     __syncthreads();
-    if (MODE == ROW_INV) {
-        inv_fft<R, LOGN, LOGE, LOGRM, K::NPASS - 1>(S, W, tid);
-    } else if (MODE == ROW_FULL || MODE == ROW_A) {
-        inv_fft<R, LOGN, LOGE, LOGRM, K::NPASS - 1, 1>(S, W, tid);
+    if constexpr (MODE == ROW_INV) {
+        inv_passes<R, LOGN, LOGE, LOGRM, K::NPASS - 1, 0>(S, Ws, tid);
+    } else if constexpr (MODE == ROW_FULL || MODE == ROW_A) {
+        inv_passes<R, LOGN, LOGE, LOGRM, K::NPASS - 1, 1>(S, Ws, tid);
         // e^{-iU tau/2}; off the x-strip block of a full row pass the second
         // half factor too
-        inv_pass0_post<R, LOGN, LOGE, LOGRM>(S, W, tid, [&](int n, C v) {
-            const VT t = __ldg(&tv[n]);
+        inv_pass0_post<R, LOGN, LOGE, LOGRM, true>(S, Ws, tid, [&](int n, C v) {
+            const VT t = Tv[n];
             v = vmul(v, t);
             if (MODE == ROW_FULL && ((n - g.blk0x) & (N - 1)) >= g.nbx) v = vmul(v, t);
             return v;
@@ -94,20 +125,29 @@ row_pass_kernel(Geo2D g, void* __restrict__ psi_v, int row0, const void* __restr
         __syncthreads();
         if (g.nbx > 0) {
             const C* cn = reinterpret_cast<const C*>(g.cnx);
-            if (MODE == ROW_FULL)
+            if constexpr (MODE == ROW_FULL)
                 strip_cn<C, T, K::CMAX, N>(S, cn, g.nbx, g.blk0x, tid, scan,
-                                           [&](int n, C v) { return vmul(v, __ldg(&tv[n])); });
+                                           [&](int n, C v) { return vmul(v, Tv[n]); });
             else
                 strip_cn<C, T, K::CMAX, N>(S, cn, g.nbx, g.blk0x, tid, scan, [](int, C v) { return v; });
             __syncthreads();
         }
     }
-    if (MODE == ROW_FULL || MODE == ROW_B || MODE == ROW_FWD) {
-        fwd_fft<R, LOGN, LOGE, LOGRM, 0>(S, W, tid);
+    if constexpr (KIN) {
+        // the potential buffer is free now: fetch the kinetic table into it
+        // (each thread the entries of its own outputs) behind the forward FFT
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            const int n = tid + j * T;
+            cp_async<sizeof(TT)>(&Tk[n], &tkx[n]);
+        }
+        cp_async_commit();
+        fwd_passes<R, LOGN, LOGE, LOGRM, 0, K::NPASS>(S, Ws, tid);
+        cp_async_wait<0>();
 #pragma unroll 4
         for (int j = 0; j < E; ++j) {
             const int n = tid + j * T;
-            row[n] = tmul(S[swz<C>(n)], __ldg(&tkx[n]));
+            row[n] = tmul(S[swz<C>(n)], Tk[n]);
         }
     } else {
 #pragma unroll 4
@@ -120,50 +160,60 @@ row_pass_kernel(Geo2D g, void* __restrict__ psi_v, int row0, const void* __restr
 
 // Column pass: TW columns per CTA, each transformed by T = ny/E threads:
 // F_y, e^{-i ky^2 tau/2}/ny, F_y^-1, with the last forward pass, the factor
-// and the first inverse pass fused (kcenter; table in its transposed order)
-// and the twiddles in shared memory.
+// and the first inverse pass fused (kcenter; table in its transposed order).
+// The column tile and the twiddles are staged in shared memory by
+// asynchronous copies issued together at the start; the kinetic table (the
+// same for every column) is read through the read-only cache.
 template <typename R, int LOGN, int LOGE, int LOGRM, int TW>
 struct ColCfg {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
+    using C = typename K::C;
+    using TT = typename K::TT;
     static constexpr int THREADS = TW * K::T;
     static constexpr int MINB = THREADS >= 512 ? 1 : 512 / THREADS;   // <= 128 registers
     // column pitch: N + 64 bytes, so that the TW columns of one row fall in
     // different banks when the tile is filled and drained row by row
-    static constexpr int PITCH = K::N + 64 / (int)sizeof(typename K::C);
-    static constexpr size_t SMEM = sizeof(typename K::C) * ((size_t)TW * PITCH + TwCount<LOGN, LOGRM>::value);
+    static constexpr int PITCH = K::N + 64 / (int)sizeof(C);
+    static constexpr int TWN = TwCount<LOGN, LOGRM>::value;
+    static constexpr size_t OFF_W = sizeof(C) * (size_t)TW * PITCH;
+    static constexpr size_t SMEM = OFF_W + sizeof(C) * TWN;
+    static_assert(OFF_W % 16 == 0, "16-byte aligned parts");
 };
 
 template <typename R, int LOGN, int LOGE, int LOGRM, int TW>
 __global__ void __launch_bounds__(ColCfg<R, LOGN, LOGE, LOGRM, TW>::THREADS, ColCfg<R, LOGN, LOGE, LOGRM, TW>::MINB)
 col_pass_kernel(LineGeo lg, void* __restrict__ psi_v, const void* __restrict__ tky_v)
 {
+    using CC = ColCfg<R, LOGN, LOGE, LOGRM, TW>;
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
     using C = typename K::C;
     using TT = typename K::TT;
     constexpr int N = K::N, T = K::T;
-    constexpr int TWN = TwCount<LOGN, LOGRM>::value;
-    constexpr int PITCH = ColCfg<R, LOGN, LOGE, LOGRM, TW>::PITCH;
+    constexpr int PITCH = CC::PITCH;
     constexpr int NIT = N / T;                      // tile elements per thread
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* S = reinterpret_cast<C*>(smem_raw);
-    C* Ws = S + TW * PITCH;
+    C* Ws = reinterpret_cast<C*>(smem_raw + CC::OFF_W);
     const int64_t nx = lg.ld;
     const int64_t gpp = nx / TW;                    // CTAs per plane
     C* __restrict__ psi = reinterpret_cast<C*>(psi_v) + (int64_t)(blockIdx.x / gpp) * lg.plane;
     const C* __restrict__ W = reinterpret_cast<const C*>(lg.W);
+    const TT* __restrict__ tky = reinterpret_cast<const TT*>(tky_v);
     const int64_t c0 = (int64_t)(blockIdx.x % gpp) * TW;
 #pragma unroll 8
     for (int it = 0; it < NIT; ++it) {              // row by row: the TW columns of a row are adjacent
         const int idx = threadIdx.x + it * TW * T;
         const int yy = idx / TW, j = idx % TW;
-        S[j * PITCH + swz<C>(yy)] = psi[(int64_t)yy * nx + c0 + j];
+        cp_async<sizeof(C)>(&S[j * PITCH + swz<C>(yy)], &psi[(int64_t)yy * nx + c0 + j]);
     }
-    for (int i = threadIdx.x; i < TWN; i += TW * T) Ws[i] = __ldg(&W[i]);
+    for (int i = threadIdx.x; i < CC::TWN; i += TW * T) cp_async<sizeof(C)>(&Ws[i], &W[i]);
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
     const int col = threadIdx.x / T, tid = threadIdx.x % T;
     C* Sc = S + col * PITCH;
     fwd_passes<R, LOGN, LOGE, LOGRM, 0, K::NPASS - 1>(Sc, Ws, tid);
-    kcenter<R, LOGN, LOGE, LOGRM>(Sc, reinterpret_cast<const TT*>(tky_v), tid);
+    kcenter<R, LOGN, LOGE, LOGRM>(Sc, tky, tid);
     __syncthreads();
     inv_passes<R, LOGN, LOGE, LOGRM, K::NPASS - 2, 0>(Sc, Ws, tid);
 #pragma unroll 8
@@ -197,13 +247,15 @@ cny_kernel(CnGeo g, void* __restrict__ psi_v)
     // rows are a chunk apart, which in global memory touched one cache
     // line per lane)
     C* Scn = S + nb * PITCH;
-    for (int i = threadIdx.x; i < 3 * nb; i += blockDim.x) Scn[i] = __ldg(&cn[i]);
-#pragma unroll 8
-    for (int idx = threadIdx.x; idx < nb * TWC; idx += blockDim.x) {   // several rows in flight
+    // asynchronous copies: every row of the tile in flight at once
+    for (int i = threadIdx.x; i < 3 * nb; i += blockDim.x) cp_async<sizeof(C)>(&Scn[i], &cn[i]);
+    for (int idx = threadIdx.x; idx < nb * TWC; idx += blockDim.x) {
         const int r = idx / TWC, j = idx % TWC;
         const int yy = (g.blk0 + r) % ny;
-        S[r * PITCH + j] = psi[(int64_t)yy * nx + c0 + j];
+        cp_async<sizeof(C)>(&S[r * PITCH + j], &psi[(int64_t)yy * nx + c0 + j]);
     }
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ch = (nb + 31) / 32;          // host guarantees ch <= CH
