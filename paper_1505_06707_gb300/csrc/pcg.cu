@@ -115,7 +115,7 @@ static int build_pc(Plan2D* Q, int type, PcgTables& T, int prec = SOFT_C128) {
     g.xfx = uc(umajor(bx, bx.xf)); g.xfy = uc(umajor(by, by.xf));
     g.xbx = uc(umajor(bx, bx.xb)); g.xby = uc(umajor(by, by.xb));
     g.lamx = uc(bx.lam); g.lamy = uc(by.lam);
-    if (prec == SOFT_C64) {      // FFT twiddles of the FP32 passes
+    {                            // FFT twiddles (the four bases per pass)
         auto ut = [&](const std::vector<cd>& v) -> const void* {
             void* d = nullptr;
             if (upload_tw(&d, v, prec)) return nullptr;
@@ -158,7 +158,6 @@ static int ensure_tables(Plan2D* Q) {
         if ((rc = build_pc(Q, f32 ? 1 : type, S->pc[type], f32 ? SOFT_C64 : SOFT_C128))) return rc;
         PcgGeo& g = S->pc[type].geo;
         g.nx = Q->nx; g.ny = Q->ny; g.N = S->N;
-        if (!f32) { g.Wx = Q->Wx; g.Wy = Q->Wy; }
         g.Kx = f32 ? S->Kx32 : S->Kx; g.Ky = f32 ? S->Ky32 : S->Ky; g.U = f32 ? S->U32 : S->U;
         g.Cx = f32 ? S->Cx32 : S->Cx; g.Cy = f32 ? S->Cy32 : S->Cy;
         g.nbx = Q->geo.nbx; g.blk0x = Q->geo.blk0x; g.nby = Q->geo.nby; g.blk0y = Q->geo.blk0y;

@@ -153,8 +153,14 @@ int create_2d(const soft_grid* grid, const double* box, double R0, double theta,
         cny = mfy; cny.insert(cny.end(), mby.begin(), mby.end()); cny.insert(cny.end(), gy.begin(), gy.end());
     }
     const int pr = o.prec;
-    if ((rc = upload_tw(&Q->Wx, pass_twiddles(lx, Q->lrx), pr))) return rc;
-    if ((rc = upload_tw(&Q->Wy, pass_twiddles(ly, Q->lry), pr))) return rc;
+    // pass twiddles: the four bases per pass (complex64); every W^{M off} of
+    // the small-stride passes (complex128, FP64-pipe bound)
+    auto twid = [&](void** d, int logn, int logrm) {
+        return pr == SOFT_C128 ? upload_c(d, pass_twiddles_full(logn, logrm, TWFULL_MAXS), pr)
+                               : upload_tw(d, pass_twiddles(logn, logrm), pr);
+    };
+    if ((rc = twid(&Q->Wx, lx, Q->lrx))) return rc;
+    if ((rc = twid(&Q->Wy, ly, Q->lry))) return rc;
     if ((rc = upload_tab(&Q->TKx, ktab(Q->ax, lx, Q->lrx, 1.0, false), pr))) return rc;
     if ((rc = upload_tab(&Q->TKhx, ktab(Q->ax, lx, Q->lrx, 0.5, false), pr))) return rc;
     if ((rc = upload_tab(&Q->TKy, ktab(Q->ay, ly, Q->lry, 1.0, true), pr))) return rc;

@@ -19,6 +19,14 @@ namespace soft {
 
 enum RowMode { ROW_FWD = 0, ROW_FULL = 1, ROW_A = 2, ROW_B = 3, ROW_INV = 4 };
 
+// Pass twiddles of the line passes: complex64 plans store the four bases
+// W^{2^k off} of each pass (float2); complex128 plans, which are bound by the
+// FP64 pipe, store every W^{M off} for the passes with a stride of at most
+// TWFULL_MAXS and W^{M off}, M = 1 .. 4, for the others (TwFullD), as the
+// complex128 1D step does.
+template <typename R> struct Tw2D { using T = typename CT<R>::C; };
+template <> struct Tw2D<double> { using T = TwFullD; };
+
 // Shared memory of the row pass: the row (swizzled) and the scan scratch of
 // the strip CN; one table buffer that holds the row's e^{-iU tau/2} while
 // the potential is applied and the kinetic table afterwards; the twiddles.
@@ -27,34 +35,37 @@ struct Cfg2DRow : Cfg1D<R, LOGN, LOGE, LOGRM> {
     using C = typename CT<R>::C;
     using VT = typename VabT<R>::T;
     using TT = typename TabT<R>::T;
+    using TWT = typename Tw2D<R>::T;
     static constexpr int N = 1 << LOGN;
-    static constexpr int TWN = TwCount<LOGN, LOGRM>::value;
+    static constexpr int TWN = TwCountT<TWT, LOGN, LOGRM>::value;
     static constexpr size_t OFF_B = sizeof(C) * (N + 64);
     static constexpr size_t BYTES_B = (sizeof(VT) > sizeof(TT) ? sizeof(VT) : sizeof(TT)) * N;
     static constexpr size_t OFF_W = OFF_B + BYTES_B;
-    static constexpr size_t SMEM2 = OFF_W + sizeof(C) * TWN;
+    static constexpr size_t SMEM2 = OFF_W + sizeof(TWT) * TWN;
     static_assert(OFF_B % 16 == 0 && OFF_W % 16 == 0, "16-byte aligned parts");
 };
 
 // Inverse pass 0 with post(n, v) applied to every output as it is stored
 // (SH: twiddles in shared memory).
-template <typename R, int LOGN, int LOGE, int LOGRM, bool SH, class Post>
-__device__ __forceinline__ void inv_pass0_post(typename CT<R>::C* S, const typename CT<R>::C* __restrict__ W,
-                                               int tid, Post post) {
+template <typename R, int LOGN, int LOGE, int LOGRM, bool SH, typename TW, class Post>
+__device__ __forceinline__ void inv_pass0_post(typename CT<R>::C* S, const TW* __restrict__ W, int tid,
+                                               Post post) {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
     using C = typename K::C;
     using G = PassGeom<LOGN, LOGRM, 0>;
     constexpr int LOGR = G::LOGR, RR = 1 << LOGR;
     constexpr int s = G::S;
-    constexpr int NB = G::LOGR;
+    constexpr bool FULL = TwLay<TW>::template full<LOGN, LOGRM, 0>();
 #pragma unroll 1
     for (int u = 0; u < K::E / RR; ++u) {
         const int off = tid + u * K::T;
         const int sb = swz<C>(off);
         C v[RR];
-        C tb[4];
-        if constexpr (s > 1) load_tw<C, NB, s, SH>(tb, W + G::TOFF + off);
-        LoadInv<C, C, RR, s, 0>::run(S, v, tb, sb, s > 1);
+        TW tb[FULL ? RR - 1 : 4];
+        if constexpr (s > 1)
+            load_tw<TW, TwLay<TW>::template rows<LOGN, LOGRM, 0>(), s, SH>(
+                tb, W + TwLay<TW>::template toff<LOGN, LOGRM, 0>() + off);
+        LoadInv<C, TW, RR, s, 0, FULL>::run(S, v, tb, sb, s > 1);
         dft_reg<C, RR, +1>(v);
 #pragma unroll
         for (int m = 0; m < RR; ++m) S[sb ^ swz<C>(m * s)] = post(off + m * s, v[bitrev_c(m, LOGR)]);
@@ -85,11 +96,12 @@ row_pass_kernel(Geo2D g, void* __restrict__ psi_v, int row0, const void* __restr
     C* scan = S + N;
     VT* Tv = reinterpret_cast<VT*>(smem_raw + RC::OFF_B);
     TT* Tk = reinterpret_cast<TT*>(smem_raw + RC::OFF_B);
-    C* Ws = reinterpret_cast<C*>(smem_raw + RC::OFF_W);
+    using TWT = typename RC::TWT;
+    TWT* Ws = reinterpret_cast<TWT*>(smem_raw + RC::OFF_W);
     const int tid = threadIdx.x;
     const int y = rows ? __ldg(&rows[row0 + (int)blockIdx.x]) : (row0 + (int)blockIdx.x) % g.ny;
     C* __restrict__ row = reinterpret_cast<C*>(psi_v) + (int64_t)y * N;
-    const C* __restrict__ W = reinterpret_cast<const C*>(g.Wx);
+    const TWT* __restrict__ W = reinterpret_cast<const TWT*>(g.Wx);
     const VT* __restrict__ tv = reinterpret_cast<const VT*>(g.TVh) + (int64_t)y * N;
     const TT* __restrict__ tkx = reinterpret_cast<const TT*>(tkx_v);
 
@@ -99,7 +111,7 @@ row_pass_kernel(Geo2D g, void* __restrict__ psi_v, int row0, const void* __restr
         cp_async<sizeof(C)>(&S[swz<C>(n)], &row[n]);
         if constexpr (POT) cp_async<sizeof(VT)>(&Tv[n], &tv[n]);
     }
-    for (int i = tid; i < RC::TWN; i += T) cp_async<sizeof(C)>(&Ws[i], &W[i]);
+    for (int i = tid; i < RC::TWN; i += T) cp_async<sizeof(TWT)>(&Ws[i], &W[i]);
     cp_async_commit();
     cp_async_wait<0>();
     if constexpr (MODE == ROW_B) {
@@ -174,9 +186,10 @@ struct ColCfg {
     // column pitch: N + 64 bytes, so that the TW columns of one row fall in
     // different banks when the tile is filled and drained row by row
     static constexpr int PITCH = K::N + 64 / (int)sizeof(C);
-    static constexpr int TWN = TwCount<LOGN, LOGRM>::value;
+    using TWT = typename Tw2D<R>::T;
+    static constexpr int TWN = TwCountT<TWT, LOGN, LOGRM>::value;
     static constexpr size_t OFF_W = sizeof(C) * (size_t)TW * PITCH;
-    static constexpr size_t SMEM = OFF_W + sizeof(C) * TWN;
+    static constexpr size_t SMEM = OFF_W + sizeof(TWT) * TWN;
     static_assert(OFF_W % 16 == 0, "16-byte aligned parts");
 };
 
@@ -193,11 +206,12 @@ col_pass_kernel(LineGeo lg, void* __restrict__ psi_v, const void* __restrict__ t
     constexpr int NIT = N / T;                      // tile elements per thread
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* S = reinterpret_cast<C*>(smem_raw);
-    C* Ws = reinterpret_cast<C*>(smem_raw + CC::OFF_W);
+    using TWT = typename CC::TWT;
+    TWT* Ws = reinterpret_cast<TWT*>(smem_raw + CC::OFF_W);
     const int64_t nx = lg.ld;
     const int64_t gpp = nx / TW;                    // CTAs per plane
     C* __restrict__ psi = reinterpret_cast<C*>(psi_v) + (int64_t)(blockIdx.x / gpp) * lg.plane;
-    const C* __restrict__ W = reinterpret_cast<const C*>(lg.W);
+    const TWT* __restrict__ W = reinterpret_cast<const TWT*>(lg.W);
     const TT* __restrict__ tky = reinterpret_cast<const TT*>(tky_v);
     const int64_t c0 = (int64_t)(blockIdx.x % gpp) * TW;
 #pragma unroll 8
@@ -206,7 +220,7 @@ col_pass_kernel(LineGeo lg, void* __restrict__ psi_v, const void* __restrict__ t
         const int yy = idx / TW, j = idx % TW;
         cp_async<sizeof(C)>(&S[j * PITCH + swz<C>(yy)], &psi[(int64_t)yy * nx + c0 + j]);
     }
-    for (int i = threadIdx.x; i < CC::TWN; i += TW * T) cp_async<sizeof(C)>(&Ws[i], &W[i]);
+    for (int i = threadIdx.x; i < CC::TWN; i += TW * T) cp_async<sizeof(TWT)>(&Ws[i], &W[i]);
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
