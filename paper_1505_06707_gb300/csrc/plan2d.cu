@@ -154,10 +154,10 @@ int create_2d(const soft_grid* grid, const double* box, double R0, double theta,
     }
     const int pr = o.prec;
     // pass twiddles: the four bases per pass (complex64); every W^{M off} of
-    // the small-stride passes (complex128, FP64-pipe bound)
+    // the small-stride passes (complex128)
     auto twid = [&](void** d, int logn, int logrm) {
-        return pr == SOFT_C128 ? upload_c(d, pass_twiddles_full(logn, logrm, TWFULL_MAXS), pr)
-                               : upload_tw(d, pass_twiddles(logn, logrm), pr);
+        return upload_tw(d, pr == SOFT_C128 ? pass_twiddles_full(logn, logrm, TWFULL_MAXS)
+                                            : pass_twiddles(logn, logrm), pr);
     };
     if ((rc = twid(&Q->Wx, lx, Q->lrx))) return rc;
     if ((rc = twid(&Q->Wy, ly, Q->lry))) return rc;

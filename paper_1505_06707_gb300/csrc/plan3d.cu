@@ -183,8 +183,8 @@ int create_3d(const soft_grid* grid, const double* box, double R0, double theta,
     };
     const int pr = o.prec;
     for (int d = 0; d < 3; ++d) {
-        if ((rc = pr == SOFT_C128 ? upload_c(&Q->W[d], pass_twiddles_full(Q->l[d], Q->lr[d], TWFULL_MAXS), pr)
-                                  : upload_tw(&Q->W[d], pass_twiddles(Q->l[d], Q->lr[d]), pr)))
+        if ((rc = upload_tw(&Q->W[d], pr == SOFT_C128 ? pass_twiddles_full(Q->l[d], Q->lr[d], TWFULL_MAXS)
+                                                     : pass_twiddles(Q->l[d], Q->lr[d]), pr)))
             return rc;
         if ((rc = upload_tab(&Q->TK[d], ktab(d, 1.0), pr))) return rc;
         if ((rc = upload_tab(&Q->TKh[d], ktab(d, 0.5), pr))) return rc;

@@ -69,8 +69,11 @@ __device__ __forceinline__ float2 tmulc(float2 x, float4 t) {
 // four bases: the products of bases cost 16 of the ~100 FP64 instructions
 // of a radix-8 butterfly, and the kernel is bound by the FP64 pipe.  Passes
 // with a larger stride keep the bases (their full table would not fit in
-// shared memory).
-struct TwFullD { double2 v; };
+// shared memory).  The complex64 line passes of the 2D and 3D steps use the
+// same layout with float2 entries.
+template <typename C> struct TwFull { C v; };
+using TwFullD = TwFull<double2>;
+using TwFullF = TwFull<float2>;
 
 template <typename R> struct TwT;
 template <> struct TwT<float> { using T = float4; };
@@ -131,22 +134,22 @@ template <typename C, typename TW, int M, bool FULL = false> struct TwMul {
     __device__ __forceinline__ static C fwd(C y, const C* b) { return cmul(y, tw_pow<C, M>(b)); }
     __device__ __forceinline__ static C inv(C y, const C* b) { return cmulc(y, tw_pow<C, M>(b)); }
 };
-// complex128 tables: full passes hold b[M - 1] = W^{M off}; the other
-// passes hold W^{M off} for M = 1 .. 4, and W^{M off} = W^{4 off} W^{(M-4) off}
-// above (radix <= 8: one product instead of up to two)
-template <int M> __device__ __forceinline__ double2 tw_d(const TwFullD* b) {
-    static_assert(M >= 1 && M < 8, "complex128 passes have radix <= 8");
+// full tables: full passes hold b[M - 1] = W^{M off}; the other passes hold
+// W^{M off} for M = 1 .. 4, and W^{M off} = W^{4 off} W^{(M-4) off} above
+// (radix 8: one product instead of up to two)
+template <typename C, int M> __device__ __forceinline__ C tw_full(const TwFull<C>* b) {
+    static_assert(M >= 1 && M < 16, "radix <= 16");
     if constexpr (M <= 4) return b[M - 1].v;
-    else return cmul(b[3].v, b[M - 5].v);
+    else return cmul(b[3].v, tw_full<C, M - 4>(b));
 }
-template <int M, bool FULL> struct TwMul<double2, TwFullD, M, FULL> {
-    __device__ __forceinline__ static double2 fwd(double2 y, const TwFullD* b) {
+template <typename C, int M, bool FULL> struct TwMul<C, TwFull<C>, M, FULL> {
+    __device__ __forceinline__ static C fwd(C y, const TwFull<C>* b) {
         if constexpr (FULL) return cmul(y, b[M - 1].v);
-        else return cmul(y, tw_d<M>(b));
+        else return cmul(y, tw_full<C, M>(b));
     }
-    __device__ __forceinline__ static double2 inv(double2 y, const TwFullD* b) {
+    __device__ __forceinline__ static C inv(C y, const TwFull<C>* b) {
         if constexpr (FULL) return cmulc(y, b[M - 1].v);
-        else return cmulc(y, tw_d<M>(b));
+        else return cmulc(y, tw_full<C, M>(b));
     }
 };
 template <int M, bool FULL> struct TwMul<float2, float4, M, FULL> {
@@ -225,7 +228,7 @@ template <typename TW> struct TwLay {      // the four bases W^{2^k off} on ever
     template <int LOGN, int LOGRM, int P> static constexpr int toff() { return PassGeom<LOGN, LOGRM, P>::TOFF; }
     template <int LOGN, int LOGRM, int P> static constexpr int rows() { return PassGeom<LOGN, LOGRM, P>::LOGR; }
 };
-template <> struct TwLay<TwFullD> {       // every W^{M off}, or M = 1 .. 4 (tw_d)
+template <typename C> struct TwLay<TwFull<C>> {   // every W^{M off}, or M = 1 .. 4 (tw_full)
     template <int LOGN, int LOGRM, int P> static constexpr bool full() { return TwGeomFull<LOGN, LOGRM, P>::FULL; }
     template <int LOGN, int LOGRM, int P> static constexpr int toff() { return TwGeomFull<LOGN, LOGRM, P>::TOFF; }
     template <int LOGN, int LOGRM, int P> static constexpr int rows() {
@@ -243,8 +246,8 @@ struct TwCount {
 // the same for the table layout of twiddle type TW
 template <typename TW, int LOGN, int LOGRM>
 struct TwCountT { static constexpr int value = TwCount<LOGN, LOGRM>::value; };
-template <int LOGN, int LOGRM>
-struct TwCountT<TwFullD, LOGN, LOGRM> {
+template <typename C, int LOGN, int LOGRM>
+struct TwCountT<TwFull<C>, LOGN, LOGRM> {
     static constexpr int NP = LOGN / LOGRM + ((LOGN % LOGRM) ? 1 : 0);
     static constexpr int value = TwGeomFull<LOGN, LOGRM, NP - 1>::TOFF +
                                  TwGeomFull<LOGN, LOGRM, NP - 1>::ROWS * PassGeom<LOGN, LOGRM, NP - 1>::S;

@@ -19,13 +19,16 @@ namespace soft {
 
 enum RowMode { ROW_FWD = 0, ROW_FULL = 1, ROW_A = 2, ROW_B = 3, ROW_INV = 4 };
 
-// Pass twiddles of the line passes: complex64 plans store the four bases
-// W^{2^k off} of each pass (float2); complex128 plans, which are bound by the
-// FP64 pipe, store every W^{M off} for the passes with a stride of at most
-// TWFULL_MAXS and W^{M off}, M = 1 .. 4, for the others (TwFullD), as the
-// complex128 1D step does.
-template <typename R> struct Tw2D { using T = typename CT<R>::C; };
-template <> struct Tw2D<double> { using T = TwFullD; };
+// Pass twiddles of the line passes.  Complex128 plans, which are bound by
+// the FP64 pipe, store every W^{M off} for the passes with a stride of at
+// most TWFULL_MAXS and W^{M off}, M = 1 .. 4, for the others (TwFull, as the
+// complex128 1D step), so a butterfly forms no products of bases.
+// Complex64 plans store the four bases W^{2^k off} per pass: their kernels
+// are bound by instruction issue with shared memory busy, and the full
+// tables' 15 loads per radix-16 butterfly measured slower than the 4 loads
+// and the products.
+template <typename R> struct Tw2D { using T = TwFull<typename CT<R>::C>; };
+template <> struct Tw2D<float> { using T = float2; };
 
 // Shared memory of the row pass: the row (swizzled) and the scan scratch of
 // the strip CN; one table buffer that holds the row's e^{-iU tau/2} while
@@ -38,8 +41,12 @@ struct Cfg2DRow : Cfg1D<R, LOGN, LOGE, LOGRM> {
     using TWT = typename Tw2D<R>::T;
     static constexpr int N = 1 << LOGN;
     static constexpr int TWN = TwCountT<TWT, LOGN, LOGRM>::value;
+    // the kinetic table is staged when it fits the potential buffer
+    // (complex128); complex64 reads its compensated float4 entries through
+    // the read-only cache, which keeps four CTAs per SM
+    static constexpr bool STAGE_K = sizeof(TT) <= sizeof(VT);
     static constexpr size_t OFF_B = sizeof(C) * (N + 64);
-    static constexpr size_t BYTES_B = (sizeof(VT) > sizeof(TT) ? sizeof(VT) : sizeof(TT)) * N;
+    static constexpr size_t BYTES_B = sizeof(VT) * N;
     static constexpr size_t OFF_W = OFF_B + BYTES_B;
     static constexpr size_t SMEM2 = OFF_W + sizeof(TWT) * TWN;
     static_assert(OFF_B % 16 == 0 && OFF_W % 16 == 0, "16-byte aligned parts");
@@ -75,8 +82,8 @@ __device__ __forceinline__ void inv_pass0_post(typename CT<R>::C* S, const TW* _
 // One CTA per row.  Rows are rows[row0 + blockIdx.x] with a row list, else
 // (row0 + blockIdx.x) mod ny.  The row, its potential factors and the
 // twiddles are staged in shared memory by asynchronous copies issued
-// together at the start; the kinetic table is fetched the same way while
-// the forward FFT runs.  The potential factor is applied as the last
+// together at the start; the kinetic table (complex128) is fetched the same
+// way while the forward FFT runs.  The potential factor is applied as the last
 // inverse pass stores, the x kinetic factor as the row is written back.
 template <typename R, int LOGN, int LOGE, int LOGRM, int MODE>
 __global__ void __launch_bounds__(Cfg1D<R, LOGN, LOGE, LOGRM>::T, Cfg1D<R, LOGN, LOGE, LOGRM>::MINB)
@@ -146,20 +153,23 @@ row_pass_kernel(Geo2D g, void* __restrict__ psi_v, int row0, const void* __restr
         }
     }
     if constexpr (KIN) {
-        // the potential buffer is free now: fetch the kinetic table into it
-        // (each thread the entries of its own outputs) behind the forward FFT
+        if constexpr (RC::STAGE_K) {
+            // the potential buffer is free now: fetch the kinetic table into
+            // it (each thread the entries of its own outputs) behind the FFT
 #pragma unroll
-        for (int j = 0; j < E; ++j) {
-            const int n = tid + j * T;
-            cp_async<sizeof(TT)>(&Tk[n], &tkx[n]);
+            for (int j = 0; j < E; ++j) {
+                const int n = tid + j * T;
+                cp_async<sizeof(TT)>(&Tk[n], &tkx[n]);
+            }
+            cp_async_commit();
         }
-        cp_async_commit();
         fwd_passes<R, LOGN, LOGE, LOGRM, 0, K::NPASS>(S, Ws, tid);
-        cp_async_wait<0>();
+        if constexpr (RC::STAGE_K) cp_async_wait<0>();
 #pragma unroll 4
         for (int j = 0; j < E; ++j) {
             const int n = tid + j * T;
-            row[n] = tmul(S[swz<C>(n)], Tk[n]);
+            if constexpr (RC::STAGE_K) row[n] = tmul(S[swz<C>(n)], Tk[n]);
+            else row[n] = tmul(S[swz<C>(n)], __ldg(&tkx[n]));
         }
     } else {
 #pragma unroll 4
