@@ -273,8 +273,8 @@ def cpu_baseline_sample():
 def bench_2d(S, torch, dev, args):
     """The 2D workload (2048^2, sharp theta = 0.4): throughput of the step in
     both precisions, and its HBM rate counting the minimum traffic of the pass
-    structure: 5 state passes-equivalent per step (row pass, column pass, and
-    the y-strip rows' extra round trips) plus the potential table once."""
+    structure: the row pass and the column pass each read and write the state
+    and read the potential table once (4 S + 2 table bytes per point-step)."""
     import numpy as np
     import workloads as W
     w = W.w3()
@@ -299,8 +299,8 @@ def bench_2d(S, torch, dev, args):
         sec = e0.elapsed_time(e1) / 1e3
         steps = nst * reps
         Sb = 8 if prec == S.SOFT_C64 else 16
-        tab = 8 if prec == S.SOFT_C64 else 16             # e^{-iU tau/2} per point (c64: minus 1, float2), read ~1.25x
-        bytes_pt = 5 * Sb + 1.25 * tab
+        tab = 8 if prec == S.SOFT_C64 else 16             # e^{-iU tau/2} per point (c64: minus 1, float2)
+        bytes_pt = 4 * Sb + 2 * tab
         gps = n * n * steps / sec
         res[name] = {"grid_point_steps_per_s": gps, "ms_per_step": 1e3 * sec / steps,
                      "hbm_GBps_alg": gps * bytes_pt / 1e9, "hbm_frac_alg": gps * bytes_pt / 1e9 / hbm,
@@ -316,9 +316,10 @@ def bench_2d(S, torch, dev, args):
 def bench_3d(S, torch, dev, args):
     """The 3D workload (256^3, sharp theta = 0.4) in both precisions, and
     512^3 in complex64: throughput of the step and its HBM rate counting the
-    minimum traffic of the pass structure, 6 state passes per step (rows, y
-    lines, z lines, each read and written once) plus the potential table
-    once; the strip rows' extra round trips are not counted."""
+    minimum traffic of the pass structure: rows, z lines and y lines each read
+    and write the state, the row and z passes read the potential table
+    (6 S + 2 table bytes per point-step; the y-strip CN pass, which touches
+    the strip block only, is not counted)."""
     import workloads as W
     w = W.w6()
     peaks, src = _peaks()
@@ -349,7 +350,7 @@ def bench_3d(S, torch, dev, args):
         steps = nst * reps
         Sb = 8 if prec == S.SOFT_C64 else 16
         tab = 8 if prec == S.SOFT_C64 else 16             # e^{-iU tau/2} per point (c64: minus 1, float2)
-        bytes_pt = 6 * Sb + tab
+        bytes_pt = 6 * Sb + 2 * tab
         pts = n ** 3
         gps = pts * steps / sec
         res[name] = {"n": n, "grid_point_steps_per_s": gps, "ms_per_step": 1e3 * sec / steps,

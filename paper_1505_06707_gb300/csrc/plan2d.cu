@@ -1,6 +1,6 @@
-// 2D plans: host FP64 tables for a [ny][nx] grid and the step driver (row,
-// column and y-strip passes, replayed from a CUDA graph).  The stationary
-// PCG entry points live in pcg.cu.
+// 2D plans: host FP64 tables for a [ny][nx] grid and the step driver (a row
+// pass and a column pass per step, replayed from a CUDA graph).  The
+// stationary PCG entry points live in pcg.cu.
 #include <cmath>
 #include <cstring>
 
@@ -39,38 +39,23 @@ Plan2D::~Plan2D() {
     free_pcg();
 }
 
-int Plan2D::row(int mode, void* psi, int row0, int nrows, const void* tkx, cudaStream_t st) {
+int Plan2D::row(int mode, void* psi, const void* tkx, cudaStream_t st) {
     ++launches;
-    if (prec == SOFT_C64) return soft2d_row_c64(lx, lex, lrx, mode, geo, psi, row0, nrows, tkx, nullptr, st);
-    return soft2d_row_c128(lx, lex, lrx, mode, geo, psi, row0, nrows, tkx, nullptr, st);
+    if (prec == SOFT_C64) return soft2d_row_c64(lx, lex, lrx, mode, geo, psi, ny, tkx, st);
+    return soft2d_row_c128(lx, lex, lrx, mode, geo, psi, ny, tkx, st);
 }
-int Plan2D::col(void* psi, const void* tky, cudaStream_t st) {
+int Plan2D::col(int mode, void* psi, const void* tky, cudaStream_t st) {
     ++launches;
-    const LineGeo lg{geo.Wy, geo.nx, 0};
-    if (prec == SOFT_C64) return soft2d_col_c64(ly, ley, lry, lg, 1, psi, tky, st);
-    return soft2d_col_c128(ly, ley, lry, lg, 1, psi, tky, st);
-}
-int Plan2D::ypass(void* psi, cudaStream_t st) {
-    ++launches;
-    const CnGeo cg{geo.cny, geo.nby, geo.blk0y, geo.ny, geo.nx, 0};
-    if (prec == SOFT_C64) return soft2d_cny_c64(cg, 1, psi, st);
-    return soft2d_cny_c128(cg, 1, psi, st);
+    const LineGeo lg{geo.Wy, geo.nx, 0, geo.cny, geo.TVh, geo.nby, geo.blk0y};
+    if (prec == SOFT_C64) return soft2d_col_c64(ly, ley, lry, mode, lg, 1, psi, tky, st);
+    return soft2d_col_c128(ly, ley, lry, mode, lg, 1, psi, tky, st);
 }
 
-// one full step in (k_x, y) representation; last = use the half kinetic tables
-int Plan2D::enqueue_step(void* psi, bool last, cudaStream_t st) {
-    const void* tkx = last ? TKhx : TKx;
-    const void* tky = last ? TKhy : TKy;
+// one step in x space: row pass K_x, V/2, CN_x; column pass CN_y, V/2, K_y
+int Plan2D::enqueue_step(void* psi, const void* tkx, const void* tky, cudaStream_t st) {
     int rc;
-    const int nb = geo.nby;
-    // rows outside the y-strip block: F_x^-1, V with CN_x, F_x, x kinetic factor
-    if ((rc = row(ROW_FULL, psi, (geo.blk0y + nb) % ny, ny - nb, tkx, st))) return rc;
-    if (nb > 0) {
-        if ((rc = row(ROW_A, psi, geo.blk0y, nb, nullptr, st))) return rc;
-        if ((rc = ypass(psi, st))) return rc;
-        if ((rc = row(ROW_B, psi, geo.blk0y, nb, tkx, st))) return rc;
-    }
-    return col(psi, tky, st);
+    if ((rc = row(ROW_KVC, psi, tkx, st))) return rc;
+    return col(COL_CVK, psi, tky, st);
 }
 
 }  // namespace soft
@@ -108,12 +93,12 @@ int create_2d(const soft_grid* grid, const double* box, double R0, double theta,
     int bx0, nbx, by0, nby;
     if ((rc = find_block(Q->ax, &bx0, &nbx))) return rc;
     if ((rc = find_block(Q->ay, &by0, &nby))) return rc;
-    // strip rows per thread of the row pass, and per lane of the y pass
+    // strip rows per thread of the row pass and of the column pass
     const int thr = (int)(nx >> Q->lex);
     if ((nbx + thr - 1) / thr > (1 << Q->lex) / 4 + 2) return SOFT_ERR_UNSUPPORTED;
-    if ((nby + 31) / 32 > 24) return SOFT_ERR_UNSUPPORTED;
-    // the y-strip pass holds an 8-column tile and the LU coefficients in shared memory
-    if ((o.prec == SOFT_C64 ? 8 : 16) * (size_t)nby * 12 > 227 * 1024) return SOFT_ERR_UNSUPPORTED;
+    const int capy = o.prec == SOFT_C64 ? soft2d_col_strip_capacity_c64(ly, Q->ley, Q->lry)
+                                        : soft2d_col_strip_capacity_c128(ly, Q->ley, Q->lry);
+    if (nby > capy) return SOFT_ERR_UNSUPPORTED;
     // potential at (z(x), z(y)) and e^{-iU tau/2}
     Q->U.resize((size_t)nx * ny);
     Q->Uabs.resize((size_t)nx * ny);
@@ -127,17 +112,17 @@ int create_2d(const soft_grid* grid, const double* box, double R0, double theta,
             Q->U[yy * nx + xx] = u;
             tvh[yy * nx + xx] = std::exp(cd(0.0, -0.5 * dt) * u);
         }
-    // kinetic factors per axis, in each FFT's output order, 1/n folded in; the
-    // column pass reads its table in the last forward pass (butterflies of R
-    // consecutive positions b*R + m, stored at m*(n/R) + b)
-    auto ktab = [&](const Axis1D& A, int logn, int logrm, double frac, bool center) {
+    // kinetic factors per axis, 1/n folded in, read by the fused center of
+    // each line FFT (butterflies of R consecutive positions b*R + m of the
+    // digit-reversed spectrum, stored at m*(n/R) + b)
+    auto ktab = [&](const Axis1D& A, int logn, int logrm, double frac) {
         const std::vector<int> perm = dif_output_order(logn, logrm);
         const int lrl = (logn % logrm) ? logn % logrm : logrm;
         const int Rl = 1 << lrl, nbf = A.n >> lrl;
         std::vector<cd> t(A.n);
         for (int p = 0; p < A.n; ++p) {
             const double k = A.k[perm[p]];
-            const int q = center ? (p % Rl) * nbf + p / Rl : p;
+            const int q = (p % Rl) * nbf + p / Rl;
             t[q] = std::polar(1.0 / A.n, -0.5 * k * k * dt * frac);
         }
         return t;
@@ -161,10 +146,10 @@ int create_2d(const soft_grid* grid, const double* box, double R0, double theta,
     };
     if ((rc = twid(&Q->Wx, lx, Q->lrx))) return rc;
     if ((rc = twid(&Q->Wy, ly, Q->lry))) return rc;
-    if ((rc = upload_tab(&Q->TKx, ktab(Q->ax, lx, Q->lrx, 1.0, false), pr))) return rc;
-    if ((rc = upload_tab(&Q->TKhx, ktab(Q->ax, lx, Q->lrx, 0.5, false), pr))) return rc;
-    if ((rc = upload_tab(&Q->TKy, ktab(Q->ay, ly, Q->lry, 1.0, true), pr))) return rc;
-    if ((rc = upload_tab(&Q->TKhy, ktab(Q->ay, ly, Q->lry, 0.5, true), pr))) return rc;
+    if ((rc = upload_tab(&Q->TKx, ktab(Q->ax, lx, Q->lrx, 1.0), pr))) return rc;
+    if ((rc = upload_tab(&Q->TKhx, ktab(Q->ax, lx, Q->lrx, 0.5), pr))) return rc;
+    if ((rc = upload_tab(&Q->TKy, ktab(Q->ay, ly, Q->lry, 1.0), pr))) return rc;
+    if ((rc = upload_tab(&Q->TKhy, ktab(Q->ay, ly, Q->lry, 0.5), pr))) return rc;
     if ((rc = upload_vtab(&Q->TVh, tvh, pr))) return rc;
     if ((rc = upload_c(&Q->cnx, cnx, pr))) return rc;
     if ((rc = upload_c(&Q->cny, cny, pr))) return rc;
@@ -173,28 +158,30 @@ int create_2d(const soft_grid* grid, const double* box, double R0, double theta,
     g.nx = (int)nx; g.ny = (int)ny;
     g.nbx = nbx; g.blk0x = bx0; g.nby = nby; g.blk0y = by0;
     // set every kernel's shared-memory attribute now, outside any stream capture
-    for (int m = ROW_FWD; m <= ROW_INV; ++m)
-        if ((rc = Q->row(m, nullptr, 0, 0, nullptr, 0))) return rc;
-    if ((rc = Q->col(nullptr, nullptr, 0))) return rc;
-    if ((rc = Q->ypass(nullptr, 0))) return rc;
+    for (int m = ROW_K; m <= ROW_KVC; ++m)
+        if ((rc = Q->row(m, nullptr, nullptr, 0))) return rc;
+    for (int m = COL_K; m <= COL_CVK; ++m)
+        if ((rc = Q->col(m, nullptr, nullptr, 0))) return rc;
     Q->launches = 0;
     *out = P.release();
     return SOFT_OK;
 }
 
-// K^1/2 (V K)^{n-1} V K^1/2: forward row pass with the half x factor, a half
-// column pass, n steps (the last with half kinetic factors), inverse row pass.
-// The middle steps are replayed from a CUDA graph captured once per state
-// pointer and stream (chunks of GRAPH_STEPS steps).
+// The call in time order: K_y/2 (column pass), then n steps of [row pass
+// K_x, V/2, CN_x; column pass CN_y, V/2, K_y] with K_x/2 in the first row
+// pass and K_y/2 in the last column pass, then K_x/2 (row pass): the
+// printed K/2 V/2 CN V/2 K/2 per step with the inner half-kinetic factors
+// merged.  The middle steps are replayed from a CUDA graph captured once per
+// state pointer and stream (chunks of GRAPH_STEPS steps).
 int soft_plan::step_2d(void* psi, int64_t nsteps, double* t_inout, cudaStream_t st) {
     Plan2D* Q = p2;
     Q->launches = 0;
     last_launches = 0;
     if (nsteps == 0) return SOFT_OK;
     int rc;
-    if ((rc = Q->row(ROW_FWD, psi, 0, Q->ny, Q->TKhx, st))) return rc;
-    if ((rc = Q->col(psi, Q->TKhy, st))) return rc;
-    int64_t mid = nsteps - 1;
+    if ((rc = Q->col(COL_K, psi, Q->TKhy, st))) return rc;
+    if ((rc = Q->enqueue_step(psi, Q->TKhx, nsteps == 1 ? Q->TKhy : Q->TKy, st))) return rc;
+    int64_t mid = nsteps >= 2 ? nsteps - 2 : 0;
     const int64_t G = Plan2D::GRAPH_STEPS;
     if (mid >= G) {
         if (!Q->graph_exec || Q->graph_psi != psi || Q->graph_stream != st) {
@@ -204,7 +191,7 @@ int soft_plan::step_2d(void* psi, int64_t nsteps, double* t_inout, cudaStream_t 
             cudaGraph_t graph;
             const int64_t before = Q->launches;
             rc = cuda_status(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-            for (int64_t s = 0; s < G && rc == SOFT_OK; ++s) rc = Q->enqueue_step(psi, false, cap);
+            for (int64_t s = 0; s < G && rc == SOFT_OK; ++s) rc = Q->enqueue_step(psi, Q->TKx, Q->TKy, cap);
             cudaError_t e = cudaStreamEndCapture(cap, &graph);
             if (rc == SOFT_OK) rc = cuda_status(e);
             if (rc == SOFT_OK) rc = cuda_status(cudaGraphInstantiate(&Q->graph_exec, graph, 0));
@@ -223,9 +210,9 @@ int soft_plan::step_2d(void* psi, int64_t nsteps, double* t_inout, cudaStream_t 
         }
     }
     for (int64_t s = 0; s < mid; ++s)
-        if ((rc = Q->enqueue_step(psi, false, st))) return rc;
-    if ((rc = Q->enqueue_step(psi, true, st))) return rc;
-    if ((rc = Q->row(ROW_INV, psi, 0, Q->ny, nullptr, st))) return rc;
+        if ((rc = Q->enqueue_step(psi, Q->TKx, Q->TKy, st))) return rc;
+    if (nsteps >= 2 && (rc = Q->enqueue_step(psi, Q->TKx, Q->TKhy, st))) return rc;
+    if ((rc = Q->row(ROW_K, psi, Q->TKhx, st))) return rc;
     last_launches = Q->launches;
     *t_inout += (double)nsteps * dt;
     return SOFT_OK;

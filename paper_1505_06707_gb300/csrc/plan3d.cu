@@ -2,19 +2,18 @@
 //
 // The scheme is the one printed after Eq. C_FD (Sec. II) with
 // K = (kx^2 + ky^2 + kz^2)/2 and C = C_x + C_y + C_z as Kronecker sums (the
-// multidimensional case named at the end of Sec. V).  The three kinetic
-// factors act on different indices and the three CN factors commute, so one
-// step is a sequence of passes over lines of the grid, each a kernel of the
-// 2D step:
-//   rows (x lines) outside both the y and the z strip blocks:
-//       F_x^-1, e^{-iU tau/2}, CN_x, e^{-iU tau/2}, F_x, e^{-i kx^2 tau/2}
-//   rows inside either block: F_x^-1, e^{-iU tau/2}, CN_x (mode A); CN_y on
-//       the y block of every (z, x) line; CN_z on the z block of every (y, x)
-//       line; e^{-iU tau/2}, F_x, e^{-i kx^2 tau/2} (mode B)
-//   y lines: F_y, e^{-i ky^2 tau/2}, F_y^-1
-//   z lines: F_z, e^{-i kz^2 tau/2}, F_z^-1
-// Between steps the state is kept in (k_x, y, z); the middle steps are
-// replayed from a CUDA graph.
+// multidimensional case named at the end of Sec. V).  In time order the
+// merged scheme is ... V/2, CN, V/2, K ... with V/2 = e^{-iU tau/2}; factors
+// on different axes commute, so one step is four passes over the grid, the
+// state kept in x space between them:
+//   X  rows (x lines):     K_x, V/2, CN_x
+//   Y1 y-strip block:      CN_y
+//   Z  z lines:            CN_z, V/2, K_z
+//   Y2 y lines:            K_y
+// which is K_x | V/2 CN_x CN_y CN_z V/2 | K_z K_y per step; a call starts
+// with K_y/2, K_z/2 and ends with K_x/2, and the first and last steps use
+// the half factors K_x/2 and K_z/2, K_y/2.  The middle steps are replayed
+// from a CUDA graph.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -33,11 +32,9 @@ static int ilog2_3d(int64_t n) {
     return (int64_t(1) << l) == n ? l : -1;
 }
 
-static bool in_block(int i, int blk0, int nb, int n) { return ((i - blk0) % n + n) % n < nb; }
-
 Plan3D::~Plan3D() {
     void* bufs[] = {W[0], W[1], W[2], TK[0], TK[1], TK[2], TKh[0], TKh[1], TKh[2],
-                    TVh, cn[0], cn[1], cn[2], rows_full, rows_strip};
+                    TVh, cn[0], cn[1], cn[2]};
     for (void* b : bufs) cudaFree(b);
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
 }
@@ -76,20 +73,22 @@ int Plan3D::set_potential(const double* Uin) {
     return refill_vtab(TVh, half_factors(*this, Uin), prec);
 }
 
-int Plan3D::row(int mode, void* psi, int row0, int nrows, const int* rows, const void* tkx, cudaStream_t st) {
+int Plan3D::row(int mode, void* psi, const void* tkx, cudaStream_t st) {
     ++launches;
-    if (prec == SOFT_C64) return soft2d_row_c64(l[0], le[0], lr[0], mode, geo, psi, row0, nrows, tkx, rows, st);
-    return soft2d_row_c128(l[0], le[0], lr[0], mode, geo, psi, row0, nrows, tkx, rows, st);
+    const int nrows = n[1] * n[2];
+    if (prec == SOFT_C64) return soft2d_row_c64(l[0], le[0], lr[0], mode, geo, psi, nrows, tkx, st);
+    return soft2d_row_c128(l[0], le[0], lr[0], mode, geo, psi, nrows, tkx, st);
 }
 
-// the FFT, kinetic factor and inverse FFT of every line along axis d = 1, 2
-int Plan3D::line(int d, void* psi, const void* tk, cudaStream_t st) {
+// a line pass along axis d = 1, 2 (COL_K, or COL_CVK with the axis' strip CN
+// and V/2)
+int Plan3D::line(int d, int mode, void* psi, const void* tk, cudaStream_t st) {
     ++launches;
     const int64_t nx = n[0], ny = n[1];
-    const LineGeo lg{W[d], d == 1 ? nx : nx * ny, d == 1 ? nx * ny : 0};
+    const LineGeo lg{W[d], d == 1 ? nx : nx * ny, d == 1 ? nx * ny : 0, cn[d], TVh, nb[d], blk0[d]};
     const int planes = d == 1 ? n[2] : 1;
-    if (prec == SOFT_C64) return soft2d_col_c64(l[d], le[d], lr[d], lg, planes, psi, tk, st);
-    return soft2d_col_c128(l[d], le[d], lr[d], lg, planes, psi, tk, st);
+    if (prec == SOFT_C64) return soft2d_col_c64(l[d], le[d], lr[d], mode, lg, planes, psi, tk, st);
+    return soft2d_col_c128(l[d], le[d], lr[d], mode, lg, planes, psi, tk, st);
 }
 
 // CN on the strip block of every line along axis d = 1, 2
@@ -103,19 +102,19 @@ int Plan3D::cnpass(int d, void* psi, cudaStream_t st) {
     return soft2d_cny_c128(cg, planes, psi, st);
 }
 
-// one full step in (k_x, y, z) representation; last = the half kinetic tables
-int Plan3D::enqueue_step(void* psi, bool last, cudaStream_t st) {
-    const void* const* tk = last ? TKh : TK;
+int Plan3D::col_capacity(int d) const {
+    return prec == SOFT_C64 ? soft2d_col_strip_capacity_c64(l[d], le[d], lr[d])
+                            : soft2d_col_strip_capacity_c128(l[d], le[d], lr[d]);
+}
+
+// one step: X (K_x, V/2, CN_x), Y1 (CN_y), Z (CN_z, V/2, K_z), Y2 (K_y); the
+// first step of a call takes K_x/2, the last K_z/2 and K_y/2
+int Plan3D::enqueue_step(void* psi, bool first, bool last, cudaStream_t st) {
     int rc;
-    if (nfull > 0 && (rc = row(ROW_FULL, psi, 0, nfull, rows_full, tk[0], st))) return rc;
-    if (nstrip > 0) {
-        if ((rc = row(ROW_A, psi, 0, nstrip, rows_strip, nullptr, st))) return rc;
-        if ((rc = cnpass(1, psi, st))) return rc;
-        if ((rc = cnpass(2, psi, st))) return rc;
-        if ((rc = row(ROW_B, psi, 0, nstrip, rows_strip, tk[0], st))) return rc;
-    }
-    if ((rc = line(1, psi, tk[1], st))) return rc;
-    return line(2, psi, tk[2], st);
+    if ((rc = row(ROW_KVC, psi, first ? TKh[0] : TK[0], st))) return rc;
+    if ((rc = cnpass(1, psi, st))) return rc;
+    if ((rc = line(2, COL_CVK, psi, last ? TKh[2] : TK[2], st))) return rc;
+    return line(1, COL_K, psi, last ? TKh[1] : TK[1], st);
 }
 
 }  // namespace soft
@@ -157,26 +156,26 @@ int create_3d(const soft_grid* grid, const double* box, double R0, double theta,
         for (int i = 0; i < Q->n[d]; ++i) Q->ua[d][i] = cf.absorber(Q->ax[d].x[i]);
         if ((rc = find_block(Q->ax[d], &Q->blk0[d], &Q->nb[d]))) return rc;
     }
-    // strip rows per thread of the row pass, and per lane of the line CN
+    // strip rows per thread of the row pass, per lane of the y-strip CN pass
+    // (an 8-column tile and the LU coefficients in shared memory), and per
+    // thread of the z line pass
     const int thr = Q->n[0] >> Q->le[0];
     if ((Q->nb[0] + thr - 1) / thr > (1 << Q->le[0]) / 4 + 2) return SOFT_ERR_UNSUPPORTED;
-    for (int d = 1; d < 3; ++d) {
-        if ((Q->nb[d] + 31) / 32 > 24) return SOFT_ERR_UNSUPPORTED;
-        if ((o.prec == SOFT_C64 ? 8 : 16) * (size_t)Q->nb[d] * 12 > 227 * 1024) return SOFT_ERR_UNSUPPORTED;
-    }
-    // kinetic factors per axis, 1/n folded in: rows in the row FFT's output
-    // order; y and z lines in the transposed order of the fused center
+    if ((Q->nb[1] + 31) / 32 > 24) return SOFT_ERR_UNSUPPORTED;
+    if ((o.prec == SOFT_C64 ? 8 : 16) * (size_t)Q->nb[1] * 12 > 227 * 1024) return SOFT_ERR_UNSUPPORTED;
+    if (Q->nb[2] > Q->col_capacity(2)) return SOFT_ERR_UNSUPPORTED;
+    // kinetic factors per axis, 1/n folded in, in the transposed order of
+    // the fused center of each line FFT
     auto ktab = [&](int d, double frac) {
         const Axis1D& A = Q->ax[d];
         const int logn = Q->l[d], logrm = Q->lr[d];
-        const bool center = d > 0;
         const std::vector<int> perm = dif_output_order(logn, logrm);
         const int lrl = (logn % logrm) ? logn % logrm : logrm;
         const int Rl = 1 << lrl, nbf = A.n >> lrl;
         std::vector<cd> t(A.n);
         for (int p = 0; p < A.n; ++p) {
             const double k = A.k[perm[p]];
-            const int q = center ? (p % Rl) * nbf + p / Rl : p;
+            const int q = (p % Rl) * nbf + p / Rl;
             t[q] = std::polar(1.0 / A.n, -0.5 * k * k * dt * frac);
         }
         return t;
@@ -198,53 +197,35 @@ int create_3d(const soft_grid* grid, const double* box, double R0, double theta,
         }
     }
     if ((rc = upload_vtab(&Q->TVh, half_factors(*Q, nullptr), pr))) return rc;
-    // rows (z ny + y) outside both the y and the z strip blocks, and inside
-    // either
-    std::vector<int> rf, rs;
-    for (int z = 0; z < Q->n[2]; ++z)
-        for (int y = 0; y < Q->n[1]; ++y) {
-            const int r = z * Q->n[1] + y;
-            if (in_block(y, Q->blk0[1], Q->nb[1], Q->n[1]) || in_block(z, Q->blk0[2], Q->nb[2], Q->n[2]))
-                rs.push_back(r);
-            else
-                rf.push_back(r);
-        }
-    Q->nfull = (int)rf.size();
-    Q->nstrip = (int)rs.size();
-    if (!rf.empty() && (rc = upload((void**)&Q->rows_full, rf.data(), rf.size() * sizeof(int)))) return rc;
-    if (!rs.empty() && (rc = upload((void**)&Q->rows_strip, rs.data(), rs.size() * sizeof(int)))) return rc;
     Geo2D& g = Q->geo;
     std::memset(&g, 0, sizeof(g));
     g.Wx = Q->W[0]; g.TVh = Q->TVh; g.cnx = Q->cn[0];
     g.nx = Q->n[0]; g.ny = Q->n[1] * Q->n[2];
     g.nbx = Q->nb[0]; g.blk0x = Q->blk0[0];
     // set every kernel's shared-memory attribute now, outside any stream capture
-    for (int m = ROW_FWD; m <= ROW_INV; ++m)
-        if ((rc = Q->row(m, nullptr, 0, 0, nullptr, nullptr, 0))) return rc;
+    for (int m = ROW_K; m <= ROW_KVC; ++m)
+        if ((rc = Q->row(m, nullptr, nullptr, 0))) return rc;
     for (int d = 1; d < 3; ++d)
-        if ((rc = Q->line(d, nullptr, nullptr, 0))) return rc;
-    // both strip CN passes share one kernel: the larger block's size last
-    const int d0 = Q->nb[1] <= Q->nb[2] ? 1 : 2;
-    if ((rc = Q->cnpass(d0, nullptr, 0)) || (rc = Q->cnpass(3 - d0, nullptr, 0))) return rc;
+        for (int m = COL_K; m <= COL_CVK; ++m)
+            if ((rc = Q->line(d, m, nullptr, nullptr, 0))) return rc;
+    if ((rc = Q->cnpass(1, nullptr, 0))) return rc;
     Q->launches = 0;
     *out = P.release();
     return SOFT_OK;
 }
 
-// K^1/2 (V K)^{n-1} V K^1/2, as the 2D driver: forward row pass with the half
-// x factor, half y and z line passes, n steps (the last with half kinetic
-// factors), inverse row pass.
+// The call: K_y/2 and K_z/2 (line passes), n steps (the first with K_x/2,
+// the last with K_z/2 and K_y/2), then K_x/2 (row pass).
 int soft_plan::step_3d(void* psi, int64_t nsteps, double* t_inout, cudaStream_t st) {
     Plan3D* Q = p3;
     Q->launches = 0;
     last_launches = 0;
     if (nsteps == 0) return SOFT_OK;
-    const int nrows = Q->n[1] * Q->n[2];
     int rc;
-    if ((rc = Q->row(ROW_FWD, psi, 0, nrows, nullptr, Q->TKh[0], st))) return rc;
-    if ((rc = Q->line(1, psi, Q->TKh[1], st))) return rc;
-    if ((rc = Q->line(2, psi, Q->TKh[2], st))) return rc;
-    int64_t mid = nsteps - 1;
+    if ((rc = Q->line(1, COL_K, psi, Q->TKh[1], st))) return rc;
+    if ((rc = Q->line(2, COL_K, psi, Q->TKh[2], st))) return rc;
+    if ((rc = Q->enqueue_step(psi, true, nsteps == 1, st))) return rc;
+    int64_t mid = nsteps >= 2 ? nsteps - 2 : 0;
     const int64_t G = Plan3D::GRAPH_STEPS;
     if (mid >= G) {
         if (!Q->graph_exec || Q->graph_psi != psi || Q->graph_stream != st) {
@@ -254,7 +235,7 @@ int soft_plan::step_3d(void* psi, int64_t nsteps, double* t_inout, cudaStream_t 
             cudaGraph_t graph;
             const int64_t before = Q->launches;
             rc = cuda_status(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-            for (int64_t s = 0; s < G && rc == SOFT_OK; ++s) rc = Q->enqueue_step(psi, false, cap);
+            for (int64_t s = 0; s < G && rc == SOFT_OK; ++s) rc = Q->enqueue_step(psi, false, false, cap);
             cudaError_t e = cudaStreamEndCapture(cap, &graph);
             if (rc == SOFT_OK) rc = cuda_status(e);
             if (rc == SOFT_OK) rc = cuda_status(cudaGraphInstantiate(&Q->graph_exec, graph, 0));
@@ -273,9 +254,9 @@ int soft_plan::step_3d(void* psi, int64_t nsteps, double* t_inout, cudaStream_t 
         }
     }
     for (int64_t s = 0; s < mid; ++s)
-        if ((rc = Q->enqueue_step(psi, false, st))) return rc;
-    if ((rc = Q->enqueue_step(psi, true, st))) return rc;
-    if ((rc = Q->row(ROW_INV, psi, 0, nrows, nullptr, nullptr, st))) return rc;
+        if ((rc = Q->enqueue_step(psi, false, false, st))) return rc;
+    if (nsteps >= 2 && (rc = Q->enqueue_step(psi, false, true, st))) return rc;
+    if ((rc = Q->row(ROW_K, psi, Q->TKh[0], st))) return rc;
     last_launches = Q->launches;
     *t_inout += (double)nsteps * dt;
     return SOFT_OK;

@@ -38,10 +38,12 @@ int sse1d_apply(soft_plan* P, double E, int what, int precond, const void* x, vo
 
 namespace soft {
 // pass kernels of the 2D and 3D steps (soft2d_c64.cu, soft2d_c128.cu)
-int soft2d_row_c64(int, int, int, int, const Geo2D&, void*, int, int, const void*, const int*, cudaStream_t);
-int soft2d_row_c128(int, int, int, int, const Geo2D&, void*, int, int, const void*, const int*, cudaStream_t);
-int soft2d_col_c64(int, int, int, const LineGeo&, int, void*, const void*, cudaStream_t);
-int soft2d_col_c128(int, int, int, const LineGeo&, int, void*, const void*, cudaStream_t);
+int soft2d_row_c64(int, int, int, int, const Geo2D&, void*, int, const void*, cudaStream_t);
+int soft2d_row_c128(int, int, int, int, const Geo2D&, void*, int, const void*, cudaStream_t);
+int soft2d_col_c64(int, int, int, int, const LineGeo&, int, void*, const void*, cudaStream_t);
+int soft2d_col_c128(int, int, int, int, const LineGeo&, int, void*, const void*, cudaStream_t);
+int soft2d_col_strip_capacity_c64(int, int, int);
+int soft2d_col_strip_capacity_c128(int, int, int);
 int soft2d_cny_c64(const CnGeo&, int, void*, cudaStream_t);
 int soft2d_cny_c128(const CnGeo&, int, void*, cudaStream_t);
 
@@ -64,17 +66,16 @@ struct Plan2D {
     cudaStream_t graph_stream = nullptr;
     struct Pcg* pcg = nullptr;
 
-    int row(int mode, void* psi, int row0, int nrows, const void* tkx, cudaStream_t st);
-    int col(void* psi, const void* tky, cudaStream_t st);
-    int ypass(void* psi, cudaStream_t st);
-    int enqueue_step(void* psi, bool last, cudaStream_t st);
+    int row(int mode, void* psi, const void* tkx, cudaStream_t st);
+    int col(int mode, void* psi, const void* tky, cudaStream_t st);
+    int enqueue_step(void* psi, const void* tkx, const void* tky, cudaStream_t st);
     void free_pcg();
     int set_potential(const double* U_re_im);   // host complex [ny][nx]
     ~Plan2D();
 };
 
-// 3D plan state (plan3d.cu): a [nz][ny][nx] grid stepped by the 2D pass
-// kernels (rows; lines along y and z; strip CN along y and z)
+// 3D plan state (plan3d.cu): a [nz][ny][nx] grid stepped by the line pass
+// kernels (rows; lines along y and z; strip CN along y)
 struct Plan3D {
     static constexpr int64_t GRAPH_STEPS = 8;
     int prec = SOFT_C128;
@@ -84,18 +85,17 @@ struct Plan3D {
     Axis1D ax[3];
     std::vector<cd> ua[3];         // comparison-absorber potential of each axis
     void *W[3] = {}, *TK[3] = {}, *TKh[3] = {}, *TVh = nullptr, *cn[3] = {};
-    int *rows_full = nullptr, *rows_strip = nullptr;
-    int nfull = 0, nstrip = 0;
     Geo2D geo{};
     int64_t launches = 0, graph_launches = 0;
     cudaGraphExec_t graph_exec = nullptr;
     void* graph_psi = nullptr;
     cudaStream_t graph_stream = nullptr;
 
-    int row(int mode, void* psi, int row0, int nrows, const int* rows, const void* tkx, cudaStream_t st);
-    int line(int d, void* psi, const void* tk, cudaStream_t st);
+    int row(int mode, void* psi, const void* tkx, cudaStream_t st);
+    int line(int d, int mode, void* psi, const void* tk, cudaStream_t st);
     int cnpass(int d, void* psi, cudaStream_t st);
-    int enqueue_step(void* psi, bool last, cudaStream_t st);
+    int enqueue_step(void* psi, bool first, bool last, cudaStream_t st);
+    int col_capacity(int d) const;
     int set_potential(const double* U_re_im);   // host complex [nz][ny][nx]
     ~Plan3D();
 };

@@ -368,7 +368,7 @@ __device__ __forceinline__ void strip_cn(C* S, const C* __restrict__ cn, int nb,
             y[c] = yl;
         }
     }
-    C carry = affine_carry<C, T, false>(Mp, yl, scan);
+    C carry = affine_carry<C, T, false>(Mp, yl, scan, tid);
     {
         C pr; pr.x = 1; pr.y = 0;
 #pragma unroll
@@ -393,7 +393,7 @@ __device__ __forceinline__ void strip_cn(C* S, const C* __restrict__ cn, int nb,
             y[c] = xl;
         }
     }
-    carry = affine_carry<C, T, true>(Mp, xl, scan);
+    carry = affine_carry<C, T, true>(Mp, xl, scan, tid);
     C pr; pr.x = 1; pr.y = 0;
 #pragma unroll
     for (int c = CMAX - 1; c >= 0; --c) {

@@ -1,23 +1,27 @@
-// 2D split-operator step (Sec. II, with K = (kx^2 + ky^2)/2 and
-// C = C_x (x) I + I (x) C_y) as passes over a row-major [ny][nx] state.
+// Line passes of the 2D and 3D split-operator steps (Sec. II with
+// K = K_x + K_y (+ K_z) and C = C_x + C_y (+ C_z) as Kronecker sums).
 //
-// Between passes the state is kept in (k_x, y) -- rows transformed along x,
-// in the row FFT's output order -- so one step is
-//   row pass   F_x^-1, e^{-iU tau/2}, CN_x, e^{-iU tau/2}, F_x, e^{-i kx^2 tau/2}
-//   column pass F_y, e^{-i ky^2 tau/2}, F_y^-1
-// The kinetic factor e^{-i(kx^2+ky^2) tau/2} splits into an x factor (row
-// pass) and a y factor (column pass) because F_x and F_y act on different
-// indices.  Rows inside the y-strip block also need e^{-iC_y tau}, which
-// couples rows: for them the row pass stops after CN_x (mode A), a column
-// pass over the y block applies CN_y, and a second row pass finishes
-// (mode B).  CN_x and CN_y commute, so this is the paper's e^{-iC tau}.
+// The merged scheme in time order is ... V/2, CN, V/2, K, V/2, CN, V/2, K ...
+// with V/2 = e^{-iU tau/2}, CN = CN_x CN_y (CN_z) and K = K_x K_y (K_z) the
+// kinetic factors.  Factors acting on different axes commute, so in 2D the
+// product of one step regroups into two passes over the grid, with the state
+// kept in x space between them:
+//   row pass    (x lines)  K_x, V/2, CN_x         (ROW_KVC)
+//   column pass (y lines)  CN_y, V/2, K_y         (COL_CVK)
+// so that K_y K_x | V/2 CN_x CN_y V/2 | K_y K_x ... is the paper's step
+// sequence.  Each K_d is F_d, e^{-i k_d^2 tau/2} (or its half at the ends of
+// a call), F_d^-1 with the last forward and first inverse FFT pass fused
+// (kcenter).  ROW_K and COL_K apply the kinetic factor alone (the ends of a
+// call).  The 3D step adds a strip CN pass along y (cny_kernel) between the
+// row pass and a COL_CVK pass along z, and a COL_K pass along y.
 #pragma once
 #include "soft1d.cuh"
 #include "soft2d_geo.h"
 
 namespace soft {
 
-enum RowMode { ROW_FWD = 0, ROW_FULL = 1, ROW_A = 2, ROW_B = 3, ROW_INV = 4 };
+enum RowMode { ROW_K = 0, ROW_KVC = 1 };
+enum ColMode { COL_K = 0, COL_CVK = 1 };
 
 // Pass twiddles of the line passes.  Complex128 plans, which are bound by
 // the FP64 pipe, store every W^{M off} for the passes with a stride of at
@@ -31,23 +35,16 @@ template <typename R> struct Tw2D { using T = TwFull<typename CT<R>::C>; };
 template <> struct Tw2D<float> { using T = float2; };
 
 // Shared memory of the row pass: the row (swizzled) and the scan scratch of
-// the strip CN; one table buffer that holds the row's e^{-iU tau/2} while
-// the potential is applied and the kinetic table afterwards; the twiddles.
+// the strip CN, the row's e^{-iU tau/2}, the twiddles.
 template <typename R, int LOGN, int LOGE, int LOGRM>
 struct Cfg2DRow : Cfg1D<R, LOGN, LOGE, LOGRM> {
     using C = typename CT<R>::C;
     using VT = typename VabT<R>::T;
-    using TT = typename TabT<R>::T;
     using TWT = typename Tw2D<R>::T;
     static constexpr int N = 1 << LOGN;
     static constexpr int TWN = TwCountT<TWT, LOGN, LOGRM>::value;
-    // the kinetic table is staged when it fits the potential buffer
-    // (complex128); complex64 reads its compensated float4 entries through
-    // the read-only cache, which keeps four CTAs per SM
-    static constexpr bool STAGE_K = sizeof(TT) <= sizeof(VT);
     static constexpr size_t OFF_B = sizeof(C) * (N + 64);
-    static constexpr size_t BYTES_B = sizeof(VT) * N;
-    static constexpr size_t OFF_W = OFF_B + BYTES_B;
+    static constexpr size_t OFF_W = OFF_B + sizeof(VT) * N;
     static constexpr size_t SMEM2 = OFF_W + sizeof(TWT) * TWN;
     static_assert(OFF_B % 16 == 0 && OFF_W % 16 == 0, "16-byte aligned parts");
 };
@@ -79,118 +76,80 @@ __device__ __forceinline__ void inv_pass0_post(typename CT<R>::C* S, const TW* _
     }
 }
 
-// One CTA per row.  Rows are rows[row0 + blockIdx.x] with a row list, else
-// (row0 + blockIdx.x) mod ny.  The row, its potential factors and the
-// twiddles are staged in shared memory by asynchronous copies issued
-// together at the start; the kinetic table (complex128) is fetched the same
-// way while the forward FFT runs.  The potential factor is applied as the last
-// inverse pass stores, the x kinetic factor as the row is written back.
+// One CTA per row (row blockIdx.x of the ny rows; 3D: ny nz).  The row,
+// its potential factors and the twiddles are staged in shared memory by
+// asynchronous copies issued together at the start.  ROW_KVC: F_x,
+// e^{-i kx^2 tau/2} (the table tkx, 1/N folded in), F_x^-1 with V/2 applied
+// as the last inverse pass stores, then CN_x on the x-strip block.  ROW_K:
+// the kinetic factor alone.
 template <typename R, int LOGN, int LOGE, int LOGRM, int MODE>
 __global__ void __launch_bounds__(Cfg1D<R, LOGN, LOGE, LOGRM>::T, Cfg1D<R, LOGN, LOGE, LOGRM>::MINB)
-row_pass_kernel(Geo2D g, void* __restrict__ psi_v, int row0, const void* __restrict__ tkx_v,
-                const int* __restrict__ rows)
+row_pass_kernel(Geo2D g, void* __restrict__ psi_v, const void* __restrict__ tkx_v)
 {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
     using RC = Cfg2DRow<R, LOGN, LOGE, LOGRM>;
     using C = typename K::C;
     using TT = typename K::TT;
     using VT = typename VabT<R>::T;
+    using TWT = typename RC::TWT;
     constexpr int N = K::N, T = K::T, E = K::E;
-    constexpr bool POT = MODE == ROW_FULL || MODE == ROW_A || MODE == ROW_B;
-    constexpr bool KIN = MODE == ROW_FULL || MODE == ROW_B || MODE == ROW_FWD;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* S = reinterpret_cast<C*>(smem_raw);
     C* scan = S + N;
     VT* Tv = reinterpret_cast<VT*>(smem_raw + RC::OFF_B);
-    TT* Tk = reinterpret_cast<TT*>(smem_raw + RC::OFF_B);
-    using TWT = typename RC::TWT;
     TWT* Ws = reinterpret_cast<TWT*>(smem_raw + RC::OFF_W);
     const int tid = threadIdx.x;
-    const int y = rows ? __ldg(&rows[row0 + (int)blockIdx.x]) : (row0 + (int)blockIdx.x) % g.ny;
-    C* __restrict__ row = reinterpret_cast<C*>(psi_v) + (int64_t)y * N;
+    const int64_t y = blockIdx.x;
+    C* __restrict__ row = reinterpret_cast<C*>(psi_v) + y * N;
     const TWT* __restrict__ W = reinterpret_cast<const TWT*>(g.Wx);
-    const VT* __restrict__ tv = reinterpret_cast<const VT*>(g.TVh) + (int64_t)y * N;
+    const VT* __restrict__ tv = reinterpret_cast<const VT*>(g.TVh) + y * N;
     const TT* __restrict__ tkx = reinterpret_cast<const TT*>(tkx_v);
 
 #pragma unroll
     for (int j = 0; j < E; ++j) {
         const int n = tid + j * T;
         cp_async<sizeof(C)>(&S[swz<C>(n)], &row[n]);
-        if constexpr (POT) cp_async<sizeof(VT)>(&Tv[n], &tv[n]);
+        if constexpr (MODE == ROW_KVC) cp_async<sizeof(VT)>(&Tv[n], &tv[n]);
     }
     for (int i = tid; i < RC::TWN; i += T) cp_async<sizeof(TWT)>(&Ws[i], &W[i]);
     cp_async_commit();
     cp_async_wait<0>();
-    if constexpr (MODE == ROW_B) {
-#pragma unroll
-        for (int j = 0; j < E; ++j) {         // the thread's own copies
-            const int n = tid + j * T;
-            S[swz<C>(n)] = vmul(S[swz<C>(n)], Tv[n]);
-        }
-    }
     __syncthreads();
-    if constexpr (MODE == ROW_INV) {
-        inv_passes<R, LOGN, LOGE, LOGRM, K::NPASS - 1, 0>(S, Ws, tid);
-    } else if constexpr (MODE == ROW_FULL || MODE == ROW_A) {
-        inv_passes<R, LOGN, LOGE, LOGRM, K::NPASS - 1, 1>(S, Ws, tid);
-        // e^{-iU tau/2}; off the x-strip block of a full row pass the second
-        // half factor too
-        inv_pass0_post<R, LOGN, LOGE, LOGRM, true>(S, Ws, tid, [&](int n, C v) {
-            const VT t = Tv[n];
-            v = vmul(v, t);
-            if (MODE == ROW_FULL && ((n - g.blk0x) & (N - 1)) >= g.nbx) v = vmul(v, t);
-            return v;
-        });
+    fwd_passes<R, LOGN, LOGE, LOGRM, 0, K::NPASS - 1>(S, Ws, tid);
+    kcenter<R, LOGN, LOGE, LOGRM>(S, tkx, tid);
+    __syncthreads();
+    if constexpr (MODE == ROW_K) {
+        inv_passes<R, LOGN, LOGE, LOGRM, K::NPASS - 2, 0>(S, Ws, tid);
+    } else {
+        inv_passes<R, LOGN, LOGE, LOGRM, K::NPASS - 2, 1>(S, Ws, tid);
+        inv_pass0_post<R, LOGN, LOGE, LOGRM, true>(S, Ws, tid, [&](int n, C v) { return vmul(v, Tv[n]); });
         __syncthreads();
         if (g.nbx > 0) {
-            const C* cn = reinterpret_cast<const C*>(g.cnx);
-            if constexpr (MODE == ROW_FULL)
-                strip_cn<C, T, K::CMAX, N>(S, cn, g.nbx, g.blk0x, tid, scan,
-                                           [&](int n, C v) { return vmul(v, Tv[n]); });
-            else
-                strip_cn<C, T, K::CMAX, N>(S, cn, g.nbx, g.blk0x, tid, scan, [](int, C v) { return v; });
+            strip_cn<C, T, K::CMAX, N>(S, reinterpret_cast<const C*>(g.cnx), g.nbx, g.blk0x, tid, scan,
+                                       [](int, C v) { return v; });
             __syncthreads();
         }
     }
-    if constexpr (KIN) {
-        if constexpr (RC::STAGE_K) {
-            // the potential buffer is free now: fetch the kinetic table into
-            // it (each thread the entries of its own outputs) behind the FFT
-#pragma unroll
-            for (int j = 0; j < E; ++j) {
-                const int n = tid + j * T;
-                cp_async<sizeof(TT)>(&Tk[n], &tkx[n]);
-            }
-            cp_async_commit();
-        }
-        fwd_passes<R, LOGN, LOGE, LOGRM, 0, K::NPASS>(S, Ws, tid);
-        if constexpr (RC::STAGE_K) cp_async_wait<0>();
 #pragma unroll 4
-        for (int j = 0; j < E; ++j) {
-            const int n = tid + j * T;
-            if constexpr (RC::STAGE_K) row[n] = tmul(S[swz<C>(n)], Tk[n]);
-            else row[n] = tmul(S[swz<C>(n)], __ldg(&tkx[n]));
-        }
-    } else {
-#pragma unroll 4
-        for (int j = 0; j < E; ++j) {
-            const int n = tid + j * T;
-            row[n] = S[swz<C>(n)];
-        }
+    for (int j = 0; j < E; ++j) {
+        const int n = tid + j * T;
+        row[n] = S[swz<C>(n)];
     }
 }
 
-// Column pass: TW columns per CTA, each transformed by T = ny/E threads:
-// F_y, e^{-i ky^2 tau/2}/ny, F_y^-1, with the last forward pass, the factor
-// and the first inverse pass fused (kcenter; table in its transposed order).
-// The column tile and the twiddles are staged in shared memory by
-// asynchronous copies issued together at the start; the kinetic table (the
-// same for every column) is read through the read-only cache.
+// Column pass: TW columns per CTA, each transformed by T = ny/E threads.
+// COL_CVK: CN_y on the column's strip block, V/2 (outside the block as the
+// tile is loaded, on it as the CN stores), then F_y, e^{-i ky^2 tau/2}/ny,
+// F_y^-1; COL_K: the kinetic factor alone.  The last forward pass, the factor
+// and the first inverse pass are fused (kcenter; table in its transposed
+// order).  The column tile, the V/2 factors of the strip rows (COL_CVK) and
+// the twiddles are staged in shared memory by asynchronous copies issued
+// together at the start; the V/2 factors of the other rows and the kinetic
+// table (the same for every column) are read through the read-only cache.
 template <typename R, int LOGN, int LOGE, int LOGRM, int TW>
 struct ColCfg {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
     using C = typename K::C;
-    using TT = typename K::TT;
     static constexpr int THREADS = TW * K::T;
     static constexpr int MINB = THREADS >= 512 ? 1 : 512 / THREADS;   // <= 128 registers
     // column pitch: N + 64 bytes, so that the TW columns of one row fall in
@@ -198,12 +157,17 @@ struct ColCfg {
     static constexpr int PITCH = K::N + 64 / (int)sizeof(C);
     using TWT = typename Tw2D<R>::T;
     static constexpr int TWN = TwCountT<TWT, LOGN, LOGRM>::value;
+    using VT = typename VabT<R>::T;
     static constexpr size_t OFF_W = sizeof(C) * (size_t)TW * PITCH;
-    static constexpr size_t SMEM = OFF_W + sizeof(TWT) * TWN;
-    static_assert(OFF_W % 16 == 0, "16-byte aligned parts");
+    static constexpr size_t OFF_SCAN = OFF_W + sizeof(TWT) * TWN;
+    static constexpr size_t OFF_V = OFF_SCAN + sizeof(C) * 32 * TW;   // scan scratch of each column
+    static constexpr int VCAP = K::T * K::CMAX;                       // strip rows a column takes
+    static constexpr size_t SMEM_K = OFF_V;
+    static constexpr size_t SMEM_CVK = OFF_V + sizeof(VT) * (size_t)TW * VCAP;   // V/2 of the strip rows
+    static_assert(OFF_W % 16 == 0 && OFF_SCAN % 16 == 0 && OFF_V % 16 == 0, "16-byte aligned parts");
 };
 
-template <typename R, int LOGN, int LOGE, int LOGRM, int TW>
+template <typename R, int LOGN, int LOGE, int LOGRM, int TW, int MODE>
 __global__ void __launch_bounds__(ColCfg<R, LOGN, LOGE, LOGRM, TW>::THREADS, ColCfg<R, LOGN, LOGE, LOGRM, TW>::MINB)
 col_pass_kernel(LineGeo lg, void* __restrict__ psi_v, const void* __restrict__ tky_v)
 {
@@ -211,31 +175,62 @@ col_pass_kernel(LineGeo lg, void* __restrict__ psi_v, const void* __restrict__ t
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
     using C = typename K::C;
     using TT = typename K::TT;
+    using VT = typename VabT<R>::T;
+    using TWT = typename CC::TWT;
     constexpr int N = K::N, T = K::T;
     constexpr int PITCH = CC::PITCH;
     constexpr int NIT = N / T;                      // tile elements per thread
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* S = reinterpret_cast<C*>(smem_raw);
-    using TWT = typename CC::TWT;
     TWT* Ws = reinterpret_cast<TWT*>(smem_raw + CC::OFF_W);
     const int64_t nx = lg.ld;
     const int64_t gpp = nx / TW;                    // CTAs per plane
-    C* __restrict__ psi = reinterpret_cast<C*>(psi_v) + (int64_t)(blockIdx.x / gpp) * lg.plane;
+    const int64_t poff = (int64_t)(blockIdx.x / gpp) * lg.plane;
+    C* __restrict__ psi = reinterpret_cast<C*>(psi_v) + poff;
+    const VT* __restrict__ tv = reinterpret_cast<const VT*>(lg.tv) + poff;   // COL_CVK
     const TWT* __restrict__ W = reinterpret_cast<const TWT*>(lg.W);
     const TT* __restrict__ tky = reinterpret_cast<const TT*>(tky_v);
     const int64_t c0 = (int64_t)(blockIdx.x % gpp) * TW;
+    VT* Tvs = reinterpret_cast<VT*>(smem_raw + CC::OFF_V);     // [TW][VCAP] (COL_CVK)
 #pragma unroll 8
     for (int it = 0; it < NIT; ++it) {              // row by row: the TW columns of a row are adjacent
         const int idx = threadIdx.x + it * TW * T;
         const int yy = idx / TW, j = idx % TW;
         cp_async<sizeof(C)>(&S[j * PITCH + swz<C>(yy)], &psi[(int64_t)yy * nx + c0 + j]);
     }
+    if constexpr (MODE == COL_CVK) {
+        for (int idx = threadIdx.x; idx < lg.nb * TW; idx += TW * T) {
+            const int i = idx / TW, j = idx % TW;
+            const int yy = (lg.blk0 + i) & (N - 1);
+            cp_async<sizeof(VT)>(&Tvs[j * CC::VCAP + i], &tv[(int64_t)yy * nx + c0 + j]);
+        }
+    }
     for (int i = threadIdx.x; i < CC::TWN; i += TW * T) cp_async<sizeof(TWT)>(&Ws[i], &W[i]);
     cp_async_commit();
     cp_async_wait<0>();
-    __syncthreads();
     const int col = threadIdx.x / T, tid = threadIdx.x % T;
     C* Sc = S + col * PITCH;
+    if constexpr (MODE == COL_CVK) {
+        // V/2 on the thread's own elements outside the strip block (CN_y is
+        // the identity there)
+#pragma unroll 8
+        for (int it = 0; it < NIT; ++it) {
+            const int idx = threadIdx.x + it * TW * T;
+            const int yy = idx / TW, j = idx % TW;
+            if (((yy - lg.blk0) & (N - 1)) >= lg.nb) {
+                C& v = S[j * PITCH + swz<C>(yy)];
+                v = vmul(v, __ldg(&tv[(int64_t)yy * nx + c0 + j]));
+            }
+        }
+        __syncthreads();
+        if (lg.nb > 0) {
+            const VT* tvc = Tvs + col * CC::VCAP;
+            C* scan = reinterpret_cast<C*>(smem_raw + CC::OFF_SCAN) + 32 * col;
+            strip_cn<C, T, K::CMAX, N>(Sc, reinterpret_cast<const C*>(lg.cn), lg.nb, lg.blk0, tid, scan,
+                                       [&](int n, C v) { return vmul(v, tvc[(n - lg.blk0) & (N - 1)]); });
+        }
+    }
+    __syncthreads();
     fwd_passes<R, LOGN, LOGE, LOGRM, 0, K::NPASS - 1>(Sc, Ws, tid);
     kcenter<R, LOGN, LOGE, LOGRM>(Sc, tky, tid);
     __syncthreads();
@@ -346,44 +341,52 @@ cny_kernel(CnGeo g, void* __restrict__ psi_v)
 }
 
 // ---------------------------------------------------------------- launchers
+// rows 0 .. nrows-1 (psi == nullptr: set the shared-memory attribute only)
 template <typename R, int LOGN, int LOGE, int LOGRM>
-int launch_row_t(int mode, const Geo2D& g, void* psi, int row0, int nrows, const void* tkx,
-                 const int* rows, cudaStream_t st) {
+int launch_row_t(int mode, const Geo2D& g, void* psi, int nrows, const void* tkx, cudaStream_t st) {
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
     const size_t smem = Cfg2DRow<R, LOGN, LOGE, LOGRM>::SMEM2;
-    void (*k)(Geo2D, void*, int, const void*, const int*) = nullptr;
+    void (*k)(Geo2D, void*, const void*) = nullptr;
     switch (mode) {
-    case ROW_FWD: k = row_pass_kernel<R, LOGN, LOGE, LOGRM, ROW_FWD>; break;
-    case ROW_FULL: k = row_pass_kernel<R, LOGN, LOGE, LOGRM, ROW_FULL>; break;
-    case ROW_A: k = row_pass_kernel<R, LOGN, LOGE, LOGRM, ROW_A>; break;
-    case ROW_B: k = row_pass_kernel<R, LOGN, LOGE, LOGRM, ROW_B>; break;
-    case ROW_INV: k = row_pass_kernel<R, LOGN, LOGE, LOGRM, ROW_INV>; break;
+    case ROW_K: k = row_pass_kernel<R, LOGN, LOGE, LOGRM, ROW_K>; break;
+    case ROW_KVC: k = row_pass_kernel<R, LOGN, LOGE, LOGRM, ROW_KVC>; break;
     default: return SOFT_ERR_INVALID_ARG;
     }
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return SOFT_ERR_CUDA;
     if (nrows <= 0 || !psi) return SOFT_OK;
-    k<<<nrows, K::T, smem, st>>>(g, psi, row0, tkx, rows);
+    k<<<nrows, K::T, smem, st>>>(g, psi, tkx);
     return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
 }
 
-// lines of planes planes (LineGeo); ld must be a multiple of TW
+// lines of `planes` planes (LineGeo); ld must be a multiple of TW
 template <typename R, int LOGN, int LOGE, int LOGRM, int TW>
-int launch_col_t(const LineGeo& g, int planes, void* psi, const void* tky, cudaStream_t st) {
+int launch_col_t(int mode, const LineGeo& g, int planes, void* psi, const void* tky, cudaStream_t st) {
     using CC = ColCfg<R, LOGN, LOGE, LOGRM, TW>;
-    const size_t smem = CC::SMEM;
-    auto k = col_pass_kernel<R, LOGN, LOGE, LOGRM, TW>;
+    using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
+    const size_t smem = mode == COL_CVK ? CC::SMEM_CVK : CC::SMEM_K;
+    void (*k)(LineGeo, void*, const void*) = nullptr;
+    switch (mode) {
+    case COL_K: k = col_pass_kernel<R, LOGN, LOGE, LOGRM, TW, COL_K>; break;
+    case COL_CVK: k = col_pass_kernel<R, LOGN, LOGE, LOGRM, TW, COL_CVK>; break;
+    default: return SOFT_ERR_INVALID_ARG;
+    }
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return SOFT_ERR_CUDA;
     if (!psi) return SOFT_OK;             // attribute set only
     if (g.ld % TW || planes < 1) return SOFT_ERR_INVALID_ARG;
+    if (mode == COL_CVK && (g.nb + K::T - 1) / K::T > K::CMAX) return SOFT_ERR_UNSUPPORTED;
     const int64_t grid = g.ld / TW * planes;
     if (grid > 0x7fffffff) return SOFT_ERR_TOO_LARGE;
     k<<<(unsigned)grid, CC::THREADS, smem, st>>>(g, psi, tky);
     return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
 }
+
+// strip rows of a column pass per thread of the column configuration
+template <typename R, int LOGN, int LOGE, int LOGRM>
+constexpr int col_strip_capacity() { return Cfg1D<R, LOGN, LOGE, LOGRM>::T * Cfg1D<R, LOGN, LOGE, LOGRM>::CMAX; }
 
 template <typename C, int CH>
 int launch_cny_t(const CnGeo& g, int planes, void* psi, cudaStream_t st) {

@@ -4,23 +4,33 @@
 
 namespace soft {
 
-int soft2d_row_c64(int logn, int loge, int logrm, int mode, const Geo2D& g, void* psi, int row0,
-                    int nrows, const void* tkx, const int* rows, cudaStream_t st) {
-#define ROWCASE(LN, LE, LR)                                                                  \
-    if (logn == LN && loge == LE && logrm == LR)                                             \
-        return launch_row_t<float, LN, LE, LR>(mode, g, psi, row0, nrows, tkx, rows, st);
+int soft2d_row_c64(int logn, int loge, int logrm, int mode, const Geo2D& g, void* psi, int nrows,
+                    const void* tkx, cudaStream_t st) {
+#define ROWCASE(LN, LE, LR) \
+    if (logn == LN && loge == LE && logrm == LR) return launch_row_t<float, LN, LE, LR>(mode, g, psi, nrows, tkx, st);
     ROWCASE(6, 1, 1) ROWCASE(7, 2, 2) ROWCASE(8, 3, 3) ROWCASE(9, 3, 3) ROWCASE(10, 4, 4) ROWCASE(11, 4, 4)
 #undef ROWCASE
     return SOFT_ERR_UNSUPPORTED;
 }
 
-int soft2d_col_c64(int logn, int loge, int logrm, const LineGeo& g, int planes, void* psi,
+int soft2d_col_c64(int logn, int loge, int logrm, int mode, const LineGeo& g, int planes, void* psi,
                     const void* tky, cudaStream_t st) {
 #define COLCASE(LN, LE, LR) \
-    if (logn == LN && loge == LE && logrm == LR) return launch_col_t<float, LN, LE, LR, 4>(g, planes, psi, tky, st);
+    if (logn == LN && loge == LE && logrm == LR) return launch_col_t<float, LN, LE, LR, 4>(mode, g, planes, psi, tky, st);
     COLCASE(6, 1, 1) COLCASE(7, 2, 2) COLCASE(8, 3, 3) COLCASE(9, 3, 3) COLCASE(10, 5, 4) COLCASE(11, 5, 4)
 #undef COLCASE
     return SOFT_ERR_UNSUPPORTED;
+}
+
+// strip rows the column pass of a configuration can take (0: not built)
+int soft2d_col_strip_capacity_c64(int logn, int loge, int logrm) {
+    if (logn == 6 && loge == 1 && logrm == 1) return col_strip_capacity<float, 6, 1, 1>();
+    if (logn == 7 && loge == 2 && logrm == 2) return col_strip_capacity<float, 7, 2, 2>();
+    if (logn == 8 && loge == 3 && logrm == 3) return col_strip_capacity<float, 8, 3, 3>();
+    if (logn == 9 && loge == 3 && logrm == 3) return col_strip_capacity<float, 9, 3, 3>();
+    if (logn == 10 && loge == 5 && logrm == 4) return col_strip_capacity<float, 10, 5, 4>();
+    if (logn == 11 && loge == 5 && logrm == 4) return col_strip_capacity<float, 11, 5, 4>();
+    return 0;
 }
 
 int soft2d_cny_c64(const CnGeo& g, int planes, void* psi, cudaStream_t st) {

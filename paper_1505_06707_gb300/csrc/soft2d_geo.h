@@ -10,7 +10,7 @@ struct Geo2D {              // passed by value to every 2D kernel
     const void* Wy;         // pass twiddles of the column FFT (length ny)
     const void* TVh;        // e^{-iU tau/2}, [ny][nx] (minus 1, float2, for complex64)
     const void* cnx;        // x-strip LU (mf, mb, g) for the row pass
-    const void* cny;        // y-strip LU (mf, mb, g) for the y-block pass
+    const void* cny;        // y-strip LU (mf, mb, g) for the column pass
     int nx, ny;             // row length; number of rows (3D: ny nz)
     int nbx, blk0x;         // x-strip block (same for every row)
     int nby, blk0y;         // y-strip block (same for every column)
@@ -22,6 +22,9 @@ struct Geo2D {              // passed by value to every 2D kernel
 struct LineGeo {
     const void* W;          // pass twiddles of the line FFT
     int64_t ld, plane;
+    const void* cn;         // strip CN LU (mf, mb, g) along the lines (COL_CVK)
+    const void* tv;         // e^{-iU tau/2}, laid out as the state (COL_CVK)
+    int nb, blk0;           // strip block along the lines (COL_CVK)
 };
 
 // The strip CN along a strided axis: the cyclic block blk0 .. blk0 + nb - 1

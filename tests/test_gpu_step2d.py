@@ -101,7 +101,7 @@ def test_small_grids_match_oracle(shape, prec):
     ref = P.Problem2D(nx, ny, box, R0, theta=0.4, a2=1.0, dt=0.02).step(psi0, 40)
     got, launches = run2d(nx, ny, box, R0, 0.4, 0.02, psi0, 40, prec, soft_a2=1.0)
     assert relerr(got, ref) < tol(prec, 40, max(nx, ny))
-    assert launches >= 5 * 40
+    assert launches == 2 * 40 + 2            # a row and a column pass per step, K_y/2 and K_x/2
 
 
 @pytest.mark.parametrize("prec", [S.SOFT_C128, S.SOFT_C64])
