@@ -156,13 +156,12 @@ int create_3d(const soft_grid* grid, const double* box, double R0, double theta,
         for (int i = 0; i < Q->n[d]; ++i) Q->ua[d][i] = cf.absorber(Q->ax[d].x[i]);
         if ((rc = find_block(Q->ax[d], &Q->blk0[d], &Q->nb[d]))) return rc;
     }
-    // strip rows per thread of the row pass, per lane of the y-strip CN pass
-    // (an 8-column tile and the LU coefficients in shared memory), and per
-    // thread of the z line pass
+    // strip rows per thread of the row pass, of the y-strip CN pass (a tile
+    // of at least 32 lines and the LU coefficients in shared memory) and of
+    // the z line pass
     const int thr = Q->n[0] >> Q->le[0];
     if ((Q->nb[0] + thr - 1) / thr > (1 << Q->le[0]) / 4 + 2) return SOFT_ERR_UNSUPPORTED;
-    if ((Q->nb[1] + 31) / 32 > 24) return SOFT_ERR_UNSUPPORTED;
-    if ((o.prec == SOFT_C64 ? 8 : 16) * (size_t)Q->nb[1] * 12 > 227 * 1024) return SOFT_ERR_UNSUPPORTED;
+    if ((o.prec == SOFT_C64 ? 8 : 16) * (size_t)Q->nb[1] * 35 > 227 * 1024) return SOFT_ERR_UNSUPPORTED;
     if (Q->nb[2] > Q->col_capacity(2)) return SOFT_ERR_UNSUPPORTED;
     // kinetic factors per axis, 1/n folded in, in the transposed order of
     // the fused center of each line FFT

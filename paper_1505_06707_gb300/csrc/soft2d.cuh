@@ -12,7 +12,7 @@
 // sequence.  Each K_d is F_d, e^{-i k_d^2 tau/2} (or its half at the ends of
 // a call), F_d^-1 with the last forward and first inverse FFT pass fused
 // (kcenter).  ROW_K and COL_K apply the kinetic factor alone (the ends of a
-// call).  The 3D step adds a strip CN pass along y (cny_kernel) between the
+// call).  The 3D step adds a strip CN pass along y (cn_lines_kernel) between the
 // row pass and a COL_CVK pass along z, and a COL_K pass along y.
 #pragma once
 #include "soft1d.cuh"
@@ -243,100 +243,52 @@ col_pass_kernel(LineGeo lg, void* __restrict__ psi_v, const void* __restrict__ t
     }
 }
 
-// y-strip Crank-Nicolson: TWC columns per CTA, one warp per column, each lane
-// a contiguous chunk of the nby block rows; the tile is staged in shared
-// memory with a padded pitch so that the lanes' strided rows hit distinct
-// banks.  Small CTAs (two per SM) let one CTA's tile loads overlap another's
-// sweeps.
-template <typename C, int CH, int TWC>
-__global__ void __launch_bounds__(32 * TWC, 512 / (32 * TWC))
-cny_kernel(CnGeo g, void* __restrict__ psi_v)
+// Strip Crank-Nicolson along a strided axis (the 3D step's y-strip pass):
+// CN(psi) = 2 M^-1 psi - psi on the block rows of every line, M = LU from
+// the host (mf, mb, g).  One thread per line: a CTA stages the block rows of
+// TWC adjacent lines (each block row a contiguous segment of TWC elements,
+// read and written coalesced) and the coefficients in shared memory, then
+// each thread runs the two sweeps of its own line, with no scan and no
+// barrier.  The forward sweep leaves y in place of the right-hand side r;
+// the backward sweep recovers r_i = y_i - mf_i y_{i-1} from the stored y.
+template <typename C, int TWC>
+__global__ void __launch_bounds__(TWC)
+cn_lines_kernel(CnGeo g, void* __restrict__ psi_v)
 {
-    constexpr int PITCH = TWC + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* S = reinterpret_cast<C*>(smem_raw);
+    const int nb = g.nb, ny = g.n;
+    C* tile = reinterpret_cast<C*>(smem_raw);         // [nb][TWC]
+    C* cf = tile + (size_t)nb * TWC;                  // mf, mb, g
     const int64_t nx = g.ld;
-    const int64_t gpp = nx / TWC;                   // CTAs per plane
+    const int64_t gpp = nx / TWC;                     // CTAs per plane
     C* __restrict__ psi = reinterpret_cast<C*>(psi_v) + (int64_t)(blockIdx.x / gpp) * g.plane;
     const C* __restrict__ cn = reinterpret_cast<const C*>(g.cn);
     const int64_t c0 = (int64_t)(blockIdx.x % gpp) * TWC;
-    const int nb = g.nb, ny = g.n;
-    // the LU coefficients (mf, mb, g) are the same for every column: one
-    // copy in shared memory, read by each lane at its own row (a warp's
-    // rows are a chunk apart, which in global memory touched one cache
-    // line per lane)
-    C* Scn = S + nb * PITCH;
-    // asynchronous copies: every row of the tile in flight at once
-    for (int i = threadIdx.x; i < 3 * nb; i += blockDim.x) cp_async<sizeof(C)>(&Scn[i], &cn[i]);
-    for (int idx = threadIdx.x; idx < nb * TWC; idx += blockDim.x) {
-        const int r = idx / TWC, j = idx % TWC;
-        const int yy = (g.blk0 + r) % ny;
-        cp_async<sizeof(C)>(&S[r * PITCH + j], &psi[(int64_t)yy * nx + c0 + j]);
+    const int t = threadIdx.x;
+    for (int i = 0; i < nb; ++i) {
+        const int yy = (g.blk0 + i) % ny;
+        cp_async<sizeof(C)>(&tile[i * TWC + t], &psi[(int64_t)yy * nx + c0 + t]);
     }
+    for (int i = t; i < 3 * nb; i += TWC) cp_async<sizeof(C)>(&cf[i], &cn[i]);
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ch = (nb + 31) / 32;          // host guarantees ch <= CH
-    const int i0 = lane * ch;
-    C yv[CH];
-    C Mp; Mp.x = 1; Mp.y = 0;
-    C yl; yl.x = 0; yl.y = 0;
-#pragma unroll
-    for (int c = 0; c < CH; ++c) {
-        const int i = i0 + c;
-        if (c < ch && i < nb) {
-            const C m = Scn[i];
-            yl = cfma(m, yl, S[i * PITCH + w]);
-            Mp = cmul(m, Mp);
-            yv[c] = yl;
-        }
+    C y = cmk<C>(0, 0);
+    for (int i = 0; i < nb; ++i) {
+        y = cfma(cf[i], y, tile[i * TWC + t]);
+        tile[i * TWC + t] = y;
     }
-    C carry = affine_carry<C, 32, false>(Mp, yl, nullptr);
-    {
-        C pr; pr.x = 1; pr.y = 0;
-#pragma unroll
-        for (int c = 0; c < CH; ++c) {
-            const int i = i0 + c;
-            if (c < ch && i < nb) {
-                pr = cmul(Scn[i], pr);
-                yv[c] = cfma(pr, carry, yv[c]);
-            }
-        }
-    }
-    Mp.x = 1; Mp.y = 0;
-    C xl; xl.x = 0; xl.y = 0;
-#pragma unroll
-    for (int c = CH - 1; c >= 0; --c) {
-        const int i = i0 + c;
-        if (c < ch && i < nb) {
-            const C m = Scn[nb + i];
-            const C gg = Scn[2 * nb + i];
-            xl = cfma(m, xl, cmul(gg, yv[c]));
-            Mp = cmul(m, Mp);
-            yv[c] = xl;
-        }
-    }
-    carry = affine_carry<C, 32, true>(Mp, xl, nullptr);
-    {
-        C pr; pr.x = 1; pr.y = 0;
-#pragma unroll
-        for (int c = CH - 1; c >= 0; --c) {
-            const int i = i0 + c;
-            if (c < ch && i < nb) {
-                pr = cmul(Scn[nb + i], pr);
-                const C xv = cfma(pr, carry, yv[c]);
-                const C rc = S[i * PITCH + w];
-                S[i * PITCH + w] = cmk<C>(2 * xv.x - rc.x, 2 * xv.y - rc.y);
-            }
-        }
+    C x = cmk<C>(0, 0);
+    for (int i = nb - 1; i >= 0; --i) {
+        const C yi = tile[i * TWC + t];
+        x = cfma(cf[nb + i], x, cmul(cf[2 * nb + i], yi));
+        const C r = i > 0 ? csub(yi, cmul(cf[i], tile[(i - 1) * TWC + t])) : yi;
+        tile[i * TWC + t] = cmk<C>(2 * x.x - r.x, 2 * x.y - r.y);
     }
     __syncthreads();
-#pragma unroll 8
-    for (int idx = threadIdx.x; idx < nb * TWC; idx += blockDim.x) {
-        const int r = idx / TWC, j = idx % TWC;
-        const int yy = (g.blk0 + r) % ny;
-        psi[(int64_t)yy * nx + c0 + j] = S[r * PITCH + j];
+    for (int i = 0; i < nb; ++i) {
+        const int yy = (g.blk0 + i) % ny;
+        psi[(int64_t)yy * nx + c0 + t] = tile[i * TWC + t];
     }
 }
 
@@ -388,20 +340,31 @@ int launch_col_t(int mode, const LineGeo& g, int planes, void* psi, const void* 
 template <typename R, int LOGN, int LOGE, int LOGRM>
 constexpr int col_strip_capacity() { return Cfg1D<R, LOGN, LOGE, LOGRM>::T * Cfg1D<R, LOGN, LOGE, LOGRM>::CMAX; }
 
-template <typename C, int CH>
-int launch_cny_t(const CnGeo& g, int planes, void* psi, cudaStream_t st) {
-    constexpr int TWC = 8;
-    const size_t smem = sizeof(C) * (size_t)g.nb * (TWC + 1 + 3);   // tile + LU coefficients
-    auto k = cny_kernel<C, CH, TWC>;
+// the strip CN pass: TWC = 128, 64 or 32 lines per CTA, the most whose
+// tile fits 100 KB of shared memory (two CTAs per SM), else 32 lines up to
+// the 227 KB limit
+template <typename C, int TWC>
+int launch_cn_lines(const CnGeo& g, int planes, void* psi, size_t smem, cudaStream_t st) {
+    auto k = cn_lines_kernel<C, TWC>;
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return SOFT_ERR_CUDA;
-    if (g.nb <= 0 || !psi) return SOFT_OK;
-    if (g.ld % TWC || planes < 1 || (g.nb + 31) / 32 > CH) return SOFT_ERR_INVALID_ARG;
+    if (!psi) return SOFT_OK;
     const int64_t grid = g.ld / TWC * planes;
     if (grid > 0x7fffffff) return SOFT_ERR_TOO_LARGE;
-    k<<<(unsigned)grid, 32 * TWC, smem, st>>>(g, psi);
+    k<<<(unsigned)grid, TWC, smem, st>>>(g, psi);
     return cudaGetLastError() == cudaSuccess ? SOFT_OK : SOFT_ERR_CUDA;
+}
+
+template <typename C>
+int launch_cny_t(const CnGeo& g, int planes, void* psi, cudaStream_t st) {
+    if (g.nb <= 0) return SOFT_OK;
+    if (planes < 1) return SOFT_ERR_INVALID_ARG;
+    auto bytes = [&](int twc) { return sizeof(C) * (size_t)g.nb * (twc + 3); };
+    if (g.ld % 128 == 0 && bytes(128) <= 100 * 1024) return launch_cn_lines<C, 128>(g, planes, psi, bytes(128), st);
+    if (g.ld % 64 == 0 && bytes(64) <= 100 * 1024) return launch_cn_lines<C, 64>(g, planes, psi, bytes(64), st);
+    if (g.ld % 32 == 0 && bytes(32) <= 227 * 1024) return launch_cn_lines<C, 32>(g, planes, psi, bytes(32), st);
+    return SOFT_ERR_UNSUPPORTED;
 }
 
 }  // namespace soft

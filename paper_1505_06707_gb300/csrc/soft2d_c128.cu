@@ -34,7 +34,7 @@ int soft2d_col_strip_capacity_c128(int logn, int loge, int logrm) {
 }
 
 int soft2d_cny_c128(const CnGeo& g, int planes, void* psi, cudaStream_t st) {
-    return launch_cny_t<double2, 24>(g, planes, psi, st);
+    return launch_cny_t<double2>(g, planes, psi, st);
 }
 
 }  // namespace soft
