@@ -51,11 +51,12 @@ int Plan2D::col(int mode, void* psi, const void* tky, cudaStream_t st) {
     return soft2d_col_c128(ly, ley, lry, mode, lg, 1, psi, tky, st);
 }
 
-// one step in x space: row pass K_x, V/2, CN_x; column pass CN_y, V/2, K_y
+// one step in x space: row pass K_x, V/2, CN_x (and the second V/2 off the
+// y-strip block); column pass CN_y, V/2 on the block rows, K_y
 int Plan2D::enqueue_step(void* psi, const void* tkx, const void* tky, cudaStream_t st) {
     int rc;
     if ((rc = row(ROW_KVC, psi, tkx, st))) return rc;
-    return col(COL_CVK, psi, tky, st);
+    return col(COL_CBK, psi, tky, st);
 }
 
 }  // namespace soft
@@ -157,10 +158,11 @@ int create_2d(const soft_grid* grid, const double* box, double R0, double theta,
     g.Wx = Q->Wx; g.Wy = Q->Wy; g.TVh = Q->TVh; g.cnx = Q->cnx; g.cny = Q->cny;
     g.nx = (int)nx; g.ny = (int)ny;
     g.nbx = nbx; g.blk0x = bx0; g.nby = nby; g.blk0y = by0;
+    g.v2 = 1;
     // set every kernel's shared-memory attribute now, outside any stream capture
     for (int m = ROW_K; m <= ROW_KVC; ++m)
         if ((rc = Q->row(m, nullptr, nullptr, 0))) return rc;
-    for (int m = COL_K; m <= COL_CVK; ++m)
+    for (int m = COL_K; m <= COL_CBK; ++m)
         if ((rc = Q->col(m, nullptr, nullptr, 0))) return rc;
     Q->launches = 0;
     *out = P.release();

@@ -9,7 +9,9 @@
 //   row pass    (x lines)  K_x, V/2, CN_x         (ROW_KVC)
 //   column pass (y lines)  CN_y, V/2, K_y         (COL_CVK)
 // so that K_y K_x | V/2 CN_x CN_y V/2 | K_y K_x ... is the paper's step
-// sequence.  Each K_d is F_d, e^{-i k_d^2 tau/2} (or its half at the ends of
+// sequence.  CN_y is the identity on the rows outside the y-strip block, so
+// the 2D row pass applies their second V/2 itself and the column pass only
+// that of the block rows (COL_CBK).  Each K_d is F_d, e^{-i k_d^2 tau/2} (or its half at the ends of
 // a call), F_d^-1 with the last forward and first inverse FFT pass fused
 // (kcenter).  ROW_K and COL_K apply the kinetic factor alone (the ends of a
 // call).  The 3D step adds a strip CN pass along y (cn_lines_kernel) between the
@@ -21,7 +23,7 @@
 namespace soft {
 
 enum RowMode { ROW_K = 0, ROW_KVC = 1 };
-enum ColMode { COL_K = 0, COL_CVK = 1 };
+enum ColMode { COL_K = 0, COL_CVK = 1, COL_CBK = 2 };
 
 // Pass twiddles of the line passes.  Complex128 plans, which are bound by
 // the FP64 pipe, store every W^{M off} for the passes with a stride of at
@@ -130,10 +132,20 @@ row_pass_kernel(Geo2D g, void* __restrict__ psi_v, const void* __restrict__ tkx_
             __syncthreads();
         }
     }
+    // 2D: rows outside the y-strip block take the second V/2 here (CN_y is
+    // the identity on them); the column pass applies it on the block rows
+    if (MODE == ROW_KVC && g.v2 && ((int)(y - g.blk0y) & (g.ny - 1)) >= g.nby) {
 #pragma unroll 4
-    for (int j = 0; j < E; ++j) {
-        const int n = tid + j * T;
-        row[n] = S[swz<C>(n)];
+        for (int j = 0; j < E; ++j) {
+            const int n = tid + j * T;
+            row[n] = vmul(S[swz<C>(n)], Tv[n]);
+        }
+    } else {
+#pragma unroll 4
+        for (int j = 0; j < E; ++j) {
+            const int n = tid + j * T;
+            row[n] = S[swz<C>(n)];
+        }
     }
 }
 
@@ -198,7 +210,7 @@ col_pass_kernel(LineGeo lg, void* __restrict__ psi_v, const void* __restrict__ t
         const int yy = idx / TW, j = idx % TW;
         cp_async<sizeof(C)>(&S[j * PITCH + swz<C>(yy)], &psi[(int64_t)yy * nx + c0 + j]);
     }
-    if constexpr (MODE == COL_CVK) {
+    if constexpr (MODE == COL_CVK || MODE == COL_CBK) {
         for (int idx = threadIdx.x; idx < lg.nb * TW; idx += TW * T) {
             const int i = idx / TW, j = idx % TW;
             const int yy = (lg.blk0 + i) & (N - 1);
@@ -210,9 +222,10 @@ col_pass_kernel(LineGeo lg, void* __restrict__ psi_v, const void* __restrict__ t
     cp_async_wait<0>();
     const int col = threadIdx.x / T, tid = threadIdx.x % T;
     C* Sc = S + col * PITCH;
+    if constexpr (MODE == COL_CBK) __syncthreads();   // the tile, complete, before the strip CN
     if constexpr (MODE == COL_CVK) {
         // V/2 on the thread's own elements outside the strip block (CN_y is
-        // the identity there)
+        // the identity there; COL_CBK: the row pass applied it there)
 #pragma unroll 8
         for (int it = 0; it < NIT; ++it) {
             const int idx = threadIdx.x + it * TW * T;
@@ -223,6 +236,8 @@ col_pass_kernel(LineGeo lg, void* __restrict__ psi_v, const void* __restrict__ t
             }
         }
         __syncthreads();
+    }
+    if constexpr (MODE == COL_CVK || MODE == COL_CBK) {
         if (lg.nb > 0) {
             const VT* tvc = Tvs + col * CC::VCAP;
             C* scan = reinterpret_cast<C*>(smem_raw + CC::OFF_SCAN) + 32 * col;
@@ -317,11 +332,12 @@ template <typename R, int LOGN, int LOGE, int LOGRM, int TW>
 int launch_col_t(int mode, const LineGeo& g, int planes, void* psi, const void* tky, cudaStream_t st) {
     using CC = ColCfg<R, LOGN, LOGE, LOGRM, TW>;
     using K = Cfg1D<R, LOGN, LOGE, LOGRM>;
-    const size_t smem = mode == COL_CVK ? CC::SMEM_CVK : CC::SMEM_K;
+    const size_t smem = mode == COL_K ? CC::SMEM_K : CC::SMEM_CVK;
     void (*k)(LineGeo, void*, const void*) = nullptr;
     switch (mode) {
     case COL_K: k = col_pass_kernel<R, LOGN, LOGE, LOGRM, TW, COL_K>; break;
     case COL_CVK: k = col_pass_kernel<R, LOGN, LOGE, LOGRM, TW, COL_CVK>; break;
+    case COL_CBK: k = col_pass_kernel<R, LOGN, LOGE, LOGRM, TW, COL_CBK>; break;
     default: return SOFT_ERR_INVALID_ARG;
     }
     if (smem > 48 * 1024 &&
@@ -329,7 +345,7 @@ int launch_col_t(int mode, const LineGeo& g, int planes, void* psi, const void* 
         return SOFT_ERR_CUDA;
     if (!psi) return SOFT_OK;             // attribute set only
     if (g.ld % TW || planes < 1) return SOFT_ERR_INVALID_ARG;
-    if (mode == COL_CVK && (g.nb + K::T - 1) / K::T > K::CMAX) return SOFT_ERR_UNSUPPORTED;
+    if (mode != COL_K && (g.nb + K::T - 1) / K::T > K::CMAX) return SOFT_ERR_UNSUPPORTED;
     const int64_t grid = g.ld / TW * planes;
     if (grid > 0x7fffffff) return SOFT_ERR_TOO_LARGE;
     k<<<(unsigned)grid, CC::THREADS, smem, st>>>(g, psi, tky);

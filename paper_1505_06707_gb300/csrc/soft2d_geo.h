@@ -14,6 +14,8 @@ struct Geo2D {              // passed by value to every 2D kernel
     int nx, ny;             // row length; number of rows (3D: ny nz)
     int nbx, blk0x;         // x-strip block (same for every row)
     int nby, blk0y;         // y-strip block (same for every column)
+    int v2;                 // 1: the row pass applies the second V/2 to the rows
+                            // outside the y-strip block (2D; ny a power of two)
 };
 
 // Lines along a strided axis: element i of line c of plane p sits at
