@@ -46,7 +46,7 @@ int Plan2D::row(int mode, void* psi, const void* tkx, cudaStream_t st) {
 }
 int Plan2D::col(int mode, void* psi, const void* tky, cudaStream_t st) {
     ++launches;
-    const LineGeo lg{geo.Wy, geo.nx, 0, geo.cny, geo.TVh, geo.nby, geo.blk0y};
+    const LineGeo lg{geo.Wy, geo.nx, 0, geo.cny, geo.TVh, geo.nby, geo.blk0y, 0, 1, 0, 0};
     if (prec == SOFT_C64) return soft2d_col_c64(ly, ley, lry, mode, lg, 1, psi, tky, st);
     return soft2d_col_c128(ly, ley, lry, mode, lg, 1, psi, tky, st);
 }
@@ -158,7 +158,7 @@ int create_2d(const soft_grid* grid, const double* box, double R0, double theta,
     g.Wx = Q->Wx; g.Wy = Q->Wy; g.TVh = Q->TVh; g.cnx = Q->cnx; g.cny = Q->cny;
     g.nx = (int)nx; g.ny = (int)ny;
     g.nbx = nbx; g.blk0x = bx0; g.nby = nby; g.blk0y = by0;
-    g.v2 = 1;
+    g.v2 = 1; g.ny1 = (int)ny; g.nz1 = 1; g.nbz1 = 0; g.blk0z1 = 0;
     // set every kernel's shared-memory attribute now, outside any stream capture
     for (int m = ROW_K; m <= ROW_KVC; ++m)
         if ((rc = Q->row(m, nullptr, nullptr, 0))) return rc;

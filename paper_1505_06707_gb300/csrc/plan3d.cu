@@ -6,9 +6,10 @@
 // merged scheme is ... V/2, CN, V/2, K ... with V/2 = e^{-iU tau/2}; factors
 // on different axes commute, so one step is four passes over the grid, the
 // state kept in x space between them:
-//   X  rows (x lines):     K_x, V/2, CN_x
+//   X  rows (x lines):     K_x, V/2, CN_x (and the second V/2 on the rows
+//                          outside the y- and z-strip blocks)
 //   Y1 y-strip block:      CN_y
-//   Z  z lines:            CN_z, V/2, K_z
+//   Z  z lines:            CN_z, V/2 (on the points not done by X), K_z
 //   Y2 y lines:            K_y
 // which is K_x | V/2 CN_x CN_y CN_z V/2 | K_z K_y per step; a call starts
 // with K_y/2, K_z/2 and ends with K_x/2, and the first and last steps use
@@ -85,7 +86,10 @@ int Plan3D::row(int mode, void* psi, const void* tkx, cudaStream_t st) {
 int Plan3D::line(int d, int mode, void* psi, const void* tk, cudaStream_t st) {
     ++launches;
     const int64_t nx = n[0], ny = n[1];
-    const LineGeo lg{W[d], d == 1 ? nx : nx * ny, d == 1 ? nx * ny : 0, cn[d], TVh, nb[d], blk0[d]};
+    // z lines (c = y nx + x): V/2 off the z-strip block only on lines with y
+    // in the y-strip block (the row pass applied it on the others)
+    const LineGeo lg{W[d], d == 1 ? nx : nx * ny, d == 1 ? nx * ny : 0, cn[d], TVh, nb[d], blk0[d],
+                     d == 2 ? nx : 0, n[1], nb[1], blk0[1]};
     const int planes = d == 1 ? n[2] : 1;
     if (prec == SOFT_C64) return soft2d_col_c64(l[d], le[d], lr[d], mode, lg, planes, psi, tk, st);
     return soft2d_col_c128(l[d], le[d], lr[d], mode, lg, planes, psi, tk, st);
@@ -201,6 +205,8 @@ int create_3d(const soft_grid* grid, const double* box, double R0, double theta,
     g.Wx = Q->W[0]; g.TVh = Q->TVh; g.cnx = Q->cn[0];
     g.nx = Q->n[0]; g.ny = Q->n[1] * Q->n[2];
     g.nbx = Q->nb[0]; g.blk0x = Q->blk0[0];
+    g.nby = Q->nb[1]; g.blk0y = Q->blk0[1];
+    g.v2 = 1; g.ny1 = Q->n[1]; g.nz1 = Q->n[2]; g.nbz1 = Q->nb[2]; g.blk0z1 = Q->blk0[2];
     // set every kernel's shared-memory attribute now, outside any stream capture
     for (int m = ROW_K; m <= ROW_KVC; ++m)
         if ((rc = Q->row(m, nullptr, nullptr, 0))) return rc;

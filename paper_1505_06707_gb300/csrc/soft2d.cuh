@@ -132,9 +132,12 @@ row_pass_kernel(Geo2D g, void* __restrict__ psi_v, const void* __restrict__ tkx_
             __syncthreads();
         }
     }
-    // 2D: rows outside the y-strip block take the second V/2 here (CN_y is
-    // the identity on them); the column pass applies it on the block rows
-    if (MODE == ROW_KVC && g.v2 && ((int)(y - g.blk0y) & (g.ny - 1)) >= g.nby) {
+    // rows outside the y- and z-strip blocks take the second V/2 here (CN_y
+    // and CN_z are the identity on them); the later passes apply it on the
+    // block rows
+    const int ry = (int)(y % g.ny1), rz = (int)(y / g.ny1);
+    if (MODE == ROW_KVC && g.v2 && ((ry - g.blk0y) & (g.ny1 - 1)) >= g.nby &&
+        ((rz - g.blk0z1) & (g.nz1 - 1)) >= g.nbz1) {
 #pragma unroll 4
         for (int j = 0; j < E; ++j) {
             const int n = tid + j * T;
@@ -222,10 +225,14 @@ col_pass_kernel(LineGeo lg, void* __restrict__ psi_v, const void* __restrict__ t
     cp_async_wait<0>();
     const int col = threadIdx.x / T, tid = threadIdx.x % T;
     C* Sc = S + col * PITCH;
-    if constexpr (MODE == COL_CBK) __syncthreads();   // the tile, complete, before the strip CN
-    if constexpr (MODE == COL_CVK) {
-        // V/2 on the thread's own elements outside the strip block (CN_y is
-        // the identity there; COL_CBK: the row pass applied it there)
+    bool off_v = MODE == COL_CVK;                    // V/2 off the strip block here
+    if (MODE == COL_CVK && lg.sel_div > 0) {
+        const int q = (int)((c0 / lg.sel_div) % lg.sel_n);
+        off_v = ((q - lg.sel_blk0) & (lg.sel_n - 1)) < lg.sel_nb;
+    }
+    if (off_v) {
+        // V/2 on the thread's own elements outside the strip block (CN along
+        // the lines is the identity there; COL_CBK: the row pass applied it)
 #pragma unroll 8
         for (int it = 0; it < NIT; ++it) {
             const int idx = threadIdx.x + it * TW * T;
@@ -235,8 +242,8 @@ col_pass_kernel(LineGeo lg, void* __restrict__ psi_v, const void* __restrict__ t
                 v = vmul(v, __ldg(&tv[(int64_t)yy * nx + c0 + j]));
             }
         }
-        __syncthreads();
     }
+    if constexpr (MODE != COL_K) __syncthreads();   // the tile, complete, before the strip CN
     if constexpr (MODE == COL_CVK || MODE == COL_CBK) {
         if (lg.nb > 0) {
             const VT* tvc = Tvs + col * CC::VCAP;

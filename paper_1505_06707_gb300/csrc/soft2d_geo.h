@@ -14,8 +14,10 @@ struct Geo2D {              // passed by value to every 2D kernel
     int nx, ny;             // row length; number of rows (3D: ny nz)
     int nbx, blk0x;         // x-strip block (same for every row)
     int nby, blk0y;         // y-strip block (same for every column)
-    int v2;                 // 1: the row pass applies the second V/2 to the rows
-                            // outside the y-strip block (2D; ny a power of two)
+    // v2 = 1: the row pass applies the second V/2 to the rows r outside the
+    // y-strip block and outside the z-strip block, y = r mod ny1 and
+    // z = r / ny1 (2D: ny1 = ny, no z block)
+    int v2, ny1, nz1, nbz1, blk0z1;
 };
 
 // Lines along a strided axis: element i of line c of plane p sits at
@@ -27,6 +29,11 @@ struct LineGeo {
     const void* cn;         // strip CN LU (mf, mb, g) along the lines (COL_CVK)
     const void* tv;         // e^{-iU tau/2}, laid out as the state (COL_CVK)
     int nb, blk0;           // strip block along the lines (COL_CVK)
+    // COL_CVK: with sel_div > 0 only lines whose (c / sel_div) mod sel_n lies
+    // in the cyclic block sel_blk0 .. + sel_nb take V/2 off the strip block
+    // (the row pass applied it on the others)
+    int64_t sel_div;
+    int sel_n, sel_nb, sel_blk0;
 };
 
 // The strip CN along a strided axis: the cyclic block blk0 .. blk0 + nb - 1
