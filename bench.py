@@ -771,12 +771,12 @@ def measure_w2(S, torch, dev, args, prec_name, steps, warmup, world=1, with_e2e=
 
 
 # DRAM bytes (read + write) per launch of the complex128 N = 16384 group
-# kernel, from an ncu capture of 69 instances x 16 steps (28.12 MB) scaled by
+# kernel, from an ncu capture of 69 instances x 16 steps (29.30 MB) scaled by
 # the instance count: each instance's 256 KB state is read and written back
 # once per launch and stays in L2 between steps (the tables are shared).
 # Valid while the kernel sources hash to src_sha1.
-TRAFFIC_C128 = {"src_sha1": "bf925e9ff4b11786c5c09d63ed73735e47513476",
-                "per_instance": (25.101824e6 + 3.019520e6) / 69}
+TRAFFIC_C128 = {"src_sha1": "a55f0e092028fe20c4774a2cfdc64a50d55e9298",
+                "per_instance": (25108992 + 4186368) / 69}
 
 
 def roofline_w2(torch, dev, m, prec_name):
