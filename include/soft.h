@@ -250,6 +250,10 @@ int soft_set_potential(soft_plan* plan, const double* U_re_im, int64_t n);
 /* sse_pcg_solve -- solve A psi_e = f for nE energies E[e] by complex-symmetric
  * CG (Sec. III: the unconjugated form r^T z replaces the inner product),
  * x0 = 0, stopping when ||r||_2 / ||f||_2 < tol (Hermitian norms, FP64).
+ * On 2D plans with precond 0, 1 and 4 the stopping residual is the true
+ * one: each energy that converged on the recursive residual restarts from
+ * its x with r = f - A x and retires after at least one more iteration
+ * (iters counts it); precond 5 decides on the true FP64 residual anyway.
  * 1D plans (single instance, N = 256 .. 2048, complex128) take precond 0
  * and 1: one CTA per energy runs the whole iteration with its vectors in
  * shared memory (one launch for all energies); 2D plans take every mode.

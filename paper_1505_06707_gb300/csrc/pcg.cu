@@ -254,6 +254,37 @@ static int apply_A(Plan2D* Q, const void* p, void* w, const double* dE, const in
     return pcg_col(Q->ly, 0, g, p, w, dE, act, part, nE, st);
 }
 
+// ||f - A x_e|| / ||f|| in FP64 for the energies with act[e] (the device
+// active flags must equal act); r holds the residuals afterwards
+static int true_relres(Plan2D* Q, const void* rhs, const void* x, int nE, const std::vector<int>& act,
+                       std::vector<double>& rel, cudaStream_t st) {
+    Pcg* S = Q->pcg;
+    const int64_t N = S->N;
+    const int np = 256;
+    int rc;
+    if ((rc = apply_A(Q, x, S->w, S->dE, S->active, S->part2, nE, st))) return rc;
+    if ((rc = vec_sub(rhs, S->w, S->r, S->active, N, nE, st))) return rc;
+    if ((rc = vec_norm2(rhs, N, S->part2, np, st))) return rc;
+    for (int e = 0; e < nE; ++e)
+        if (act[e] && (rc = vec_norm2(static_cast<const double2*>(S->r) + (int64_t)e * N, N,
+                                      S->part + (int64_t)e * np, np, st)))
+            return rc;
+    Q->launches += 3 + nE;
+    std::vector<double2> pf(np), pr((size_t)nE * np);
+    if ((rc = cuda_status(cudaMemcpyAsync(pf.data(), S->part2, sizeof(double2) * np, cudaMemcpyDeviceToHost, st)))) return rc;
+    if ((rc = cuda_status(cudaMemcpyAsync(pr.data(), S->part, sizeof(double2) * pr.size(), cudaMemcpyDeviceToHost, st)))) return rc;
+    if ((rc = cuda_status(cudaStreamSynchronize(st)))) return rc;
+    double f2 = 0.0;
+    for (const double2& v : pf) f2 += v.x;
+    for (int e = 0; e < nE; ++e) {
+        if (!act[e]) continue;
+        double r2 = 0.0;
+        for (int i = 0; i < np; ++i) r2 += pr[(size_t)e * np + i].x;
+        rel[e] = std::sqrt(r2 / f2);
+    }
+    return SOFT_OK;
+}
+
 // COCG (Sec. III) with preconditioner type precond (0, 1 or 4) over the
 // energies in s.active, from x = 0 or (warm) from the x already in psi_out
 static int solve_cocg(Plan2D* Q, const PcgState& s, const void* rhs, void* psi_out, int maxit, int nE,
@@ -555,6 +586,36 @@ int sse_pcg_solve(soft_plan* P, const double* E, int nE, const void* rhs, void* 
         }
     } else if (!flexible) {
         if ((rc = solve_cocg(Q, s, rhs, psi_out, maxit, nE, precond, false, st))) return rc;
+        // The recursive residual decided convergence and may have drifted
+        // from f - A x.  The true residual of every converged energy is
+        // evaluated in FP64 and reported; an energy whose true residual is
+        // not below tol restarts from its x with r = f - A x (at most
+        // VERIFY_MAXIT further iterations).
+        std::vector<int> stat_h(nE), act(nE, 0), redo(nE, 0);
+        if ((rc = cuda_status(cudaStreamSynchronize(st)))) return rc;
+        if ((rc = cuda_status(cudaMemcpy(stat_h.data(), S->status, sizeof(int) * nE, cudaMemcpyDeviceToHost)))) return rc;
+        int nver = 0, nredo = 0;
+        for (int e = 0; e < nE; ++e)
+            if (stat_h[e] == SOFT_OK) { act[e] = 1; ++nver; }
+        if (nver > 0) {
+            if ((rc = cuda_status(cudaMemcpy(S->active, act.data(), sizeof(int) * nE, cudaMemcpyHostToDevice)))) return rc;
+            std::vector<double> rel(nE, 0.0), rr(nE);
+            if ((rc = true_relres(Q, rhs, psi_out, nE, act, rel, st))) return rc;
+            if ((rc = cuda_status(cudaMemcpy(rr.data(), S->relres, sizeof(double) * nE, cudaMemcpyDeviceToHost)))) return rc;
+            for (int e = 0; e < nE; ++e) {
+                if (!act[e]) continue;
+                rr[e] = rel[e];
+                if (!(rel[e] < tol)) { redo[e] = 1; stat_h[e] = SOFT_ERR_NOT_CONVERGED; ++nredo; }
+            }
+            if ((rc = cuda_status(cudaMemcpy(S->relres, rr.data(), sizeof(double) * nE, cudaMemcpyHostToDevice)))) return rc;
+        }
+        if (nredo > 0) {
+            constexpr int VERIFY_MAXIT = 50;
+            if ((rc = cuda_status(cudaMemcpy(S->active, redo.data(), sizeof(int) * nE, cudaMemcpyHostToDevice)))) return rc;
+            if ((rc = cuda_status(cudaMemcpy(S->status, stat_h.data(), sizeof(int) * nE, cudaMemcpyHostToDevice)))) return rc;
+            if ((rc = cuda_status(cudaMemcpy(S->nactive, &nredo, sizeof(int), cudaMemcpyHostToDevice)))) return rc;
+            if ((rc = solve_cocg(Q, s, rhs, psi_out, VERIFY_MAXIT, nE, precond, true, st))) return rc;
+        }
     } else {
         // x = 0, r = f, ||f||^2
         if ((rc = vec_init(rhs, psi_out, S->r, N, nE, st))) return rc;

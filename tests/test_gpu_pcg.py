@@ -16,6 +16,12 @@ from oracle import stationary as ST  # noqa: E402
 from oracle import tables as T  # noqa: E402
 
 
+# the solver stops on the true FP64 residual f - A x (< 1e-8); recomputed
+# with the oracle's A (numpy FFTs, another rounding order) it may differ
+# from the solver's own evaluation by rounding only
+TRUE_RES_TOL = 1e-8 * (1 + 1e-4)
+
+
 def relerr(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
@@ -111,7 +117,7 @@ def test_pcg_fp32_preconditioner():
         xs = host(out)
         for e, E in enumerate(Es):
             res = np.linalg.norm(st.apply_A(xs[e], E) - f) / np.linalg.norm(f)
-            assert res < 2e-8, (E, res, its4[e])
+            assert res < TRUE_RES_TOL, (E, res, its4[e])
             # FP32 rounding leaves the preconditioner inexact and not exactly
             # symmetric; measured cost up to ~25 % more iterations
             assert its4[e] <= 1.3 * its1[e] + 5, (its1, its4)
@@ -174,7 +180,7 @@ def test_pcg_contours_and_absorbers(contour):
             xs = host(out)
             for e, E in enumerate(Es):
                 res = np.linalg.norm(st.apply_A(xs[e], E) - f) / np.linalg.norm(f)
-                assert res < 2e-8, (pc, E, res, its[e])
+                assert res < TRUE_RES_TOL, (pc, E, res, its[e])
             print("contour", contour, "precond", pc, "iterations", its)
     finally:
         S.soft_destroy(plan)
@@ -196,7 +202,7 @@ def test_pcg_solves_batch_small(precond):
         xs = host(out)
         for e, E in enumerate(Es):
             res = np.linalg.norm(st.apply_A(xs[e], E) - f) / np.linalg.norm(f)
-            assert res < 2e-8, (E, res, its[e])
+            assert res < TRUE_RES_TOL, (E, res, its[e])
             assert rr[e] < 1e-8
         # the oracle's own COCG reaches the same solution
         xo, ito, _ = ST.cocg(lambda v: st.apply_A(v, Es[1]),
@@ -262,7 +268,7 @@ def test_w4_full_size_sampled_energies():
             xs = host(out)
             for e, E in enumerate(Es):
                 res = np.linalg.norm(st.apply_A(xs[e], E) - w["f"]) / np.linalg.norm(w["f"])
-                assert res < 2 * w["tol"], (pc, E, res)
+                assert res < w["tol"] * (1 + 1e-4), (pc, E, res)
             print("W4 iterations (band, precond %d):" % pc, its)
     finally:
         S.soft_destroy(plan)
