@@ -80,6 +80,21 @@ def test_step3d_smallest_axes(prec, kind, theta):
     assert relerr(got, exp) < tol(prec)
 
 
+@pytest.mark.parametrize("prec", [S.SOFT_C128, S.SOFT_C64])
+def test_step3d_wide_y_strip(prec):
+    """A long y axis with a wide strip block (320 of 512 rows): the y-strip
+    CN pass takes its narrowest tile (32 lines per CTA) and its longest
+    sweeps; 10 steps against the oracle."""
+    n, box, R0 = (64, 512, 64), (-16.0, 16.0, -32.0, 32.0, -16.0, 16.0), 12.0
+    dt = 0.02
+    psi0 = W.w6_state(n, box, seed=13, noise=1e-3)
+    ref = P.Problem3D(n, box, R0, theta=0.5, kind=T.SECS, dt=dt, a2=1.0)
+    assert int((np.abs(ref.C[1][1]) > 0).sum()) >= 300
+    exp = ref.step(psi0, 10)
+    got, _ = run3d(n, box, R0, 0.5, dt, psi0, 10, prec, contour=T.SECS, soft_a2=1.0)
+    assert relerr(got, exp) < tol(prec)
+
+
 def test_step3d_free_gaussian_closed_form():
     """theta = 0, U = 0: the product of three closed-form free Gaussians
     summed over the periodic images of each axis (200 steps, complex128)."""
