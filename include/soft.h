@@ -232,14 +232,15 @@ int soft_step_surface(soft_plan* plan, void* psi, int64_t nsteps, const soft_fie
 int sse_surff(soft_plan* plan, int nE, const double* E, const void* phi, const void* samples,
               int64_t nsamples, double t0, int rule, void* amp, void* stream);
 
-/* soft_set_potential -- replace the static potential of a single 1D plan or
- * a 2D plan.  It enters the step as e^{-iU tau/2} (Sec. II, the scheme
- * after Eq. C_FD) and A as U - E (Sec. III, Eq. linsys); the default is the
- * soft-Coulomb potential of soft_options.
+/* soft_set_potential -- replace the static potential of a single 1D plan,
+ * a 2D plan or a 3D plan.  It enters the step as e^{-iU tau/2} (Sec. II, the
+ * scheme after Eq. C_FD) and A as U - E (Sec. III, Eq. linsys); the default
+ * is the soft-Coulomb potential of soft_options.
  *   U_re_im  host double[2n], interleaved complex: U at the complex-scaled
- *            grid points z(x_i) (2D: [ny][nx], x fastest).  The plan's
- *            comparison-absorber potential (CAP / TFAP contours) is added.
- *   n        grid points (N, or nx * ny).
+ *            grid points z(x_i) (2D: [ny][nx], 3D: [nz][ny][nx], x fastest).
+ *            The plan's comparison-absorber potential (CAP / TFAP contours)
+ *            is added.
+ *   n        grid points (N, nx * ny or nx * ny * nz).
  * The plan's potential tables (and the stationary solver's, once built) are
  * rewritten in place after a device synchronisation, so call it between
  * steps; captured graphs stay valid.  SOFT_ERR_UNSUPPORTED for batch plans,
