@@ -11,11 +11,12 @@
 // so that K_y K_x | V/2 CN_x CN_y V/2 | K_y K_x ... is the paper's step
 // sequence.  CN_y is the identity on the rows outside the y-strip block, so
 // the 2D row pass applies their second V/2 itself and the column pass only
-// that of the block rows (COL_CBK).  Each K_d is F_d, e^{-i k_d^2 tau/2} (or its half at the ends of
-// a call), F_d^-1 with the last forward and first inverse FFT pass fused
-// (kcenter).  ROW_K and COL_K apply the kinetic factor alone (the ends of a
-// call).  The 3D step adds a strip CN pass along y (cn_lines_kernel) between the
-// row pass and a COL_CVK pass along z, and a COL_K pass along y.
+// that of the block rows (COL_CBK).  Each K_d is F_d, e^{-i k_d^2 tau/2} (or
+// its half at the ends of a call), F_d^-1 with the last forward and first
+// inverse FFT pass fused (kcenter).  ROW_K and COL_K apply the kinetic factor
+// alone (the ends of a call).  The 3D step adds a strip CN pass along y
+// (cn_lines_kernel) between the row pass and a COL_CVK pass along z, and a
+// COL_K pass along y.
 #pragma once
 #include "soft1d.cuh"
 #include "soft2d_geo.h"
@@ -153,12 +154,13 @@ row_pass_kernel(Geo2D g, void* __restrict__ psi_v, const void* __restrict__ tkx_
 }
 
 // Column pass: TW columns per CTA, each transformed by T = ny/E threads.
-// COL_CVK: CN_y on the column's strip block, V/2 (outside the block as the
+// COL_CVK: CN_y on the column's strip block, V/2 (outside the block once the
 // tile is loaded, on it as the CN stores), then F_y, e^{-i ky^2 tau/2}/ny,
-// F_y^-1; COL_K: the kinetic factor alone.  The last forward pass, the factor
-// and the first inverse pass are fused (kcenter; table in its transposed
-// order).  The column tile, the V/2 factors of the strip rows (COL_CVK) and
-// the twiddles are staged in shared memory by asynchronous copies issued
+// F_y^-1; COL_CBK: the same with V/2 on the block rows only (the row pass
+// applied the rest); COL_K: the kinetic factor alone.  The last forward
+// pass, the factor and the first inverse pass are fused (kcenter; table in
+// its transposed order).  The column tile, the V/2 factors of the strip rows
+// and the twiddles are staged in shared memory by asynchronous copies issued
 // together at the start; the V/2 factors of the other rows and the kinetic
 // table (the same for every column) are read through the read-only cache.
 template <typename R, int LOGN, int LOGE, int LOGRM, int TW>
