@@ -63,8 +63,17 @@ static std::vector<cd> half_factors(const Plan3D& Q, const double* Uin) {
     };
     const int nt = std::max(1, std::min({(int)std::thread::hardware_concurrency(), 32, nz}));
     std::vector<std::thread> pool;
-    for (int t = 0; t < nt; ++t) pool.emplace_back(planes, (int)((int64_t)nz * t / nt), (int)((int64_t)nz * (t + 1) / nt));
+    int done = 0;                  // planes handed to threads; the rest run here
+    try {
+        for (int t = 0; t < nt; ++t) {
+            const int z0 = (int)((int64_t)nz * t / nt), z1 = (int)((int64_t)nz * (t + 1) / nt);
+            pool.emplace_back(planes, z0, z1);
+            done = z1;
+        }
+    } catch (...) {                // no thread could be started: no exception crosses the C ABI
+    }
     for (auto& th : pool) th.join();
+    if (done < nz) planes(done, nz);
     return tvh;
 }
 
