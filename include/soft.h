@@ -48,7 +48,7 @@ typedef enum {
     SOFT_OK = 0,
     SOFT_ERR_INVALID_ARG = -1,   /* NULL pointer, non-positive size, bad enum  */
     SOFT_ERR_NOT_POW2 = -2,      /* grid size not a power of two              */
-    SOFT_ERR_OOM = -3,           /* cudaMalloc failed                         */
+    SOFT_ERR_OOM = -3,           /* cudaMalloc or a host allocation failed    */
     SOFT_ERR_CUDA = -4,          /* a CUDA runtime call failed                */
     SOFT_ERR_NOT_CONVERGED = -5, /* PCG hit maxit; outputs are still written  */
     SOFT_ERR_BREAKDOWN = -6,     /* PCG: p^T A p or r^T z vanished            */

@@ -393,23 +393,29 @@ static NNState* nn_of(soft_plan* P, int* rc) {
 
 extern "C" {
 
-int sse_nn_set_weights(soft_plan* P, const float* w) {
+static int sse_nn_set_weights_impl(soft_plan* P, const float* w) {
     int rc;
     NNState* S = nn_of(P, &rc);
     if (!S) return rc;
     if (!w) return SOFT_ERR_INVALID_ARG;
     return S->set(w);
 }
+int sse_nn_set_weights(soft_plan* P, const float* w) {
+    return abi_guard([&] { return sse_nn_set_weights_impl(P, w); });
+}
 
-int sse_nn_get_weights(soft_plan* P, float* w) {
+static int sse_nn_get_weights_impl(soft_plan* P, float* w) {
     int rc;
     NNState* S = nn_of(P, &rc);
     if (!S) return rc;
     if (!w) return SOFT_ERR_INVALID_ARG;
     return cuda_status(cudaMemcpy(w, S->P, sizeof(float) * NN_PARAMS, cudaMemcpyDeviceToHost));
 }
+int sse_nn_get_weights(soft_plan* P, float* w) {
+    return abi_guard([&] { return sse_nn_get_weights_impl(P, w); });
+}
 
-int sse_nn_forward(soft_plan* P, const void* x, int nfields, int H, int W, void* out, void* stream) {
+static int sse_nn_forward_impl(soft_plan* P, const void* x, int nfields, int H, int W, void* out, void* stream) {
     int rc;
     NNState* S = nn_of(P, &rc);
     if (!S) return rc;
@@ -420,9 +426,12 @@ int sse_nn_forward(soft_plan* P, const void* x, int nfields, int H, int W, void*
     return cuda_status(cudaMemcpyAsync(out, S->out, sizeof(float) * 2 * (size_t)nfields * H * W,
                                        cudaMemcpyDeviceToDevice, st));
 }
+int sse_nn_forward(soft_plan* P, const void* x, int nfields, int H, int W, void* out, void* stream) {
+    return abi_guard([&] { return sse_nn_forward_impl(P, x, nfields, H, W, out, stream); });
+}
 
-int sse_nn_grad(soft_plan* P, const void* inputs, const void* targets, int n, int H, int W,
-                float* grad_out, double* loss_out, void* stream) {
+static int sse_nn_grad_impl(soft_plan* P, const void* inputs, const void* targets, int n, int H, int W,
+                            float* grad_out, double* loss_out, void* stream) {
     int rc;
     NNState* S = nn_of(P, &rc);
     if (!S) return rc;
@@ -437,9 +446,13 @@ int sse_nn_grad(soft_plan* P, const void* inputs, const void* targets, int n, in
     if (loss_out) *loss_out = l;
     return SOFT_OK;
 }
+int sse_nn_grad(soft_plan* P, const void* inputs, const void* targets, int n, int H, int W,
+                float* grad_out, double* loss_out, void* stream) {
+    return abi_guard([&] { return sse_nn_grad_impl(P, inputs, targets, n, H, W, grad_out, loss_out, stream); });
+}
 
-int sse_nn_train(soft_plan* P, const void* inputs, const void* targets, int ncrops, int H, int W,
-                 int steps, int batch, double lr, uint64_t seed, double* loss_out, void* stream) {
+static int sse_nn_train_impl(soft_plan* P, const void* inputs, const void* targets, int ncrops, int H, int W,
+                             int steps, int batch, double lr, uint64_t seed, double* loss_out, void* stream) {
     int rc;
     NNState* S = nn_of(P, &rc);
     if (!S) return rc;
@@ -486,6 +499,10 @@ int sse_nn_train(soft_plan* P, const void* inputs, const void* targets, int ncro
     if ((rc = cuda_status(cudaStreamSynchronize(st)))) return rc;
     if (loss_out) std::memcpy(loss_out, losses.data(), sizeof(double) * steps);
     return SOFT_OK;
+}
+int sse_nn_train(soft_plan* P, const void* inputs, const void* targets, int ncrops, int H, int W,
+                 int steps, int batch, double lr, uint64_t seed, double* loss_out, void* stream) {
+    return abi_guard([&] { return sse_nn_train_impl(P, inputs, targets, ncrops, H, W, steps, batch, lr, seed, loss_out, stream); });
 }
 
 }  // extern "C"

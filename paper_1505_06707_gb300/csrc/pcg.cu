@@ -460,7 +460,7 @@ void Plan2D::free_pcg() {
 
 extern "C" {
 
-int sse_apply_A(soft_plan* P, double E, const void* x, void* y, void* stream) {
+static int sse_apply_A_impl(soft_plan* P, double E, const void* x, void* y, void* stream) {
     if (P && P->kind == 1 && x && y && std::isfinite(E)) return sse1d_apply(P, E, 0, 0, x, y, (cudaStream_t)stream);
     if (!P || !x || !y || P->kind != 2 || !std::isfinite(E)) return SOFT_ERR_INVALID_ARG;
     if (P->prec != SOFT_C128) return SOFT_ERR_UNSUPPORTED;
@@ -475,8 +475,11 @@ int sse_apply_A(soft_plan* P, double E, const void* x, void* y, void* stream) {
     P->last_launches = Q->launches;
     return rc;
 }
+int sse_apply_A(soft_plan* P, double E, const void* x, void* y, void* stream) {
+    return abi_guard([&] { return sse_apply_A_impl(P, E, x, y, stream); });
+}
 
-int sse_apply_A32(soft_plan* P, double E, const void* x, void* y, void* stream) {
+static int sse_apply_A32_impl(soft_plan* P, double E, const void* x, void* y, void* stream) {
     if (P && P->kind == 1) return SOFT_ERR_UNSUPPORTED;
     if (!P || !x || !y || P->kind != 2 || !std::isfinite(E)) return SOFT_ERR_INVALID_ARG;
     if (P->prec != SOFT_C128) return SOFT_ERR_UNSUPPORTED;
@@ -491,8 +494,11 @@ int sse_apply_A32(soft_plan* P, double E, const void* x, void* y, void* stream) 
     P->last_launches = Q->launches;
     return rc;
 }
+int sse_apply_A32(soft_plan* P, double E, const void* x, void* y, void* stream) {
+    return abi_guard([&] { return sse_apply_A32_impl(P, E, x, y, stream); });
+}
 
-int sse_apply_precond(soft_plan* P, double E, int precond, const void* x, void* y, void* stream) {
+static int sse_apply_precond_impl(soft_plan* P, double E, int precond, const void* x, void* y, void* stream) {
     if (P && P->kind == 1 && x && y && std::isfinite(E)) {
         if (precond != 0 && precond != 1 && precond != 4) return SOFT_ERR_INVALID_ARG;
         return sse1d_apply(P, E, 1, precond, x, y, (cudaStream_t)stream);
@@ -511,9 +517,12 @@ int sse_apply_precond(soft_plan* P, double E, int precond, const void* x, void* 
     P->last_launches = Q->launches;
     return rc;
 }
+int sse_apply_precond(soft_plan* P, double E, int precond, const void* x, void* y, void* stream) {
+    return abi_guard([&] { return sse_apply_precond_impl(P, E, precond, x, y, stream); });
+}
 
-int sse_pcg_solve(soft_plan* P, const double* E, int nE, const void* rhs, void* psi_out, double tol,
-                  int maxit, int precond, int* iters_out, double* relres_out, void* stream) {
+static int sse_pcg_solve_impl(soft_plan* P, const double* E, int nE, const void* rhs, void* psi_out, double tol,
+                              int maxit, int precond, int* iters_out, double* relres_out, void* stream) {
     if (!P || !E || nE <= 0 || !rhs || !psi_out || !(tol > 0) || maxit <= 0) return SOFT_ERR_INVALID_ARG;
     if (precond < 0 || precond > 5) return SOFT_ERR_INVALID_ARG;
     if (P->kind == 1) {                  // 1D plans: the resident solver of sse1d.cu
@@ -665,6 +674,10 @@ int sse_pcg_solve(soft_plan* P, const double* E, int nE, const void* rhs, void* 
         if (stat_h[e] != SOFT_OK) out = SOFT_ERR_NOT_CONVERGED;
     }
     return out;
+}
+int sse_pcg_solve(soft_plan* P, const double* E, int nE, const void* rhs, void* psi_out, double tol,
+                  int maxit, int precond, int* iters_out, double* relres_out, void* stream) {
+    return abi_guard([&] { return sse_pcg_solve_impl(P, E, nE, rhs, psi_out, tol, maxit, precond, iters_out, relres_out, stream); });
 }
 
 }  // extern "C"

@@ -436,8 +436,8 @@ static int create_1d(int count, const soft_grid* grids, const double* boxes, con
     return SOFT_OK;
 }
 
-int soft_create(const soft_grid* grid, const double* box, double R0, double theta, double dt,
-                const soft_options* opt, soft_plan** out) {
+static int soft_create_impl(const soft_grid* grid, const double* box, double R0, double theta, double dt,
+                            const soft_options* opt, soft_plan** out) {
     if (!grid || !box || !out) return SOFT_ERR_INVALID_ARG;
     *out = nullptr;
     if (!std::isfinite(dt) || dt == 0.0 || !std::isfinite(theta)) return SOFT_ERR_INVALID_ARG;
@@ -449,10 +449,14 @@ int soft_create(const soft_grid* grid, const double* box, double R0, double thet
     if (grid->ndim == 3) return create_3d(grid, box, R0, theta, dt, o, out);
     return SOFT_ERR_INVALID_ARG;
 }
+int soft_create(const soft_grid* grid, const double* box, double R0, double theta, double dt,
+                const soft_options* opt, soft_plan** out) {
+    return abi_guard([&] { return soft_create_impl(grid, box, R0, theta, dt, opt, out); });
+}
 
-int soft_create_batch(int count, const soft_grid* grids, const double* boxes, const double* R0,
-                      const double* theta, const soft_field* fields, double dt,
-                      const soft_options* opt, soft_plan** out) {
+static int soft_create_batch_impl(int count, const soft_grid* grids, const double* boxes, const double* R0,
+                                  const double* theta, const soft_field* fields, double dt,
+                                  const soft_options* opt, soft_plan** out) {
     if (count <= 0 || !grids || !boxes || !R0 || !theta || !out) return SOFT_ERR_INVALID_ARG;
     *out = nullptr;
     if (!std::isfinite(dt) || dt == 0.0) return SOFT_ERR_INVALID_ARG;
@@ -460,6 +464,11 @@ int soft_create_batch(int count, const soft_grid* grids, const double* boxes, co
     int rc = check_opts(opt, &o);
     if (rc) return rc;
     return create_1d(count, grids, boxes, R0, theta, fields, dt, o, false, out);
+}
+int soft_create_batch(int count, const soft_grid* grids, const double* boxes, const double* R0,
+                      const double* theta, const soft_field* fields, double dt,
+                      const soft_options* opt, soft_plan** out) {
+    return abi_guard([&] { return soft_create_batch_impl(count, grids, boxes, R0, theta, fields, dt, opt, out); });
 }
 
 int soft_batch_layout(const soft_plan* P, int64_t* offsets, int64_t* total) {
@@ -470,8 +479,8 @@ int soft_batch_layout(const soft_plan* P, int64_t* offsets, int64_t* total) {
     return SOFT_OK;
 }
 
-int soft_step(soft_plan* P, void* psi, int64_t nsteps, const soft_field* field, double* t_inout,
-              void* stream) {
+static int soft_step_impl(soft_plan* P, void* psi, int64_t nsteps, const soft_field* field, double* t_inout,
+                          void* stream) {
     if (!P || !psi || !t_inout || nsteps < 0) return SOFT_ERR_INVALID_ARG;
     if (P->kind == 2) return P->step_2d(psi, nsteps, t_inout, (cudaStream_t)stream);
     if (P->kind == 3) return P->step_3d(psi, nsteps, t_inout, (cudaStream_t)stream);
@@ -482,10 +491,17 @@ int soft_step(soft_plan* P, void* psi, int64_t nsteps, const soft_field* field, 
     }
     return P->step_1d(psi, nsteps, t_inout, (cudaStream_t)stream);
 }
+int soft_step(soft_plan* P, void* psi, int64_t nsteps, const soft_field* field, double* t_inout,
+              void* stream) {
+    return abi_guard([&] { return soft_step_impl(P, psi, nsteps, field, t_inout, stream); });
+}
 
-int soft_step_batch(soft_plan* P, void* psi, int64_t nsteps, double* t_inout, void* stream) {
+static int soft_step_batch_impl(soft_plan* P, void* psi, int64_t nsteps, double* t_inout, void* stream) {
     if (!P || !psi || !t_inout || nsteps < 0 || P->kind != 1) return SOFT_ERR_INVALID_ARG;
     return P->step_1d(psi, nsteps, t_inout, (cudaStream_t)stream);
+}
+int soft_step_batch(soft_plan* P, void* psi, int64_t nsteps, double* t_inout, void* stream) {
+    return abi_guard([&] { return soft_step_batch_impl(P, psi, nsteps, t_inout, stream); });
 }
 
 int soft_observe(const soft_plan* P, const void* psi, double* norm_in, double* flux, void* stream) {
@@ -508,7 +524,7 @@ int soft_step_status(soft_plan* P, void* stream) {
     return rc ? rc : SOFT_ERR_NONFINITE;
 }
 
-int soft_set_potential(soft_plan* P, const double* U, int64_t n) {
+static int soft_set_potential_impl(soft_plan* P, const double* U, int64_t n) {
     if (!P || !U || n <= 0) return SOFT_ERR_INVALID_ARG;
     for (int64_t i = 0; i < 2 * n; ++i)
         if (!std::isfinite(U[i])) return SOFT_ERR_NONFINITE;
@@ -532,6 +548,9 @@ int soft_set_potential(soft_plan* P, const double* U, int64_t n) {
     if ((rc = refill_vtab(T->TV, tv, T->prec))) return rc;
     if ((rc = refill_vtab(T->TVs, tvs, T->prec))) return rc;
     return sse1d_refill_potential(P);
+}
+int soft_set_potential(soft_plan* P, const double* U, int64_t n) {
+    return abi_guard([&] { return soft_set_potential_impl(P, U, n); });
 }
 
 void soft_destroy(soft_plan* P) { delete P; }

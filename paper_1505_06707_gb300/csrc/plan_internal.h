@@ -5,8 +5,23 @@
 
 #include "internal.h"
 
+#include <new>
+
 namespace soft {
 int cuda_status(cudaError_t e);
+// Runs an entry point's body so that no C++ exception crosses the C ABI: a
+// failed host allocation returns SOFT_ERR_OOM, any other exception
+// SOFT_ERR_SETUP.
+template <class F>
+int abi_guard(F&& f) noexcept {
+    try {
+        return f();
+    } catch (const std::bad_alloc&) {
+        return SOFT_ERR_OOM;
+    } catch (...) {
+        return SOFT_ERR_SETUP;
+    }
+}
 int upload(void** dst, const void* src, size_t bytes);
 int upload_c(void** dst, const std::vector<cd>& v, int prec);
 int upload_tab(void** dst, const std::vector<cd>& v, int prec);

@@ -238,8 +238,8 @@ static bool surf_plan(const soft_plan* P) {
 
 using namespace soft;
 
-extern "C" int soft_step_surface(soft_plan* P, void* psi, int64_t nsteps, const soft_field* field,
-                                 double* t_inout, void* samples, void* stream) {
+static int soft_step_surface_impl(soft_plan* P, void* psi, int64_t nsteps, const soft_field* field,
+                                             double* t_inout, void* samples, void* stream) {
     if (!P || !psi || !t_inout || !samples || nsteps < 0) return SOFT_ERR_INVALID_ARG;
     if (!surf_plan(P)) return SOFT_ERR_UNSUPPORTED;
     const Group1D& g = P->groups[0];
@@ -273,9 +273,13 @@ extern "C" int soft_step_surface(soft_plan* P, void* psi, int64_t nsteps, const 
     *t_inout = t0 + (double)nsteps * P->dt;
     return SOFT_OK;
 }
+extern "C" int soft_step_surface(soft_plan* P, void* psi, int64_t nsteps, const soft_field* field,
+                                 double* t_inout, void* samples, void* stream) {
+    return abi_guard([&] { return soft_step_surface_impl(P, psi, nsteps, field, t_inout, samples, stream); });
+}
 
-extern "C" int sse_surff(soft_plan* P, int nE, const double* E, const void* phi, const void* samples,
-                         int64_t nsamples, double t0, int rule, void* amp, void* stream) {
+static int sse_surff_impl(soft_plan* P, int nE, const double* E, const void* phi, const void* samples,
+                                     int64_t nsamples, double t0, int rule, void* amp, void* stream) {
     if (!P || nE <= 0 || !E || !phi || !samples || !amp || nsamples < 3 || (nsamples - 1) % 2)
         return SOFT_ERR_INVALID_ARG;
     if (rule != 0 && rule != 1) return SOFT_ERR_INVALID_ARG;
@@ -300,4 +304,8 @@ extern "C" int sse_surff(soft_plan* P, int nE, const double* E, const void* phi,
                                      (double2*)amp);
     P->last_launches = 1;
     return cuda_status(cudaGetLastError());
+}
+extern "C" int sse_surff(soft_plan* P, int nE, const double* E, const void* phi, const void* samples,
+                         int64_t nsamples, double t0, int rule, void* amp, void* stream) {
+    return abi_guard([&] { return sse_surff_impl(P, nE, E, phi, samples, nsamples, t0, rule, amp, stream); });
 }
