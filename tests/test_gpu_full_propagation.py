@@ -13,6 +13,9 @@ benchmark times.
     theta = 0.4, U = -1/sqrt(x^2 + y^2 + 1), four seeded Gaussians) on a
     256^2 grid for its whole 10000 steps, and on the full 2048^2 grid for
     200 steps: complex128 to 1e-11.
+  - The 3D workload's contour and potential ([-40, 40]^3, sharp theta = 0.4,
+    U = -1/sqrt(r^2 + 1), four seeded Gaussians) on a 64^3 grid for 1000
+    steps: complex128 to 1e-11.
 The error is relative to the oracle's state at the end (its norm stays
 above 0.5 here)."""
 import numpy as np
@@ -117,3 +120,23 @@ def test_w3_full_size_200_steps_c128():
     ref = P.Problem2D(w["nx"], w["ny"], w["box"], w["R0"], theta=w["theta"], a2=w["a2"],
                       dt=w["dt"]).step(w["psi0"], nst)
     assert relerr(w3_gpu(w, nst), ref) < 1e-11
+
+
+def test_w6_contour_1000_steps_on_64cube():
+    w = W.w6(n=64)
+    psi0 = W.w6_state(w["n"], w["box"], seed=0)
+    nst = 1000
+    ref = P.Problem3D(w["n"], w["box"], w["R0"], theta=w["theta"], kind=w["kind"], a2=w["a2"],
+                      dt=w["dt"]).step(psi0, nst)
+    plan = S.soft_create(w["n"], w["box"], w["R0"], w["theta"], w["dt"], prec=S.SOFT_C128,
+                         contour=w["kind"], soft_a2=w["a2"])
+    try:
+        d = torch.tensor(psi0, dtype=torch.complex128, device="cuda")
+        S.soft_step(plan, d, nst, 0.0)
+        torch.cuda.synchronize()
+        got = d.cpu().numpy()
+    finally:
+        S.soft_destroy(plan)
+    h = 80.0 / 64
+    assert np.linalg.norm(ref) * h ** 1.5 > 0.5
+    assert relerr(got, ref) < 1e-11

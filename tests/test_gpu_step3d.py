@@ -146,16 +146,16 @@ def w6_case():
     psi0 = W.w6_state(cfg["n"], cfg["box"], seed=0)
     ref = P.Problem3D(cfg["n"], cfg["box"], cfg["R0"], theta=cfg["theta"], kind=cfg["kind"],
                       dt=cfg["dt"], a2=cfg["a2"])
-    return cfg, psi0, ref.step(psi0, 3)
+    return cfg, psi0, ref.step(psi0, 10)
 
 
 @pytest.mark.parametrize("prec", [S.SOFT_C128, S.SOFT_C64])
 def test_w6_full_size_few_steps(prec, w6_case):
-    """The benchmark's 3D workload at full size (256^3), 3 steps in the
-    launch configuration the benchmark times, every element against the
-    oracle."""
+    """The benchmark's 3D workload at full size (256^3), 10 steps (one
+    8-step graph replay between the first and last step) in the launch
+    configuration the benchmark times, every element against the oracle."""
     cfg, psi0, exp = w6_case
-    got, _ = run3d(cfg["n"], cfg["box"], cfg["R0"], cfg["theta"], cfg["dt"], psi0, 3, prec,
+    got, _ = run3d(cfg["n"], cfg["box"], cfg["R0"], cfg["theta"], cfg["dt"], psi0, 10, prec,
                    contour=cfg["kind"], soft_a2=cfg["a2"])
     assert relerr(got, exp) < tol(prec)
 
