@@ -171,3 +171,21 @@ def test_w3_full_size_few_steps(prec):
     got, _ = run2d(w["nx"], w["ny"], w["box"], w["R0"], w["theta"], w["dt"], w["psi0"], nst,
                    prec, soft_a2=w["a2"])
     assert relerr(got, ref) < tol(prec, nst, w["nx"])
+
+
+@pytest.mark.parametrize("prec", [S.SOFT_C128, S.SOFT_C64])
+@pytest.mark.parametrize("nsteps", [0, 1, 2, 3, 17, 18])
+def test_call_lengths_2d(nsteps, prec):
+    """Calls of 0 (no-op), 1 (the first step is also the last: both half
+    kinetic factors in one step), 2 (no middle steps), 3, 17 and 18 steps
+    (a 16-step graph replay plus a remainder) against the oracle."""
+    nx, ny = 256, 512
+    box = (-40.0, 40.0, -40.0, 40.0)
+    psi0 = packet2d(nx, ny, box, 21)
+    ref = P.Problem2D(nx, ny, box, 30.0, theta=0.4, a2=1.0, dt=0.02).step(psi0, nsteps)
+    got, launches = run2d(nx, ny, box, 30.0, 0.4, 0.02, psi0, nsteps, prec, soft_a2=1.0)
+    assert launches == (2 * nsteps + 2 if nsteps else 0)
+    if nsteps == 0:
+        assert np.array_equal(got, psi0.astype(np.complex64 if prec == S.SOFT_C64 else np.complex128))
+    else:
+        assert relerr(got, ref) < tol(prec)

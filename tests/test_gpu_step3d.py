@@ -167,3 +167,21 @@ def test_step3d_rejects_bad_grids():
             S.soft_create(n, box, 8.0, 0.4, 0.02, prec=S.SOFT_C64)
     with pytest.raises(ValueError):
         S.soft_create((64, 64, 64), box[:4], 8.0, 0.4, 0.02, prec=S.SOFT_C64)
+
+
+@pytest.mark.parametrize("prec", [S.SOFT_C128, S.SOFT_C64])
+@pytest.mark.parametrize("nsteps", [0, 1, 2, 3, 10, 11])
+def test_call_lengths_3d(nsteps, prec):
+    """Calls of 0 (no-op), 1 (the first step is also the last), 2 (no middle
+    steps), 3, 10 and 11 steps (an 8-step graph replay plus a remainder)
+    against the oracle."""
+    n, box, R0 = (128, 64, 64), (-20.0, 20.0, -16.0, 16.0, -16.0, 16.0), 10.0
+    psi0 = W.w6_state(n, box, seed=17, noise=1e-3)
+    ref = P.Problem3D(n, box, R0, theta=0.5, kind=T.SECS, dt=0.02, a2=1.0).step(psi0, nsteps)
+    got, launches = run3d(n, box, R0, 0.5, 0.02, psi0, nsteps, prec, contour=T.SECS, soft_a2=1.0)
+    if nsteps == 0:
+        assert launches == 0
+        assert np.array_equal(got, psi0.astype(np.complex64 if prec == S.SOFT_C64 else np.complex128))
+    else:
+        assert launches == 4 * nsteps + 3               # 4 passes per step, K_y/2, K_z/2, K_x/2
+        assert relerr(got, ref) < tol(prec)
