@@ -452,3 +452,21 @@ def test_persistent_batch_matches_group_kernels(prec):
     offs = np.concatenate([[0], np.cumsum([w["n"] for w in ws])[:-1]])
     for i, r in zip(sample, refs):
         assert relerr(outs[0][offs[i]:offs[i] + ws[i]["n"]].astype(np.complex128), r) < tol(prec)
+
+
+@pytest.mark.parametrize("prec", [S.SOFT_C128, S.SOFT_C64])
+@pytest.mark.parametrize("n,nsteps", [(1024, 1), (1024, 2), (1024, 3), (16384, 1), (16384, 2)])
+def test_call_lengths_1d(n, nsteps, prec):
+    """Calls of 1 step (the first step is also the last: both half kinetic
+    factors in one step), 2 steps (no middle step) and 3 steps, in a laser
+    field, on the shared-memory and the N = 16384 configurations."""
+    rng = np.random.default_rng(n + 31 * nsteps)
+    psi0 = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    hw = 8.0 * n / 1024
+    R0 = 0.75 * hw
+    field, t0 = (0.05, 0.057, 4.0), 100.0
+    ref = P.Problem1D(n, -hw, hw, R0, theta=0.5, kind=T.SECS, a2=2.0, dt=0.02).step(
+        psi0, nsteps, t0=t0, field=field)
+    got = gpu_run(n, (-hw, hw), R0, 0.5, 0.02, psi0, nsteps, prec=prec, field=field, t0=t0,
+                  contour=S.CONTOUR_SECS)
+    assert relerr(got, ref) < (1e-12 if prec == S.SOFT_C128 else 2e-6)
