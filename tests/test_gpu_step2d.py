@@ -189,3 +189,21 @@ def test_call_lengths_2d(nsteps, prec):
         assert np.array_equal(got, psi0.astype(np.complex64 if prec == S.SOFT_C64 else np.complex128))
     else:
         assert relerr(got, ref) < tol(prec)
+
+
+@pytest.mark.parametrize("prec", [S.SOFT_C128, S.SOFT_C64])
+@pytest.mark.parametrize("shape", [(1024, 256), (256, 1024), (2048, 256), (256, 2048)])
+def test_axis_lengths_2d(shape, prec):
+    """Axes of 1024 and 2048 points beside a 256-point axis (the row and
+    column kernels of the longest lines with the shortest), one box, so h
+    differs fourfold or eightfold between the axes; SECS theta = 0.5 from
+    R0 = 32 (a 410-row strip block on a 2048-point axis); 20 steps (a
+    16-step graph replay) against the oracle."""
+    nx, ny = shape
+    box = (-40.0, 40.0, -40.0, 40.0)
+    psi0 = packet2d(nx, ny, box, 3 * nx + ny)
+    ref = P.Problem2D(nx, ny, box, 32.0, theta=0.5, kind=T.SECS, a2=1.0, dt=0.02)
+    exp = ref.step(psi0, 20)
+    got, launches = run2d(nx, ny, box, 32.0, 0.5, 0.02, psi0, 20, prec, contour=T.SECS, soft_a2=1.0)
+    assert launches == 2 * 20 + 2
+    assert relerr(got, exp) < tol(prec)

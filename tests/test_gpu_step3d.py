@@ -2,6 +2,8 @@
 Sec. II with K = K_x + K_y + K_z and C = C_x + C_y + C_z as Kronecker sums;
 the multidimensional case named at the end of Sec. V) against the oracle's
 literal 4-FFT 3D step.  complex128: rel-L2 <= 1e-11; complex64: 1e-5."""
+import functools
+
 import numpy as np
 import pytest
 
@@ -185,3 +187,30 @@ def test_call_lengths_3d(nsteps, prec):
     else:
         assert launches == 4 * nsteps + 3               # 4 passes per step, K_y/2, K_z/2, K_x/2
         assert relerr(got, ref) < tol(prec)
+
+
+@functools.lru_cache(maxsize=None)
+def longest_axis_case(axis):
+    n = [64, 64, 64]
+    n[axis] = 2048
+    n = tuple(n)
+    box = (-16.0, 16.0) * 3
+    psi0 = W.w6_state(n, box, seed=19 + axis, noise=1e-3)
+    ref = P.Problem3D(n, box, 13.0, theta=0.5, kind=T.SECS, dt=0.02, a2=1.0)
+    assert int((np.abs(ref.C[axis][1]) > 0).sum()) >= 380
+    return n, box, psi0, ref.step(psi0, 6)
+
+
+@pytest.mark.parametrize("prec", [S.SOFT_C128, S.SOFT_C64])
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_step3d_longest_axis(axis, prec):
+    """One axis of 2048 points (the longest the 3D plan takes) with two of
+    64 in one box [-16, 16]^3: the x row pass, the y-strip CN pass and the y
+    lines, or the z lines, at their longest.  SECS theta = 0.5 from R0 = 13
+    puts a 386-row strip block on the long axis (h = 1/64; for complex128
+    on y that is near the y-strip pass's shared-memory limit) and a 14-row
+    one on the short axes (h = 1/2); 6 steps against the oracle."""
+    n, box, psi0, exp = longest_axis_case(axis)
+    got, launches = run3d(n, box, 13.0, 0.5, 0.02, psi0, 6, prec, contour=T.SECS, soft_a2=1.0)
+    assert launches == 4 * 6 + 3
+    assert relerr(got, exp) < tol(prec)
