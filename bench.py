@@ -531,7 +531,7 @@ def bench_conv(S, torch, dev, args, plan=None):
     return {"fields": nf, "ms": fms, "tflops": flops / (fms / 1e3) / 1e12,
             "peak_bf16_tflops": bf16, "frac": flops / (fms / 1e3) / 1e12 / bf16,
             "peak_source": psrc, "flop_per_point": flops / (nf * n * n),
-            "path": "warp mma.sync m16n8k16 BF16, FP32 accumulate"}
+            "path": "tcgen05.mma kind::f16 (BF16 in shared memory, FP32 accumulators in TMEM) for the 32-input-channel layers; warp mma.sync m16n8k16 for the 2-input-channel layer"}
 
 
 CROPS_PER_FIELD = 1024        # learned correction: training crops per harvested field
@@ -611,6 +611,57 @@ def bench_learned(S, torch, dev, args):
                      "max_relres": float(np.max(rr))}
     S.soft_destroy(plan)
     return res
+
+
+def bench_w1(S, torch, dev, args):
+    """The single 1D instance (N = 1024 on [-200, 200], sharp ECS R0 = 150,
+    theta = 0.5, soft-Coulomb a^2 = 2, dt = 0.05): the whole 2000-step run
+    as one soft_step call, in both precisions.  One instance is one CTA on
+    one SM with its state in shared memory, so this is the latency of the
+    step's dependent passes, not a throughput bound (the batch is the
+    throughput form)."""
+    import workloads as W
+    w = W.w1()
+    st = torch.cuda.current_stream(dev)
+    res = {}
+    for prec, name in ((S.SOFT_C128, "c128"), (S.SOFT_C64, "c64")):
+        plan = S.soft_create(w["n"], (w["a"], w["b"]), w["R0"], w["theta"], w["dt"], prec=prec,
+                             soft_a2=w["a2"])
+        ct = torch.complex64 if prec == S.SOFT_C64 else torch.complex128
+        d = torch.tensor(w["psi0"], dtype=ct, device=dev)
+        S.soft_step(plan, d, w["nsteps"], 0.0, stream=st)          # warm-up
+        torch.cuda.synchronize()
+        reps = 3
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            d.copy_(torch.tensor(w["psi0"], dtype=ct))
+            S.soft_step(plan, d, w["nsteps"], 0.0, stream=st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3 / reps
+        res[name] = {"ms_per_run": 1e3 * sec, "us_per_step": 1e6 * sec / w["nsteps"],
+                     "grid_point_steps_per_s": w["n"] * w["nsteps"] / sec,
+                     "launches_per_call": S.soft_last_launches(plan)}
+        S.soft_destroy(plan)
+    res["workload"] = ("N = 1024 on [-200,200], sharp ECS R0 = 150 theta = 0.5, U = -1/sqrt(x^2+2), "
+                       "dt = 0.05, 2000 steps in one call (the timed region includes a 16 KB "
+                       "host-to-device reset of the state per run)")
+    return res
+
+
+def oracle_w1_sample():
+    """The FP64 oracle on the whole single-instance 1D run (2000 steps)."""
+    from oracle import propagate as P
+    import workloads as W
+    w = W.w1()
+    prob = P.Problem1D(w["n"], w["a"], w["b"], w["R0"], theta=w["theta"], a2=w["a2"], dt=w["dt"])
+    prob.step(w["psi0"], 10)
+    t = time.perf_counter()
+    prob.step(w["psi0"], w["nsteps"])
+    sec = time.perf_counter() - t
+    return {"value": w["n"] * w["nsteps"] / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "the whole run: N = 1024 x 2000 steps, FP64 C oracle, one instance on one core"}
 
 
 def bench_pcg1d(S, torch, dev, args):
@@ -839,7 +890,7 @@ def main():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the other precision, the 2D step and the stationary-solver measurements")
     ap.add_argument("--only", choices=["2d", "3d", "pcg", "learned", "conv", "accuracy", "peaks", "w2",
-                                       "pcg1d"],
+                                       "pcg1d", "w1"],
                     default=None,
                     help="run one measurement alone (for profiling captures; not a bench line)")
     ap.add_argument("--persistent", type=int, default=1, choices=[0, 1],
@@ -868,7 +919,7 @@ def main():
             r["roofline"] = roofline_w2(torch, dev, r, args.prec)
         else:
             fn = {"2d": bench_2d, "3d": bench_3d, "pcg": bench_pcg, "learned": bench_learned,
-                  "conv": bench_conv, "pcg1d": bench_pcg1d}[args.only]
+                  "conv": bench_conv, "pcg1d": bench_pcg1d, "w1": bench_w1}[args.only]
             r = fn(S, torch, dev, args)
         print(json.dumps({"only": args.only, "result": r}))
         return
@@ -915,6 +966,7 @@ def main():
             mo["group_kernels_ms_per_step"] = g["ms_per_step"]
         out[other] = mo
         out["fp32_accuracy"] = bench_accuracy(S, torch, dev, args, sizes=(2048, 4096, 8192, 16384))
+        out["w1_1d"] = bench_w1(S, torch, dev, args)
         out["pcg1d_paper_test"] = bench_pcg1d(S, torch, dev, args)
         out["w3_2d"] = bench_2d(S, torch, dev, args)
         out["w6_3d"] = bench_3d(S, torch, dev, args)
@@ -923,6 +975,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_sample()
         if not args.no_extra:
+            out["w1_1d"]["cpu_baseline"] = oracle_w1_sample()
             out["w3_2d"]["cpu_baseline"] = oracle_2d_sample()
             out["w6_3d"]["cpu_baseline"] = oracle_3d_sample()
             pc = out["w4_pcg"]

@@ -1,5 +1,7 @@
 // 3x3 convolution with periodic padding as an implicit GEMM on the tensor
 // cores (BF16 inputs, FP32 accumulation, warp-level mma.sync m16n8k16).
+// The network uses it for the layers with 2 input channels; the layers with
+// 32 input channels run on tcgen05 (conv_tc.cuh).
 //
 //   out[p][o] = b[o] + sum_k A[p][k] W[o][k],  k = (tap, c):
 //     CIN = 32: k = 32 tap + c   (K = 288)
@@ -31,6 +33,7 @@ struct ConvArgs {
     const float* out_scale;    // per-field multiplier of OUT_ADD_C128 (NULL = 1)
     const __nv_bfloat16* mask; // OUT_BF16_MASK: the forward activation [F][H][W][COUT]
     const int* active;         // per-field flags (NULL: all)
+    unsigned* err;             // bit 0 set by a tensor-core CTA whose completion wait ran out (NULL: none)
     int H, W;
     int64_t field_stride_in, field_stride_out;   // elements (pixels) per field
 };

@@ -1,7 +1,8 @@
 // The learned correction to the FFT preconditioner: a 2 -> 32 -> 32 -> 2
 // 3x3 convolution network (ReLU between layers, periodic padding) whose
 // output is added to z = P^-1 r inside a flexible CG.  Forward and
-// backward-data passes run on the tensor cores (conv.cuh); weight gradients,
+// backward-data passes run on the tensor cores (tcgen05 for the layers with
+// 32 input channels, conv_tc.cuh; mma.sync for those with 2, conv.cuh); weight gradients,
 // the loss and Adam are plain reductions here.  Parameters are FP32 masters
 // with BF16 copies packed for the convolution kernels.
 #include <algorithm>
@@ -10,6 +11,7 @@
 #include <random>
 
 #include "conv.cuh"
+#include "conv_tc.cuh"
 #include "nn.h"
 #include "plan_internal.h"
 
@@ -213,7 +215,7 @@ __global__ void rms_kernel(const double2* __restrict__ z, int64_t N, const int* 
 // ------------------------------------------------------------------ state
 NNState::~NNState() {
     void* v[] = {P, G, M, V, w1, w2, w3, b3, b2, h1, h2, g1, g2, out, gout, xin, tgt, part,
-                 lpart, lval, idx, sin_, sout};
+                 lpart, lval, idx, sin_, sout, err};
     for (void* b : v) cudaFree(b);
 }
 
@@ -231,6 +233,8 @@ int NNState::init(uint64_t seed) {
     if ((rc = nn_alloc((void**)&b3, sizeof(__nv_bfloat16) * PB3))) return rc;
     if ((rc = nn_alloc((void**)&b2, sizeof(__nv_bfloat16) * PB2))) return rc;
     if ((rc = nn_alloc((void**)&lval, sizeof(double)))) return rc;
+    if ((rc = nn_alloc((void**)&err, sizeof(unsigned)))) return rc;
+    if ((rc = cuda_status(cudaMemset(err, 0, sizeof(unsigned))))) return rc;
     // He-style initial weights, small last layer (the correction starts near 0)
     std::vector<float> h(NN_PARAMS, 0.f);
     std::mt19937_64 gen(seed);
@@ -273,12 +277,23 @@ int NNState::ensure_act(int64_t npix, int fields) {
     return SOFT_OK;
 }
 
-static ConvArgs cargs(const void* in, const __nv_bfloat16* w, const float* bias, void* out, int H, int W) {
+static ConvArgs cargs(const void* in, const __nv_bfloat16* w, const float* bias, void* out, int H, int W,
+                      unsigned* err = nullptr) {
     ConvArgs a;
     std::memset(&a, 0, sizeof(a));
-    a.in = in; a.w = w; a.bias = bias; a.out = out; a.H = H; a.W = W;
+    a.in = in; a.w = w; a.bias = bias; a.out = out; a.H = H; a.W = W; a.err = err;
     a.field_stride_in = a.field_stride_out = (int64_t)H * W;
     return a;
+}
+
+int NNState::take_err(cudaStream_t st) {
+    unsigned h = 0;
+    int rc;
+    if ((rc = cuda_status(cudaMemcpyAsync(&h, err, sizeof(unsigned), cudaMemcpyDeviceToHost, st)))) return rc;
+    if ((rc = cuda_status(cudaStreamSynchronize(st)))) return rc;
+    if (!h) return SOFT_OK;
+    if ((rc = cuda_status(cudaMemsetAsync(err, 0, sizeof(unsigned), st)))) return rc;
+    return SOFT_ERR_TIMEOUT;
 }
 
 // forward of a batch of complex64 fields [F][H][W] -> out float2 [F][H][W]
@@ -286,10 +301,10 @@ int NNState::forward_c64(const void* x, int F, int H, int W, cudaStream_t st) {
     int rc;
     ConvArgs a = cargs(x, w1, P + P_B1, h1, H, W);
     if ((rc = launch_conv<2, 32, IN_C64, OUT_BF16_RELU>(a, F, st))) return SOFT_ERR_CUDA;
-    a = cargs(h1, w2, P + P_B2, h2, H, W);
-    if ((rc = launch_conv<32, 32, IN_BF16, OUT_BF16_RELU>(a, F, st))) return SOFT_ERR_CUDA;
-    a = cargs(h2, w3, P + P_B3, out, H, W);
-    if ((rc = launch_conv<32, 2, IN_BF16, OUT_F32>(a, F, st))) return SOFT_ERR_CUDA;
+    a = cargs(h1, w2, P + P_B2, h2, H, W, err);
+    if ((rc = launch_conv32_tc<32, OUT_BF16_RELU>(a, F, st))) return SOFT_ERR_CUDA;
+    a = cargs(h2, w3, P + P_B3, out, H, W, err);
+    if ((rc = launch_conv32_tc<2, OUT_F32>(a, F, st))) return SOFT_ERR_CUDA;
     return SOFT_OK;
 }
 
@@ -332,9 +347,9 @@ int NNState::grad(const void* x, const void* t, int F, int H, int W, cudaStream_
     if ((rc = launch_conv<2, 32, IN_C64, OUT_BF16_MASK>(a, F, st))) return SOFT_ERR_CUDA;
     // layer 2
     if ((rc = wgrad<32, 32, IN_BF16, 0>(*this, h1, g2, F, H, W, G + P_W2, G + P_B2, st))) return rc;
-    a = cargs(g2, b2, nullptr, g1, H, W);
+    a = cargs(g2, b2, nullptr, g1, H, W, err);
     a.mask = h1;
-    if ((rc = launch_conv<32, 32, IN_BF16, OUT_BF16_MASK>(a, F, st))) return SOFT_ERR_CUDA;
+    if ((rc = launch_conv32_tc<32, OUT_BF16_MASK>(a, F, st))) return SOFT_ERR_CUDA;
     // layer 1
     return wgrad<2, 32, IN_C64, 0>(*this, x, g1, F, H, W, G + P_W1, G + P_B1, st);
 }
@@ -367,12 +382,12 @@ int NNState::correct_c128(void* z, int F, int H, int W, const int* active, cudaS
     ConvArgs a = cargs(z, w1, P + P_B1, h1, H, W);
     a.in_scale = sin_; a.active = active;
     if ((rc = launch_conv<2, 32, IN_C128, OUT_BF16_RELU>(a, F, st))) return SOFT_ERR_CUDA;
-    a = cargs(h1, w2, P + P_B2, h2, H, W);
+    a = cargs(h1, w2, P + P_B2, h2, H, W, err);
     a.active = active;
-    if ((rc = launch_conv<32, 32, IN_BF16, OUT_BF16_RELU>(a, F, st))) return SOFT_ERR_CUDA;
-    a = cargs(h2, w3, P + P_B3, z, H, W);
+    if ((rc = launch_conv32_tc<32, OUT_BF16_RELU>(a, F, st))) return SOFT_ERR_CUDA;
+    a = cargs(h2, w3, P + P_B3, z, H, W, err);
     a.active = active; a.out_scale = sout;
-    if ((rc = launch_conv<32, 2, IN_BF16, OUT_ADD_C128>(a, F, st))) return SOFT_ERR_CUDA;
+    if ((rc = launch_conv32_tc<2, OUT_ADD_C128>(a, F, st))) return SOFT_ERR_CUDA;
     return SOFT_OK;
 }
 
@@ -443,6 +458,7 @@ static int sse_nn_grad_impl(soft_plan* P, const void* inputs, const void* target
     double l = 0;
     if ((rc = cuda_status(cudaMemcpyAsync(&l, S->lval, sizeof(double), cudaMemcpyDeviceToHost, st)))) return rc;
     if ((rc = cuda_status(cudaStreamSynchronize(st)))) return rc;
+    if ((rc = S->take_err(st))) return rc;
     if (loss_out) *loss_out = l;
     return SOFT_OK;
 }
@@ -497,6 +513,7 @@ static int sse_nn_train_impl(soft_plan* P, const void* inputs, const void* targe
                 return rc;
     }
     if ((rc = cuda_status(cudaStreamSynchronize(st)))) return rc;
+    if ((rc = S->take_err(st))) return rc;
     if (loss_out) std::memcpy(loss_out, losses.data(), sizeof(double) * steps);
     return SOFT_OK;
 }

@@ -18,6 +18,7 @@ struct NNState {
     double *lpart = nullptr, *lval = nullptr;
     int* idx = nullptr;
     float *sin_ = nullptr, *sout = nullptr;
+    unsigned* err = nullptr;           // tensor-core convolution wait ran out (bit 0)
     int64_t act_cap = 0, part_cap = 0, batch_cap = 0;
     int scale_cap = 0;
     int adam_t = 0;
@@ -30,6 +31,7 @@ struct NNState {
     int grad(const void* x, const void* t, int F, int H, int W, cudaStream_t st);
     int train_step(const void* x, const void* t, int F, int H, int W, float lr, cudaStream_t st);
     int correct_c128(void* z, int F, int H, int W, const int* active, cudaStream_t st);
+    int take_err(cudaStream_t st);     // SOFT_ERR_TIMEOUT if a convolution wait ran out (clears it)
     ~NNState();
 };
 

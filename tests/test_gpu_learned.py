@@ -79,6 +79,30 @@ def test_forward_matches_oracle():
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 3e-2
 
 
+def test_forward_odd_height_matches_oracle():
+    """Height 131 (not a multiple of 4: every convolution takes one output
+    row per CTA) and width 256 (two 128-pixel segments per row, periodic
+    wrap across both), three fields: the network output against the oracle
+    with the same BF16-rounded weights and inputs."""
+    rng = np.random.default_rng(5)
+    params = CV.init_params(rng, scale_last=1.0)
+    for W_, b_ in params:
+        b_[:] = 0.1 * rng.standard_normal(b_.shape)
+    x = (rng.standard_normal((3, 131, 256)) + 1j * rng.standard_normal((3, 131, 256))).astype(np.complex64)
+    plan = small_plan()
+    try:
+        S.sse_nn_set_weights(plan, flat(params))
+        out = torch.zeros((3, 131, 256, 2), dtype=torch.float32, device="cuda")
+        S.sse_nn_forward(plan, torch.tensor(x, device="cuda"), out)
+        torch.cuda.synchronize()
+        got = np.moveaxis(out.cpu().numpy(), 3, 1)
+    finally:
+        S.soft_destroy(plan)
+    assert np.isfinite(got).all()
+    ref, _ = CV.forward([[bf16(W), b] for W, b in params], bf16(to_chw(x)))
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 3e-2
+
+
 def test_gradients_match_oracle():
     rng = np.random.default_rng(4)
     params = CV.init_params(rng, scale_last=1.0)
