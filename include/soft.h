@@ -348,7 +348,11 @@ int soft_step_noalloc(const soft_plan* plan, void* psi, int64_t nsteps, const so
  *   (host float[10434]); no update.
  * sse_nn_train: `steps` Adam steps (lr, beta 0.9/0.999) on minibatches of
  *   `batch` fields drawn from the n inputs with the seed; loss_out: host
- *   double[steps] or NULL. */
+ *   double[steps] or NULL.
+ * The convolutions with 32 input channels run on tcgen05 with a bounded
+ * completion wait; if one runs out, its outputs are NaN and sse_nn_grad /
+ * sse_nn_train return SOFT_ERR_TIMEOUT (sse_nn_forward and the solver's
+ * correction show it as non-finite values). */
 int sse_nn_set_weights(soft_plan* plan, const float* w);
 int sse_nn_get_weights(soft_plan* plan, float* w);
 int sse_nn_forward(soft_plan* plan, const void* x, int n, int H, int W, void* out, void* stream);

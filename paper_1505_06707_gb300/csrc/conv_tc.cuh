@@ -4,7 +4,7 @@
 //
 //   out[p][o] = b[o] + sum_{tap, c} in[y + dy][x + dx][c] W[o][32 tap + c]
 //
-// One CTA of 128 threads computes ROWS consecutive rows of a 128-pixel
+// One CTA of 256 threads computes ROWS consecutive rows of a 128-pixel
 // segment of one field for all output channels.  The MMA shape is
 // M = 128 pixels (one row), N = NP output channels (COUT padded to 16),
 // K = 16 input channels; a row takes 9 taps x 2 channel halves = 18 MMAs
@@ -22,9 +22,11 @@
 //     stride byte offset) and the two channel groups of a K-step one slab,
 //     130 x 16 bytes, apart (the leading byte offset);
 //   weights [9 taps][4 channel groups][NP outputs][8 channels].
-// Epilogue: warp w reads TMEM lanes 32w .. 32w+31 (pixel = lane) with
-// tcgen05.ld, adds the bias, applies ReLU or the backward mask, and writes
-// 64 contiguous bytes per pixel.
+// Epilogue: warp w reads TMEM lanes 32 (w mod 4) + lane (pixel = lane) with
+// tcgen05.ld for the rows ry = w / 4, w / 4 + 2, ..., adds the bias,
+// applies ReLU or the backward mask, and writes 64 contiguous bytes per
+// pixel.  All 8 warps stage the tile (the CTA's input rows are in flight
+// together); one thread issues the MMAs.
 //
 // The completion wait is bounded: if it runs out, the CTA sets bit 0 of
 // *err (when given), writes NaN to its outputs, frees its TMEM and returns.
@@ -140,11 +142,11 @@ struct ConvTC {
 };
 
 template <int COUT, int OUTK, int ROWS>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(256)
 conv3x3_tc_kernel(ConvArgs a)
 {
     using Q = ConvTC<COUT, ROWS>;
-    constexpr int NP = Q::NP, SLAB = Q::SLAB, TP = Q::TP;
+    constexpr int NP = Q::NP, SLAB = Q::SLAB, TP = Q::TP, NT = 256;
     constexpr int KP = ConvK<32>::KPITCH;
     const int f = blockIdx.z;
     if (a.active && !a.active[f]) return;
@@ -160,19 +162,27 @@ conv3x3_tc_kernel(ConvArgs a)
     if (warp == 0) tc5::tmem_alloc<Q::NCOL>(&tslot);
     if (tid == 0) tc5::bar_init(&bar);
     // weights: the 16 bytes (tap, channel group g, output n) = packed row n at k = 32 tap + 8 g
-    for (int i = tid; i < 9 * 4 * NP; i += 128) {
+    for (int i = tid; i < 9 * 4 * NP; i += NT) {
         const int n = i % NP, g = (i / NP) & 3, tap = i / (4 * NP);
         uint4* dst = reinterpret_cast<uint4*>(wsm) + i;
         if (n < Q::WROWS) cp_async<16>(dst, a.w + (size_t)n * KP + 32 * tap + 8 * g);
         else *dst = make_uint4(0u, 0u, 0u, 0u);
     }
-    // input rows y0-1 .. y0+ROWS, pixels x0-1 .. x0+128 (periodic), 4 x 16 bytes per pixel
-    const unsigned char* in = reinterpret_cast<const unsigned char*>(a.in);
-    for (int i = tid; i < (ROWS + 2) * TP * 4; i += 128) {
-        const int g = i & 3, px = (i >> 2) % TP, r = (i >> 2) / TP;
-        const int yy = (y0 + r - 1 + H) % H, xx = (x0 + px - 1 + W) % W;
-        const int64_t pix = (int64_t)f * a.field_stride_in + (int64_t)yy * W + xx;
-        cp_async<16>(tile + ((r * 4 + g) * TP + px) * 16, in + pix * 64 + g * 16);
+    // input rows y0-1 .. y0+ROWS, pixels x0-1 .. x0+128 (periodic: each
+    // index is at most one period outside), 4 x 16 bytes per pixel
+    const unsigned char* in = reinterpret_cast<const unsigned char*>(a.in) + (int64_t)f * a.field_stride_in * 64;
+#pragma unroll 1
+    for (int r = 0; r < ROWS + 2; ++r) {
+        int yy = y0 + r - 1;
+        yy = yy < 0 ? yy + H : (yy >= H ? yy - H : yy);
+        const unsigned char* row = in + (int64_t)yy * W * 64;
+        unsigned char* trow = tile + r * 4 * SLAB;
+        for (int j = tid; j < TP * 4; j += NT) {
+            const int px = j >> 2, g = j & 3;
+            int xx = x0 + px - 1;
+            xx = xx < 0 ? xx + W : (xx >= W ? xx - W : xx);
+            cp_async<16>(trow + (g * TP + px) * 16, row + (int64_t)xx * 64 + g * 16);
+        }
     }
     cp_async_commit();
     cp_async_wait<0>();
@@ -202,10 +212,13 @@ conv3x3_tc_kernel(ConvArgs a)
     tc5::fence_after();
     if (!ok && lane == 0 && a.err) atomicOr(a.err, 1u);
 
-    const int p = 32 * warp + lane;            // pixel of the segment = TMEM lane
-    const uint32_t tl = tbase + ((uint32_t)(32 * warp) << 16);
+    float bias[COUT];
+#pragma unroll
+    for (int j = 0; j < COUT; ++j) bias[j] = a.bias ? a.bias[j] : 0.0f;
+    const int p = 32 * (warp & 3) + lane;      // pixel of the segment = TMEM lane
+    const uint32_t tl = tbase + ((uint32_t)(32 * (warp & 3)) << 16);
 #pragma unroll 1
-    for (int ry = 0; ry < ROWS; ++ry) {
+    for (int ry = warp >> 2; ry < ROWS; ry += NT / 128) {
         uint32_t r[NP];
         if (ok) {
             tc5::tmem_ld<NP>(tl + (uint32_t)(ry * NP), r);
@@ -235,8 +248,8 @@ conv3x3_tc_kernel(ConvArgs a)
             } else {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    float v0 = __uint_as_float(r[2 * j]), v1 = __uint_as_float(r[2 * j + 1]);
-                    if (a.bias) { v0 += a.bias[2 * j]; v1 += a.bias[2 * j + 1]; }
+                    const float v0 = __uint_as_float(r[2 * j]) + bias[2 * j];
+                    const float v1 = __uint_as_float(r[2 * j + 1]) + bias[2 * j + 1];
                     pk[j] = pack_bf16(fmaxf(v0, 0.0f), fmaxf(v1, 0.0f));
                 }
             }
@@ -245,8 +258,7 @@ conv3x3_tc_kernel(ConvArgs a)
             for (int q = 0; q < 4; ++q) o[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
         } else {
             static_assert(COUT == 2, "two output channels");
-            float v0 = __uint_as_float(r[0]), v1 = __uint_as_float(r[1]);
-            if (a.bias) { v0 += a.bias[0]; v1 += a.bias[1]; }
+            const float v0 = __uint_as_float(r[0]) + bias[0], v1 = __uint_as_float(r[1]) + bias[1];
             if constexpr (OUTK == OUT_F32) {
                 reinterpret_cast<float2*>(a.out)[pix] = make_float2(v0, v1);
             } else {
@@ -274,7 +286,7 @@ int launch_conv_tc_rows(const ConvArgs& a, int nfields, cudaStream_t st) {
     if (nfields <= 0) return 0;
     if (a.W % 128 != 0 || a.H % ROWS != 0) return -2;
     dim3 grid(a.W / 128, a.H / ROWS, nfields);
-    k<<<grid, 128, Q::SMEM, st>>>(a);
+    k<<<grid, 256, Q::SMEM, st>>>(a);
     return cudaGetLastError() == cudaSuccess ? 0 : -4;
 }
 
