@@ -341,7 +341,9 @@ int soft_step_noalloc(const soft_plan* plan, void* psi, int64_t nsteps, const so
  * W3[2][32][3][3], b3[2] (out[o](y,x) = b[o] + sum W[o][i][dy+1][dx+1]
  * in[i](y+dy, x+dx), indices mod H, W).  Every 2D plan owns one network,
  * initialised from a fixed seed on first use.
- *   Fields: device complex64 arrays [n][H][W], W a multiple of 128, H >= 3.
+ *   Fields: device complex64 arrays [n][H][W], W a multiple of 128, H >= 3,
+ *   at most 65535 fields per call (SOFT_ERR_TOO_LARGE beyond; for the
+ *   solver's learned modes, at most 65535 energies).
  * sse_nn_set_weights / sse_nn_get_weights: host float[10434].
  * sse_nn_forward: out = NN(x), device float [n][H][W][2].
  * sse_nn_grad: mean-square loss of NN(x) against targets and its gradient

@@ -370,6 +370,7 @@ int NNState::train_step(const void* x, const void* t, int F, int H, int W, float
 // z += rms(z) NN(z / rms(z)) for the active complex128 fields [F][H][W]
 int NNState::correct_c128(void* z, int F, int H, int W, const int* active, cudaStream_t st) {
     int rc;
+    if (F > NN_MAX_FIELDS) return SOFT_ERR_TOO_LARGE;
     if ((rc = ensure_act((int64_t)F * H * W, F))) return rc;
     if (F > scale_cap) {
         cudaFree(sin_); cudaFree(sout);
@@ -435,6 +436,7 @@ static int sse_nn_forward_impl(soft_plan* P, const void* x, int nfields, int H, 
     NNState* S = nn_of(P, &rc);
     if (!S) return rc;
     if (!x || !out || nfields <= 0 || H < 3 || W < 128 || W % 128) return SOFT_ERR_INVALID_ARG;
+    if (nfields > NN_MAX_FIELDS) return SOFT_ERR_TOO_LARGE;
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = S->ensure_act((int64_t)nfields * H * W, nfields))) return rc;
     if ((rc = S->forward_c64(x, nfields, H, W, st))) return rc;
@@ -451,6 +453,7 @@ static int sse_nn_grad_impl(soft_plan* P, const void* inputs, const void* target
     NNState* S = nn_of(P, &rc);
     if (!S) return rc;
     if (!inputs || !targets || !grad_out || n <= 0 || H < 3 || W < 128 || W % 128) return SOFT_ERR_INVALID_ARG;
+    if (n > NN_MAX_FIELDS) return SOFT_ERR_TOO_LARGE;
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = S->ensure_act((int64_t)n * H * W, n))) return rc;
     if ((rc = S->grad(inputs, targets, n, H, W, st))) return rc;
@@ -477,6 +480,7 @@ static int sse_nn_train_impl(soft_plan* P, const void* inputs, const void* targe
         return SOFT_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const int B = std::min(batch, ncrops);
+    if (B > NN_MAX_FIELDS) return SOFT_ERR_TOO_LARGE;
     const int64_t fsz = (int64_t)H * W;
     if ((rc = S->ensure_act((int64_t)B * fsz, B))) return rc;
     if (B * fsz > S->batch_cap) {

@@ -8,6 +8,9 @@ namespace soft {
 
 constexpr int NN_PARAMS = 32 * 2 * 9 + 32 + 32 * 32 * 9 + 32 + 2 * 32 * 9 + 2;   // 10434
 
+// fields per convolution launch (the grid's z dimension)
+constexpr int NN_MAX_FIELDS = 65535;
+
 struct NNState {
     float *P = nullptr, *G = nullptr, *M = nullptr, *V = nullptr;     // FP32 master, grad, Adam
     __nv_bfloat16 *w1 = nullptr, *w2 = nullptr, *w3 = nullptr, *b3 = nullptr, *b2 = nullptr;

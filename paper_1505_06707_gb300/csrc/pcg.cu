@@ -540,6 +540,7 @@ static int sse_pcg_solve_impl(soft_plan* P, const double* E, int nE, const void*
     const bool learned = precond == 2;
     if (learned) {
         if (!P->p2 || P->p2->nx % 128) return SOFT_ERR_UNSUPPORTED;
+        if (nE > NN_MAX_FIELDS) return SOFT_ERR_TOO_LARGE;
         if (!P->nn) {
             P->nn = new NNState();
             int r0 = P->nn->init(1505);
