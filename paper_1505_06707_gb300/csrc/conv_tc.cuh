@@ -29,7 +29,8 @@
 // together); one thread issues the MMAs.
 //
 // The completion wait is bounded: if it runs out, the CTA sets bit 0 of
-// *err (when given), writes NaN to its outputs, frees its TMEM and returns.
+// *err (when given), writes NaN to its outputs, waits once more (bounded)
+// for its MMAs, frees its TMEM and returns.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -271,6 +272,9 @@ conv3x3_tc_kernel(ConvArgs a)
             }
         }
     }
+    // after a wait that ran out, wait once more (bounded) for the MMAs before
+    // the accumulator columns are released
+    if (!ok) tc5::bar_wait(&bar, 0, tc5::WAIT_POLLS);
     tc5::fence_before();
     __syncthreads();
     if (warp == 0) tc5::tmem_free<Q::NCOL>(tbase);
